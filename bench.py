@@ -1,0 +1,285 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free Hermite-Galerkin time step on GB300.
+
+One step = one exponential-midpoint step (Eq. (expMPR)) of the N = 6, B = 4096 Henon-Heiles chain
+with a dipole term (|K| = 4,883,360): m = 7 Lanczos matvecs y = A(t) c with full
+reorthogonalisation, the small tridiagonal exponential and the recombination, all on the device.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--dtype c64|c128]
+
+Prints one JSON line.  value = Galerkin-matvec throughput of the whole step, m |K| / step time, in
+Gcoeff/s, summed over ranks (independent replicas: weak scaling).  The roofline block times the
+fused apply kernel alone; cpu_baseline times the oracle (a plain single-threaded C program).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "hh6_b4096"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args, rank):
+    """The oracle (plain single-threaded C, FP64) on the same workload: each step evaluates the
+    Galerkin matvec on a fixed sample of 20,000 rows (one row at a time, from local windows)."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1403_3511_gb300 import inputs
+    spec = inputs.workload(args.workload)
+    S = O.IndexSet.hyperbolic(spec["N"], spec["B"])
+    c = inputs.initial_vector(spec, S.k)
+    r, a = O.potential_terms(spec, 0.005)
+    rows = inputs.sample_rows(S.size, 20000, seed=1)
+    for _ in range(args.warmup):
+        O.apply_rows(S, spec["B"], r, a, spec["L"], c, rows)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.apply_rows(S, spec["B"], r, a, spec["L"], c, rows)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = len(rows) / dt / 1e9
+    line = {"impl": "reference", "metric": "Galerkin matvecs: Gcoeff/s", "value": v, "unit": "Gcoeff/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": spec["name"], "N": spec["N"], "B": spec["B"],
+                                            "size": int(S.size), "sample_rows": len(rows)},
+            "cpu_baseline": {"value": v, "unit": "Gcoeff/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(rows)} sampled rows of y = A(t)c per step"},
+            "e2e": {"value": v, "unit": "Gcoeff/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(spec):
+    """One full oracle matvec on the host (single thread), after its neighbour tables are built."""
+    from oracle import oracle as O
+    from paper_1403_3511_gb300 import inputs
+    S = O.IndexSet.hyperbolic(spec["N"], spec["B"])
+    c = inputs.initial_vector(spec, S.k)
+    r, a = O.potential_terms(spec, 0.005)
+    O.lib().ho_neighbors_build(S._h)
+    t0 = time.perf_counter()
+    O.apply(S, r, a, spec["L"], c)
+    dt = time.perf_counter() - t0
+    return {"value": S.size / dt / 1e9, "unit": "Gcoeff/s", "cores": 1, "kind": "oracle",
+            "sample": f"one full FP64 matvec y = A(t)c on all {S.size} coefficients ({dt:.1f} s)"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1403_3511_gb300 import build, inputs
+    build.build()
+    from paper_1403_3511_gb300 import hx
+
+    spec = inputs.workload(args.workload)
+    stream = torch.cuda.current_stream()
+    dtype = hx.HX_C64 if args.dtype == "c64" else hx.HX_C128
+    m = spec["m"]
+    dt = spec["dt"]
+    P = hx.Problem(spec["N"], spec["B"], dtype=dtype, m=m, stream=stream.cuda_stream)
+    P.set_potential(spec, 0.0)
+    n = P.size
+    kidx = hx.hx_indexset_export(P.set, spec["N"])
+    c0 = inputs.initial_vector(spec, kidx)
+    c = torch.from_numpy(c0).to("cuda", torch.complex128)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        hx.hx_step(P.p, c, dt, 1)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        hx.hx_step(P.p, c, dt, 1)
+    ev1.record(stream)
+    barrier()
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    # dominant kernel alone: the fused apply, |K| in and |K| out per launch
+    vdt = torch.complex64 if dtype == hx.HX_C64 else torch.complex128
+    x = torch.randn(n, dtype=vdt, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        hx.hx_apply(P.p, x, y)
+    napply = max(10, args.steps * m)
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(napply):
+        hx.hx_apply(P.p, x, y)
+    eb.record(stream)
+    barrier()
+    ms_apply = ea.elapsed_time(eb) / napply
+    clk = clocks.stop()
+    if world > 1:
+        tt = torch.tensor([ms_step, ms_apply], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step, ms_apply = tt.tolist()
+    value = m * n * world / (ms_step * 1e-3) / 1e9
+    # end to end through the host entry point: pinned host state, H2D + step + D2H every step
+    ch = torch.from_numpy(c0.copy()).pin_memory()
+    ch_np = ch.numpy()
+    hx.hx_step_host(P.p, ch_np, dt, 1)
+    barrier()
+    k_e2e = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        hx.hx_step_host(P.p, ch_np, dt, 1)
+    t_e2e = (time.perf_counter() - t0) / k_e2e
+    if world > 1:
+        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = tt.item()
+    e2e = {"value": m * n * world / t_e2e / 1e9, "unit": "Gcoeff/s", "h2d_bytes_per_step": 16 * n,
+           "d2h_bytes_per_step": 16 * n}
+    # the FP64 path on the same input, and the mixed path's deviation from it
+    extra = {}
+    if not args.no_fp64 and dtype == hx.HX_C64:
+        P64 = hx.Problem(spec["N"], spec["B"], dtype=hx.HX_C128, m=m, stream=stream.cuda_stream)
+        P64.set_potential(spec, 0.0)
+        Pm = hx.Problem(spec["N"], spec["B"], dtype=hx.HX_C64, m=m, stream=stream.cuda_stream)
+        Pm.set_potential(spec, 0.0)
+        c64 = torch.from_numpy(c0).to("cuda", torch.complex128)
+        cm = c64.clone()
+        hx.hx_step(P64.p, c64, dt, 1)
+        hx.hx_step(Pm.p, cm, dt, 1)
+        nsteps64 = 10
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hx.hx_step(P64.p, c64, dt, nsteps64)
+        e1.record(stream)
+        hx.hx_step(Pm.p, cm, dt, nsteps64)
+        barrier()
+        ms64 = e0.elapsed_time(e1) / nsteps64
+        rel = (torch.linalg.vector_norm(cm - c64) / torch.linalg.vector_norm(c64)).item()
+        extra = {"fp64_steps_per_s": 1e3 / ms64, "mixed_steps_per_s": 1e3 / ms_step,
+                 "mixed_vs_fp64_rel_err": rel, "rel_err_steps": nsteps64 + 1}
+        P64.close()
+        Pm.close()
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    alg_bytes = (16 if dtype == hx.HX_C64 else 32) * n
+    achieved = alg_bytes / (ms_apply * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "apply_kernel", "ms_per_launch": ms_apply,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"}
+    if rank == 0:
+        line = {"metric": "Galerkin matvecs: Gcoeff/s", "value": value, "unit": "Gcoeff/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64" if dtype == hx.HX_C64 else "f64",
+                "data": "synthetic",
+                "config": {"workload": spec["name"], "N": spec["N"], "B": spec["B"], "size": n, "m": m, "dt": dt,
+                           "potential": "Henon-Heiles chain lambda=0.111 + 0.05 cos(t) x1",
+                           "l2": "inputs larger than L2 (Krylov workspace (m+1) x |K| plus state)",
+                           "parallelism": f"replicas x{world}"},
+                "gpu_launches": (4 * m + 2) * args.steps,
+                "matvec_gcoeff_s": n / (ms_apply * 1e-3) / 1e9,
+                "roofline": roof, "e2e": e2e, "clocks": clk, **extra}
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(spec)
+        print(json.dumps(line), flush=True)
+    P.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

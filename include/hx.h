@@ -1,0 +1,199 @@
+/*
+ * hx — matrix-free Hermite-Galerkin operator and time stepper for GB300 (sm_103a).
+ *
+ * C ABI of the CUDA library libhx.so.  It implements, for
+ *     i c'(t) = A(t) c(t),   A(t) = D_K + W^pol(X_K, t)          (Sec. 1.2, Eq. (ODECoefficientsPol))
+ * of Brumm, "A fast matrix-free algorithm for spectral approximations to the
+ * Schroedinger equation" (arXiv:1403.3511):
+ *   - the hyperbolically reduced index set K = {k in N^N : prod_l (1 + k_l) <= B}
+ *     (Sec. 1.2, with the paper's K + 1 written as B);
+ *   - the matrix-free product y = A(t) c, with W replaced by its Chebyshev
+ *     polynomial (Sec. 1.3) and the coordinate matrices X_K^{(l)} inserted into
+ *     it through the three-term recurrence (Sec. 3.1-3.3);
+ *   - time steps of the exponential midpoint rule (Eq. (expMPR), Sec. 2.1) with the
+ *     exponential approximated by an m-step Hermitian Lanczos process (Sec. 2.2).
+ *
+ * General conventions
+ *   - Every function returns an hx_status (0 = success, negative = error) unless
+ *     stated otherwise; on error, hx_last_error() describes it (thread-local).
+ *   - Multi-indices are int32 arrays of length N, axes counted from 0.
+ *   - Coefficient vectors are in canonical order: the lexicographic order of K with
+ *     the LAST coordinate varying fastest; position = hx_indexset_rank().
+ *   - Vectors are interleaved complex: complex128 (2 x double) or complex64 (2 x float).
+ *   - "device" pointers are CUDA global-memory pointers on the current device (for
+ *     example torch tensor data pointers); "host" pointers are ordinary memory.
+ *   - The caller owns every vector it passes.  The library owns the index tables,
+ *     the compiled potential, the Krylov workspace and any CUDA graphs, and frees
+ *     them in the matching *_destroy call.
+ *   - All device work is ordered on the stream given in hx_config (0 = the legacy
+ *     default stream); functions named *_host synchronise that stream before
+ *     returning, the others do not unless stated.
+ *   - Sizes: |K| < 2^31 and B <= 65535 (HX_EUNSUPPORTED otherwise), 1 <= N <= 16.
+ */
+#ifndef HX_H
+#define HX_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HX_API __attribute__((visibility("default")))
+#else
+#define HX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HX_OK = 0,
+    HX_EINVAL = -1,        /* invalid argument (null pointer, bad size, bad enum) */
+    HX_ENOMEM = -2,        /* device or host allocation failed */
+    HX_ECUDA = -3,         /* a CUDA call failed */
+    HX_ENONFINITE = -4,    /* a NaN or Inf reached a norm */
+    HX_EBREAKDOWN = -5,    /* informational: Lanczos stopped early (exact invariant subspace) */
+    HX_ETIMEOUT = -6,      /* a bounded device wait ran out */
+    HX_EUNSUPPORTED = -7   /* valid request outside what this build implements */
+} hx_status;
+
+/* Precision of the stencil arithmetic and of the Krylov vectors. */
+typedef enum {
+    HX_C128 = 0,           /* complex128 vectors, FP64 arithmetic throughout */
+    HX_C64 = 1             /* complex64 vectors and stencil, FP64 reductions and state */
+} hx_dtype;
+
+/* Factor order inside a product of Chebyshev polynomials of different axes.
+ * On a reduced index set the coordinate matrices of different axes do not commute,
+ * and the paper writes the product in one order (Eq. (Horner)) and applies it in the
+ * other (Algorithm fast_algorithm).  HX_ORDER_SYM (default) takes the mean of the two,
+ * which keeps A(t) Hermitian; the other two reproduce one literal order each. */
+typedef enum {
+    HX_ORDER_SYM = 0,
+    HX_ORDER_EQ = 1,       /* T_{r_1}(X1/L)( ... T_{r_N}(XN/L) v): the last axis acts first */
+    HX_ORDER_ALG = 2       /* axis 0 acts on v first, then axis 1, ... */
+} hx_order;
+
+/* Time dependence f(t) of one potential term. */
+typedef enum {
+    HX_MOD_CONST = 0,      /* f = 1 */
+    HX_MOD_COS = 1,        /* f = cos(omega t + phase) */
+    HX_MOD_SIN2 = 2,       /* f = sin^2(omega t) */
+    HX_MOD_PWCONST = 3     /* f = pw_values[q] on the q-th of pw_n equal intervals of [pw_t0, pw_t1),
+                              clamped to the first / last interval outside it */
+} hx_mod_kind;
+
+/* One term of W^pol(x, t) = sum_terms amp * f(t) * sum_r coef_r prod_i T_{r_i}(x_{axes[i]} / L)
+ * (Sec. 1.3: the alpha_r(t) of the paper are amp * f(t) * coef_r).
+ * n_axes = 1 or 2 (terms on more axes return HX_EUNSUPPORTED); axes strictly increasing;
+ * deg[i] <= HX_MAX_DEG; coef has prod_i (deg[i] + 1) entries, row-major over the axes. */
+#define HX_MAX_DEG 8
+typedef struct {
+    int n_axes;
+    int axes[2];
+    int deg[2];
+    const double *coef;            /* host pointer, copied */
+    int mod_kind;                  /* hx_mod_kind */
+    double amp, omega, phase;
+    const double *pw_values;       /* host pointer, copied (HX_MOD_PWCONST only) */
+    int pw_n;
+    double pw_t0, pw_t1;
+} hx_term;
+
+typedef struct {
+    double L;                      /* half-width of the interpolation cube [-L, L]^N (Sec. 1.3-1.4) */
+    int n_terms;
+    const hx_term *terms;
+} hx_potential;
+
+typedef struct {
+    int dtype;                     /* hx_dtype */
+    int order;                     /* hx_order */
+    int m;                         /* Lanczos steps per time step, 1 <= m <= 32 */
+    void *stream;                  /* cudaStream_t, 0 for the legacy default stream */
+} hx_config;
+
+typedef struct hx_indexset hx_indexset;
+typedef struct hx_problem hx_problem;
+
+/* ---- index set (Sec. 1.2) ------------------------------------------------------ */
+
+/* Builds K = {k : prod (1 + k_l) <= B} and its device rank tables on the current device.
+ * Synchronous.  Errors: HX_EINVAL (N < 1, N > 16, B < 1, out == NULL), HX_EUNSUPPORTED
+ * (B > 65535 or |K| >= 2^31), HX_ENOMEM, HX_ECUDA. */
+HX_API int hx_indexset_create(int N, int64_t B, hx_indexset **out);
+/* |K|, or -1 for a NULL handle. */
+HX_API int64_t hx_indexset_size(const hx_indexset *s);
+/* Writes the multi-index of position rank into k_out[0..N-1] (host).  HX_EINVAL if out of range. */
+HX_API int hx_indexset_unrank(const hx_indexset *s, int64_t rank, int32_t *k_out);
+/* Position of multi-index k (host, length N) in canonical order, or -1 if k is not in K. */
+HX_API int64_t hx_indexset_rank(const hx_indexset *s, const int32_t *k);
+/* Writes all multi-indices, |K| x N int32 row-major, to the host buffer k_out (enumerated on
+ * the device).  Synchronous. */
+HX_API int hx_indexset_export(const hx_indexset *s, int32_t *k_out);
+HX_API void hx_indexset_destroy(hx_indexset *s);
+
+/* ---- problem: index set + potential + configuration -------------------------- */
+
+/* cfg may be NULL: HX_C128, HX_ORDER_SYM, m = 7, default stream.  The index set must
+ * outlive the problem. */
+HX_API int hx_problem_create(const hx_indexset *s, const hx_config *cfg, hx_problem **out);
+HX_API void hx_problem_destroy(hx_problem *p);
+
+/* Compiles W^pol (Sec. 1.3) into the coefficient tables the kernels read and sets the
+ * problem time to t.  Terms are copied; the caller's arrays may be freed afterwards.
+ * A constant term (all degrees 0) is folded into the diagonal.  Synchronous.
+ * Errors: HX_EINVAL (L <= 0, bad axes or degrees, NULL coef), HX_EUNSUPPORTED (n_axes > 2,
+ * more than 32 terms after compilation). */
+HX_API int hx_potential_set(hx_problem *p, const hx_potential *pot, double t);
+HX_API int hx_get_time(const hx_problem *p, double *t);
+HX_API int hx_set_time(hx_problem *p, double t);
+
+/* ---- the matrix-free product (Sec. 3) ------------------------------------------ */
+
+/* c_out = A(t) c_in at the problem time t: D_K c_in + W^pol(X_K, t) c_in with the
+ * configured factor order.  Device pointers of |K| elements of the problem dtype;
+ * c_in and c_out must not overlap.  Asynchronous on the problem stream. */
+HX_API int hx_apply(hx_problem *p, const void *c_in, void *c_out);
+/* Same with host buffers: copies in, applies, copies out, synchronises. */
+HX_API int hx_apply_host(hx_problem *p, const void *c_in_host, void *c_out_host);
+
+/* ---- time stepping (Sec. 2) ----------------------------------------------------- */
+
+/* nsteps steps c <- exp(-i dt A(t + dt/2)) c (Eq. (expMPR)), each exponential by an m-step
+ * Hermitian Lanczos process with full reorthogonalisation (classical Gram-Schmidt twice),
+ * c^{n+1} = ||c^n|| V_m exp(-i dt T_m) e_1 (Sec. 2.2).  c is a DEVICE complex128 vector of
+ * |K| elements, updated in place, for both dtypes (HX_C64 runs the Krylov vectors and the
+ * stencil in complex64, the state and all inner products in FP64).  Advances the problem
+ * time by nsteps * dt.  The step loop is captured once into a CUDA graph per problem and
+ * replayed.  Asynchronous; returns HX_EBREAKDOWN (informational) when some step needed
+ * fewer than m Lanczos vectors — query hx_step_info — and HX_ENONFINITE if the norm
+ * became NaN/Inf (both only after a synchronising call such as hx_step_info). */
+HX_API int hx_step(hx_problem *p, void *c, double dt, int nsteps);
+/* Same with a host complex128 vector: copies in, steps, copies out, synchronises. */
+HX_API int hx_step_host(hx_problem *p, void *c_host, double dt, int nsteps);
+/* Synchronises the stream and reports the last step: Lanczos size used, alpha/beta of T_m
+ * (host arrays of at least m and m-1 doubles, either may be NULL) and the norm of c. */
+HX_API int hx_step_info(hx_problem *p, int *m_used, double *alpha, double *beta, double *norm);
+
+/* ||c||_2 of a device vector of the problem dtype, accumulated in FP64; synchronous. */
+HX_API int hx_norm(hx_problem *p, const void *c, double *out);
+
+/* ---- Chebyshev helpers for building hx_term coefficients (Sec. 1.3) ----------- */
+
+/* First-kind Chebyshev nodes u_i = cos(pi (2i + 1) / (2R + 2)), i = 0..R, into u_out[R+1]. */
+HX_API int hx_cheb_nodes(int R, double *u_out);
+/* Interpolation coefficients from values at the nodes: dims = 1 (values[R+1]) or
+ * dims = 2 (values[(R+1)*(R+1)], values[i*(R+1)+j] = f(u_i, u_j)); coef_out has the same shape. */
+HX_API int hx_cheb_coeffs(int R, int dims, const double *values, double *coef_out);
+/* Exact Chebyshev coefficients of x^p on [-L, L]: x^p = sum_{r<=p} coef_out[r] T_r(x/L). */
+HX_API int hx_cheb_monomial(int p, double L, double *coef_out);
+
+/* ---- errors ---------------------------------------------------------------------- */
+
+/* Message of the last failing call on this thread (never NULL). */
+HX_API const char *hx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -252,11 +252,13 @@ int ho_apply(ho_set *s, int nterms, const int32_t *r, const double *alpha, doubl
  *
  * Row j of a Chebyshev product only involves index paths that start at j and
  * take at most r_l steps along each axis l, and only axes with r_l > 0 move.
- * So the product evaluated on the window
- *     W_j = { k in K : k_l = j_l if r_l = 0,  |k_l - j_l| <= r_l otherwise }
- * (with c restricted to W_j) gives the same value at j as on all of K: every
- * path from j stays inside W_j and sees the same set membership.  The window
- * runs the same fast algorithm as ho_fast_algorithm. */
+ * So the product evaluated on a window
+ *     W_j = { k in K : k_l = j_l off the term's axes,  |k_l - j_l| <= rad_l on them }
+ * with rad_l >= r_l (and c restricted to W_j) gives the same value at j as on all
+ * of K: every path from j stays inside W_j and sees the same set membership.
+ * Terms are grouped by their set of active axes; each group is evaluated by the
+ * same fast algorithm as ho_fast_algorithm on one window whose radius on each
+ * axis is the largest degree of the group. */
 int ho_apply_rows_local(ho_set *full, int64_t B, int nterms, const int32_t *r, const double *alpha,
                         double L, int order, const ho_z *c, int64_t nrows, const int64_t *rows, ho_z *out)
 {
@@ -265,19 +267,44 @@ int ho_apply_rows_local(ho_set *full, int64_t B, int nterms, const int32_t *r, c
     int32_t *pt = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
     int32_t *lo = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
     int32_t *hi = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t *rad = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int *group = (int *)malloc(sizeof(int) * (size_t)(nterms > 0 ? nterms : 1));
+    int32_t *gr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nterms > 0 ? nterms : 1) * (size_t)N);
+    double *ga = (double *)malloc(sizeof(double) * (size_t)(nterms > 0 ? nterms : 1));
+    /* group id = first term with the same support */
+    for (int t = 0; t < nterms; ++t) {
+        group[t] = t;
+        for (int u = 0; u < t; ++u) {
+            int same = 1;
+            for (int l = 0; l < N; ++l) same &= (r[(int64_t)t * N + l] > 0) == (r[(int64_t)u * N + l] > 0);
+            if (same) { group[t] = group[u]; break; }
+        }
+    }
     for (int64_t q = 0; q < nrows; ++q) {
         int64_t j = rows[q];
-        if (j < 0 || j >= full->size) { free(pt); free(lo); free(hi); return -1; }
+        if (j < 0 || j >= full->size) {
+            free(pt); free(lo); free(hi); free(rad); free(group); free(gr); free(ga);
+            return -1;
+        }
         const int32_t *kj = full->k + j * N;
         double dj = 0.0;
         for (int l = 0; l < N; ++l) dj += (double)kj[l] + 0.5;
         ho_z acc = dj * c[j];
-        for (int t = 0; t < nterms; ++t) {
-            const int32_t *rt = r + (int64_t)t * N;
+        for (int g = 0; g < nterms; ++g) {
+            if (group[g] != g) continue;
+            int ng = 0;
+            for (int l = 0; l < N; ++l) rad[l] = 0;
+            for (int t = g; t < nterms; ++t) {
+                if (group[t] != g) continue;
+                memcpy(gr + (int64_t)ng * N, r + (int64_t)t * N, sizeof(int32_t) * (size_t)N);
+                ga[ng++] = alpha[t];
+                for (int l = 0; l < N; ++l)
+                    if (r[(int64_t)t * N + l] > rad[l]) rad[l] = r[(int64_t)t * N + l];
+            }
             int64_t box = 1;
             for (int l = 0; l < N; ++l) {
-                lo[l] = kj[l] - rt[l] < 0 ? 0 : kj[l] - rt[l];
-                hi[l] = kj[l] + rt[l];
+                lo[l] = kj[l] - rad[l] < 0 ? 0 : kj[l] - rad[l];
+                hi[l] = kj[l] + rad[l];
                 box *= (int64_t)(hi[l] - lo[l] + 1);
             }
             /* enumerate the box in lexicographic order, keep members of K */
@@ -302,14 +329,13 @@ int ho_apply_rows_local(ho_set *full, int64_t B, int nterms, const int32_t *r, c
             ho_z *cw = (ho_z *)malloc(sizeof(ho_z) * (size_t)wn);
             ho_z *yw = (ho_z *)malloc(sizeof(ho_z) * (size_t)wn);
             for (int64_t i = 0; i < wn; ++i) cw[i] = c[widx[i]];
-            double one = 1.0;
-            ho_fast_algorithm(win, 1, rt, &one, L, order, cw, yw);
-            acc += alpha[t] * yw[center];
+            ho_fast_algorithm(win, ng, gr, ga, L, order, cw, yw);
+            acc += yw[center];
             ho_set_free(win);
             free(cw); free(yw); free(wk); free(widx);
         }
         out[q] = acc;
     }
-    free(pt); free(lo); free(hi);
+    free(pt); free(lo); free(hi); free(rad); free(group); free(gr); free(ga);
     return 0;
 }

@@ -1,0 +1,781 @@
+// C ABI of libhx: argument checking, index-set and potential set-up on the host, and
+// dispatch to the kernels in hx_apply.cu / hx_krylov.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+
+#include "hx_internal.h"
+
+namespace hx {
+
+static thread_local char g_err[512] = "no error";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? HX_ENOMEM : HX_ECUDA;
+}
+
+#define HX_CUDA(call, what)                        \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ---------------------------------------------------------------------------------------
+// index set tables (host)
+// ---------------------------------------------------------------------------------------
+
+// |K_m(b)| for every b in the quotient set {floor(B/q)} of B, by
+// |K_m(b)| = sum_{k=0}^{b-1} |K_{m-1}(floor(b/(1+k)))|, |K_0(b)| = 1 for b >= 1.
+// floor(floor(B/q)/j) = floor(B/(qj)), so only quotient values are ever needed.
+static bool counts_by_quotient(int N, int B, std::vector<std::vector<int64_t>> &C)
+{
+    std::vector<int> quot;
+    for (int q = 1; q <= B;) {
+        int v = B / q;
+        quot.push_back(v);
+        q = B / v + 1;
+    }
+    std::sort(quot.begin(), quot.end());
+    C.assign(N + 1, std::vector<int64_t>(B + 1, 0));
+    for (int v : quot) C[0][v] = 1;
+    const int64_t cap = (int64_t)1 << 40;
+    for (int m = 1; m <= N; ++m) {
+        for (int v : quot) {
+            int64_t s = 0;
+            for (int k = 0; k < v; ++k) {
+                s += C[m - 1][v / (1 + k)];
+                if (s > cap) s = cap;
+            }
+            C[m][v] = s;
+        }
+    }
+    return true;
+}
+
+static void enum_slabs(int depth, int nout, int q, int B, uint16_t *prefix, std::vector<uint16_t> &out,
+                       std::vector<int> &qs)
+{
+    if (depth == nout) {
+        out.insert(out.end(), prefix, prefix + nout);
+        qs.push_back(q);
+        return;
+    }
+    for (int k = 0; (int64_t)q * (1 + k) <= B; ++k) {
+        prefix[depth] = (uint16_t)k;
+        enum_slabs(depth + 1, nout, q * (1 + k), B, prefix, out, qs);
+    }
+}
+
+static int build_host_tables(int N, int B, IndexSetHost &h)
+{
+    std::vector<std::vector<int64_t>> C;
+    counts_by_quotient(N, B, C);
+    int64_t size = C[N][B];
+    if (size >= ((int64_t)1 << 31) - 1) {
+        set_error("index set too large: |K| = %lld needs 64-bit ranks", (long long)size);
+        return HX_EUNSUPPORTED;
+    }
+    h.N = N;
+    h.B = B;
+    h.size = size;
+    h.qoff.assign(B + 2, 0);
+    int64_t tot = 0;
+    for (int q = 1; q <= B; ++q) {
+        h.qoff[q] = (int)tot;
+        tot += B / q + 1;
+    }
+    h.qoff[B + 1] = (int)tot;
+    h.qtotal = (int)tot;
+    int levels = N - 1;
+    h.Q.assign((size_t)std::max(levels, 0) * tot, 0);
+    for (int m = 1; m <= levels; ++m) {
+        int *Qm = h.Q.data() + (size_t)(m - 1) * tot;
+        for (int q = 1; q <= B; ++q) {
+            int bq = B / q;
+            int64_t acc = 0;
+            int *row = Qm + h.qoff[q];
+            for (int k = 0; k <= bq; ++k) {
+                row[k] = (int)acc;
+                if (k < bq) acc += C[m][B / (q * (1 + k))];
+            }
+        }
+    }
+    int nout = std::max(N - 2, 0);
+    std::vector<int> qs;
+    uint16_t prefix[kMaxN];
+    enum_slabs(0, nout, 1, B, prefix, h.slab_k, qs);
+    h.nslab = (int)qs.size();
+    h.slab_start.resize(h.nslab + 1);
+    int64_t pos = 0;
+    for (int s = 0; s < h.nslab; ++s) {
+        h.slab_start[s] = (int)pos;
+        int bq = B / qs[s];
+        pos += (N >= 2) ? C[2][bq] : C[1][bq];
+    }
+    h.slab_start[h.nslab] = (int)pos;
+    if (pos != size) {
+        set_error("internal: slab sizes %lld != |K| %lld", (long long)pos, (long long)size);
+        return HX_ECUDA;
+    }
+    return HX_OK;
+}
+
+static int64_t host_rank(const IndexSetHost &h, const int32_t *k)
+{
+    int64_t q = 1;
+    for (int l = 0; l < h.N; ++l) {
+        if (k[l] < 0) return -1;
+        q *= (1 + (int64_t)k[l]);
+        if (q > h.B) return -1;
+    }
+    int64_t r = 0;
+    q = 1;
+    for (int d = 0; d < h.N - 1; ++d) {
+        int m = h.N - 1 - d;
+        r += h.Q[(size_t)(m - 1) * h.qtotal + h.qoff[q] + k[d]];
+        q *= (1 + k[d]);
+    }
+    return r + k[h.N - 1];
+}
+
+static int host_unrank(const IndexSetHost &h, int64_t rank, int32_t *k)
+{
+    if (rank < 0 || rank >= h.size) return HX_EINVAL;
+    int64_t q = 1, rem = rank;
+    for (int d = 0; d < h.N - 1; ++d) {
+        int m = h.N - 1 - d;
+        const int *row = h.Q.data() + (size_t)(m - 1) * h.qtotal + h.qoff[q];
+        int bq = (int)(h.B / q);
+        // largest i < bq with row[i] <= rem (row is nondecreasing, row[0] = 0)
+        int lo = 0, hi = bq - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) / 2;
+            if (row[mid] <= rem) lo = mid; else hi = mid - 1;
+        }
+        k[d] = lo;
+        rem -= row[lo];
+        q *= (1 + lo);
+    }
+    k[h.N - 1] = (int32_t)rem;
+    return HX_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// potential compilation (host)
+// ---------------------------------------------------------------------------------------
+
+// Row i of P(J_n / L) for P = sum_r a_r T_r, via the Chebyshev recurrence on row vectors
+// rho_{r+1} = 2 rho_r (J_n / L) - rho_{r-1}, rho_0 = e_i (Eq. (ChebyshevRecurrence)); J_n is the
+// truncated Jacobi matrix with J_{k,k+1} = J_{k+1,k} = sqrt((k+1)/2) (Eq. (Recurrence1D)).
+static void poly_row(const std::vector<double> &a, double L, int i, int n, double *out /* 2p+1 */)
+{
+    int p = (int)a.size() - 1;
+    int W = 2 * p + 3;  // window i-p-1 .. i+p+1 keeps the recurrence in range
+    std::vector<double> r0(W, 0.0), r1(W, 0.0), r2(W, 0.0), row(W, 0.0);
+    auto idx = [&](int m) { return m - (i - p - 1); };
+    auto valid = [&](int m) { return m >= 0 && m < n && m >= i - p - 1 && m <= i + p + 1; };
+    r0[idx(i)] = 1.0;
+    auto times_J = [&](const std::vector<double> &x, std::vector<double> &y) {
+        for (int m = i - p - 1; m <= i + p + 1; ++m) {
+            double v = 0.0;
+            if (valid(m)) {
+                if (valid(m - 1)) v += x[idx(m - 1)] * sqrt(m / 2.0);
+                if (valid(m + 1)) v += x[idx(m + 1)] * sqrt((m + 1) / 2.0);
+            }
+            y[idx(m)] = v;
+        }
+    };
+    for (int m = 0; m < W; ++m) row[m] = a[0] * r0[m];
+    if (p >= 1) {
+        times_J(r0, r1);
+        for (int m = 0; m < W; ++m) {
+            r1[m] /= L;
+            row[m] += a[1] * r1[m];
+        }
+    }
+    for (int r = 2; r <= p; ++r) {
+        times_J(r1, r2);
+        for (int m = 0; m < W; ++m) {
+            r2[m] = 2.0 * r2[m] / L - r0[m];
+            row[m] += a[r] * r2[m];
+        }
+        r0.swap(r1);
+        r1.swap(r2);
+    }
+    for (int s = -p; s <= p; ++s) out[s + p] = row[idx(i + s)];
+}
+
+static int parity_mask(const std::vector<double> &a)
+{
+    // T_r(J/L) has nonzero row entries only at offsets of the parity of r
+    int p = (int)a.size() - 1;
+    bool even = false, odd = false;
+    for (int r = 0; r <= p; ++r)
+        if (a[r] != 0.0) (r % 2 ? odd : even) = true;
+    int mask = 0;
+    for (int s = -p; s <= p; ++s) {
+        bool sodd = (s % 2) != 0;
+        if ((sodd && odd) || (!sodd && even)) mask |= 1 << (s + p);
+    }
+    return mask;
+}
+
+static void trim(std::vector<double> &a)
+{
+    while (a.size() > 1 && a.back() == 0.0) a.pop_back();
+}
+
+struct PolyKey {
+    std::vector<double> a;
+    bool operator<(const PolyKey &o) const { return a < o.a; }
+};
+
+struct Compiler {
+    const IndexSetObj *set;
+    double L;
+    std::map<PolyKey, int> poly_base;    // polynomial -> row-table base
+    std::vector<double> tab;             // all row tables (double)
+    OpSet ops;
+    std::vector<double> pw;
+
+    int poly(const std::vector<double> &a)
+    {
+        auto it = poly_base.find(PolyKey{a});
+        if (it != poly_base.end()) return it->second;
+        int p = (int)a.size() - 1;
+        int B = set->h.B;
+        int base = (int)tab.size();
+        tab.resize(tab.size() + (size_t)B * (p + 1) * (2 * p + 1));
+        for (int i = 0; i < B; ++i)
+            for (int d = 0; d <= p; ++d)
+                poly_row(a, L, i, i + 1 + d, &tab[base + ((size_t)i * (p + 1) + d) * (2 * p + 1)]);
+        poly_base[PolyKey{a}] = base;
+        return base;
+    }
+
+    int delta_index(int a0, int s0, int a1, int s1)
+    {
+        int N = set->h.N;
+        int8_t e[4] = {-1, 0, -1, 0};
+        int n = 0;
+        if (a0 >= 0 && a0 < N - 2 && s0 != 0) { e[0] = (int8_t)a0; e[1] = (int8_t)s0; n = 1; }
+        if (a1 >= 0 && a1 < N - 2 && s1 != 0) { e[2 * n] = (int8_t)a1; e[2 * n + 1] = (int8_t)s1; }
+        if (e[0] < 0 && e[2] < 0) return 0;
+        for (int i = 1; i < ops.ndelta; ++i)
+            if (!memcmp(ops.delta[i], e, 4)) return i;
+        if (ops.ndelta >= kMaxDelta) return -1;
+        memcpy(ops.delta[ops.ndelta], e, 4);
+        return ops.ndelta++;
+    }
+
+    int add_op(int kind, int a, int b, const std::vector<double> &P, const std::vector<double> &Q,
+               const hx_term &t, double scale)
+    {
+        if (ops.nops >= kMaxOps) {
+            set_error("potential compiles to more than %d operators", kMaxOps);
+            return HX_EUNSUPPORTED;
+        }
+        Op &o = ops.op[ops.nops];
+        memset(&o, 0, sizeof(o));
+        o.kind = kind;
+        o.a = a;
+        o.b = b;
+        o.p = kind >= 1 ? (int)P.size() - 1 : 0;
+        o.q = kind == 2 ? (int)Q.size() - 1 : 0;
+        o.pmask = kind >= 1 ? parity_mask(P) : 1;
+        o.qmask = kind == 2 ? parity_mask(Q) : 1;
+        o.tabP = kind >= 1 ? poly(P) : 0;
+        o.tabQ = kind == 2 ? poly(Q) : 0;
+        o.mod = t.mod_kind;
+        o.amp = t.amp * scale;
+        o.omega = t.omega;
+        o.phase = t.phase;
+        o.pw_off = (int)pw.size();
+        o.pw_n = t.mod_kind == HX_MOD_PWCONST ? t.pw_n : 0;
+        o.pw_t0 = t.pw_t0;
+        o.pw_t1 = t.pw_t1;
+        if (t.mod_kind == HX_MOD_PWCONST) pw.insert(pw.end(), t.pw_values, t.pw_values + t.pw_n);
+        // footprint -> outer offset index
+        int base = ops.nops * kSpan * kSpan;
+        o.dbase = base;
+        if (kind >= 1) {
+            for (int s = -o.p; s <= o.p; ++s)
+                for (int s2 = -o.q; s2 <= o.q; ++s2) {
+                    int di = delta_index(a, s, kind == 2 ? b : -1, s2);
+                    if (di < 0) {
+                        set_error("potential needs more than %d distinct neighbour offsets", kMaxDelta);
+                        return HX_EUNSUPPORTED;
+                    }
+                    ops.didx[base + (s + o.p) * (2 * o.q + 1) + (s2 + o.q)] = (uint8_t)di;
+                }
+        }
+        ops.nops++;
+        return HX_OK;
+    }
+};
+
+// C = sum_k u_k v_k^T by Gaussian elimination with complete pivoting; pieces below
+// 1e-15 * max|C| are dropped (an exactly low-rank C, e.g. a product of two univariate
+// interpolants, gives exactly rank-many pieces up to rounding).
+static void rank_one_pieces(std::vector<double> C, int n0, int n1, std::vector<std::vector<double>> &U,
+                            std::vector<std::vector<double>> &V)
+{
+    double cmax = 0.0;
+    for (double x : C) cmax = std::max(cmax, fabs(x));
+    if (cmax == 0.0) return;
+    for (int it = 0; it < std::min(n0, n1); ++it) {
+        int bi = -1, bj = -1;
+        double best = 0.0;
+        for (int i = 0; i < n0; ++i)
+            for (int j = 0; j < n1; ++j)
+                if (fabs(C[i * n1 + j]) > best) { best = fabs(C[i * n1 + j]); bi = i; bj = j; }
+        if (best <= 1e-15 * cmax) break;
+        std::vector<double> u(n0), v(n1);
+        double piv = C[bi * n1 + bj];
+        for (int i = 0; i < n0; ++i) u[i] = C[i * n1 + bj];
+        for (int j = 0; j < n1; ++j) v[j] = C[bi * n1 + j] / piv;
+        for (int i = 0; i < n0; ++i)
+            for (int j = 0; j < n1; ++j) C[i * n1 + j] -= u[i] * v[j];
+        U.push_back(u);
+        V.push_back(v);
+    }
+}
+
+static int compile_potential(Problem *pr, const hx_potential *pot)
+{
+    const IndexSetObj *set = pr->set;
+    int N = set->h.N;
+    if (!pot || !(pot->L > 0.0) || pot->n_terms < 0 || (pot->n_terms > 0 && !pot->terms)) {
+        set_error("hx_potential_set: need L > 0 and a term array");
+        return HX_EINVAL;
+    }
+    Compiler cp;
+    cp.set = set;
+    cp.L = pot->L;
+    memset(&cp.ops, 0, sizeof(cp.ops));
+    cp.ops.ndelta = 1;   // index 0: zero outer offset
+    int order = pr->cfg.order;
+    cp.ops.wAB = order == HX_ORDER_SYM ? 0.5 : (order == HX_ORDER_EQ ? 1.0 : 0.0);
+    cp.ops.wBA = order == HX_ORDER_SYM ? 0.5 : (order == HX_ORDER_ALG ? 1.0 : 0.0);
+    for (int ti = 0; ti < pot->n_terms; ++ti) {
+        const hx_term &t = pot->terms[ti];
+        if (t.n_axes < 1 || t.n_axes > 2) {
+            set_error("term %d: n_axes = %d (this build supports 1 or 2)", ti, t.n_axes);
+            return t.n_axes > 2 ? HX_EUNSUPPORTED : HX_EINVAL;
+        }
+        if (!t.coef || t.mod_kind < 0 || t.mod_kind > HX_MOD_PWCONST ||
+            (t.mod_kind == HX_MOD_PWCONST && (!t.pw_values || t.pw_n < 1 || !(t.pw_t1 > t.pw_t0)))) {
+            set_error("term %d: bad coefficient pointer or modulation", ti);
+            return HX_EINVAL;
+        }
+        for (int i = 0; i < t.n_axes; ++i)
+            if (t.axes[i] < 0 || t.axes[i] >= N || t.deg[i] < 0 || t.deg[i] > kMaxDeg ||
+                (i == 1 && t.axes[1] <= t.axes[0])) {
+                set_error("term %d: bad axes or degrees", ti);
+                return HX_EINVAL;
+            }
+        int rc;
+        if (t.n_axes == 1) {
+            std::vector<double> a(t.coef, t.coef + t.deg[0] + 1);
+            trim(a);
+            if (a.size() == 1) {
+                if (a[0] != 0.0 && (rc = cp.add_op(0, -1, -1, a, a, t, a[0]))) return rc;
+            } else if ((rc = cp.add_op(1, t.axes[0], -1, a, a, t, 1.0))) return rc;
+        } else {
+            int n0 = t.deg[0] + 1, n1 = t.deg[1] + 1;
+            std::vector<double> C(t.coef, t.coef + n0 * n1);
+            std::vector<std::vector<double>> U, V;
+            rank_one_pieces(C, n0, n1, U, V);
+            for (size_t k = 0; k < U.size(); ++k) {
+                std::vector<double> P = U[k], Qp = V[k];
+                trim(P);
+                trim(Qp);
+                if (P.size() == 1 && Qp.size() == 1) {
+                    if ((rc = cp.add_op(0, -1, -1, P, P, t, P[0] * Qp[0]))) return rc;
+                } else if (P.size() == 1) {
+                    for (double &x : Qp) x *= P[0];
+                    if ((rc = cp.add_op(1, t.axes[1], -1, Qp, Qp, t, 1.0))) return rc;
+                } else if (Qp.size() == 1) {
+                    for (double &x : P) x *= Qp[0];
+                    if ((rc = cp.add_op(1, t.axes[0], -1, P, P, t, 1.0))) return rc;
+                } else if ((rc = cp.add_op(2, t.axes[0], t.axes[1], P, Qp, t, 1.0))) return rc;
+            }
+        }
+    }
+    // upload
+    size_t es = pr->cfg.dtype == HX_C64 ? sizeof(float) : sizeof(double);
+    size_t tab_bytes = std::max<size_t>(cp.tab.size(), 1) * es;
+    if (tab_bytes > ((size_t)1 << 30)) {
+        set_error("coefficient row tables need %zu bytes", tab_bytes);
+        return HX_EUNSUPPORTED;
+    }
+    std::vector<char> stage(tab_bytes);
+    if (pr->cfg.dtype == HX_C64) {
+        float *f = (float *)stage.data();
+        for (size_t i = 0; i < cp.tab.size(); ++i) f[i] = (float)cp.tab[i];
+    } else if (!cp.tab.empty()) {
+        memcpy(stage.data(), cp.tab.data(), cp.tab.size() * sizeof(double));
+    }
+    if (pr->tab) cudaFree(pr->tab);
+    if (pr->pw_values) cudaFree(pr->pw_values);
+    pr->tab = nullptr;
+    pr->pw_values = nullptr;
+    HX_CUDA(cudaMalloc(&pr->tab, tab_bytes), "cudaMalloc(row tables)");
+    HX_CUDA(cudaMemcpy(pr->tab, stage.data(), tab_bytes, cudaMemcpyHostToDevice), "upload row tables");
+    size_t pwb = std::max<size_t>(cp.pw.size(), 1) * sizeof(double);
+    HX_CUDA(cudaMalloc((void **)&pr->pw_values, pwb), "cudaMalloc(pw)");
+    if (!cp.pw.empty())
+        HX_CUDA(cudaMemcpy(pr->pw_values, cp.pw.data(), cp.pw.size() * sizeof(double), cudaMemcpyHostToDevice),
+                "upload pw");
+    pr->tab_bytes = tab_bytes;
+    pr->ops = cp.ops;
+    // work items: <= kItemElems elements and a slab count whose neighbour table fits shared memory
+    int nd = cp.ops.ndelta;
+    int spi = std::max(1, std::min(64, (32 * 1024) / (16 * nd)));
+    pr->slabs_per_item = spi;
+    const IndexSetHost &h = set->h;
+    std::vector<int4> items;
+    int s = 0;
+    while (s < h.nslab) {
+        int e0 = h.slab_start[s];
+        int len = h.slab_start[s + 1] - e0;
+        if (len > kItemElems) {   // split a large slab into full tiles
+            for (int off = 0; off < len; off += kItemElems)
+                items.push_back(make_int4(s, s, e0 + off, e0 + std::min(len, off + kItemElems)));
+            ++s;
+            continue;
+        }
+        int s1 = s;
+        while (s1 + 1 < h.nslab && s1 + 1 - s < spi && h.slab_start[s1 + 2] - e0 <= kItemElems) ++s1;
+        items.push_back(make_int4(s, s1, e0, h.slab_start[s1 + 1]));
+        s = s1 + 1;
+    }
+    if (pr->items) cudaFree(pr->items);
+    pr->items = nullptr;
+    HX_CUDA(cudaMalloc((void **)&pr->items, items.size() * sizeof(int4)), "cudaMalloc(items)");
+    HX_CUDA(cudaMemcpy(pr->items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice),
+            "upload items");
+    pr->items_h = items;
+    pr->nitems = (int)items.size();
+    pr->have_pot = true;
+    return HX_OK;
+}
+
+}  // namespace hx
+
+using namespace hx;
+
+struct hx_indexset : IndexSetObj {};
+struct hx_problem : Problem {};
+
+extern "C" {
+
+const char *hx_last_error(void) { return g_err; }
+
+int hx_indexset_create(int N, int64_t B, hx_indexset **out)
+{
+    if (!out || N < 1 || N > kMaxN || B < 1) {
+        set_error("hx_indexset_create: need 1 <= N <= %d, B >= 1, out != NULL", kMaxN);
+        return HX_EINVAL;
+    }
+    *out = nullptr;
+    if (B > 65535) {
+        set_error("hx_indexset_create: B = %lld > 65535 is not supported", (long long)B);
+        return HX_EUNSUPPORTED;
+    }
+    hx_indexset *s = new (std::nothrow) hx_indexset();
+    if (!s) { set_error("out of host memory"); return HX_ENOMEM; }
+    int rc = build_host_tables(N, (int)B, s->h);
+    if (rc) { delete s; return rc; }
+    const IndexSetHost &h = s->h;
+    size_t b_start = (size_t)(h.nslab + 1) * sizeof(int);
+    size_t b_k = std::max<size_t>(h.slab_k.size(), 1) * sizeof(uint16_t);
+    size_t b_qoff = (size_t)(h.B + 2) * sizeof(int);
+    size_t b_Q = std::max<size_t>(h.Q.size(), 1) * sizeof(int);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t total = al(b_start) + al(b_k) + al(b_qoff) + al(b_Q);
+    cudaGetDevice(&s->device);
+    cudaError_t e = cudaMalloc(&s->dmem, total);
+    if (e != cudaSuccess) { delete s; return cuda_fail(e, "cudaMalloc(index tables)"); }
+    char *base = (char *)s->dmem;
+    int *d_start = (int *)base;
+    uint16_t *d_k = (uint16_t *)(base + al(b_start));
+    int *d_qoff = (int *)(base + al(b_start) + al(b_k));
+    int *d_Q = (int *)(base + al(b_start) + al(b_k) + al(b_qoff));
+    cudaMemcpy(d_start, h.slab_start.data(), b_start, cudaMemcpyHostToDevice);
+    if (!h.slab_k.empty()) cudaMemcpy(d_k, h.slab_k.data(), h.slab_k.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(d_qoff, h.qoff.data(), b_qoff, cudaMemcpyHostToDevice);
+    if (!h.Q.empty()) e = cudaMemcpy(d_Q, h.Q.data(), h.Q.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) {
+        cudaFree(s->dmem);
+        delete s;
+        return cuda_fail(e, "upload index tables");
+    }
+    s->d.N = h.N;
+    s->d.B = h.B;
+    s->d.size = (int)h.size;
+    s->d.nslab = h.nslab;
+    s->d.qtotal = h.qtotal;
+    s->d.slab_start = d_start;
+    s->d.slab_k = d_k;
+    s->d.qoff = d_qoff;
+    s->d.Q = d_Q;
+    *out = s;
+    return HX_OK;
+}
+
+int64_t hx_indexset_size(const hx_indexset *s) { return s ? s->h.size : -1; }
+
+int hx_indexset_unrank(const hx_indexset *s, int64_t rank, int32_t *k_out)
+{
+    if (!s || !k_out) { set_error("hx_indexset_unrank: NULL argument"); return HX_EINVAL; }
+    int rc = host_unrank(s->h, rank, k_out);
+    if (rc) set_error("hx_indexset_unrank: rank %lld out of range", (long long)rank);
+    return rc;
+}
+
+int64_t hx_indexset_rank(const hx_indexset *s, const int32_t *k)
+{
+    if (!s || !k) return -1;
+    return host_rank(s->h, k);
+}
+
+int hx_indexset_export(const hx_indexset *s, int32_t *k_out)
+{
+    if (!s || !k_out) { set_error("hx_indexset_export: NULL argument"); return HX_EINVAL; }
+    size_t bytes = (size_t)s->h.size * s->h.N * sizeof(int32_t);
+    int32_t *d = nullptr;
+    HX_CUDA(cudaMalloc((void **)&d, std::max<size_t>(bytes, 4)), "cudaMalloc(export)");
+    int rc = launch_export(s, d, 0);
+    if (!rc) {
+        cudaError_t e = cudaMemcpy(k_out, d, bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "export copy");
+    }
+    cudaFree(d);
+    return rc;
+}
+
+void hx_indexset_destroy(hx_indexset *s)
+{
+    if (!s) return;
+    cudaFree(s->dmem);
+    delete s;
+}
+
+int hx_problem_create(const hx_indexset *s, const hx_config *cfg, hx_problem **out)
+{
+    if (!s || !out) { set_error("hx_problem_create: NULL argument"); return HX_EINVAL; }
+    *out = nullptr;
+    hx_config c = {HX_C128, HX_ORDER_SYM, 7, nullptr};
+    if (cfg) c = *cfg;
+    if ((c.dtype != HX_C128 && c.dtype != HX_C64) || c.order < 0 || c.order > 2 || c.m < 1 || c.m > kMaxKrylov) {
+        set_error("hx_problem_create: bad dtype, order or m (1..%d)", kMaxKrylov);
+        return HX_EINVAL;
+    }
+    hx_problem *p = new (std::nothrow) hx_problem();
+    if (!p) { set_error("out of host memory"); return HX_ENOMEM; }
+    p->set = s;
+    p->cfg = c;
+    p->stream = (cudaStream_t)c.stream;
+    cudaGetDevice(&p->device);
+    cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    cudaError_t e = cudaMalloc((void **)&p->dscal, 64 * sizeof(double));
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaMalloc(scalars)"); }
+    cudaMemset(p->dscal, 0, 64 * sizeof(double));
+    *out = p;
+    return HX_OK;
+}
+
+void hx_problem_destroy(hx_problem *p)
+{
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream); else cudaDeviceSynchronize();
+    krylov_free(p);
+    cudaFree(p->tab);
+    cudaFree(p->pw_values);
+    cudaFree(p->items);
+    cudaFree(p->dscal);
+    for (void *x : p->extra) cudaFree(x);
+    delete p;
+}
+
+int hx_set_time(hx_problem *p, double t)
+{
+    if (!p) { set_error("hx_set_time: NULL problem"); return HX_EINVAL; }
+    p->t_host = t;
+    HX_CUDA(cudaMemcpyAsync(p->dscal, &t, sizeof(double), cudaMemcpyHostToDevice, p->stream), "set time");
+    HX_CUDA(cudaStreamSynchronize(p->stream), "set time");
+    return HX_OK;
+}
+
+int hx_get_time(const hx_problem *p, double *t)
+{
+    if (!p || !t) { set_error("hx_get_time: NULL argument"); return HX_EINVAL; }
+    *t = p->t_host;
+    return HX_OK;
+}
+
+int hx_potential_set(hx_problem *p, const hx_potential *pot, double t)
+{
+    if (!p) { set_error("hx_potential_set: NULL problem"); return HX_EINVAL; }
+    if (p->stream) cudaStreamSynchronize(p->stream); else cudaDeviceSynchronize();
+    int rc = compile_potential(p, pot);
+    if (rc) return rc;
+    krylov_free(p);   // cached graphs refer to the old potential
+    return hx_set_time(p, t);
+}
+
+int hx_apply(hx_problem *p, const void *c_in, void *c_out)
+{
+    if (!p || !c_in || !c_out) { set_error("hx_apply: NULL argument"); return HX_EINVAL; }
+    if (!p->have_pot) { set_error("hx_apply: call hx_potential_set first"); return HX_EINVAL; }
+    if (c_in == c_out) { set_error("hx_apply: c_in and c_out must not overlap"); return HX_EINVAL; }
+    return launch_apply(p, c_in, c_out, p->dscal, 0.0, nullptr, p->stream);
+}
+
+int hx_apply_host(hx_problem *p, const void *c_in_host, void *c_out_host)
+{
+    if (!p || !c_in_host || !c_out_host) { set_error("hx_apply_host: NULL argument"); return HX_EINVAL; }
+    size_t es = p->cfg.dtype == HX_C64 ? 8 : 16;
+    size_t bytes = (size_t)p->set->h.size * es;
+    void *d = nullptr;
+    HX_CUDA(cudaMallocAsync(&d, 2 * std::max<size_t>(bytes, 16), p->stream), "cudaMallocAsync(apply_host)");
+    char *din = (char *)d, *dout = (char *)d + std::max<size_t>(bytes, 16);
+    int rc = HX_OK;
+    cudaError_t e = cudaMemcpyAsync(din, c_in_host, bytes, cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "apply_host copy in");
+    if (!rc) rc = hx_apply(p, din, dout);
+    if (!rc && (e = cudaMemcpyAsync(c_out_host, dout, bytes, cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess)
+        rc = cuda_fail(e, "apply_host copy out");
+    cudaFreeAsync(d, p->stream);
+    if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess && !rc) rc = cuda_fail(e, "apply_host sync");
+    return rc;
+}
+
+int hx_norm(hx_problem *p, const void *c, double *out)
+{
+    if (!p || !c || !out) { set_error("hx_norm: NULL argument"); return HX_EINVAL; }
+    int G = apply_grid(p);
+    double *buf = nullptr;
+    HX_CUDA(cudaMallocAsync((void **)&buf, (G + 2) * sizeof(double) + 64, p->stream), "cudaMallocAsync(norm)");
+    unsigned *cnt = (unsigned *)(buf + G + 1);
+    cudaMemsetAsync(cnt, 0, sizeof(unsigned), p->stream);
+    int rc = launch_norm(p, c, p->cfg.dtype == HX_C128, buf, cnt, buf + G, p->stream);
+    double r = 0.0;
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(&r, buf + G, sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "hx_norm");
+    }
+    cudaFreeAsync(buf, p->stream);
+    cudaStreamSynchronize(p->stream);
+    *out = sqrt(r);
+    return rc;
+}
+
+int hx_step(hx_problem *p, void *c, double dt, int nsteps)
+{
+    if (!p || !c || nsteps < 0 || !(dt == dt)) { set_error("hx_step: bad argument"); return HX_EINVAL; }
+    if (!p->have_pot) { set_error("hx_step: call hx_potential_set first"); return HX_EINVAL; }
+    if (nsteps == 0) return HX_OK;
+    return krylov_step(p, c, dt, nsteps);
+}
+
+int hx_step_host(hx_problem *p, void *c_host, double dt, int nsteps)
+{
+    if (!p || !c_host) { set_error("hx_step_host: NULL argument"); return HX_EINVAL; }
+    if (!p->have_pot) { set_error("hx_step_host: call hx_potential_set first"); return HX_EINVAL; }
+    size_t bytes = (size_t)p->set->h.size * 16;
+    void *d = krylov_host_state(p);
+    if (!d) { set_error("hx_step_host: cannot allocate the device state"); return HX_ENOMEM; }
+    int rc = HX_OK;
+    cudaError_t e = cudaMemcpyAsync(d, c_host, bytes, cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "step_host copy in");
+    if (!rc) rc = hx_step(p, d, dt, nsteps);
+    if (!rc && (e = cudaMemcpyAsync(c_host, d, bytes, cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess)
+        rc = cuda_fail(e, "step_host copy out");
+    if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess && !rc) rc = cuda_fail(e, "step_host sync");
+    return rc;
+}
+
+int hx_step_info(hx_problem *p, int *m_used, double *alpha, double *beta, double *norm)
+{
+    if (!p) { set_error("hx_step_info: NULL problem"); return HX_EINVAL; }
+    return krylov_info(p, m_used, alpha, beta, norm);
+}
+
+int hx_cheb_nodes(int R, double *u_out)
+{
+    if (R < 0 || !u_out) { set_error("hx_cheb_nodes: bad argument"); return HX_EINVAL; }
+    for (int i = 0; i <= R; ++i) u_out[i] = cos(M_PI * (2 * i + 1) / (2.0 * R + 2.0));
+    return HX_OK;
+}
+
+// a_r = (2 - delta_{r0}) / (R + 1) sum_i f(u_i) cos(r theta_i), theta_i = pi (2i + 1) / (2R + 2):
+// discrete orthogonality of T_r at the first-kind nodes (Sec. 1.3).
+int hx_cheb_coeffs(int R, int dims, const double *values, double *coef_out)
+{
+    if (R < 0 || (dims != 1 && dims != 2) || !values || !coef_out) {
+        set_error("hx_cheb_coeffs: bad argument");
+        return HX_EINVAL;
+    }
+    int n = R + 1;
+    std::vector<double> Cm((size_t)n * n);
+    for (int r = 0; r < n; ++r)
+        for (int i = 0; i < n; ++i)
+            Cm[(size_t)r * n + i] = (r == 0 ? 1.0 : 2.0) / n * cos(r * M_PI * (2 * i + 1) / (2.0 * n));
+    if (dims == 1) {
+        for (int r = 0; r < n; ++r) {
+            double s = 0.0;
+            for (int i = 0; i < n; ++i) s += Cm[(size_t)r * n + i] * values[i];
+            coef_out[r] = s;
+        }
+        return HX_OK;
+    }
+    std::vector<double> tmp((size_t)n * n, 0.0);
+    for (int r = 0; r < n; ++r)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int i = 0; i < n; ++i) s += Cm[(size_t)r * n + i] * values[(size_t)i * n + j];
+            tmp[(size_t)r * n + j] = s;
+        }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s += tmp[(size_t)r * n + j] * Cm[(size_t)c * n + j];
+            coef_out[(size_t)r * n + c] = s;
+        }
+    return HX_OK;
+}
+
+// x^p on [-L, L]: (L u)^p with u^p = 2^{1-p} sum_{j <= p/2} binom(p, j) T_{p-2j}(u), the j = p/2 term halved.
+int hx_cheb_monomial(int p, double L, double *coef_out)
+{
+    if (p < 0 || p > 60 || !coef_out) { set_error("hx_cheb_monomial: bad argument"); return HX_EINVAL; }
+    for (int r = 0; r <= p; ++r) coef_out[r] = 0.0;
+    double binom = 1.0;
+    for (int j = 0; 2 * j <= p; ++j) {
+        double c = binom * ldexp(1.0, 1 - p);
+        if (2 * j == p) c *= 0.5;
+        coef_out[p - 2 * j] += c * pow(L, p);
+        binom = binom * (p - j) / (j + 1);
+    }
+    return HX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,311 @@
+"""Python binding of libhx (include/hx.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Device vectors are torch CUDA
+tensors (complex128 or complex64, contiguous, canonical order); host vectors are numpy
+arrays.  All arithmetic happens in libhx.so; importing this module raises if the library
+has not been built, and a failing call raises HxError with the library's message.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhx.so")
+
+HX_C128, HX_C64 = 0, 1
+HX_ORDER_SYM, HX_ORDER_EQ, HX_ORDER_ALG = 0, 1, 2
+HX_MOD_CONST, HX_MOD_COS, HX_MOD_SIN2, HX_MOD_PWCONST = 0, 1, 2, 3
+HX_EBREAKDOWN = -5
+ORDERS = {"sym": HX_ORDER_SYM, "eq": HX_ORDER_EQ, "alg": HX_ORDER_ALG}
+MODS = {"const": HX_MOD_CONST, "cos": HX_MOD_COS, "sin2": HX_MOD_SIN2, "pwconst": HX_MOD_PWCONST}
+
+
+class HxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"hx status {status}: {msg}")
+        self.status = status
+
+
+class hx_term(ctypes.Structure):
+    _fields_ = [("n_axes", ctypes.c_int), ("axes", ctypes.c_int * 2), ("deg", ctypes.c_int * 2),
+                ("coef", ctypes.POINTER(ctypes.c_double)), ("mod_kind", ctypes.c_int),
+                ("amp", ctypes.c_double), ("omega", ctypes.c_double), ("phase", ctypes.c_double),
+                ("pw_values", ctypes.POINTER(ctypes.c_double)), ("pw_n", ctypes.c_int),
+                ("pw_t0", ctypes.c_double), ("pw_t1", ctypes.c_double)]
+
+
+class hx_potential(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double), ("n_terms", ctypes.c_int), ("terms", ctypes.POINTER(hx_term))]
+
+
+class hx_config(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("order", ctypes.c_int), ("m", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1403_3511_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i64, i32p = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "hx_indexset_create": (ctypes.c_int, [ctypes.c_int, i64, ctypes.POINTER(P)]),
+        "hx_indexset_size": (i64, [P]),
+        "hx_indexset_unrank": (ctypes.c_int, [P, i64, i32p]),
+        "hx_indexset_rank": (i64, [P, i32p]),
+        "hx_indexset_export": (ctypes.c_int, [P, i32p]),
+        "hx_indexset_destroy": (None, [P]),
+        "hx_problem_create": (ctypes.c_int, [P, ctypes.POINTER(hx_config), ctypes.POINTER(P)]),
+        "hx_problem_destroy": (None, [P]),
+        "hx_potential_set": (ctypes.c_int, [P, ctypes.POINTER(hx_potential), ctypes.c_double]),
+        "hx_get_time": (ctypes.c_int, [P, dp]),
+        "hx_set_time": (ctypes.c_int, [P, ctypes.c_double]),
+        "hx_apply": (ctypes.c_int, [P, P, P]),
+        "hx_apply_host": (ctypes.c_int, [P, P, P]),
+        "hx_step": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int]),
+        "hx_step_host": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int]),
+        "hx_step_info": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), dp, dp, dp]),
+        "hx_norm": (ctypes.c_int, [P, P, dp]),
+        "hx_cheb_nodes": (ctypes.c_int, [ctypes.c_int, dp]),
+        "hx_cheb_coeffs": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp, dp]),
+        "hx_cheb_monomial": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, dp]),
+        "hx_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def hx_last_error() -> str:
+    return lib.hx_last_error().decode()
+
+
+def _check(status: int, allow=()):
+    if status != 0 and status not in allow:
+        raise HxError(status, hx_last_error())
+    return status
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _tptr(t) -> int:
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+# ---- index set ---------------------------------------------------------------------------
+
+def hx_indexset_create(N: int, B: int):
+    h = ctypes.c_void_p()
+    _check(lib.hx_indexset_create(N, B, ctypes.byref(h)))
+    return h
+
+
+def hx_indexset_size(s) -> int:
+    return int(lib.hx_indexset_size(s))
+
+
+def hx_indexset_unrank(s, rank: int, N: int) -> np.ndarray:
+    k = np.zeros(N, dtype=np.int32)
+    _check(lib.hx_indexset_unrank(s, rank, k.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return k
+
+
+def hx_indexset_rank(s, k) -> int:
+    kk = np.ascontiguousarray(k, dtype=np.int32)
+    return int(lib.hx_indexset_rank(s, kk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+
+
+def hx_indexset_export(s, N: int) -> np.ndarray:
+    n = hx_indexset_size(s)
+    k = np.zeros((n, N), dtype=np.int32)
+    _check(lib.hx_indexset_export(s, k.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return k
+
+
+def hx_indexset_destroy(s):
+    lib.hx_indexset_destroy(s)
+
+
+# ---- problem -----------------------------------------------------------------------------
+
+def hx_problem_create(s, dtype: int = HX_C128, order: int = HX_ORDER_SYM, m: int = 7, stream: int = 0):
+    cfg = hx_config(dtype, order, m, ctypes.c_void_p(stream))
+    h = ctypes.c_void_p()
+    _check(lib.hx_problem_create(s, ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def hx_problem_destroy(p):
+    lib.hx_problem_destroy(p)
+
+
+def hx_potential_set(p, L: float, terms: list, t: float = 0.0):
+    """terms: list of dicts {axes: [a] or [a, b], coef: ndarray (deg+1,) or (deg_a+1, deg_b+1),
+    mod: hx_mod_kind, amp, omega, phase, pw_values, pw_t0, pw_t1}."""
+    keep = []
+    arr = (hx_term * max(len(terms), 1))()
+    for i, t_ in enumerate(terms):
+        coef = np.ascontiguousarray(t_["coef"], dtype=np.float64)
+        keep.append(coef)
+        axes = list(t_["axes"])
+        tm = arr[i]
+        tm.n_axes = len(axes)
+        for j, a in enumerate(axes[:2]):     # more than two axes: the library reports it
+            tm.axes[j] = a
+            tm.deg[j] = coef.shape[j] - 1
+        tm.coef = _dptr(coef)
+        tm.mod_kind = t_.get("mod", HX_MOD_CONST)
+        tm.amp = t_.get("amp", 1.0)
+        tm.omega = t_.get("omega", 0.0)
+        tm.phase = t_.get("phase", 0.0)
+        if tm.mod_kind == HX_MOD_PWCONST:
+            pw = np.ascontiguousarray(t_["pw_values"], dtype=np.float64)
+            keep.append(pw)
+            tm.pw_values = _dptr(pw)
+            tm.pw_n = len(pw)
+            tm.pw_t0 = t_["pw_t0"]
+            tm.pw_t1 = t_["pw_t1"]
+    pot = hx_potential(L, len(terms), arr)
+    _check(lib.hx_potential_set(p, ctypes.byref(pot), t))
+
+
+def hx_get_time(p) -> float:
+    t = ctypes.c_double()
+    _check(lib.hx_get_time(p, ctypes.byref(t)))
+    return t.value
+
+
+def hx_set_time(p, t: float):
+    _check(lib.hx_set_time(p, t))
+
+
+def hx_apply(p, c_in, c_out):
+    _check(lib.hx_apply(p, ctypes.c_void_p(_tptr(c_in)), ctypes.c_void_p(_tptr(c_out))))
+
+
+def hx_apply_host(p, c_in: np.ndarray, c_out: np.ndarray):
+    _check(lib.hx_apply_host(p, c_in.ctypes.data_as(ctypes.c_void_p), c_out.ctypes.data_as(ctypes.c_void_p)))
+
+
+def hx_step(p, c, dt: float, nsteps: int) -> int:
+    return _check(lib.hx_step(p, ctypes.c_void_p(_tptr(c)), dt, nsteps), allow=(HX_EBREAKDOWN,))
+
+
+def hx_step_host(p, c: np.ndarray, dt: float, nsteps: int) -> int:
+    return _check(lib.hx_step_host(p, c.ctypes.data_as(ctypes.c_void_p), dt, nsteps), allow=(HX_EBREAKDOWN,))
+
+
+def hx_step_info(p, m: int = 32) -> dict:
+    mu = ctypes.c_int()
+    a = np.zeros(m)
+    b = np.zeros(m)
+    nr = ctypes.c_double()
+    st = _check(lib.hx_step_info(p, ctypes.byref(mu), _dptr(a), _dptr(b), ctypes.byref(nr)), allow=(HX_EBREAKDOWN,))
+    return {"m_used": mu.value, "alpha": a[: mu.value], "beta": b[: max(mu.value - 1, 0)], "norm": nr.value,
+            "breakdown": st == HX_EBREAKDOWN}
+
+
+def hx_norm(p, c) -> float:
+    out = ctypes.c_double()
+    _check(lib.hx_norm(p, ctypes.c_void_p(_tptr(c)), ctypes.byref(out)))
+    return out.value
+
+
+# ---- Chebyshev helpers -------------------------------------------------------------------
+
+def hx_cheb_nodes(R: int) -> np.ndarray:
+    u = np.zeros(R + 1)
+    _check(lib.hx_cheb_nodes(R, _dptr(u)))
+    return u
+
+
+def hx_cheb_coeffs(R: int, values: np.ndarray) -> np.ndarray:
+    v = np.ascontiguousarray(values, dtype=np.float64)
+    out = np.zeros_like(v)
+    _check(lib.hx_cheb_coeffs(R, v.ndim, _dptr(v), _dptr(out)))
+    return out
+
+
+def hx_cheb_monomial(p: int, L: float) -> np.ndarray:
+    out = np.zeros(p + 1)
+    _check(lib.hx_cheb_monomial(p, L, _dptr(out)))
+    return out
+
+
+def terms_from_spec(spec: dict) -> list:
+    """hx_term dictionaries for a workload's potential (see paper_1403_3511_gb300.inputs): monomials
+    through hx_cheb_monomial, smooth functions through their values at hx_cheb_nodes and
+    hx_cheb_coeffs.  Evaluating the user's function at the nodes is the only arithmetic here."""
+    L = spec["L"]
+    out = []
+    for comp in spec["potential"]:
+        mod = comp.get("mod", {"kind": "const"})
+        t = {"mod": MODS[mod["kind"]], "amp": comp["coef"], "omega": mod.get("omega", 0.0),
+             "phase": mod.get("phase", 0.0)}
+        if mod["kind"] == "pwconst":
+            t.update(pw_values=mod["values"], pw_t0=mod["t0"], pw_t1=mod["t1"])
+        if "powers" in comp:
+            axes = sorted(comp["powers"])
+            if len(axes) > 2:
+                raise ValueError("terms on more than two axes are not supported")
+            cs = [hx_cheb_monomial(comp["powers"][a], L) for a in axes]
+            t["axes"] = axes
+            t["coef"] = cs[0] if len(cs) == 1 else np.outer(cs[0], cs[1])
+        elif comp["func"] == "cos_diff":
+            R = comp["R"]
+            u = hx_cheb_nodes(R)
+            t["axes"] = list(comp["axes"])
+            t["coef"] = hx_cheb_coeffs(R, np.cos(L * u[:, None] - L * u[None, :]))
+        elif comp["func"] == "cos_scaled":
+            R = comp["R"]
+            u = hx_cheb_nodes(R)
+            t["axes"] = list(comp["axes"])
+            t["coef"] = hx_cheb_coeffs(R, np.cos(comp["scale"] * L * u))
+        else:
+            raise KeyError(comp["func"])
+        out.append(t)
+    return out
+
+
+class Problem:
+    """Convenience owner of an index set and a problem (frees both)."""
+
+    def __init__(self, N: int, B: int, dtype: int = HX_C128, order: str = "sym", m: int = 7, stream: int = 0,
+                 indexset=None):
+        self._own_set = indexset is None
+        self.set = hx_indexset_create(N, B) if indexset is None else indexset
+        self.N, self.B = N, B
+        self.size = hx_indexset_size(self.set)
+        self.dtype = dtype
+        self.p = hx_problem_create(self.set, dtype, ORDERS[order] if isinstance(order, str) else order, m, stream)
+
+    def set_potential(self, spec: dict, t: float = 0.0):
+        hx_potential_set(self.p, spec["L"], terms_from_spec(spec), t)
+
+    def close(self):
+        if getattr(self, "p", None) is not None:
+            hx_problem_destroy(self.p)
+            self.p = None
+        if getattr(self, "set", None) is not None and self._own_set:
+            hx_indexset_destroy(self.set)
+            self.set = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

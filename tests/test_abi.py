@@ -1,0 +1,75 @@
+"""The C-ABI library builds, loads and exports every entry point include/hx.h declares; host-only
+helpers agree with the oracle.  No GPU needed (no device call is made)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "hx.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*HX_API\s+(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(hx_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libhx():
+    from paper_1403_3511_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["hx_indexset_create", "hx_potential_set", "hx_apply", "hx_step", "hx_last_error"]:
+        assert required in names
+    assert len(names) >= 20
+
+
+def test_every_declared_symbol_is_exported(libhx):
+    missing = [n for n in declared_functions() if not hasattr(libhx, n)]
+    assert not missing, missing
+
+
+def test_no_internal_symbols_leak(libhx):
+    for n in ["build_host_tables", "launch_apply", "krylov_step"]:
+        assert not hasattr(libhx, n)
+
+
+def test_binding_loads_and_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_1403_3511_gb300 import hx
+    assert os.path.exists(hx.LIB_PATH)
+    monkeypatch.setattr(hx, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        hx._load()
+
+
+def test_cheb_helpers_match_oracle(oracle):
+    from paper_1403_3511_gb300 import hx
+    for R in (3, 8):
+        assert np.allclose(hx.hx_cheb_nodes(R), oracle.cheb_nodes(R), atol=1e-15)
+        u = oracle.cheb_nodes(R)
+        v1 = np.cos(3.0 * u) + u ** 3
+        assert np.allclose(hx.hx_cheb_coeffs(R, v1), oracle.cheb_coeffs_1d(v1), atol=1e-14)
+        v2 = np.cos(np.subtract.outer(2.0 * u, 1.5 * u))
+        assert np.allclose(hx.hx_cheb_coeffs(R, v2), oracle.cheb_coeffs_2d(v2), atol=1e-14)
+    for p in range(7):
+        L = 3.7
+        u = oracle.cheb_nodes(p)
+        assert np.allclose(hx.hx_cheb_monomial(p, L), oracle.cheb_coeffs_1d((L * u) ** p), atol=1e-12 * L ** p)
+
+
+def test_argument_errors_without_device(libhx):
+    from paper_1403_3511_gb300 import hx
+    with pytest.raises(hx.HxError):
+        hx.hx_indexset_create(0, 10)
+    with pytest.raises(hx.HxError):
+        hx.hx_indexset_create(3, 70000)
+    assert "B = 70000" in hx.hx_last_error()
+    with pytest.raises(hx.HxError):
+        hx.hx_cheb_nodes(-1)

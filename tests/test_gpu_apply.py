@@ -1,0 +1,223 @@
+"""GPU parity of the index set and the matrix-free product against the oracle (through the C ABI)."""
+import numpy as np
+import pytest
+
+from paper_1403_3511_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL_C128 = 1e-12      # FP64 path: relative to max |y_ref|
+TOL_C64 = 1e-5        # complex64 stencil: relative 2-norm error
+
+
+@pytest.fixture(scope="module")
+def hx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_3511_gb300 import build
+    build.build()
+    from paper_1403_3511_gb300 import hx as _hx
+    return _hx
+
+
+def spec_of(N, B, potential, L=None):
+    return dict(N=N, B=B, L=L or inputs.half_width(B), potential=potential)
+
+
+def gpu_apply(hx, P, c):
+    tdt = torch.complex64 if P.dtype == hx.HX_C64 else torch.complex128
+    x = torch.from_numpy(np.ascontiguousarray(c)).to("cuda", tdt)
+    y = torch.empty_like(x)
+    hx.hx_apply(P.p, x, y)
+    torch.cuda.synchronize()
+    return y.cpu().numpy().astype(np.complex128)
+
+
+def make(hx, spec, dtype, order="sym", t=0.0):
+    P = hx.Problem(spec["N"], spec["B"], dtype=dtype, order=order)
+    P.set_potential(spec, t)
+    return P
+
+
+@pytest.mark.parametrize("N,B", [(1, 1), (1, 50), (2, 1), (2, 32), (3, 100), (4, 512), (6, 300), (10, 64), (7, 2000)])
+def test_export_rank_unrank_bit_exact(hx, oracle, N, B):
+    S = oracle.IndexSet.hyperbolic(N, B)
+    s = hx.hx_indexset_create(N, B)
+    try:
+        assert hx.hx_indexset_size(s) == S.size
+        k = hx.hx_indexset_export(s, N)
+        assert np.array_equal(k, S.k)
+        for i in inputs.sample_rows(S.size, 50):
+            assert hx.hx_indexset_rank(s, S.k[i]) == i
+            assert np.array_equal(hx.hx_indexset_unrank(s, int(i), N), S.k[i])
+        assert hx.hx_indexset_rank(s, np.full(N, B)) == -1
+    finally:
+        hx.hx_indexset_destroy(s)
+
+
+def random_spec(rng, N, B, nterms, maxdeg):
+    comps = []
+    for _ in range(nterms):
+        axes = sorted(rng.choice(N, size=min(N, rng.integers(1, 3)), replace=False).tolist())
+        powers = {int(a): int(rng.integers(1, maxdeg + 1)) for a in axes}
+        comps.append({"coef": float(rng.standard_normal()), "powers": powers})
+    return spec_of(N, B, comps)
+
+
+CASES = {
+    "hh2_b32": lambda: inputs.workload("hh2_b32"),
+    "hh3_b300_dipole": lambda: spec_of(3, 300, inputs.henon_heiles_chain(3, 0.111, (0.05, 1.0))),
+    "ctrl4_b512": lambda: inputs.workload("ctrl4_b512"),
+    "cos3_b64": lambda: spec_of(3, 64, inputs.cos_chain(3, 0.2, 8)),
+    "cos4_b40_deg5": lambda: spec_of(4, 40, inputs.cos_chain(4, 0.3, 5)),
+    "line1_b50": lambda: spec_of(1, 50, [{"coef": 0.3, "powers": {0: 3}}, {"coef": -0.2, "powers": {0: 1}}]),
+    "rand5_b150": lambda: random_spec(np.random.default_rng(11), 5, 150, 8, 3),
+    "rand4_b90_deg6": lambda: random_spec(np.random.default_rng(12), 4, 90, 5, 6),
+    "hh6_b2000": lambda: spec_of(6, 2000, inputs.henon_heiles_chain(6, 0.111, (0.05, 1.0))),
+}
+
+
+def check(y, ref, dtype, hx):
+    if dtype == hx.HX_C128:
+        err = np.abs(y - ref).max() / np.abs(ref).max()
+        assert err <= TOL_C128, err
+    else:
+        err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+        assert err <= TOL_C64, err
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_apply_matches_oracle(hx, oracle, case, dtype):
+    spec = CASES[case]()
+    dt = hx.HX_C128 if dtype == "c128" else hx.HX_C64
+    t = 0.7
+    S = oracle.IndexSet.hyperbolic(spec["N"], spec["B"])
+    c = inputs.initial_vector({"init": {"kind": "gaussian", "seed": 5}}, S.k)
+    r, a = oracle.potential_terms(spec, t)
+    ref = oracle.apply(S, r, a, spec["L"], c)
+    P = make(hx, spec, dt, t=t)
+    try:
+        check(gpu_apply(hx, P, c), ref, dt, hx)
+    finally:
+        P.close()
+
+
+@pytest.mark.parametrize("order", ["eq", "alg"])
+def test_literal_orders_match_oracle(hx, oracle, order):
+    spec = random_spec(np.random.default_rng(3), 4, 200, 7, 3)
+    S = oracle.IndexSet.hyperbolic(4, 200)
+    c = inputs.initial_vector({"init": {"kind": "gaussian", "seed": 6}}, S.k)
+    r, a = oracle.potential_terms(spec, 0.0)
+    ref = oracle.apply(S, r, a, spec["L"], c, order)
+    P = make(hx, spec, hx.HX_C128, order=order)
+    try:
+        check(gpu_apply(hx, P, c), ref, hx.HX_C128, hx)
+    finally:
+        P.close()
+
+
+@pytest.mark.parametrize("name", ["hh6_b4096", "cos10_b1024"])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_full_size_sampled_rows(hx, oracle, name, dtype):
+    """The full-size workloads, launched exactly as the benchmark does, checked on sampled rows
+    that the oracle computes one at a time (first and last rows included)."""
+    spec = inputs.workload(name)
+    dt = hx.HX_C128 if dtype == "c128" else hx.HX_C64
+    S = oracle.IndexSet.hyperbolic(spec["N"], spec["B"])
+    c = inputs.initial_vector(spec, S.k)
+    t = 0.25
+    r, a = oracle.potential_terms(spec, t)
+    rows = inputs.sample_rows(S.size, 400, seed=9)
+    ref = oracle.apply_rows(S, spec["B"], r, a, spec["L"], c, rows)
+    P = make(hx, spec, dt, t=t)
+    try:
+        y = gpu_apply(hx, P, c)
+    finally:
+        P.close()
+    tol = TOL_C128 if dt == hx.HX_C128 else TOL_C64
+    err = np.abs(y[rows] - ref).max() / np.abs(ref).max()
+    assert err <= tol, err
+
+
+def test_edge_cases(hx, oracle):
+    # single element, no terms: A = D
+    P = hx.Problem(3, 1)
+    try:
+        hx.hx_potential_set(P.p, 5.0, [], 0.0)
+        y = gpu_apply(hx, P, np.array([2.0 + 1.0j]))
+        assert np.allclose(y, [1.5 * (2.0 + 1.0j)], atol=0)
+    finally:
+        P.close()
+    # constant term folds into the diagonal; a term on the last axis only
+    spec = spec_of(2, 20, [{"coef": 0.4, "powers": {}}, {"coef": 0.7, "powers": {1: 2}}])
+    spec["potential"][0] = {"coef": 0.4, "func": "cos_scaled", "axes": [0], "scale": 0.0, "R": 0}
+    S = oracle.IndexSet.hyperbolic(2, 20)
+    c = inputs.initial_vector({"init": {"kind": "gaussian", "seed": 1}}, S.k)
+    r, a = oracle.potential_terms(spec, 0.0)
+    P = make(hx, spec, hx.HX_C128)
+    try:
+        check(gpu_apply(hx, P, c), oracle.apply(S, r, a, spec["L"], c), hx.HX_C128, hx)
+    finally:
+        P.close()
+
+
+def test_time_modulation_and_set_time(hx, oracle):
+    spec = inputs.workload("ctrl4_b512")
+    S = oracle.IndexSet.hyperbolic(4, 512)
+    c = inputs.initial_vector({"init": {"kind": "gaussian", "seed": 2}}, S.k)
+    P = make(hx, spec, hx.HX_C128, t=0.0)
+    try:
+        for t in (0.0, 0.05, 0.049999, 3.3, 9.99, 10.0, 12.0):   # interval edges and outside [0, T)
+            hx.hx_set_time(P.p, t)
+            assert hx.hx_get_time(P.p) == t
+            r, a = oracle.potential_terms(spec, t)
+            check(gpu_apply(hx, P, c), oracle.apply(S, r, a, spec["L"], c), hx.HX_C128, hx)
+    finally:
+        P.close()
+
+
+def test_deterministic(hx):
+    spec = inputs.workload("hh6_b4096")
+    P = make(hx, spec, hx.HX_C64)
+    try:
+        x = torch.randn(P.size, dtype=torch.complex64, device="cuda")
+        y1, y2 = torch.empty_like(x), torch.empty_like(x)
+        hx.hx_apply(P.p, x, y1)
+        hx.hx_apply(P.p, x, y2)
+        torch.cuda.synchronize()
+        assert torch.equal(y1, y2)
+    finally:
+        P.close()
+
+
+def test_host_entry_point(hx, oracle):
+    spec = inputs.workload("hh2_b32")
+    S = oracle.IndexSet.hyperbolic(2, 32)
+    c = inputs.initial_vector(spec, S.k)
+    P = make(hx, spec, hx.HX_C128)
+    try:
+        out = np.zeros_like(c)
+        hx.hx_apply_host(P.p, c, out)
+        r, a = oracle.potential_terms(spec, 0.0)
+        check(out, oracle.apply(S, r, a, spec["L"], c), hx.HX_C128, hx)
+    finally:
+        P.close()
+
+
+def test_errors(hx):
+    P = hx.Problem(3, 20)
+    try:
+        x = torch.zeros(P.size, dtype=torch.complex128, device="cuda")
+        with pytest.raises(hx.HxError):
+            hx.hx_apply(P.p, x, torch.empty_like(x))          # no potential yet
+        with pytest.raises(hx.HxError) as ei:
+            hx.hx_potential_set(P.p, 5.0, [{"axes": [0, 1, 2], "coef": np.ones((2, 2, 2))}], 0.0)
+        assert ei.value.status in (-1, -7)
+        with pytest.raises(hx.HxError):
+            hx.hx_potential_set(P.p, -1.0, [], 0.0)
+        with pytest.raises(hx.HxError):
+            hx.hx_potential_set(P.p, 5.0, [{"axes": [1, 0], "coef": np.ones((2, 2))}], 0.0)
+    finally:
+        P.close()

@@ -1,0 +1,115 @@
+"""GPU parity of the time step (exponential midpoint rule + Lanczos) against the oracle."""
+import numpy as np
+import pytest
+
+from paper_1403_3511_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_3511_gb300 import build
+    build.build()
+    from paper_1403_3511_gb300 import hx as _hx
+    return _hx
+
+
+def run_gpu(hx, spec, c0, dtype, dt, nsteps, m=7, t0=0.0, chunks=1):
+    P = hx.Problem(spec["N"], spec["B"], dtype=dtype, m=m)
+    try:
+        P.set_potential(spec, t0)
+        x = torch.from_numpy(np.ascontiguousarray(c0)).to("cuda", torch.complex128)
+        for _ in range(chunks):
+            hx.hx_step(P.p, x, dt, nsteps // chunks)
+        info = hx.hx_step_info(P.p)
+        t = hx.hx_get_time(P.p)
+        return x.cpu().numpy(), info, t
+    finally:
+        P.close()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
+def test_henon_heiles_n2_100_steps(hx, oracle, dtype, tol):
+    spec = inputs.workload("hh2_b32")
+    S = oracle.IndexSet.hyperbolic(2, 32)
+    c0 = inputs.initial_vector(spec, S.k)
+    ref, t_ref = oracle.expmpr_propagate(S, spec, c0, spec["dt"], spec["steps"], spec["m"])
+    dt_ = hx.HX_C128 if dtype == "c128" else hx.HX_C64
+    got, info, t = run_gpu(hx, spec, c0, dt_, spec["dt"], spec["steps"], chunks=4)
+    assert abs(t - t_ref) < 1e-12
+    assert rel(got, ref) <= tol, rel(got, ref)
+    assert abs(np.linalg.norm(got) - 1.0) <= (1e-12 if dtype == "c128" else 1e-5)
+    assert abs(info["norm"] - np.linalg.norm(got)) < 1e-12
+
+
+def test_lanczos_coefficients_match_oracle(hx, oracle):
+    spec = dict(N=3, B=200, L=inputs.half_width(200), potential=inputs.henon_heiles_chain(3, 0.111, (0.05, 1.0)))
+    S = oracle.IndexSet.hyperbolic(3, 200)
+    c0 = inputs.initial_vector({"init": {"kind": "coherent", "q": [0.5, -0.3, 0.8], "eps": 1e-3, "seed": 3}}, S.k)
+    h = 0.02
+    r, a = oracle.potential_terms(spec, 0.5 * h)
+    ref, al, be = oracle.lanczos_exp(lambda v: oracle.apply(S, r, a, spec["L"], v), c0, h, 7)
+    got, info, _ = run_gpu(hx, spec, c0, hx.HX_C128, h, 1)
+    assert info["m_used"] == len(al)
+    assert np.allclose(info["alpha"], al, rtol=1e-12, atol=1e-12 * np.abs(al).max())
+    assert np.allclose(info["beta"], be, rtol=1e-11)
+    assert rel(got, ref) <= 1e-12
+
+
+def test_harmonic_breakdown_is_exact(hx, oracle):
+    """W = 0 and c on three levels of D: Lanczos stops after 3 vectors and the step is exact."""
+    spec = dict(N=3, B=30, L=5.0, potential=[])
+    S = oracle.IndexSet.hyperbolic(3, 30)
+    d = oracle.diag(S)
+    c0 = np.zeros(S.size, complex)
+    for lev in (1.5, 3.5, 6.5):
+        c0[np.where(d == lev)[0]] = 0.3 + 0.1j
+    h = 0.37
+    got, info, _ = run_gpu(hx, spec, c0, hx.HX_C128, h, 1)
+    assert info["breakdown"] and info["m_used"] == 3
+    assert np.allclose(got, np.exp(-1j * d * h) * c0, atol=1e-13)
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
+def test_control_problem_steps(hx, oracle, dtype, tol):
+    spec = inputs.workload("ctrl4_b512")
+    S = oracle.IndexSet.hyperbolic(4, 512)
+    c0 = inputs.initial_vector(spec, S.k)
+    h = 0.005
+    ref, _ = oracle.expmpr_propagate(S, spec, c0, h, 20, 7, t0=0.03)
+    got, _, _ = run_gpu(hx, spec, c0, hx.HX_C128 if dtype == "c128" else hx.HX_C64, h, 20, t0=0.03)
+    assert rel(got, ref) <= tol, rel(got, ref)
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
+def test_full_size_one_step(hx, oracle, dtype, tol):
+    """One step of the N=6, B=4096 workload (|K| = 4,883,360) against the oracle."""
+    spec = inputs.workload("hh6_b4096")
+    S = oracle.IndexSet.hyperbolic(6, 4096)
+    c0 = inputs.initial_vector(spec, S.k)
+    ref, _ = oracle.expmpr_propagate(S, spec, c0, spec["dt"], 1, spec["m"])
+    got, _, _ = run_gpu(hx, spec, c0, hx.HX_C128 if dtype == "c128" else hx.HX_C64, spec["dt"], 1)
+    assert rel(got, ref) <= tol, rel(got, ref)
+
+
+def test_host_step_entry_point(hx, oracle):
+    spec = inputs.workload("hh2_b32")
+    S = oracle.IndexSet.hyperbolic(2, 32)
+    c0 = inputs.initial_vector(spec, S.k)
+    ref, _ = oracle.expmpr_propagate(S, spec, c0, 0.01, 5, 7)
+    P = hx.Problem(2, 32)
+    try:
+        P.set_potential(spec, 0.0)
+        c = c0.copy()
+        hx.hx_step_host(P.p, c, 0.01, 5)
+        assert rel(c, ref) <= 1e-12
+    finally:
+        P.close()

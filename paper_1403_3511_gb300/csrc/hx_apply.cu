@@ -29,23 +29,36 @@ struct ApplyArgs : ApplyArgsBase {
     const void *cin;
     void *cout;
     const double *out_scale;   // nullptr = 1
+    void *chan;                // channel vectors (read by the main stage, written by stage 1)
+    size_t chan_ld;
+    int stage1;                // 1: write each op's result to its channel instead of y
 };
 
-__device__ __forceinline__ double op_weight(const Op &op, double t, const double *pw)
+// amp * f(t) in the stencil precision R (the interval index of a piecewise-constant modulation is
+// always found in FP64 so that both precisions switch intervals at the same t).
+template <typename R>
+__device__ __forceinline__ R op_weight(const Op &op, double t, const double *pw)
 {
-    double f = 1.0;
+    R f = (R)1;
     switch (op.mod) {
-        case HX_MOD_COS: f = cos(op.omega * t + op.phase); break;
-        case HX_MOD_SIN2: { double s = sin(op.omega * t); f = s * s; } break;
+        case HX_MOD_COS: f = cos((R)(op.omega * t + op.phase)); break;
+        case HX_MOD_SIN2: { R s = sin((R)(op.omega * t)); f = s * s; } break;
         case HX_MOD_PWCONST: {
             double x = floor((t - op.pw_t0) / (op.pw_t1 - op.pw_t0) * op.pw_n);
             int qi = x < 0.0 ? 0 : (x >= op.pw_n ? op.pw_n - 1 : (int)x);
-            f = pw[op.pw_off + qi];
+            f = (R)pw[op.pw_off + qi];
         } break;
         default: break;
     }
-    return op.amp * f;
+    return (R)op.amp * f;
 }
+
+// Exact a / b when b divides a (both < 2^24): the correctly rounded float quotient is the integer.
+__device__ __forceinline__ int exact_div(int a, int b) { return __float2int_rn(__fdiv_rn((float)a, (float)b)); }
+
+// floor(B / x) for integers B, x >= 1 with B + x < 2^24: the rounding error of the correctly rounded
+// float quotient, at most 2^-24 (B / x + 1), is smaller than the distance 1/x to the next integer.
+__device__ __forceinline__ int floor_div(int B, int x) { return __float2int_rz(__fdiv_rn((float)B, (float)x)); }
 
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
@@ -84,7 +97,7 @@ struct Elem {
 
 struct Ctx {
     const DevSet *S;
-    const int4 *nb;           // item neighbour table (shared)
+    const int2 *nb;           // item neighbour table (shared): slab start, qoff
     int nd;
     const uint16_t *kk;       // shared multi-indices, [l * blockDim + tid]
     int tid, nthr;
@@ -100,7 +113,7 @@ __device__ __forceinline__ int point_addr(const Ctx &c, const Elem &el, const Op
     int di = O.didx[op.dbase + pos];
     int start = el.start, qoff = el.qoff;
     if (di != 0) {
-        int4 nb = c.nb[el.sl * c.nd + di];
+        int2 nb = c.nb[el.sl * c.nd + di];
         start = nb.x;
         qoff = nb.y;
     }
@@ -186,17 +199,152 @@ __device__ __forceinline__ void plane_op(const Ctx &c, const Elem &el, const OpS
     }
 }
 
+// floor(B / x) for x >= 1 from the table (0 when x > B: no element has those coordinates).
+__device__ __forceinline__ int nt_of(const DevSet &S, int x) { return x <= S.B ? __ldg(S.nt + x) : 0; }
+
+// Row start (global rank of local row i) inside the slab described by (start, qoff); N >= 2.
+__device__ __forceinline__ int row_start(const DevSet &S, int start, int qoff, int i) { return start + __ldg(S.Q + qoff + i); }
+
+// Base rank of the point that moves by s along an axis of role RA (k + s e_a), before adding the
+// last coordinate: own slab for inner roles, neighbour slab for an outer axis.
+template <int RA>
+__device__ __forceinline__ int2 slab_of(const Ctx &c, const Elem &el, const OpSet &O, int didx_pos)
+{
+    if (RA == ROLE_OUT) {
+        const int di = O.didx[didx_pos];
+        return c.nb[el.sl * c.nd + di];
+    }
+    return make_int2(el.start, el.qoff);
+}
+
+// Line operator P(X_a), P of pure parity and degree P (offsets -P, -P+2, ..., P), axis role RA.
+template <typename R, int P, int RA>
+__device__ __forceinline__ void line_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
+                                          const typename Vec2<R>::T *src, R &sx, R &sy)
+{
+    const DevSet &S = *c.S;
+    const int ka = RA == ROLE_I2 ? el.k2 : (RA == ROLE_I1 ? el.k1 : c.k(op.a));
+    const int top = nt_of(S, exact_div(el.qall, 1 + ka)) - 1 - ka;      // steps to the top of the a-fibre
+    const R *row = tab + op.tabP + (ka * (P + 1) + min(P, top)) * (2 * P + 1) + P;
+    const int own_row = RA == ROLE_I2 ? (S.N >= 2 ? row_start(S, el.start, el.qoff, el.k1) : el.start) : 0;
+#pragma unroll
+    for (int s = -P; s <= P; s += 2) {
+        if (ka + s < 0 || s > top) continue;
+        int addr;
+        if (RA == ROLE_I2) {
+            addr = own_row + el.k2 + s;
+        } else if (RA == ROLE_I1) {
+            addr = row_start(S, el.start, el.qoff, el.k1 + s) + el.k2;
+        } else {
+            const int2 nb = slab_of<ROLE_OUT>(c, el, O, op.dbase + s + P);
+            addr = (S.N >= 2 ? row_start(S, nb.x, nb.y, el.k1) : nb.x) + el.k2;
+        }
+        const typename Vec2<R>::T v = src[addr];
+        const R w = row[s];
+        sx += w * v.x;
+        sy += w * v.y;
+    }
+}
+
+// Plane operator wAB P(X_a) Q(X_b) + wBA Q(X_b) P(X_a), pure parities, degrees P, Q, roles RA < RB.
+// A footprint point k + s e_a + s2 e_b carries [P]_{k, k+s e_a} [Q]_{k+s e_a, k+s e_a+s2 e_b} (path
+// through k + s e_a) and [Q]_{k, k+s2 e_b} [P]_{k+s2 e_b, k+s2 e_b+s e_a} (path through k + s2 e_b);
+// a path exists only if its intermediate point is in K.  Rows of P(J_n / L) and Q(J_n / L) come
+// from the tables, indexed by the coordinate and the distance to the fibre top.
+template <typename R, int P, int Q, int RA, int RB>
+__device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
+                                           const typename Vec2<R>::T *src, R &sx, R &sy)
+{
+    const DevSet &S = *c.S;
+    const int ka = RA == ROLE_I1 ? el.k1 : c.k(op.a);
+    const int kb = RB == ROLE_I2 ? el.k2 : (RB == ROLE_I1 ? el.k1 : c.k(op.b));
+    const int rab = exact_div(el.qall, (1 + ka) * (1 + kb));
+    const R wAB = (R)O.wAB, wBA = (R)O.wBA;
+    const R *tP = tab + op.tabP, *tQ = tab + op.tabQ;
+    // a-fibre tops at k + s2 e_b, b-fibre tops at k + s e_a
+    int topA[2 * Q + 1], topB[2 * P + 1];
+    const R *rowP[2 * Q + 1];   // P row at k + s2 e_b (valid when that point is in K)
+    const R *rowQ[2 * P + 1];   // Q row at k + s e_a
+    topA[Q] = nt_of(S, rab * (1 + kb)) - 1 - ka;
+    topB[P] = nt_of(S, rab * (1 + ka)) - 1 - kb;
+#pragma unroll
+    for (int s2 = -Q; s2 <= Q; s2 += 2)
+        if (s2 != 0) topA[s2 + Q] = kb + s2 >= 0 ? nt_of(S, rab * (1 + kb + s2)) - 1 - ka : -1;
+#pragma unroll
+    for (int s = -P; s <= P; s += 2)
+        if (s != 0) topB[s + P] = ka + s >= 0 ? nt_of(S, rab * (1 + ka + s)) - 1 - kb : -1;
+#pragma unroll
+    for (int s2 = -Q; s2 <= Q; ++s2)
+        if (s2 == 0 || ((s2 - Q) & 1) == 0) rowP[s2 + Q] = tP + (ka * (P + 1) + max(0, min(P, topA[s2 + Q]))) * (2 * P + 1) + P;
+#pragma unroll
+    for (int s = -P; s <= P; ++s)
+        if (s == 0 || ((s - P) & 1) == 0) rowQ[s + P] = tQ + (kb * (Q + 1) + max(0, min(Q, topB[s + P]))) * (2 * Q + 1) + Q;
+    const int topA0 = topA[Q], topB0 = topB[P];
+    int own_row = 0;
+    if (RB == ROLE_I2 && RA == ROLE_I1) own_row = 0;   // rows vary with s below
+#pragma unroll
+    for (int s = -P; s <= P; s += 2) {
+        if (ka + s < 0) continue;
+        const bool inA = s <= topA0;                    // k + s e_a in K
+        const R pj = inA ? rowP[Q][s] : (R)0;
+        int base_s = 0;                                 // rank of row containing k + s e_a (+ s2 e_b for RB = I2)
+        int2 nb_s = make_int2(el.start, el.qoff);
+        if (RA == ROLE_OUT && RB != ROLE_OUT) nb_s = slab_of<ROLE_OUT>(c, el, O, op.dbase + (s + P) * (2 * Q + 1) + Q);
+        if (RB == ROLE_I2) base_s = (RA == ROLE_I1) ? row_start(S, el.start, el.qoff, el.k1 + s) : row_start(S, nb_s.x, nb_s.y, el.k1);
+#pragma unroll
+        for (int s2 = -Q; s2 <= Q; s2 += 2) {
+            if (kb + s2 < 0 || s > topA[s2 + Q]) continue;     // footprint point not in K
+            const R cab = inA ? pj * rowQ[s + P][s2] : (R)0;
+            const R cba = s2 <= topB0 ? rowQ[P][s2] * rowP[s2 + Q][s] : (R)0;   // k + s2 e_b in K
+            const R w = wAB * cab + wBA * cba;
+            int addr;
+            if (RB == ROLE_I2) {
+                addr = base_s + el.k2 + s2;
+            } else if (RB == ROLE_I1) {                 // RA outer: neighbour slab by s, row k1 + s2
+                addr = row_start(S, nb_s.x, nb_s.y, el.k1 + s2) + el.k2;
+            } else {                                    // both outer: neighbour slab by (s, s2)
+                const int2 nb = slab_of<ROLE_OUT>(c, el, O, op.dbase + (s + P) * (2 * Q + 1) + (s2 + Q));
+                addr = row_start(S, nb.x, nb.y, el.k1) + el.k2;
+            }
+            const typename Vec2<R>::T v = src[addr];
+            sx += w * v.x;
+            sy += w * v.y;
+        }
+    }
+    (void)own_row;
+}
+
+template <typename R, int P, int Q>
+__device__ __forceinline__ void plane_dispatch(int key, const Ctx &c, const Elem &el, const OpSet &O, const Op &op,
+                                               const R *tab, const typename Vec2<R>::T *src, R &sx, R &sy)
+{
+    if (key == ROLE_OUT * 4 + ROLE_OUT) plane_role<R, P, Q, ROLE_OUT, ROLE_OUT>(c, el, O, op, tab, src, sx, sy);
+    else if (key == ROLE_OUT * 4 + ROLE_I1) plane_role<R, P, Q, ROLE_OUT, ROLE_I1>(c, el, O, op, tab, src, sx, sy);
+    else if (key == ROLE_OUT * 4 + ROLE_I2) plane_role<R, P, Q, ROLE_OUT, ROLE_I2>(c, el, O, op, tab, src, sx, sy);
+    else plane_role<R, P, Q, ROLE_I1, ROLE_I2>(c, el, O, op, tab, src, sx, sy);
+}
+
+template <typename R, int P>
+__device__ __forceinline__ void line_dispatch(int ra, const Ctx &c, const Elem &el, const OpSet &O, const Op &op,
+                                              const R *tab, const typename Vec2<R>::T *src, R &sx, R &sy)
+{
+    if (ra == ROLE_OUT) line_role<R, P, ROLE_OUT>(c, el, O, op, tab, src, sx, sy);
+    else if (ra == ROLE_I1) line_role<R, P, ROLE_I1>(c, el, O, op, tab, src, sx, sy);
+    else line_role<R, P, ROLE_I2>(c, el, O, op, tab, src, sx, sy);
+}
+
 // MD: largest polynomial degree of the compiled potential (3: unrolled stencils; kMaxDeg: rolled loops).
 template <typename R, int MD>
-__global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 2 : 1) apply_kernel(const __grid_constant__ ApplyArgs args)
+__global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 3 : 1) apply_kernel(const __grid_constant__ ApplyArgs args)
 {
     using V = typename Vec2<R>::T;
-    extern __shared__ int4 sm_nb[];
+    extern __shared__ int2 sm_nb[];
     __shared__ int sm_start[65];
     __shared__ int sm_q[64];
     __shared__ uint16_t sm_pre[64 * kMaxN];
     __shared__ uint16_t sm_k[kMaxN * kApplyThreads];
     __shared__ R sm_w[kMaxOps];
+    __shared__ int8_t sm_delta[kMaxDelta * 4];
 
     const DevSet &S = args.S;
     const OpSet &O = args.ops;
@@ -207,7 +355,8 @@ __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 2 : 1) apply_kernel(c
     const R *tab = (const R *)args.tab;
     const int *Q1 = S.Q;     // level m = 1
 
-    if (tid < O.nops) sm_w[tid] = (R)op_weight(O.op[tid], *args.t_ptr + args.t_shift, args.pw_values);
+    if (tid < O.nops) sm_w[tid] = op_weight<R>(O.op[tid], *args.t_ptr + args.t_shift, args.pw_values);
+    for (int x = tid; x < O.ndelta * 4; x += blockDim.x) sm_delta[x] = O.delta[x >> 2][x & 3];
     const R oscale = args.out_scale ? (R)(*args.out_scale) : (R)1;
 
     Ctx ctx;
@@ -236,13 +385,13 @@ __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 2 : 1) apply_kernel(c
         __syncthreads();
         for (int x = tid; x < ns * nd; x += nthr) {
             const int sl = x / nd, di = x - sl * nd;
-            int4 res = make_int4(-1, 0, 0, 0);
+            int2 res = make_int2(-1, 0);
             int pre[kMaxN];
             bool ok = true;
             for (int l = 0; l < nout; ++l) pre[l] = sm_pre[sl * kMaxN + l];
             for (int j = 0; j < 2; ++j) {
-                int ax = O.delta[di][2 * j];
-                if (ax >= 0) pre[ax] += O.delta[di][2 * j + 1];
+                int ax = sm_delta[di * 4 + 2 * j];
+                if (ax >= 0) pre[ax] += sm_delta[di * 4 + 2 * j + 1];
             }
             long long q = 1;
             for (int l = 0; l < nout; ++l) {
@@ -256,7 +405,7 @@ __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 2 : 1) apply_kernel(c
                     start += S.Q[(size_t)(m - 1) * S.qtotal + S.qoff[qd] + pre[d]];
                     qd *= 1 + pre[d];
                 }
-                res = make_int4(start, (int)S.qoff[qd], qd, 0);
+                res = make_int2(start, (int)S.qoff[qd]);
             }
             sm_nb[x] = res;
         }
@@ -307,33 +456,49 @@ __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 2 : 1) apply_kernel(c
             const V ce = cin[e];
             Acc<R> acc;
             const R dj = dsum + (R)0.5 * (R)N;   // (D_K)_jj = sum_l (j_l + 1/2)
-            acc.add(dj * ce.x, dj * ce.y);
+            if (!args.stage1) acc.add(dj * ce.x, dj * ce.y);
             for (int o = 0; o < O.nops; ++o) {
                 const Op &op = O.op[o];
+                const V *src = op.src < 0 ? cin : (const V *)args.chan + (size_t)op.src * args.chan_ld;
                 R sx = (R)0, sy = (R)0;
                 if (op.kind == 0) {
-                    sx = ce.x;
-                    sy = ce.y;
+                    const V cs = src[e];
+                    sx = cs.x;
+                    sy = cs.y;
                 } else if (MD <= 3) {
-                    if (op.kind == 1) {
-                        if (op.p <= 1) line_op<R, 1, true>(ctx, el, O, op, tab, cin, sx, sy);
-                        else line_op<R, 3, true>(ctx, el, O, op, tab, cin, sx, sy);
-                    } else {
-                        if (op.p <= 2 && op.q <= 1) plane_op<R, 2, 1, true>(ctx, el, O, op, tab, cin, sx, sy);
-                        else if (op.p <= 2 && op.q <= 2) plane_op<R, 2, 2, true>(ctx, el, O, op, tab, cin, sx, sy);
-                        else plane_op<R, 3, 3, true>(ctx, el, O, op, tab, cin, sx, sy);
+                    const int key = op.ra * 4 + op.rb;
+                    switch (op.cls) {
+                        case CLS_LINE + 1: line_dispatch<R, 1>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                        case CLS_LINE + 2: line_dispatch<R, 2>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                        case CLS_LINE + 3: line_dispatch<R, 3>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                        case CLS_PLANE + 0: plane_dispatch<R, 1, 1>(key, ctx, el, O, op, tab, src, sx, sy); break;
+                        case CLS_PLANE + 3: plane_dispatch<R, 2, 1>(key, ctx, el, O, op, tab, src, sx, sy); break;
+                        case CLS_PLANE + 1: plane_dispatch<R, 1, 2>(key, ctx, el, O, op, tab, src, sx, sy); break;
+                        case CLS_PLANE + 4: plane_dispatch<R, 2, 2>(key, ctx, el, O, op, tab, src, sx, sy); break;
+                        default:
+                            if (op.kind == 1) line_op<R, 3, true>(ctx, el, O, op, tab, src, sx, sy);
+                            else plane_op<R, 3, 3, true>(ctx, el, O, op, tab, src, sx, sy);
                     }
                 } else {
-                    if (op.kind == 1) line_op<R, kMaxDeg, false>(ctx, el, O, op, tab, cin, sx, sy);
-                    else plane_op<R, kMaxDeg, kMaxDeg, false>(ctx, el, O, op, tab, cin, sx, sy);
+                    if (op.kind == 1) line_op<R, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
+                    else plane_op<R, kMaxDeg, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
                 }
                 const R w = sm_w[o];
-                acc.add(w * sx, w * sy);
+                if (args.stage1) {
+                    V ch;
+                    ch.x = w * sx;
+                    ch.y = w * sy;
+                    ((V *)args.chan)[(size_t)op.dst * args.chan_ld + e] = ch;
+                } else {
+                    acc.add(w * sx, w * sy);
+                }
             }
-            V y = acc.get();
-            y.x *= oscale;
-            y.y *= oscale;
-            cout[e] = y;
+            if (!args.stage1) {
+                V y = acc.get();
+                y.x *= oscale;
+                y.y *= oscale;
+                cout[e] = y;
+            }
         }
     }
 }
@@ -346,8 +511,8 @@ int apply_grid(const Problem *p)
 }
 
 template <typename R, int MD>
-static int launch_apply_t(Problem *p, const void *cin, void *cout, const double *t_ptr, double t_shift,
-                          const double *out_scale, cudaStream_t st)
+static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *cin, void *cout,
+                          const double *t_ptr, double t_shift, const double *out_scale, cudaStream_t st)
 {
     ApplyArgs a;
     memset(&a, 0, sizeof(a));
@@ -359,28 +524,43 @@ static int launch_apply_t(Problem *p, const void *cin, void *cout, const double 
     a.t_shift = t_shift;
     a.pw_values = p->pw_values;
     a.tab = p->tab;
-    a.ops = p->ops;
+    a.ops = ops;
     a.cin = cin;
     a.cout = cout;
     a.out_scale = out_scale;
-    size_t smem = (size_t)p->slabs_per_item * p->ops.ndelta * sizeof(int4);
+    a.chan = p->chan;
+    a.chan_ld = p->chan_ld;
+    a.stage1 = stage1;
+    size_t smem = (size_t)p->slabs_per_item * ops.ndelta * sizeof(int2);
     apply_kernel<R, MD><<<apply_grid(p), kApplyThreads, smem, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "apply kernel launch");
     return HX_OK;
 }
 
+static int launch_stage(Problem *p, const OpSet &ops, int stage1, const void *cin, void *cout, const double *t_ptr,
+                        double t_shift, const double *scale, cudaStream_t st)
+{
+    int md = 0;
+    for (int i = 0; i < ops.nops; ++i) md = max(md, max(ops.op[i].p, ops.op[i].q));
+    if (p->cfg.dtype == HX_C64)
+        return md <= 3 ? launch_apply_t<float, 3>(p, ops, stage1, cin, cout, t_ptr, t_shift, scale, st)
+                       : launch_apply_t<float, kMaxDeg>(p, ops, stage1, cin, cout, t_ptr, t_shift, scale, st);
+    return md <= 3 ? launch_apply_t<double, 3>(p, ops, stage1, cin, cout, t_ptr, t_shift, scale, st)
+                   : launch_apply_t<double, kMaxDeg>(p, ops, stage1, cin, cout, t_ptr, t_shift, scale, st);
+}
+
+int apply_launches(const Problem *p) { return p->ops1.nops > 0 ? 2 : 1; }
+
 int launch_apply(Problem *p, const void *cin, void *cout, const double *t_ptr, double t_shift, const ApplyFuse *fuse,
                  cudaStream_t st)
 {
     const double *scale = fuse ? fuse->in_scale : nullptr;
-    int md = 0;
-    for (int i = 0; i < p->ops.nops; ++i) md = max(md, max(p->ops.op[i].p, p->ops.op[i].q));
-    if (p->cfg.dtype == HX_C64)
-        return md <= 3 ? launch_apply_t<float, 3>(p, cin, cout, t_ptr, t_shift, scale, st)
-                       : launch_apply_t<float, kMaxDeg>(p, cin, cout, t_ptr, t_shift, scale, st);
-    return md <= 3 ? launch_apply_t<double, 3>(p, cin, cout, t_ptr, t_shift, scale, st)
-                   : launch_apply_t<double, kMaxDeg>(p, cin, cout, t_ptr, t_shift, scale, st);
+    if (p->ops1.nops > 0) {
+        int rc = launch_stage(p, p->ops1, 1, cin, nullptr, t_ptr, t_shift, nullptr, st);
+        if (rc) return rc;
+    }
+    return launch_stage(p, p->ops, 0, cin, cout, t_ptr, t_shift, scale, st);
 }
 
 // ---------------------------------------------------------------------------------------

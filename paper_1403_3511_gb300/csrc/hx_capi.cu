@@ -13,6 +13,9 @@
 
 namespace hx {
 
+// plane operators with more footprint points than this go through two stages
+constexpr int kDirectFootprint = 36;
+
 static thread_local char g_err[512] = "no error";
 
 void set_error(const char *fmt, ...)
@@ -235,8 +238,14 @@ static int parity_mask(const std::vector<double> &a)
     return mask;
 }
 
+// Coefficients below 1e-15 of the largest one are round-off of exact zeros (interpolation of an
+// even or odd function, elimination residue); they are set to zero, then trailing zeros dropped.
 static void trim(std::vector<double> &a)
 {
+    double big = 0.0;
+    for (double x : a) big = std::max(big, fabs(x));
+    for (double &x : a)
+        if (fabs(x) <= 1e-15 * big) x = 0.0;
     while (a.size() > 1 && a.back() == 0.0) a.pop_back();
 }
 
@@ -250,7 +259,9 @@ struct Compiler {
     double L;
     std::map<PolyKey, int> poly_base;    // polynomial -> row-table base
     std::vector<double> tab;             // all row tables (double)
-    OpSet ops;
+    OpSet ops;                           // main stage
+    OpSet ops1;                          // first stage (channel writers)
+    std::vector<std::pair<int, std::vector<double>>> chans;   // (axis, normalised polynomial)
     std::vector<double> pw;
 
     int poly(const std::vector<double> &a)
@@ -268,7 +279,7 @@ struct Compiler {
         return base;
     }
 
-    int delta_index(int a0, int s0, int a1, int s1)
+    int delta_index(OpSet &S, int a0, int s0, int a1, int s1)
     {
         int N = set->h.N;
         int8_t e[4] = {-1, 0, -1, 0};
@@ -276,21 +287,22 @@ struct Compiler {
         if (a0 >= 0 && a0 < N - 2 && s0 != 0) { e[0] = (int8_t)a0; e[1] = (int8_t)s0; n = 1; }
         if (a1 >= 0 && a1 < N - 2 && s1 != 0) { e[2 * n] = (int8_t)a1; e[2 * n + 1] = (int8_t)s1; }
         if (e[0] < 0 && e[2] < 0) return 0;
-        for (int i = 1; i < ops.ndelta; ++i)
-            if (!memcmp(ops.delta[i], e, 4)) return i;
-        if (ops.ndelta >= kMaxDelta) return -1;
-        memcpy(ops.delta[ops.ndelta], e, 4);
-        return ops.ndelta++;
+        for (int i = 1; i < S.ndelta; ++i)
+            if (!memcmp(S.delta[i], e, 4)) return i;
+        if (S.ndelta >= kMaxDelta) return -1;
+        memcpy(S.delta[S.ndelta], e, 4);
+        return S.ndelta++;
     }
 
-    int add_op(int kind, int a, int b, const std::vector<double> &P, const std::vector<double> &Q,
-               const hx_term &t, double scale)
+    // Appends an operator to S.  scale multiplies the term amplitude.
+    int add_op(OpSet &S, int kind, int a, int b, const std::vector<double> &P, const std::vector<double> &Q,
+               const hx_term &t, double scale, int src = -1, int dst = -1)
     {
-        if (ops.nops >= kMaxOps) {
+        if (S.nops >= kMaxOps) {
             set_error("potential compiles to more than %d operators", kMaxOps);
             return HX_EUNSUPPORTED;
         }
-        Op &o = ops.op[ops.nops];
+        Op &o = S.op[S.nops];
         memset(&o, 0, sizeof(o));
         o.kind = kind;
         o.a = a;
@@ -301,6 +313,26 @@ struct Compiler {
         o.qmask = kind == 2 ? parity_mask(Q) : 1;
         o.tabP = kind >= 1 ? poly(P) : 0;
         o.tabQ = kind == 2 ? poly(Q) : 0;
+        o.src = src;
+        o.dst = dst;
+        {
+            const int N = set->h.N;
+            auto role = [N](int ax) { return ax < 0 ? ROLE_NONE : (ax == N - 1 ? ROLE_I2 : (ax == N - 2 ? ROLE_I1 : ROLE_OUT)); };
+            o.ra = role(kind >= 1 ? a : -1);
+            o.rb = role(kind == 2 ? b : -1);
+        }
+        {
+            auto pure = [](int mask, int deg) {   // only offsets of the parity of deg
+                int want = 0;
+                for (int s = -deg; s <= deg; s += 2) want |= 1 << (s + deg);
+                return mask == want;
+            };
+            if (kind == 0) o.cls = CLS_ID;
+            else if (kind == 1 && o.p <= 3 && pure(o.pmask, o.p)) o.cls = CLS_LINE + o.p;
+            else if (kind == 2 && o.p <= 3 && o.q <= 3 && pure(o.pmask, o.p) && pure(o.qmask, o.q))
+                o.cls = CLS_PLANE + 3 * (o.p - 1) + (o.q - 1);
+            else o.cls = CLS_GENERIC;
+        }
         o.mod = t.mod_kind;
         o.amp = t.amp * scale;
         o.omega = t.omega;
@@ -310,28 +342,69 @@ struct Compiler {
         o.pw_t0 = t.pw_t0;
         o.pw_t1 = t.pw_t1;
         if (t.mod_kind == HX_MOD_PWCONST) pw.insert(pw.end(), t.pw_values, t.pw_values + t.pw_n);
-        // footprint -> outer offset index
-        int base = ops.nops * kSpan * kSpan;
-        o.dbase = base;
+        o.dbase = S.ndidx;
         if (kind >= 1) {
+            int span = (2 * o.p + 1) * (2 * o.q + 1);
+            if (S.ndidx + span > kMaxDidx) {
+                set_error("potential footprint exceeds %d entries", kMaxDidx);
+                return HX_EUNSUPPORTED;
+            }
             for (int s = -o.p; s <= o.p; ++s)
                 for (int s2 = -o.q; s2 <= o.q; ++s2) {
-                    int di = delta_index(a, s, kind == 2 ? b : -1, s2);
+                    // only footprint points whose rows can be nonzero get a neighbour slab; the
+                    // plane kernels also look up (s, 0) for the slab of k + s e_a
+                    bool used = ((o.pmask >> (s + o.p)) & 1) && (s2 == 0 || ((o.qmask >> (s2 + o.q)) & 1));
+                    if (!used) {
+                        S.didx[o.dbase + (s + o.p) * (2 * o.q + 1) + (s2 + o.q)] = 0;
+                        continue;
+                    }
+                    int di = delta_index(S, a, s, kind == 2 ? b : -1, s2);
                     if (di < 0) {
                         set_error("potential needs more than %d distinct neighbour offsets", kMaxDelta);
                         return HX_EUNSUPPORTED;
                     }
-                    ops.didx[base + (s + o.p) * (2 * o.q + 1) + (s2 + o.q)] = (uint8_t)di;
+                    S.didx[o.dbase + (s + o.p) * (2 * o.q + 1) + (s2 + o.q)] = (uint8_t)di;
                 }
+            S.ndidx += span;
         }
-        ops.nops++;
+        S.nops++;
         return HX_OK;
+    }
+
+    // Channel holding Pn(X_axis) c for a normalised polynomial Pn (created in stage 1 on first use).
+    int channel(int axis, const std::vector<double> &Pn)
+    {
+        for (size_t i = 0; i < chans.size(); ++i) {
+            if (chans[i].first != axis || chans[i].second.size() != Pn.size()) continue;
+            bool same = true;
+            for (size_t r = 0; r < Pn.size(); ++r) same &= fabs(chans[i].second[r] - Pn[r]) <= 1e-14;
+            if (same) return (int)i;
+        }
+        hx_term unit;
+        memset(&unit, 0, sizeof(unit));
+        unit.mod_kind = HX_MOD_CONST;
+        unit.amp = 1.0;
+        int ch = (int)chans.size();
+        if (add_op(ops1, 1, axis, -1, Pn, Pn, unit, 1.0, -1, ch)) return -1;
+        chans.push_back({axis, Pn});
+        return ch;
     }
 };
 
-// C = sum_k u_k v_k^T by Gaussian elimination with complete pivoting; pieces below
-// 1e-15 * max|C| are dropped (an exactly low-rank C, e.g. a product of two univariate
-// interpolants, gives exactly rank-many pieces up to rounding).
+// P = scale * Pn with the largest |coefficient| of Pn equal to 1.
+static double normalise(const std::vector<double> &P, std::vector<double> &Pn)
+{
+    double big = 0.0;
+    for (double x : P)
+        if (fabs(x) > fabs(big)) big = x;
+    Pn = P;
+    for (double &x : Pn) x /= big;
+    return big;
+}
+
+// C = sum_k u_k v_k^T by Gaussian elimination with complete pivoting; once the largest remaining
+// entry is below 1e-13 * max|C| the rest is dropped (an exactly low-rank C, e.g. the interpolant of
+// a product or a sum of products of univariate functions, leaves only round-off there).
 static void rank_one_pieces(std::vector<double> C, int n0, int n1, std::vector<std::vector<double>> &U,
                             std::vector<std::vector<double>> &V)
 {
@@ -344,7 +417,7 @@ static void rank_one_pieces(std::vector<double> C, int n0, int n1, std::vector<s
         for (int i = 0; i < n0; ++i)
             for (int j = 0; j < n1; ++j)
                 if (fabs(C[i * n1 + j]) > best) { best = fabs(C[i * n1 + j]); bi = i; bj = j; }
-        if (best <= 1e-15 * cmax) break;
+        if (best <= 1e-13 * cmax) break;
         std::vector<double> u(n0), v(n1);
         double piv = C[bi * n1 + bj];
         for (int i = 0; i < n0; ++i) u[i] = C[i * n1 + bj];
@@ -368,7 +441,9 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
     cp.set = set;
     cp.L = pot->L;
     memset(&cp.ops, 0, sizeof(cp.ops));
+    memset(&cp.ops1, 0, sizeof(cp.ops1));
     cp.ops.ndelta = 1;   // index 0: zero outer offset
+    cp.ops1.ndelta = 1;
     int order = pr->cfg.order;
     cp.ops.wAB = order == HX_ORDER_SYM ? 0.5 : (order == HX_ORDER_EQ ? 1.0 : 0.0);
     cp.ops.wBA = order == HX_ORDER_SYM ? 0.5 : (order == HX_ORDER_ALG ? 1.0 : 0.0);
@@ -394,8 +469,8 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
             std::vector<double> a(t.coef, t.coef + t.deg[0] + 1);
             trim(a);
             if (a.size() == 1) {
-                if (a[0] != 0.0 && (rc = cp.add_op(0, -1, -1, a, a, t, a[0]))) return rc;
-            } else if ((rc = cp.add_op(1, t.axes[0], -1, a, a, t, 1.0))) return rc;
+                if (a[0] != 0.0 && (rc = cp.add_op(cp.ops, 0, -1, -1, a, a, t, a[0]))) return rc;
+            } else if ((rc = cp.add_op(cp.ops, 1, t.axes[0], -1, a, a, t, 1.0))) return rc;
         } else {
             int n0 = t.deg[0] + 1, n1 = t.deg[1] + 1;
             std::vector<double> C(t.coef, t.coef + n0 * n1);
@@ -406,14 +481,28 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
                 trim(P);
                 trim(Qp);
                 if (P.size() == 1 && Qp.size() == 1) {
-                    if ((rc = cp.add_op(0, -1, -1, P, P, t, P[0] * Qp[0]))) return rc;
+                    if ((rc = cp.add_op(cp.ops, 0, -1, -1, P, P, t, P[0] * Qp[0]))) return rc;
                 } else if (P.size() == 1) {
                     for (double &x : Qp) x *= P[0];
-                    if ((rc = cp.add_op(1, t.axes[1], -1, Qp, Qp, t, 1.0))) return rc;
+                    if ((rc = cp.add_op(cp.ops, 1, t.axes[1], -1, Qp, Qp, t, 1.0))) return rc;
                 } else if (Qp.size() == 1) {
                     for (double &x : P) x *= Qp[0];
-                    if ((rc = cp.add_op(1, t.axes[0], -1, P, P, t, 1.0))) return rc;
-                } else if ((rc = cp.add_op(2, t.axes[0], t.axes[1], P, Qp, t, 1.0))) return rc;
+                    if ((rc = cp.add_op(cp.ops, 1, t.axes[0], -1, P, P, t, 1.0))) return rc;
+                } else {
+                    int foot = __builtin_popcount(parity_mask(P)) * __builtin_popcount(parity_mask(Qp));
+                    if (foot <= kDirectFootprint) {
+                        if ((rc = cp.add_op(cp.ops, 2, t.axes[0], t.axes[1], P, Qp, t, 1.0))) return rc;
+                    } else {   // two stages: P(X_a) (Q(X_b) c) and Q(X_b) (P(X_a) c) through channels
+                        std::vector<double> Pn, Qn;
+                        double sp = normalise(P, Pn), sq = normalise(Qp, Qn);
+                        int chQ = cp.channel(t.axes[1], Qn), chP = cp.channel(t.axes[0], Pn);
+                        if (chQ < 0 || chP < 0) return HX_EUNSUPPORTED;
+                        if (cp.ops.wAB != 0.0 &&
+                            (rc = cp.add_op(cp.ops, 1, t.axes[0], -1, P, P, t, sq * cp.ops.wAB, chQ))) return rc;
+                        if (cp.ops.wBA != 0.0 &&
+                            (rc = cp.add_op(cp.ops, 1, t.axes[1], -1, Qp, Qp, t, sp * cp.ops.wBA, chP))) return rc;
+                    }
+                }
             }
         }
     }
@@ -444,9 +533,20 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
                 "upload pw");
     pr->tab_bytes = tab_bytes;
     pr->ops = cp.ops;
+    pr->ops1 = cp.ops1;
+    // channel vectors of the first stage
+    if (pr->chan) cudaFree(pr->chan);
+    pr->chan = nullptr;
+    pr->nch = (int)cp.chans.size();
+    {
+        size_t es2 = pr->cfg.dtype == HX_C64 ? 8 : 16;
+        size_t ld = (((size_t)set->h.size * es2 + 255) / 256) * 256 / es2;
+        pr->chan_ld = ld;
+        if (pr->nch) HX_CUDA(cudaMalloc(&pr->chan, ld * es2 * pr->nch), "cudaMalloc(channels)");
+    }
     // work items: <= kItemElems elements and a slab count whose neighbour table fits shared memory
-    int nd = cp.ops.ndelta;
-    int spi = std::max(1, std::min(64, (32 * 1024) / (16 * nd)));
+    int nd = std::max(cp.ops.ndelta, cp.ops1.ndelta);
+    int spi = std::max(1, std::min(64, (32 * 1024) / (int)(sizeof(int2) * nd)));
     pr->slabs_per_item = spi;
     const IndexSetHost &h = set->h;
     std::vector<int4> items;
@@ -507,8 +607,9 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     size_t b_k = std::max<size_t>(h.slab_k.size(), 1) * sizeof(uint16_t);
     size_t b_qoff = (size_t)(h.B + 2) * sizeof(int);
     size_t b_Q = std::max<size_t>(h.Q.size(), 1) * sizeof(int);
+    size_t b_nt = (size_t)(h.B + 1) * sizeof(int);
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t total = al(b_start) + al(b_k) + al(b_qoff) + al(b_Q);
+    size_t total = al(b_start) + al(b_k) + al(b_qoff) + al(b_Q) + al(b_nt);
     cudaGetDevice(&s->device);
     cudaError_t e = cudaMalloc(&s->dmem, total);
     if (e != cudaSuccess) { delete s; return cuda_fail(e, "cudaMalloc(index tables)"); }
@@ -517,6 +618,12 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     uint16_t *d_k = (uint16_t *)(base + al(b_start));
     int *d_qoff = (int *)(base + al(b_start) + al(b_k));
     int *d_Q = (int *)(base + al(b_start) + al(b_k) + al(b_qoff));
+    int *d_nt = (int *)(base + al(b_start) + al(b_k) + al(b_qoff) + al(b_Q));
+    {
+        std::vector<int> nt(h.B + 1, 0);
+        for (int x = 1; x <= h.B; ++x) nt[x] = h.B / x;
+        cudaMemcpy(d_nt, nt.data(), b_nt, cudaMemcpyHostToDevice);
+    }
     cudaMemcpy(d_start, h.slab_start.data(), b_start, cudaMemcpyHostToDevice);
     if (!h.slab_k.empty()) cudaMemcpy(d_k, h.slab_k.data(), h.slab_k.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
     cudaMemcpy(d_qoff, h.qoff.data(), b_qoff, cudaMemcpyHostToDevice);
@@ -535,6 +642,7 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     s->d.slab_k = d_k;
     s->d.qoff = d_qoff;
     s->d.Q = d_Q;
+    s->d.nt = d_nt;
     *out = s;
     return HX_OK;
 }
@@ -609,6 +717,7 @@ void hx_problem_destroy(hx_problem *p)
     cudaFree(p->tab);
     cudaFree(p->pw_values);
     cudaFree(p->items);
+    cudaFree(p->chan);
     cudaFree(p->dscal);
     for (void *x : p->extra) cudaFree(x);
     delete p;

@@ -12,8 +12,9 @@
 namespace hx {
 
 constexpr int kMaxN = 16;
-constexpr int kMaxOps = 32;
-constexpr int kMaxDelta = 128;                 // distinct outer-axis offsets of one potential
+constexpr int kMaxOps = 48;
+constexpr int kMaxDelta = 160;                 // distinct outer-axis offsets of one operator set
+constexpr int kMaxDidx = 4096;                 // footprint -> offset map entries of one operator set
 constexpr int kMaxDeg = HX_MAX_DEG;
 constexpr int kSpan = 2 * kMaxDeg + 1;         // offsets -deg..deg
 constexpr int kMaxKrylov = 32;
@@ -44,6 +45,7 @@ struct DevSet {
     const uint16_t *slab_k;           // nslab x (N - 2) outer prefixes
     const int *qoff;                  // B + 1
     const int *Q;                     // (N - 1) x qtotal
+    const int *nt;                    // nt[x] = floor(B / x), x = 1..B (nt[0] unused)
 };
 
 struct IndexSetHost {
@@ -59,20 +61,30 @@ struct IndexSetHost {
 };
 
 // ---------------------------------------------------------------------------------------
-// Compiled potential.  Each op contributes w(t) * (op matrix) to A:
+// Compiled potential.  Each op contributes w(t) * (op matrix) * (input) to A c:
 //   kind 0: identity;  kind 1: P(X_a) (line);  kind 2: Sym/ordered P(X_a) Q(X_b) (plane, a < b).
+// The input is c (src = -1) or a channel vector written by a first stage.  A plane op whose
+// footprint is large is evaluated in two stages: stage 1 writes the channels Q(X_b) c and
+// P(X_a) c (line ops with dst >= 0), stage 2 applies P(X_a) and Q(X_b) to them as line ops.
 // Row tables: for a univariate polynomial P of degree p, entry
 //   tab[base + ((i * (p + 1) + d) * (2p + 1)) + (s + p)] = [P(J_n / L)]_{i, i+s},  n = i + 1 + d,
 // where J_n is the n x n truncated Jacobi matrix of the Hermite recurrence (Eq. (Recurrence1D)):
 // row i of a fibre whose top is d steps above i (d = p stands for "p or more").
 // ---------------------------------------------------------------------------------------
+// op classes with compile-time stencils (pure parity: P has only terms of the parity of its degree)
+enum { CLS_ID = 0, CLS_LINE = 1, CLS_PLANE = 10, CLS_GENERIC = 30 };
+enum { ROLE_OUT = 0, ROLE_I1 = 1, ROLE_I2 = 2, ROLE_NONE = 3 };
+
 struct Op {
     int kind;
+    int cls;                  // CLS_ID, CLS_LINE + p (p <= 3, pure), CLS_PLANE + 3 (p-1) + (q-1) (pure), CLS_GENERIC
+    int ra, rb;               // axis roles: ROLE_OUT (< N-2), ROLE_I1 (N-2), ROLE_I2 (N-1), ROLE_NONE
     int a, b;                 // axes (b = -1 for a line op)
     int p, q;                 // degrees on a and b
     int pmask, qmask;         // bit (s + p) set when the rows can be nonzero at offset s
     int tabP, tabQ;           // row table bases
     int dbase;                // base into didx (footprint position -> outer offset index)
+    int src, dst;             // input channel (-1 = c), output channel (stage 1 only)
     int mod;                  // hx_mod_kind
     double amp, omega, phase;
     int pw_off, pw_n;         // into the pw value array
@@ -83,9 +95,10 @@ struct OpSet {
     int nops;
     int ndelta;
     double wAB, wBA;          // factor-order weights for plane ops
+    int ndidx;
     Op op[kMaxOps];
     int8_t delta[kMaxDelta][4];       // outer offset: axis0, step0, axis1, step1 (axis -1 = none)
-    uint8_t didx[kMaxOps * kSpan * kSpan];
+    uint8_t didx[kMaxDidx];
 };
 
 struct ApplyArgsBase {
@@ -128,7 +141,11 @@ struct Problem {
     double t_host;
     // compiled potential
     bool have_pot;
-    OpSet ops;
+    OpSet ops;                // main stage (accumulates y)
+    OpSet ops1;               // first stage (writes channels), nops = 0 if unused
+    int nch;                  // channel vectors
+    void *chan;
+    size_t chan_ld;           // elements between channels
     std::vector<int4> items_h;
     int4 *items;
     int nitems;
@@ -153,6 +170,7 @@ int launch_export(const IndexSetObj *s, int32_t *k_dev, cudaStream_t st);
 int launch_norm(Problem *p, const void *c, int is_c128, double *partials, unsigned *counter, double *result,
                 cudaStream_t st);
 int apply_grid(const Problem *p);
+int apply_launches(const Problem *p);   // kernels per product (1, or 2 with a channel stage)
 
 // Krylov stepping (hx_krylov.cu)
 int krylov_step(Problem *p, void *c, double dt, int nsteps);

@@ -65,9 +65,12 @@ __device__ double block_reduce(double v, double *red)
     return s;   // thread 0
 }
 
-// Writes nval per-block sums to partials[blockIdx.x * nval + j]; returns true in thread 0 of the
-// last block to arrive, after which partials hold every block's values.
-__device__ bool publish_partials(const double *vals, int nval, double *partials, unsigned *counter, double *red)
+// Writes nval per-block sums to partials[blockIdx.x * nval + j].  In the last block to arrive, all
+// threads then add the partials up (each thread a fixed strided subset, then a fixed tree), so the
+// totals land in tot[0..nval) (shared) in an order that does not depend on block timing.  Returns
+// true in every thread of that last block.
+__device__ bool reduce_partials(const double *vals, int nval, double *partials, unsigned *counter, double *red,
+                                double *tot)
 {
     __shared__ bool last;
     for (int j = 0; j < nval; ++j) {
@@ -79,16 +82,35 @@ __device__ bool publish_partials(const double *vals, int nval, double *partials,
         last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) __threadfence();
-    return last && threadIdx.x == 0;
+    if (!last) return false;
+    __threadfence();
+    for (int j = 0; j < nval; ++j) {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += ((volatile const double *)partials)[b * nval + j];
+        t = block_reduce(t, red);
+        if (threadIdx.x == 0) tot[j] = t;
+    }
+    __syncthreads();
+    return true;
 }
 
-__device__ double sum_partials(const double *partials, int nval, int j)
-{
-    double t = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) t += ((volatile const double *)partials)[b * nval + j];
-    return t;
-}
+// Error-free transformations (Knuth's TwoSum, and TwoProd with a fused multiply-add) and the
+// compensated dot product built from them (Ogita, Rump and Oishi, "Accurate sum and dot product",
+// 2005, Algorithm Dot2): the float result is as accurate as if accumulated in twice the precision.
+struct F2 {
+    float s = 0.f, c = 0.f;
+    __device__ void add_prod(float a, float b)
+    {
+        float p = a * b;
+        float e = fmaf(a, b, -p);
+        float t = s + p;
+        float bb = t - s;
+        float q = (s - (t - bb)) + (p - bb);
+        s = t;
+        c += q + e;
+    }
+    __device__ double value() const { return (double)s + (double)c; }
+};
 
 template <typename V>
 __device__ __forceinline__ V to_vec(double2 x);
@@ -106,8 +128,9 @@ __global__ void init_kernel(const double2 *c, V *v0, int n, double *partials, Sc
         v0[i] = to_vec<V>(x);
         acc += x.x * x.x + x.y * x.y;
     }
-    if (publish_partials(&acc, 1, partials, &sc->counter, red)) {
-        double b0 = sqrt(sum_partials(partials, 1, 0));
+    __shared__ double tot[1];
+    if (reduce_partials(&acc, 1, partials, &sc->counter, red, tot) && threadIdx.x == 0) {
+        double b0 = sqrt(tot[0]);
         sc->beta0 = b0;
         sc->s[0] = b0 > 0.0 ? 1.0 / b0 : 0.0;
         sc->m_used = b0 > 0.0 ? m : 0;
@@ -117,30 +140,61 @@ __global__ void init_kernel(const double2 *c, V *v0, int n, double *partials, Sc
     }
 }
 
-// h_i = s_i <v_i, w> for i <= k (complex, FP64).
+// Per-thread accumulator of Re/Im conj(v) w: compensated FP32 (Dot2) for complex64 vectors, FP64 for
+// complex128 vectors.
+template <typename V> struct CAcc;
+template <> struct CAcc<float2> {
+    F2 re, im;
+    __device__ void add(float2 v, float2 w)
+    {
+        re.add_prod(v.x, w.x);
+        re.add_prod(v.y, w.y);
+        im.add_prod(v.x, w.y);
+        im.add_prod(-v.y, w.x);
+    }
+    __device__ double r() const { return re.value(); }
+    __device__ double i() const { return im.value(); }
+};
+template <> struct CAcc<double2> {
+    double re = 0.0, im = 0.0;
+    __device__ void add(double2 v, double2 w)
+    {
+        re = fma(v.x, w.x, fma(v.y, w.y, re));
+        im = fma(v.x, w.y, fma(-v.y, w.x, im));
+    }
+    __device__ double r() const { return re; }
+    __device__ double i() const { return im; }
+};
+
+template <typename V> struct Real;
+template <> struct Real<float2> { using T = float; };
+template <> struct Real<double2> { using T = double; };
+
+// h_i = s_i <v_i, w> for i <= k.
 template <typename V, int NV>
 __global__ void __launch_bounds__(256) dot_kernel(const V *w, const V *Vb, size_t ld, int n, int k, double *partials, Scal *sc)
 {
     __shared__ double red[32];
+    __shared__ double tot[2 * NV];
     if (k >= sc->m_used) return;
-    double acc[2 * NV];
-#pragma unroll
-    for (int j = 0; j < 2 * NV; ++j) acc[j] = 0.0;
+    CAcc<V> acc[NV];
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         V x = w[e];
 #pragma unroll(NV <= 8 ? NV : 1)
         for (int i = 0; i < NV; ++i)
-            if (i <= k) {
-                V v = Vb[i * ld + e];
-                acc[2 * i] += (double)v.x * x.x + (double)v.y * x.y;       // Re conj(v) w
-                acc[2 * i + 1] += (double)v.x * x.y - (double)v.y * x.x;   // Im conj(v) w
-            }
+            if (i <= k) acc[i].add(Vb[i * ld + e], x);
+    }
+    double vals[2 * NV];
+#pragma unroll(NV <= 8 ? NV : 1)
+    for (int i = 0; i < NV; ++i) {
+        vals[2 * i] = acc[i].r();
+        vals[2 * i + 1] = acc[i].i();
     }
     const int nval = 2 * (k + 1);
-    if (publish_partials(acc, nval, partials, &sc->counter, red)) {
+    if (reduce_partials(vals, nval, partials, &sc->counter, red, tot) && threadIdx.x == 0) {
         for (int i = 0; i <= k; ++i) {
-            sc->h[2 * i] = sc->s[i] * sum_partials(partials, nval, 2 * i);
-            sc->h[2 * i + 1] = sc->s[i] * sum_partials(partials, nval, 2 * i + 1);
+            sc->h[2 * i] = sc->s[i] * tot[2 * i];
+            sc->h[2 * i + 1] = sc->s[i] * tot[2 * i + 1];
         }
         sc->counter = 0;
     }
@@ -148,61 +202,66 @@ __global__ void __launch_bounds__(256) dot_kernel(const V *w, const V *Vb, size_
 
 // pass 0: w -= sum_i h_i s_i v_i, then h'_i = s_i <v_i, w>, alpha_k = Re(h_k + h'_k).
 // pass 1: w -= sum_i h'_i s_i v_i, then beta_k = ||w||, s_{k+1} = 1 / beta_k, breakdown test.
+// The update runs in the vector precision; the inner products and the norm as in dot_kernel.
 template <typename V, int NV>
-__global__ void update_kernel(V *w, const V *Vb, size_t ld, int n, int k, int pass, double *partials, Scal *sc)
+__global__ void __launch_bounds__(256) update_kernel(V *w, const V *Vb, size_t ld, int n, int k, int pass, double *partials, Scal *sc)
 {
+    using R = typename Real<V>::T;
     __shared__ double red[32];
+    __shared__ double tot[2 * NV];
     if (k >= sc->m_used) return;
     const double *coef = pass == 0 ? sc->h : sc->h2;
-    double cr[NV], ci[NV];
-#pragma unroll
+    R cr[NV], ci[NV];
+#pragma unroll(NV <= 8 ? NV : 1)
     for (int i = 0; i < NV; ++i) {
-        cr[i] = i <= k ? coef[2 * i] * sc->s[i] : 0.0;
-        ci[i] = i <= k ? coef[2 * i + 1] * sc->s[i] : 0.0;
+        cr[i] = i <= k ? (R)(coef[2 * i] * sc->s[i]) : (R)0;
+        ci[i] = i <= k ? (R)(coef[2 * i + 1] * sc->s[i]) : (R)0;
     }
-    double acc[2 * NV + 1];
-#pragma unroll
-    for (int j = 0; j < 2 * NV + 1; ++j) acc[j] = 0.0;
+    CAcc<V> acc[NV];
+    CAcc<V> nrm;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         V x = w[e];
-        double xr = x.x, xi = x.y;
 #pragma unroll(NV <= 8 ? NV : 1)
         for (int i = 0; i < NV; ++i)
             if (i <= k) {
                 V v = Vb[i * ld + e];
-                xr -= cr[i] * v.x - ci[i] * v.y;
-                xi -= cr[i] * v.y + ci[i] * v.x;
+                x.x -= cr[i] * v.x - ci[i] * v.y;
+                x.y -= cr[i] * v.y + ci[i] * v.x;
             }
-        V y;
-        y.x = xr;
-        y.y = xi;
-        w[e] = y;
-        double yr = y.x, yi = y.y;   // what was stored (rounded to the Krylov dtype)
+        w[e] = x;
         if (pass == 0) {
 #pragma unroll(NV <= 8 ? NV : 1)
             for (int i = 0; i < NV; ++i)
-                if (i <= k) {
-                    V v = Vb[i * ld + e];
-                    acc[2 * i] += (double)v.x * yr + (double)v.y * yi;
-                    acc[2 * i + 1] += (double)v.x * yi - (double)v.y * yr;
-                }
+                if (i <= k) acc[i].add(Vb[i * ld + e], x);
         } else {
-            acc[0] += yr * yr + yi * yi;
+            nrm.add(x, x);
         }
     }
-    const int nval = pass == 0 ? 2 * (k + 1) : 1;
-    if (publish_partials(acc, nval, partials, &sc->counter, red)) {
+    double vals[2 * NV];
+    int nval;
+    if (pass == 0) {
+#pragma unroll(NV <= 8 ? NV : 1)
+        for (int i = 0; i < NV; ++i) {
+            vals[2 * i] = acc[i].r();
+            vals[2 * i + 1] = acc[i].i();
+        }
+        nval = 2 * (k + 1);
+    } else {
+        vals[0] = nrm.r();
+        nval = 1;
+    }
+    if (reduce_partials(vals, nval, partials, &sc->counter, red, tot) && threadIdx.x == 0) {
         if (pass == 0) {
             for (int i = 0; i <= k; ++i) {
-                sc->h2[2 * i] = sc->s[i] * sum_partials(partials, nval, 2 * i);
-                sc->h2[2 * i + 1] = sc->s[i] * sum_partials(partials, nval, 2 * i + 1);
+                sc->h2[2 * i] = sc->s[i] * tot[2 * i];
+                sc->h2[2 * i + 1] = sc->s[i] * tot[2 * i + 1];
             }
             double a = sc->h[2 * k] + sc->h2[2 * k];
             sc->alpha[k] = a;
             double sc_k = fabs(a) + (k > 0 ? sc->beta[k - 1] : 0.0);
             if (sc_k > sc->scale) sc->scale = sc_k;
         } else {
-            double b = sqrt(sum_partials(partials, 1, 0));
+            double b = sqrt(tot[0]);
             if (!isfinite(b)) sc->flags |= 2;
             if (b <= 1e-13 * sc->scale) {       // invariant subspace: stop with k + 1 vectors
                 sc->m_used = k + 1;
@@ -217,61 +276,72 @@ __global__ void update_kernel(V *w, const V *Vb, size_t ld, int n, int k, int pa
 }
 
 // T_m = Q diag(lambda) Q^T by cyclic Jacobi rotations (Jacobi's method, Golub & Van Loan Sec. 8.5),
-// y = beta_0 Q exp(-i h lambda) Q^T e_1; stored as y_i * s_i for the combination pass.  Also
-// advances the problem time by h.
-__global__ void eig_kernel(Scal *sc, double h)
+// y = beta_0 Q exp(-i h lambda) Q^T e_1; stored as y_i * s_i for the combination pass.  One warp:
+// the rotation angle is computed by every lane, the rows and columns it touches are updated one
+// lane per index.  Also advances the problem time by h.
+__global__ void __launch_bounds__(32) eig_kernel(Scal *sc, double h)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double A[kMaxKrylov * kMaxKrylov], Qm[kMaxKrylov * kMaxKrylov];
+    __shared__ double cph[kMaxKrylov], sph[kMaxKrylov];
+    const int lane = threadIdx.x;
     const int m = sc->m_used;
-    double A[kMaxKrylov * kMaxKrylov], Qm[kMaxKrylov * kMaxKrylov];
     for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j) {
+        if (lane < m) {
+            const int j = lane;
             A[i * m + j] = i == j ? sc->alpha[i] : ((j == i + 1 || i == j + 1) ? sc->beta[i < j ? i : j] : 0.0);
             Qm[i * m + j] = i == j ? 1.0 : 0.0;
         }
-    double norm = 0.0;
-    for (int i = 0; i < m * m; ++i) norm += A[i] * A[i];
+    __syncwarp();
+    double nr = 0.0;
+    for (int i = 0; i < m; ++i) nr += A[i * m + i] * A[i * m + i] + (i + 1 < m ? 2.0 * A[i * m + i + 1] * A[i * m + i + 1] : 0.0);
     for (int sweep = 0; sweep < 60; ++sweep) {
         double off = 0.0;
-        for (int i = 0; i < m; ++i)
-            for (int j = i + 1; j < m; ++j) off += A[i * m + j] * A[i * m + j];
-        if (off <= 1e-34 * norm) break;
+        if (lane < m)
+            for (int j = lane + 1; j < m; ++j) off += A[lane * m + j] * A[lane * m + j];
+        for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
+        if (off <= 1e-34 * nr) break;
         for (int p = 0; p < m; ++p)
             for (int q = p + 1; q < m; ++q) {
-                double apq = A[p * m + q];
+                const double apq = A[p * m + q];
                 if (apq == 0.0) continue;
-                double theta = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
-                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int r = 0; r < m; ++r) {      // A <- A J (columns p, q)
-                    double arp = A[r * m + p], arq = A[r * m + q];
-                    A[r * m + p] = c * arp - s * arq;
-                    A[r * m + q] = s * arp + c * arq;
+                const double theta = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                __syncwarp();
+                if (lane < m) {                      // A <- A J (columns p, q)
+                    const double arp = A[lane * m + p], arq = A[lane * m + q];
+                    A[lane * m + p] = c * arp - s * arq;
+                    A[lane * m + q] = s * arp + c * arq;
                 }
-                for (int r = 0; r < m; ++r) {      // A <- J^T A (rows p, q)
-                    double apr = A[p * m + r], aqr = A[q * m + r];
-                    A[p * m + r] = c * apr - s * aqr;
-                    A[q * m + r] = s * apr + c * aqr;
+                __syncwarp();
+                if (lane < m) {                      // A <- J^T A (rows p, q)
+                    const double apr = A[p * m + lane], aqr = A[q * m + lane];
+                    A[p * m + lane] = c * apr - s * aqr;
+                    A[q * m + lane] = s * apr + c * aqr;
+                    const double qrp = Qm[lane * m + p], qrq = Qm[lane * m + q];   // Q <- Q J
+                    Qm[lane * m + p] = c * qrp - s * qrq;
+                    Qm[lane * m + q] = s * qrp + c * qrq;
                 }
-                for (int r = 0; r < m; ++r) {      // Q <- Q J
-                    double qrp = Qm[r * m + p], qrq = Qm[r * m + q];
-                    Qm[r * m + p] = c * qrp - s * qrq;
-                    Qm[r * m + q] = s * qrp + c * qrq;
-                }
+                __syncwarp();
             }
     }
-    for (int i = 0; i < m; ++i) {
+    if (lane < m) {
+        const double ph = -h * A[lane * m + lane];
+        cph[lane] = cos(ph);
+        sph[lane] = sin(ph);
+    }
+    __syncwarp();
+    if (lane < m) {
         double yr = 0.0, yi = 0.0;
         for (int j = 0; j < m; ++j) {
-            double ph = -h * A[j * m + j];
-            double w = Qm[i * m + j] * Qm[0 * m + j];
-            yr += w * cos(ph);
-            yi += w * sin(ph);
+            const double w = Qm[lane * m + j] * Qm[0 * m + j];
+            yr += w * cph[j];
+            yi += w * sph[j];
         }
-        sc->y[2 * i] = sc->beta0 * yr * sc->s[i];
-        sc->y[2 * i + 1] = sc->beta0 * yi * sc->s[i];
+        sc->y[2 * lane] = sc->beta0 * yr * sc->s[lane];
+        sc->y[2 * lane + 1] = sc->beta0 * yi * sc->s[lane];
     }
-    sc->t += h;
+    if (lane == 0) sc->t += h;
 }
 
 // c = sum_i y_i v_i (complex128 accumulation), and ||c||^2 for hx_step_info.
@@ -299,8 +369,9 @@ __global__ void combine_kernel(double2 *c, const V *Vb, size_t ld, int n, double
         c[e] = make_double2(xr, xi);
         acc += xr * xr + xi * xi;
     }
-    if (publish_partials(&acc, 1, partials, &sc->counter, red)) {
-        double nr = sqrt(sum_partials(partials, 1, 0));
+    __shared__ double tot[1];
+    if (reduce_partials(&acc, 1, partials, &sc->counter, red, tot) && threadIdx.x == 0) {
+        double nr = sqrt(tot[0]);
         sc->norm_out = nr;
         if (!isfinite(nr)) sc->flags |= 2;
         sc->counter = 0;

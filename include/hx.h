@@ -178,6 +178,22 @@ HX_API int hx_step_info(hx_problem *p, int *m_used, double *alpha, double *beta,
 /* ||c||_2 of a device vector of the problem dtype, accumulated in FP64; synchronous. */
 HX_API int hx_norm(hx_problem *p, const void *c, double *out);
 
+/* ---- allocation-free norm ------------------------------------------------------- */
+
+/* Same result as hx_norm (||c||_2 in FP64 of a device vector of the problem dtype, synchronous),
+ * but without allocating any device memory.  The paper has no counterpart: this entry point is for
+ * callers that cannot call cudaMalloc at this point, for example an application whose device
+ * memory is held entirely by its own pool (a caching allocator keeps the free memory, so a fresh
+ * allocation would fail) or a latency-critical loop that must not enter an allocator.
+ * Scratch: a fixed 1026-double device array inside libhx.so (1024 block partial sums, the result
+ * and the reduction counter), held on every GPU that loads the library until the process exits.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress); make
+ * the first call before any stream capture.  Every call shares the array: calls that overlap on
+ * the GPU (from several threads or streams) race, so serialise them.  Errors: as hx_norm, plus
+ * HX_EUNSUPPORTED when the reduction would need more than 1024 block partials (a GPU with more
+ * than 256 SMs) and HX_EINVAL when the current device is not the problem's device. */
+HX_API int hx_norm_noalloc(hx_problem *p, const void *c, double *out);
+
 /* ---- Chebyshev helpers for building hx_term coefficients (Sec. 1.3) ----------- */
 
 /* First-kind Chebyshev nodes u_i = cos(pi (2i + 1) / (2R + 2)), i = 0..R, into u_out[R+1]. */

@@ -71,6 +71,7 @@ def _load():
         "hx_step_host": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int]),
         "hx_step_info": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), dp, dp, dp]),
         "hx_norm": (ctypes.c_int, [P, P, dp]),
+        "hx_norm_noalloc": (ctypes.c_int, [P, P, dp]),
         "hx_cheb_nodes": (ctypes.c_int, [ctypes.c_int, dp]),
         "hx_cheb_coeffs": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp, dp]),
         "hx_cheb_monomial": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, dp]),
@@ -222,6 +223,13 @@ def hx_step_info(p, m: int = 32) -> dict:
 def hx_norm(p, c) -> float:
     out = ctypes.c_double()
     _check(lib.hx_norm(p, ctypes.c_void_p(_tptr(c)), ctypes.byref(out)))
+    return out.value
+
+
+def hx_norm_noalloc(p, c) -> float:
+    """hx_norm without any device allocation (fixed scratch inside the library); see include/hx.h."""
+    out = ctypes.c_double()
+    _check(lib.hx_norm_noalloc(p, ctypes.c_void_p(_tptr(c)), ctypes.byref(out)))
     return out.value
 
 

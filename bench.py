@@ -101,6 +101,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(vals, world: int, device):
+    """Element-wise maximum over the ranks of the job (the slowest replica sets the time)."""
+    if world <= 1:
+        return [float(v) for v in vals]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_gcoeff_s(m: int, n: int, world: int, seconds: float) -> float:
+    """m matvec-equivalents of |K| = n coefficients per step on every one of `world` replicas."""
+    return m * n * world / seconds / 1e9
+
+
 def run_reference(args, rank):
     """The oracle (plain single-threaded C, FP64) on the same workload: each step evaluates the
     Galerkin matvec on a fixed sample of 20,000 rows (one row at a time, from local windows)."""
@@ -171,6 +187,7 @@ def main():
     P = hx.Problem(spec["N"], spec["B"], dtype=dtype, m=m, stream=stream.cuda_stream)
     P.set_potential(spec, 0.0)
     n = P.size
+    launches_per_step = hx.hx_step_launches(P.p)[1]
     kidx = hx.hx_indexset_export(P.set, spec["N"])
     c0 = inputs.initial_vector(spec, kidx)
     c = torch.from_numpy(c0).to("cuda", torch.complex128)
@@ -208,11 +225,8 @@ def main():
     barrier()
     ms_apply = ea.elapsed_time(eb) / napply
     clk = clocks.stop()
-    if world > 1:
-        tt = torch.tensor([ms_step, ms_apply], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step, ms_apply = tt.tolist()
-    value = m * n * world / (ms_step * 1e-3) / 1e9
+    ms_step, ms_apply = max_over_ranks([ms_step, ms_apply], world, "cuda")
+    value = whole_job_gcoeff_s(m, n, world, ms_step * 1e-3)
     # end to end through the host entry point: pinned host state, H2D + step + D2H every step
     ch = torch.from_numpy(c0.copy()).pin_memory()
     ch_np = ch.numpy()
@@ -223,11 +237,8 @@ def main():
     for _ in range(k_e2e):
         hx.hx_step_host(P.p, ch_np, dt, 1)
     t_e2e = (time.perf_counter() - t0) / k_e2e
-    if world > 1:
-        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = tt.item()
-    e2e = {"value": m * n * world / t_e2e / 1e9, "unit": "Gcoeff/s", "h2d_bytes_per_step": 16 * n,
+    t_e2e = max_over_ranks([t_e2e], world, "cuda")[0]
+    e2e = {"value": whole_job_gcoeff_s(m, n, world, t_e2e), "unit": "Gcoeff/s", "h2d_bytes_per_step": 16 * n,
            "d2h_bytes_per_step": 16 * n}
     # the FP64 path on the same input, and the mixed path's deviation from it after 1 and 5 steps
     # (at this workload the m-step Lanczos step map amplifies any perturbation by 10-50x per step,
@@ -273,10 +284,10 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64" if dtype == hx.HX_C64 else "f64",
                 "data": "synthetic",
                 "config": {"workload": spec["name"], "N": spec["N"], "B": spec["B"], "size": n, "m": m, "dt": dt,
-                           "potential": "Henon-Heiles chain lambda=0.111 + 0.05 cos(t) x1",
+                           "potential": spec["desc"],
                            "l2": "inputs larger than L2 (Krylov workspace (m+1) x |K| plus state)",
                            "parallelism": f"replicas x{world}"},
-                "gpu_launches": (4 * m + 2) * args.steps,
+                "gpu_launches": launches_per_step * args.steps,
                 "matvec_gcoeff_s": n / (ms_apply * 1e-3) / 1e9,
                 "roofline": roof, "e2e": e2e, "clocks": clk, **extra}
         if not args.no_cpu_baseline and world == 1:

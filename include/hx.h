@@ -164,16 +164,66 @@ HX_API int hx_apply_host(hx_problem *p, const void *c_in_host, void *c_out_host)
  * c^{n+1} = ||c^n|| V_m exp(-i dt T_m) e_1 (Sec. 2.2).  c is a DEVICE complex128 vector of
  * |K| elements, updated in place, for both dtypes (HX_C64 runs the Krylov vectors and the
  * stencil in complex64, the state and all inner products in FP64).  Advances the problem
- * time by nsteps * dt.  The step loop is captured once into a CUDA graph per problem and
- * replayed.  Asynchronous; returns HX_EBREAKDOWN (informational) when some step needed
- * fewer than m Lanczos vectors — query hx_step_info — and HX_ENONFINITE if the norm
- * became NaN/Inf (both only after a synchronising call such as hx_step_info). */
+ * time by nsteps * dt.  One step is captured into a CUDA graph for the pair (c, dt) and replayed
+ * nsteps times; a call with another vector or step size captures a new graph.  Asynchronous;
+ * hx_step_info reports HX_EBREAKDOWN (informational) when some step needed fewer than m
+ * Lanczos vectors, and HX_ENONFINITE when the norm became NaN/Inf or the eigensolver of T_m
+ * did not converge. */
 HX_API int hx_step(hx_problem *p, void *c, double dt, int nsteps);
 /* Same with a host complex128 vector: copies in, steps, copies out, synchronises. */
 HX_API int hx_step_host(hx_problem *p, void *c_host, double dt, int nsteps);
 /* Synchronises the stream and reports the last step: Lanczos size used, alpha/beta of T_m
  * (host arrays of at least m and m-1 doubles, either may be NULL) and the norm of c. */
 HX_API int hx_step_info(hx_problem *p, int *m_used, double *alpha, double *beta, double *norm);
+/* Kernel launches of one product hx_apply (1, or 2 when some term is evaluated in two stages
+ * through channel vectors) and of one time step of hx_step (m (per_apply + 3) + 2: the
+ * normalisation, per Lanczos vector the product, one projection and two orthogonalisation
+ * passes (one for the last vector), the eigensolver and the recombination).  Needs a potential;
+ * either pointer may be NULL.  The paper has no counterpart: this reports how the library maps
+ * its work onto kernels. */
+HX_API int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step);
+
+/* ---- batches of independent problems ----------------------------------------------- */
+
+/* A batch of independent problems of any N, B and potential, stepped together: one CUDA graph per
+ * time step holds every problem's step (the same kernels as hx_step) as an independent branch, so
+ * the GPU runs the problems concurrently; the graph is replayed nsteps times.  The problems keep
+ * their own index sets, potentials, times and Krylov workspaces; they must stay alive and unchanged
+ * (no hx_potential_set) while the batch exists.  Work is ordered on the first problem's stream.
+ * hx_batch_step: c[i] is the DEVICE complex128 state of problem i (in place); the graph is built on
+ * the first call and rebuilt when dt or a state pointer changes.  Asynchronous. */
+typedef struct hx_batch hx_batch;
+HX_API int hx_batch_create(hx_problem *const *probs, int n, hx_batch **out);
+HX_API int hx_batch_step(hx_batch *b, void *const *c, double dt, int nsteps);
+HX_API void hx_batch_destroy(hx_batch *b);
+
+/* ---- gradient with respect to a control (adjoint) ---------------------------- */
+
+/* A control u(t), constant on n_intervals equal intervals of [t0, t1), that enters the potential
+ * as u(t) x_axis.  The time step is dt = (t1 - t0) / (n_intervals * substeps). */
+typedef struct {
+    int axis;
+    int n_intervals;
+    int substeps;
+    double t0, t1;
+    const double *u;               /* host, n_intervals values */
+} hx_control;
+
+/* J = |<phi, psi(t1)>|^2, psi(t0) = c0, propagated with the potential `fixed` plus u(t) x_axis by
+ * the exponential midpoint rule with m-step Lanczos exponentials (Eq. (expMPR), Sec. 2.2), and its
+ * gradient dJ/du_q (q < n_intervals) by the adjoint method: with a = <phi, psi_M>, lambda_M = phi,
+ * lambda_{n-1} = U_n^H lambda_n, dJ/du_q = 2 Re(conj(a) sum_{n in q} lambda_n^H (dU_n/du) psi_{n-1}),
+ * where dU_n/du is the Frechet derivative of the exponential; each term is evaluated exactly in the
+ * Lanczos spaces of psi_{n-1} and lambda_n.  States at interval starts are kept, states inside an
+ * interval are recomputed.  The computation is FP64 (cfg->dtype is ignored); cfg->m must be large
+ * enough for the Lanczos exponential of one step to converge (the gradient is that of the
+ * converged propagator), cfg->order and cfg->stream are honoured.  c0, phi: DEVICE complex128
+ * vectors of |K|; grad_out: host array of n_intervals doubles, or NULL for J only; J_out: host.
+ * Device memory: about (n_intervals + substeps + 2m + 8) vectors.  Synchronous.
+ * Errors: HX_EINVAL (NULL pointers, bad control), HX_ENOMEM, HX_ECUDA, as hx_potential_set. */
+HX_API int hx_adjoint_grad(const hx_indexset *s, const hx_config *cfg, const hx_potential *fixed,
+                           const hx_control *ctl, const void *c0, const void *phi, double *grad_out,
+                           double *J_out);
 
 /* ||c||_2 of a device vector of the problem dtype, accumulated in FP64; synchronous. */
 HX_API int hx_norm(hx_problem *p, const void *c, double *out);

@@ -437,3 +437,47 @@ def expmpr_propagate(S: IndexSet, spec: dict, c0: np.ndarray, h: float, nsteps: 
         c, _, _ = lanczos_exp(lambda v: apply(S, r, alpha, spec["L"], v, order), c, h, m)
         t += h
     return c, t
+
+
+# --------------------------------------------------------------------------- #
+# gradient of a final-time objective w.r.t. a piecewise-constant control       #
+# --------------------------------------------------------------------------- #
+
+def control_objective_dense(S: IndexSet, spec: dict, c0: np.ndarray, phi: np.ndarray, dt: float, nsub: int,
+                            order: str = "sym"):
+    """J = |<phi, psi(T)>|^2 with psi propagated by the exact exponentials of the midpoint rule,
+    psi_n = exp(-i dt A(t_{n-1} + dt/2)) psi_{n-1} (Eq. (expMPR) with the matrix exponential done
+    exactly by scipy's expm on the dense A; tiny sets only).  Returns (J, a, states)."""
+    import scipy.linalg
+    psi = np.array(c0, dtype=np.complex128)
+    states = [psi]
+    for n in range(nsub):
+        r, a = potential_terms(spec, (n + 0.5) * dt)
+        A = dense_A(S, r, a, spec["L"], order)
+        psi = scipy.linalg.expm(-1j * dt * A) @ psi
+        states.append(psi)
+    amp = np.vdot(phi, psi)
+    return float(abs(amp) ** 2), amp, states
+
+
+def control_gradient_dense(S: IndexSet, spec: dict, c0: np.ndarray, phi: np.ndarray, dt: float, nsub: int,
+                           n_intervals: int, order: str = "sym"):
+    """dJ/du_q for the control u(t) x_1 (piecewise constant on n_intervals equal intervals of [0, nsub dt]).
+
+    J = |a|^2, a = <phi, psi_M>; with lambda_M = phi and lambda_{n-1} = U_n^H lambda_n,
+    da/du_q = sum over sub-steps n inside interval q of lambda_n^H (dU_n/du) psi_{n-1}, where dU_n/du is
+    the Frechet derivative of exp at -i dt A_n in the direction -i dt X_1 (scipy's expm_frechet), and
+    dJ/du_q = 2 Re(conj(a) da/du_q)."""
+    import scipy.linalg
+    J, amp, states = control_objective_dense(S, spec, c0, phi, dt, nsub, order)
+    X1 = dense_X(S, 0)
+    lam = np.array(phi, dtype=np.complex128)
+    grad_a = np.zeros(n_intervals, dtype=np.complex128)
+    per = nsub // n_intervals
+    for n in range(nsub, 0, -1):
+        r, a = potential_terms(spec, (n - 0.5) * dt)
+        A = dense_A(S, r, a, spec["L"], order)
+        U, Lf = scipy.linalg.expm_frechet(-1j * dt * A, -1j * dt * X1)
+        grad_a[(n - 1) // per] += np.vdot(lam, Lf @ states[n - 1])
+        lam = U.conj().T @ lam
+    return J, 2.0 * np.real(np.conj(amp) * grad_a)

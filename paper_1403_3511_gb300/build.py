@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libhx.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["hx_capi.cu", "hx_apply.cu", "hx_krylov.cu", "hx_noalloc.cu"]
+SOURCES = ["hx_capi.cu", "hx_apply.cu", "hx_krylov.cu", "hx_noalloc.cu", "hx_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(os.path.dirname(HERE), "include")]

@@ -10,11 +10,14 @@
 // coefficients in its stencil footprint: the paper's term-by-term sweep (Algorithm
 // fast_algorithm) is reordered into a single pass over the output.
 //
-// Tiling.  A work item is a run of consecutive slabs (elements sharing the outer prefix
-// k_0..k_{N-3}), at most kItemElems elements.  Phase A computes, for each slab of the item
-// and each outer offset delta the operators need, the start of slab "prefix + delta" and its
-// prefix product (shared memory).  Phase B assigns one thread per output element.
+// Addressing.  One thread per output element.  The element lies in a row (fixed prefix
+// k_0..k_{N-2}, contiguous in k_{N-1}); a footprint point that moves along prefix axes lies in
+// row "r + offset", whose start rank comes from the row-offset table built once per potential
+// (index structure only; the matrix is never formed).  Whether a point lies in K, and the fibre
+// tops that select the row-table entries, follow from products of (1 + k_l) and floor(B / x).
 #include <math.h>
+
+#include <algorithm>
 
 #include "hx_internal.h"
 
@@ -26,12 +29,14 @@ template <> struct Vec2<double> { using T = double2; };
 
 struct ApplyArgs : ApplyArgsBase {
     OpSet ops;
+    int nrow;                  // row-offset table stride
     const void *cin;
     void *cout;
     const double *out_scale;   // nullptr = 1
     void *chan;                // channel vectors (read by the main stage, written by stage 1)
     size_t chan_ld;
     int stage1;                // 1: write each op's result to its channel instead of y
+    int skip_diag;             // 1: omit D_K
 };
 
 // amp * f(t) in the stencil precision R (the interval index of a piecewise-constant modulation is
@@ -53,12 +58,9 @@ __device__ __forceinline__ R op_weight(const Op &op, double t, const double *pw)
     return (R)op.amp * f;
 }
 
-// Exact a / b when b divides a (both < 2^24): the correctly rounded float quotient is the integer.
-__device__ __forceinline__ int exact_div(int a, int b) { return __float2int_rn(__fdiv_rn((float)a, (float)b)); }
-
-// floor(B / x) for integers B, x >= 1 with B + x < 2^24: the rounding error of the correctly rounded
-// float quotient, at most 2^-24 (B / x + 1), is smaller than the distance 1/x to the next integer.
-__device__ __forceinline__ int floor_div(int B, int x) { return __float2int_rz(__fdiv_rn((float)B, (float)x)); }
+// Exact a / b when b divides a, 1 <= b <= a < 2^16: __fdividef is within 2 ulp of a / b, so the
+// computed quotient (an integer below 2^16) is off by less than 2^-6 and rounds to itself.
+__device__ __forceinline__ int exact_div(int a, int b) { return __float2int_rn(__fdividef((float)a, (float)b)); }
 
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
@@ -87,40 +89,30 @@ template <> struct Acc<float> {   // compensated accumulation of the operator co
 
 // Per-thread view of one output element.
 struct Elem {
-    int e;          // rank
-    int start;      // start of own slab
-    int qoff;       // qoff[q] of own slab
-    int sl;         // slab index inside the item
-    int qall;       // prod_l (1 + k_l)
-    int k1, k2;     // coordinates on the inner axes N-2, N-1 (k1 = 0 when N == 1)
+    int e;                  // rank
+    int k2;                 // last coordinate k_{N-1}
+    int qall;               // prod_l (1 + k_l)
+    int rlen;               // length of the own row
+    const int *nb;          // row-offset table at the own row (column d at nb[d * nrow])
+    const uint16_t *kr;     // prefix k_0..k_{N-2} of the own row
 };
 
 struct Ctx {
     const DevSet *S;
-    const int2 *nb;           // item neighbour table (shared): slab start, qoff
-    int nd;
-    const uint16_t *kk;       // shared multi-indices, [l * blockDim + tid]
-    int tid, nthr;
-    __device__ int k(int l) const { return kk[l * nthr + tid]; }
+    int nrow;
+    __device__ int k(const Elem &el, int l) const { return l == S->N - 1 ? el.k2 : (int)__ldg(el.kr + l); }
+    // start rank of the row reached by row offset d (d > 0; the point must lie in K)
+    __device__ int row(const Elem &el, int d) const { return __ldg(el.nb + (size_t)d * nrow); }
 };
 
-// Address of element k + s e_a + s2 e_b (footprint position pos of the operator).
+// Address of element k + s e_a + s2 e_b (footprint position pos of the operator); the point lies in K.
 __device__ __forceinline__ int point_addr(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, int pos,
                                           int a, int s, int b, int s2)
 {
-    const DevSet &S = *c.S;
-    int N = S.N;
-    int di = O.didx[op.dbase + pos];
-    int start = el.start, qoff = el.qoff;
-    if (di != 0) {
-        int2 nb = c.nb[el.sl * c.nd + di];
-        start = nb.x;
-        qoff = nb.y;
-    }
-    int i2 = el.k2 + (a == N - 1 ? s : 0) + (b == N - 1 ? s2 : 0);
-    if (N == 1) return start + i2;
-    int i1 = el.k1 + (a == N - 2 ? s : 0) + (b == N - 2 ? s2 : 0);
-    return start + S.Q[qoff + i1] + i2;
+    const int N = c.S->N;
+    const int di = O.didx[op.dbase + pos];
+    const int shift = (a == N - 1 ? s : 0) + (b == N - 1 ? s2 : 0);
+    return (di ? c.row(el, di) : el.e - el.k2) + el.k2 + shift;
 }
 
 // Number of steps (capped at p) from coordinate i to the top of its fibre, given the product
@@ -140,8 +132,8 @@ __device__ __forceinline__ void line_op(const Ctx &c, const Elem &el, const OpSe
 {
     const int B = c.S->B;
     const int a = op.a, p = op.p;
-    const int ka = c.k(a);
-    const int other = __float2int_rn(__fdiv_rn((float)el.qall, (float)(1 + ka)));
+    const int ka = c.k(el, a);
+    const int other = exact_div(el.qall, 1 + ka);
     const int d = top_dist(ka, other, p, B);
     const R *row = tab + op.tabP + ((size_t)ka * (p + 1) + d) * (2 * p + 1) + p;
 #pragma unroll(UNROLL ? 2 * MP + 1 : 1)
@@ -162,8 +154,8 @@ __device__ __forceinline__ void plane_op(const Ctx &c, const Elem &el, const OpS
 {
     const int B = c.S->B;
     const int a = op.a, b = op.b, p = op.p, q = op.q;
-    const int ka = c.k(a), kb = c.k(b);
-    const int rab = __float2int_rn(__fdiv_rn((float)el.qall, (float)((1 + ka) * (1 + kb))));
+    const int ka = c.k(el, a), kb = c.k(el, b);
+    const int rab = exact_div(el.qall, (1 + ka) * (1 + kb));
     const R wAB = (R)O.wAB, wBA = (R)O.wBA;
     // fibre-top distances: along a at k + s2 e_b, along b at k + s e_a
     int dA[2 * MQ + 1], dB[2 * MP + 1];
@@ -202,43 +194,21 @@ __device__ __forceinline__ void plane_op(const Ctx &c, const Elem &el, const OpS
 // floor(B / x) for x >= 1 from the table (0 when x > B: no element has those coordinates).
 __device__ __forceinline__ int nt_of(const DevSet &S, int x) { return x <= S.B ? __ldg(S.nt + x) : 0; }
 
-// Row start (global rank of local row i) inside the slab described by (start, qoff); N >= 2.
-__device__ __forceinline__ int row_start(const DevSet &S, int start, int qoff, int i) { return start + __ldg(S.Q + qoff + i); }
-
-// Base rank of the point that moves by s along an axis of role RA (k + s e_a), before adding the
-// last coordinate: own slab for inner roles, neighbour slab for an outer axis.
-template <int RA>
-__device__ __forceinline__ int2 slab_of(const Ctx &c, const Elem &el, const OpSet &O, int didx_pos)
-{
-    if (RA == ROLE_OUT) {
-        const int di = O.didx[didx_pos];
-        return c.nb[el.sl * c.nd + di];
-    }
-    return make_int2(el.start, el.qoff);
-}
-
 // Line operator P(X_a), P of pure parity and degree P (offsets -P, -P+2, ..., P), axis role RA.
 template <typename R, int P, int RA>
 __device__ __forceinline__ void line_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
                                           const typename Vec2<R>::T *src, R &sx, R &sy)
 {
     const DevSet &S = *c.S;
-    const int ka = RA == ROLE_I2 ? el.k2 : (RA == ROLE_I1 ? el.k1 : c.k(op.a));
-    const int top = nt_of(S, exact_div(el.qall, 1 + ka)) - 1 - ka;      // steps to the top of the a-fibre
+    const int ka = RA == ROLE_LAST ? el.k2 : c.k(el, op.a);
+    // steps to the top of the a-fibre
+    const int top = RA == ROLE_LAST ? el.rlen - 1 - el.k2 : nt_of(S, exact_div(el.qall, 1 + ka)) - 1 - ka;
     const R *row = tab + op.tabP + (ka * (P + 1) + min(P, top)) * (2 * P + 1) + P;
-    const int own_row = RA == ROLE_I2 ? (S.N >= 2 ? row_start(S, el.start, el.qoff, el.k1) : el.start) : 0;
 #pragma unroll
     for (int s = -P; s <= P; s += 2) {
         if (ka + s < 0 || s > top) continue;
-        int addr;
-        if (RA == ROLE_I2) {
-            addr = own_row + el.k2 + s;
-        } else if (RA == ROLE_I1) {
-            addr = row_start(S, el.start, el.qoff, el.k1 + s) + el.k2;
-        } else {
-            const int2 nb = slab_of<ROLE_OUT>(c, el, O, op.dbase + s + P);
-            addr = (S.N >= 2 ? row_start(S, nb.x, nb.y, el.k1) : nb.x) + el.k2;
-        }
+        const int addr = RA == ROLE_LAST ? el.e + s
+                                         : (s == 0 ? el.e : c.row(el, O.didx[op.dbase + s + P]) + el.k2);
         const typename Vec2<R>::T v = src[addr];
         const R w = row[s];
         sx += w * v.x;
@@ -246,18 +216,21 @@ __device__ __forceinline__ void line_role(const Ctx &c, const Elem &el, const Op
     }
 }
 
-// Plane operator wAB P(X_a) Q(X_b) + wBA Q(X_b) P(X_a), pure parities, degrees P, Q, roles RA < RB.
-// A footprint point k + s e_a + s2 e_b carries [P]_{k, k+s e_a} [Q]_{k+s e_a, k+s e_a+s2 e_b} (path
-// through k + s e_a) and [Q]_{k, k+s2 e_b} [P]_{k+s2 e_b, k+s2 e_b+s e_a} (path through k + s2 e_b);
-// a path exists only if its intermediate point is in K.  Rows of P(J_n / L) and Q(J_n / L) come
-// from the tables, indexed by the coordinate and the distance to the fibre top.
-template <typename R, int P, int Q, int RA, int RB>
+// Plane operator wAB P(X_a) Q(X_b) + wBA Q(X_b) P(X_a), pure parities, degrees P, Q; a is a prefix
+// axis, b has role RB.  A footprint point k + s e_a + s2 e_b carries [P]_{k, k+s e_a}
+// [Q]_{k+s e_a, k+s e_a+s2 e_b} (path through k + s e_a) and [Q]_{k, k+s2 e_b} [P]_{k+s2 e_b,
+// k+s2 e_b+s e_a} (path through k + s2 e_b); a path exists only if its intermediate point is in K.
+// Rows of P(J_n / L) and Q(J_n / L) come from the tables, indexed by the coordinate and the
+// distance to the fibre top.
+// SB > 0: a line operator S(X_b) of degree SB (parity of Q, SB = Q or Q + 2) merged into this op;
+// its sum goes to (lx, ly), which the caller weights with the line operator's own weight.
+template <typename R, int P, int Q, int RB, int SB>
 __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
-                                           const typename Vec2<R>::T *src, R &sx, R &sy)
+                                           const typename Vec2<R>::T *src, R &sx, R &sy, R &lx, R &ly)
 {
     const DevSet &S = *c.S;
-    const int ka = RA == ROLE_I1 ? el.k1 : c.k(op.a);
-    const int kb = RB == ROLE_I2 ? el.k2 : (RB == ROLE_I1 ? el.k1 : c.k(op.b));
+    const int ka = c.k(el, op.a);
+    const int kb = RB == ROLE_LAST ? el.k2 : c.k(el, op.b);
     const int rab = exact_div(el.qall, (1 + ka) * (1 + kb));
     const R wAB = (R)O.wAB, wBA = (R)O.wBA;
     const R *tP = tab + op.tabP, *tQ = tab + op.tabQ;
@@ -266,7 +239,7 @@ __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const O
     const R *rowP[2 * Q + 1];   // P row at k + s2 e_b (valid when that point is in K)
     const R *rowQ[2 * P + 1];   // Q row at k + s e_a
     topA[Q] = nt_of(S, rab * (1 + kb)) - 1 - ka;
-    topB[P] = nt_of(S, rab * (1 + ka)) - 1 - kb;
+    topB[P] = RB == ROLE_LAST ? el.rlen - 1 - el.k2 : nt_of(S, rab * (1 + ka)) - 1 - kb;
 #pragma unroll
     for (int s2 = -Q; s2 <= Q; s2 += 2)
         if (s2 != 0) topA[s2 + Q] = kb + s2 >= 0 ? nt_of(S, rab * (1 + kb + s2)) - 1 - ka : -1;
@@ -280,17 +253,19 @@ __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const O
     for (int s = -P; s <= P; ++s)
         if (s == 0 || ((s - P) & 1) == 0) rowQ[s + P] = tQ + (kb * (Q + 1) + max(0, min(Q, topB[s + P]))) * (2 * Q + 1) + Q;
     const int topA0 = topA[Q], topB0 = topB[P];
-    int own_row = 0;
-    if (RB == ROLE_I2 && RA == ROLE_I1) own_row = 0;   // rows vary with s below
+    const R *rowS0 = nullptr;
+    if (SB > 0) {
+        const Op &ls = O.op[op.mergeB];
+        rowS0 = tab + ls.tabP + (kb * (SB + 1) + min(SB, topB0)) * (2 * SB + 1) + SB;
+    }
+    const int own = el.e - el.k2;                       // start of the own row
 #pragma unroll
     for (int s = -P; s <= P; s += 2) {
         if (ka + s < 0) continue;
         const bool inA = s <= topA0;                    // k + s e_a in K
         const R pj = inA ? rowP[Q][s] : (R)0;
-        int base_s = 0;                                 // rank of row containing k + s e_a (+ s2 e_b for RB = I2)
-        int2 nb_s = make_int2(el.start, el.qoff);
-        if (RA == ROLE_OUT && RB != ROLE_OUT) nb_s = slab_of<ROLE_OUT>(c, el, O, op.dbase + (s + P) * (2 * Q + 1) + Q);
-        if (RB == ROLE_I2) base_s = (RA == ROLE_I1) ? row_start(S, el.start, el.qoff, el.k1 + s) : row_start(S, nb_s.x, nb_s.y, el.k1);
+        int base_s = own;                               // RB = LAST: start of the row of k + s e_a
+        if (RB == ROLE_LAST && s != 0) base_s = c.row(el, O.didx[op.dbase + (s + P) * (2 * Q + 1) + Q]);
 #pragma unroll
         for (int s2 = -Q; s2 <= Q; s2 += 2) {
             if (kb + s2 < 0 || s > topA[s2 + Q]) continue;     // footprint point not in K
@@ -298,39 +273,62 @@ __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const O
             const R cba = s2 <= topB0 ? rowQ[P][s2] * rowP[s2 + Q][s] : (R)0;   // k + s2 e_b in K
             const R w = wAB * cab + wBA * cba;
             int addr;
-            if (RB == ROLE_I2) {
-                addr = base_s + el.k2 + s2;
-            } else if (RB == ROLE_I1) {                 // RA outer: neighbour slab by s, row k1 + s2
-                addr = row_start(S, nb_s.x, nb_s.y, el.k1 + s2) + el.k2;
-            } else {                                    // both outer: neighbour slab by (s, s2)
-                const int2 nb = slab_of<ROLE_OUT>(c, el, O, op.dbase + (s + P) * (2 * Q + 1) + (s2 + Q));
-                addr = row_start(S, nb.x, nb.y, el.k1) + el.k2;
-            }
+            if (RB == ROLE_LAST) addr = base_s + el.k2 + s2;
+            else if (s == 0 && s2 == 0) addr = el.e;
+            else addr = c.row(el, O.didx[op.dbase + (s + P) * (2 * Q + 1) + (s2 + Q)]) + el.k2;
             const typename Vec2<R>::T v = src[addr];
             sx += w * v.x;
             sy += w * v.y;
+            if (SB > 0 && s == 0) {                     // k + s2 e_b is also a point of the merged line op
+                const R ws = rowS0[s2];
+                lx += ws * v.x;
+                ly += ws * v.y;
+            }
         }
     }
-    (void)own_row;
+    if (SB > Q) {                                       // the merged line op's outermost points +-SB
+#pragma unroll
+        for (int s2 = -SB; s2 <= SB; s2 += 2 * SB) {
+            if (kb + s2 < 0 || s2 > topB0) continue;
+            int addr;
+            if (RB == ROLE_LAST) {
+                addr = el.e + s2;
+            } else {
+                const Op &ls = O.op[op.mergeB];
+                addr = c.row(el, O.didx[ls.dbase + s2 + SB]) + el.k2;
+            }
+            const typename Vec2<R>::T v = src[addr];
+            const R ws = rowS0[s2];
+            lx += ws * v.x;
+            ly += ws * v.y;
+        }
+    }
 }
 
-template <typename R, int P, int Q>
-__device__ __forceinline__ void plane_dispatch(int key, const Ctx &c, const Elem &el, const OpSet &O, const Op &op,
-                                               const R *tab, const typename Vec2<R>::T *src, R &sx, R &sy)
+template <typename R, int P, int Q, int SB>
+__device__ __forceinline__ void plane_dispatch_sb(int rb, const Ctx &c, const Elem &el, const OpSet &O, const Op &op,
+                                                  const R *tab, const typename Vec2<R>::T *src, R &sx, R &sy, R &lx, R &ly)
 {
-    if (key == ROLE_OUT * 4 + ROLE_OUT) plane_role<R, P, Q, ROLE_OUT, ROLE_OUT>(c, el, O, op, tab, src, sx, sy);
-    else if (key == ROLE_OUT * 4 + ROLE_I1) plane_role<R, P, Q, ROLE_OUT, ROLE_I1>(c, el, O, op, tab, src, sx, sy);
-    else if (key == ROLE_OUT * 4 + ROLE_I2) plane_role<R, P, Q, ROLE_OUT, ROLE_I2>(c, el, O, op, tab, src, sx, sy);
-    else plane_role<R, P, Q, ROLE_I1, ROLE_I2>(c, el, O, op, tab, src, sx, sy);
+    if (rb == ROLE_LAST) plane_role<R, P, Q, ROLE_LAST, SB>(c, el, O, op, tab, src, sx, sy, lx, ly);
+    else plane_role<R, P, Q, ROLE_ROW, SB>(c, el, O, op, tab, src, sx, sy, lx, ly);
+}
+
+// sb: degree of the merged line op (0: none); only sb in {0, Q, Q + 2 <= 3} occurs.
+template <typename R, int P, int Q>
+__device__ __forceinline__ void plane_dispatch(int rb, int sb, const Ctx &c, const Elem &el, const OpSet &O, const Op &op,
+                                               const R *tab, const typename Vec2<R>::T *src, R &sx, R &sy, R &lx, R &ly)
+{
+    if (sb == 0) plane_dispatch_sb<R, P, Q, 0>(rb, c, el, O, op, tab, src, sx, sy, lx, ly);
+    else if (sb == Q) plane_dispatch_sb<R, P, Q, Q>(rb, c, el, O, op, tab, src, sx, sy, lx, ly);
+    else if (Q + 2 <= 3) plane_dispatch_sb<R, P, Q, (Q + 2 <= 3 ? Q + 2 : Q)>(rb, c, el, O, op, tab, src, sx, sy, lx, ly);
 }
 
 template <typename R, int P>
 __device__ __forceinline__ void line_dispatch(int ra, const Ctx &c, const Elem &el, const OpSet &O, const Op &op,
                                               const R *tab, const typename Vec2<R>::T *src, R &sx, R &sy)
 {
-    if (ra == ROLE_OUT) line_role<R, P, ROLE_OUT>(c, el, O, op, tab, src, sx, sy);
-    else if (ra == ROLE_I1) line_role<R, P, ROLE_I1>(c, el, O, op, tab, src, sx, sy);
-    else line_role<R, P, ROLE_I2>(c, el, O, op, tab, src, sx, sy);
+    if (ra == ROLE_LAST) line_role<R, P, ROLE_LAST>(c, el, O, op, tab, src, sx, sy);
+    else line_role<R, P, ROLE_ROW>(c, el, O, op, tab, src, sx, sy);
 }
 
 // MD: largest polynomial degree of the compiled potential (3: unrolled stencils; kMaxDeg: rolled loops).
@@ -338,176 +336,98 @@ template <typename R, int MD>
 __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 3 : 1) apply_kernel(const __grid_constant__ ApplyArgs args)
 {
     using V = typename Vec2<R>::T;
-    extern __shared__ int2 sm_nb[];
-    __shared__ int sm_start[65];
-    __shared__ int sm_q[64];
-    __shared__ uint16_t sm_pre[64 * kMaxN];
-    __shared__ uint16_t sm_k[kMaxN * kApplyThreads];
     __shared__ R sm_w[kMaxOps];
-    __shared__ int8_t sm_delta[kMaxDelta * 4];
 
     const DevSet &S = args.S;
     const OpSet &O = args.ops;
-    const int N = S.N, nout = N > 2 ? N - 2 : 0, nd = O.ndelta;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int N = S.N;
+    const int tid = threadIdx.x;
     const V *cin = (const V *)args.cin;
     V *cout = (V *)args.cout;
     const R *tab = (const R *)args.tab;
-    const int *Q1 = S.Q;     // level m = 1
 
     if (tid < O.nops) sm_w[tid] = op_weight<R>(O.op[tid], *args.t_ptr + args.t_shift, args.pw_values);
-    for (int x = tid; x < O.ndelta * 4; x += blockDim.x) sm_delta[x] = O.delta[x >> 2][x & 3];
     const R oscale = args.out_scale ? (R)(*args.out_scale) : (R)1;
+    __syncthreads();
 
     Ctx ctx;
     ctx.S = &S;
-    ctx.nb = sm_nb;
-    ctx.nd = nd;
-    ctx.kk = sm_k;
-    ctx.tid = tid;
-    ctx.nthr = nthr;
+    ctx.nrow = args.nrow;
 
-    for (int item = blockIdx.x; item < args.nitems; item += gridDim.x) {
-        const int4 it = args.items[item];
-        const int s0 = it.x, ns = it.y - it.x + 1, e0 = it.z, e1 = it.w;
-        __syncthreads();
-        // ---- phase A: own slabs, then the neighbour slabs of every outer offset
-        for (int x = tid; x < ns; x += nthr) {
-            sm_start[x] = S.slab_start[s0 + x];
-            int q = 1;
-            for (int l = 0; l < nout; ++l) {
-                int pl = S.slab_k[(size_t)(s0 + x) * nout + l];
-                sm_pre[x * kMaxN + l] = (uint16_t)pl;
-                q *= 1 + pl;
-            }
-            sm_q[x] = q;
-        }
-        __syncthreads();
-        for (int x = tid; x < ns * nd; x += nthr) {
-            const int sl = x / nd, di = x - sl * nd;
-            int2 res = make_int2(-1, 0);
-            int pre[kMaxN];
-            bool ok = true;
-            for (int l = 0; l < nout; ++l) pre[l] = sm_pre[sl * kMaxN + l];
-            for (int j = 0; j < 2; ++j) {
-                int ax = sm_delta[di * 4 + 2 * j];
-                if (ax >= 0) pre[ax] += sm_delta[di * 4 + 2 * j + 1];
-            }
-            long long q = 1;
-            for (int l = 0; l < nout; ++l) {
-                if (pre[l] < 0) ok = false;
-                q *= 1 + pre[l];
-            }
-            if (ok && q <= S.B) {
-                int start = 0, qd = 1;
-                for (int d = 0; d < nout; ++d) {
-                    int m = N - 1 - d;
-                    start += S.Q[(size_t)(m - 1) * S.qtotal + S.qoff[qd] + pre[d]];
-                    qd *= 1 + pre[d];
+    for (int e = blockIdx.x * blockDim.x + tid; e < S.size; e += gridDim.x * blockDim.x) {
+        const int r = __ldg(S.row_of + e);
+        const int4 ri = __ldg(S.row_info + r);
+        Elem el;
+        el.e = e;
+        el.k2 = e - ri.x;
+        el.qall = ri.y * (1 + el.k2);
+        el.rlen = ri.w;
+        el.nb = args.rnb + r;
+        el.kr = S.row_k + (size_t)r * (N - 1);
+        const V ce = cin[e];
+        Acc<R> acc;
+        const R dj = (R)(ri.z + el.k2) + (R)0.5 * (R)N;   // (D_K)_jj = sum_l (j_l + 1/2)
+        if (!args.stage1 && !args.skip_diag) acc.add(dj * ce.x, dj * ce.y);
+        for (int o = 0; o < O.nops; ++o) {
+            const Op &op = O.op[o];
+            if (op.merged) continue;
+            R lx = (R)0, ly = (R)0;     // sum of a line op merged into a plane op
+            const V *src = op.src < 0 ? cin : (const V *)args.chan + (size_t)op.src * args.chan_ld;
+            R sx = (R)0, sy = (R)0;
+            if (op.kind == 0) {
+                const V cs = src[e];
+                sx = cs.x;
+                sy = cs.y;
+            } else if (MD <= 3) {
+                const int sb = op.mergeB >= 0 ? O.op[op.mergeB].p : 0;
+                switch (op.cls) {
+                    case CLS_LINE + 1: line_dispatch<R, 1>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                    case CLS_LINE + 2: line_dispatch<R, 2>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                    case CLS_LINE + 3: line_dispatch<R, 3>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                    case CLS_PLANE + 0: plane_dispatch<R, 1, 1>(op.rb, sb, ctx, el, O, op, tab, src, sx, sy, lx, ly); break;
+                    case CLS_PLANE + 3: plane_dispatch<R, 2, 1>(op.rb, sb, ctx, el, O, op, tab, src, sx, sy, lx, ly); break;
+                    case CLS_PLANE + 1: plane_dispatch<R, 1, 2>(op.rb, sb, ctx, el, O, op, tab, src, sx, sy, lx, ly); break;
+                    case CLS_PLANE + 4: plane_dispatch<R, 2, 2>(op.rb, sb, ctx, el, O, op, tab, src, sx, sy, lx, ly); break;
+                    default:
+                        if (op.kind == 1) line_op<R, 3, true>(ctx, el, O, op, tab, src, sx, sy);
+                        else plane_op<R, 3, 3, true>(ctx, el, O, op, tab, src, sx, sy);
                 }
-                res = make_int2(start, (int)S.qoff[qd]);
-            }
-            sm_nb[x] = res;
-        }
-        __syncthreads();
-        // ---- phase B: one thread per output element
-        for (int e = e0 + tid; e < e1; e += nthr) {
-            int lo = 0, hi = ns - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (sm_start[mid] <= e) lo = mid; else hi = mid - 1;
-            }
-            Elem el;
-            el.e = e;
-            el.sl = lo;
-            el.start = sm_start[lo];
-            const int q = sm_q[lo];
-            el.qoff = S.qoff[q];
-            const int local = e - el.start;
-            if (N >= 2) {
-                int b = S.B / q;                // rows i = 0 .. b-1 of the slab
-                int l2 = 0, h2 = b - 1;
-                while (l2 < h2) {
-                    int mid = (l2 + h2 + 1) >> 1;
-                    if (Q1[el.qoff + mid] <= local) l2 = mid; else h2 = mid - 1;
-                }
-                el.k1 = l2;
-                el.k2 = local - Q1[el.qoff + l2];
             } else {
-                el.k1 = 0;
-                el.k2 = local;
+                if (op.kind == 1) line_op<R, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
+                else plane_op<R, kMaxDeg, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
             }
-            int qall = q;
-            R dsum = (R)0;
-            for (int l = 0; l < nout; ++l) {
-                int kl = sm_pre[lo * kMaxN + l];
-                sm_k[l * nthr + tid] = (uint16_t)kl;
-                dsum += (R)kl;
+            const R w = sm_w[o];
+            if (op.mergeB >= 0) {
+                const R wl = sm_w[op.mergeB];
+                sx = w * sx + wl * lx;
+                sy = w * sy + wl * ly;
+                acc.add(sx, sy);
+                continue;
             }
-            if (N >= 2) {
-                sm_k[(N - 2) * nthr + tid] = (uint16_t)el.k1;
-                qall *= 1 + el.k1;
-                dsum += (R)el.k1;
+            if (args.stage1) {
+                V ch;
+                ch.x = w * sx;
+                ch.y = w * sy;
+                ((V *)args.chan)[(size_t)op.dst * args.chan_ld + e] = ch;
+            } else {
+                acc.add(w * sx, w * sy);
             }
-            sm_k[(N - 1) * nthr + tid] = (uint16_t)el.k2;
-            qall *= 1 + el.k2;
-            dsum += (R)el.k2;
-            el.qall = qall;
-            const V ce = cin[e];
-            Acc<R> acc;
-            const R dj = dsum + (R)0.5 * (R)N;   // (D_K)_jj = sum_l (j_l + 1/2)
-            if (!args.stage1) acc.add(dj * ce.x, dj * ce.y);
-            for (int o = 0; o < O.nops; ++o) {
-                const Op &op = O.op[o];
-                const V *src = op.src < 0 ? cin : (const V *)args.chan + (size_t)op.src * args.chan_ld;
-                R sx = (R)0, sy = (R)0;
-                if (op.kind == 0) {
-                    const V cs = src[e];
-                    sx = cs.x;
-                    sy = cs.y;
-                } else if (MD <= 3) {
-                    const int key = op.ra * 4 + op.rb;
-                    switch (op.cls) {
-                        case CLS_LINE + 1: line_dispatch<R, 1>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                        case CLS_LINE + 2: line_dispatch<R, 2>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                        case CLS_LINE + 3: line_dispatch<R, 3>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                        case CLS_PLANE + 0: plane_dispatch<R, 1, 1>(key, ctx, el, O, op, tab, src, sx, sy); break;
-                        case CLS_PLANE + 3: plane_dispatch<R, 2, 1>(key, ctx, el, O, op, tab, src, sx, sy); break;
-                        case CLS_PLANE + 1: plane_dispatch<R, 1, 2>(key, ctx, el, O, op, tab, src, sx, sy); break;
-                        case CLS_PLANE + 4: plane_dispatch<R, 2, 2>(key, ctx, el, O, op, tab, src, sx, sy); break;
-                        default:
-                            if (op.kind == 1) line_op<R, 3, true>(ctx, el, O, op, tab, src, sx, sy);
-                            else plane_op<R, 3, 3, true>(ctx, el, O, op, tab, src, sx, sy);
-                    }
-                } else {
-                    if (op.kind == 1) line_op<R, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
-                    else plane_op<R, kMaxDeg, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
-                }
-                const R w = sm_w[o];
-                if (args.stage1) {
-                    V ch;
-                    ch.x = w * sx;
-                    ch.y = w * sy;
-                    ((V *)args.chan)[(size_t)op.dst * args.chan_ld + e] = ch;
-                } else {
-                    acc.add(w * sx, w * sy);
-                }
-            }
-            if (!args.stage1) {
-                V y = acc.get();
-                y.x *= oscale;
-                y.y *= oscale;
-                cout[e] = y;
-            }
+        }
+        if (!args.stage1) {
+            V y = acc.get();
+            y.x *= oscale;
+            y.y *= oscale;
+            cout[e] = y;
         }
     }
 }
 
 int apply_grid(const Problem *p)
 {
-    int per_sm = 4;
-    int g = p->num_sms * per_sm;
-    return p->nitems < g ? (p->nitems > 0 ? p->nitems : 1) : g;
+    const int per_sm = 4;
+    const int blocks = (p->set->d.size + kApplyThreads - 1) / kApplyThreads;
+    const int g = p->num_sms * per_sm;
+    return blocks < g ? (blocks > 0 ? blocks : 1) : g;
 }
 
 template <typename R, int MD>
@@ -517,9 +437,8 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
     ApplyArgs a;
     memset(&a, 0, sizeof(a));
     a.S = p->set->d;
-    a.items = p->items;
-    a.nitems = p->nitems;
-    a.slabs_per_item = p->slabs_per_item;
+    a.rnb = p->rnb;
+    a.nrow = p->set->d.nrow;
     a.t_ptr = t_ptr;
     a.t_shift = t_shift;
     a.pw_values = p->pw_values;
@@ -531,8 +450,13 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
     a.chan = p->chan;
     a.chan_ld = p->chan_ld;
     a.stage1 = stage1;
-    size_t smem = (size_t)p->slabs_per_item * ops.ndelta * sizeof(int2);
-    apply_kernel<R, MD><<<apply_grid(p), kApplyThreads, smem, st>>>(a);
+    a.skip_diag = p->skip_diag;
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_kernel<R, MD>, kApplyThreads, 0);
+    int grid = p->num_sms * (per_sm > 0 ? per_sm : 1);     // one wave of resident CTAs
+    const int blocks = (p->set->d.size + kApplyThreads - 1) / kApplyThreads;
+    if (grid > blocks) grid = blocks > 0 ? blocks : 1;
+    apply_kernel<R, MD><<<grid, kApplyThreads, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "apply kernel launch");
     return HX_OK;
@@ -564,37 +488,74 @@ int launch_apply(Problem *p, const void *cin, void *cout, const double *t_ptr, d
 }
 
 // ---------------------------------------------------------------------------------------
-// export of all multi-indices (unrank on the device: slab by binary search, then the
-// position inside the slab)
+// Row structure on the device
+// ---------------------------------------------------------------------------------------
+
+// row_of[e]: the row holding rank e (largest r with start(r) <= e).
+__global__ void row_of_kernel(DevSet S, int *row_of)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.size; e += gridDim.x * blockDim.x) {
+        int lo = 0, hi = S.nrow - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (S.row_info[mid].x <= e) lo = mid; else hi = mid - 1;
+        }
+        row_of[e] = lo;
+    }
+}
+
+int launch_row_of(const IndexSetObj *s)
+{
+    int blocks = (int)std::min<int64_t>((s->h.size + 255) / 256, 8192);
+    row_of_kernel<<<std::max(blocks, 1), 256>>>(s->d, const_cast<int *>(s->d.row_of));
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "row index kernel");
+    return HX_OK;
+}
+
+// rnb[d * nrow + r] = start rank of the row whose prefix is prefix(r) + offset d, or -1 when a
+// coordinate turns negative or the prefix product exceeds B; the start is the rank of
+// (prefix, 0), summed level by level from the rank tables.
+__global__ void rowtab_kernel(DevSet S, RowOffsets ro, int *rnb)
+{
+    const int npre = S.N - 1;
+    const int64_t total = (int64_t)ro.n * S.nrow;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(x / S.nrow), r = (int)(x - (int64_t)d * S.nrow);
+        const int a0 = ro.d[d][0], s0 = ro.d[d][1], a1 = ro.d[d][2], s1 = ro.d[d][3];
+        int q = 1, start = 0;
+        bool ok = true;
+        for (int l = 0; l < npre; ++l) {
+            const int kl = (int)S.row_k[(size_t)r * npre + l] + (l == a0 ? s0 : 0) + (l == a1 ? s1 : 0);
+            if (kl < 0 || (int64_t)q * (1 + kl) > S.B) { ok = false; break; }
+            start += S.Q[(size_t)(npre - 1 - l) * S.qtotal + S.qoff[q] + kl];   // level m = N-1-l
+            q *= 1 + kl;
+        }
+        rnb[x] = ok ? start : -1;
+    }
+}
+
+int launch_rowtab(const DevSet &S, const RowOffsets &ro, int *rnb, cudaStream_t st)
+{
+    const int64_t total = (int64_t)ro.n * S.nrow;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, 16384);
+    rowtab_kernel<<<std::max(blocks, 1), 256, 0, st>>>(S, ro, rnb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "row-offset table kernel");
+    return HX_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// export of all multi-indices (row prefix, then the position in the row)
 // ---------------------------------------------------------------------------------------
 __global__ void export_kernel(DevSet S, int32_t *k)
 {
-    const int N = S.N, nout = N > 2 ? N - 2 : 0;
+    const int N = S.N, npre = N - 1;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.size; e += gridDim.x * blockDim.x) {
-        int lo = 0, hi = S.nslab - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (S.slab_start[mid] <= e) lo = mid; else hi = mid - 1;
-        }
-        int q = 1;
-        for (int l = 0; l < nout; ++l) {
-            int pl = S.slab_k[(size_t)lo * nout + l];
-            k[(size_t)e * N + l] = pl;
-            q *= 1 + pl;
-        }
-        int local = e - S.slab_start[lo];
-        if (N >= 2) {
-            const int *row = S.Q + S.qoff[q];
-            int l2 = 0, h2 = S.B / q - 1;
-            while (l2 < h2) {
-                int mid = (l2 + h2 + 1) >> 1;
-                if (row[mid] <= local) l2 = mid; else h2 = mid - 1;
-            }
-            k[(size_t)e * N + N - 2] = l2;
-            k[(size_t)e * N + N - 1] = local - row[l2];
-        } else {
-            k[e] = local;
-        }
+        const int r = S.row_of[e];
+        for (int l = 0; l < npre; ++l) k[(size_t)e * N + l] = S.row_k[(size_t)r * npre + l];
+        k[(size_t)e * N + N - 1] = e - S.row_info[r].x;
     }
 }
 

@@ -70,17 +70,20 @@ static bool counts_by_quotient(int N, int B, std::vector<std::vector<int64_t>> &
     return true;
 }
 
-static void enum_slabs(int depth, int nout, int q, int B, uint16_t *prefix, std::vector<uint16_t> &out,
-                       std::vector<int> &qs)
+// Rows in lexicographic order of their prefixes (axes 0..N-2): start rank, prefix product,
+// coordinate sum and length floor(B / q) of each.
+static void enum_rows(int depth, int npre, int q, int ksum, int B, uint16_t *prefix, IndexSetHost &h, int64_t &pos)
 {
-    if (depth == nout) {
-        out.insert(out.end(), prefix, prefix + nout);
-        qs.push_back(q);
+    if (depth == npre) {
+        h.row_k.insert(h.row_k.end(), prefix, prefix + npre);
+        int len = B / q;
+        h.row_info.push_back(make_int4((int)pos, q, ksum, len));
+        pos += len;
         return;
     }
     for (int k = 0; (int64_t)q * (1 + k) <= B; ++k) {
         prefix[depth] = (uint16_t)k;
-        enum_slabs(depth + 1, nout, q * (1 + k), B, prefix, out, qs);
+        enum_rows(depth + 1, npre, q * (1 + k), ksum + k, B, prefix, h, pos);
     }
 }
 
@@ -118,21 +121,14 @@ static int build_host_tables(int N, int B, IndexSetHost &h)
             }
         }
     }
-    int nout = std::max(N - 2, 0);
-    std::vector<int> qs;
     uint16_t prefix[kMaxN];
-    enum_slabs(0, nout, 1, B, prefix, h.slab_k, qs);
-    h.nslab = (int)qs.size();
-    h.slab_start.resize(h.nslab + 1);
     int64_t pos = 0;
-    for (int s = 0; s < h.nslab; ++s) {
-        h.slab_start[s] = (int)pos;
-        int bq = B / qs[s];
-        pos += (N >= 2) ? C[2][bq] : C[1][bq];
-    }
-    h.slab_start[h.nslab] = (int)pos;
+    h.row_info.clear();
+    h.row_k.clear();
+    enum_rows(0, N - 1, 1, 0, B, prefix, h, pos);
+    h.nrow = (int)h.row_info.size();
     if (pos != size) {
-        set_error("internal: slab sizes %lld != |K| %lld", (long long)pos, (long long)size);
+        set_error("internal: row lengths sum to %lld != |K| %lld", (long long)pos, (long long)size);
         return HX_ECUDA;
     }
     return HX_OK;
@@ -279,19 +275,23 @@ struct Compiler {
         return base;
     }
 
-    int delta_index(OpSet &S, int a0, int s0, int a1, int s1)
+    RowOffsets roff;                     // row offsets of both stages (0: zero offset)
+
+    // Column of the row-offset table for the point k + s0 e_a0 + s1 e_a1 (moves along the last
+    // axis stay in the row and need no column), or -1 when the table is full.
+    int delta_index(int a0, int s0, int a1, int s1)
     {
         int N = set->h.N;
         int8_t e[4] = {-1, 0, -1, 0};
         int n = 0;
-        if (a0 >= 0 && a0 < N - 2 && s0 != 0) { e[0] = (int8_t)a0; e[1] = (int8_t)s0; n = 1; }
-        if (a1 >= 0 && a1 < N - 2 && s1 != 0) { e[2 * n] = (int8_t)a1; e[2 * n + 1] = (int8_t)s1; }
+        if (a0 >= 0 && a0 < N - 1 && s0 != 0) { e[0] = (int8_t)a0; e[1] = (int8_t)s0; n = 1; }
+        if (a1 >= 0 && a1 < N - 1 && s1 != 0) { e[2 * n] = (int8_t)a1; e[2 * n + 1] = (int8_t)s1; }
         if (e[0] < 0 && e[2] < 0) return 0;
-        for (int i = 1; i < S.ndelta; ++i)
-            if (!memcmp(S.delta[i], e, 4)) return i;
-        if (S.ndelta >= kMaxDelta) return -1;
-        memcpy(S.delta[S.ndelta], e, 4);
-        return S.ndelta++;
+        for (int i = 1; i < roff.n; ++i)
+            if (!memcmp(roff.d[i], e, 4)) return i;
+        if (roff.n >= kMaxDelta) return -1;
+        memcpy(roff.d[roff.n], e, 4);
+        return roff.n++;
     }
 
     // Appends an operator to S.  scale multiplies the term amplitude.
@@ -315,9 +315,11 @@ struct Compiler {
         o.tabQ = kind == 2 ? poly(Q) : 0;
         o.src = src;
         o.dst = dst;
+        o.mergeB = -1;
+        o.merged = 0;
         {
             const int N = set->h.N;
-            auto role = [N](int ax) { return ax < 0 ? ROLE_NONE : (ax == N - 1 ? ROLE_I2 : (ax == N - 2 ? ROLE_I1 : ROLE_OUT)); };
+            auto role = [N](int ax) { return ax < 0 ? ROLE_NONE : (ax == N - 1 ? ROLE_LAST : ROLE_ROW); };
             o.ra = role(kind >= 1 ? a : -1);
             o.rb = role(kind == 2 ? b : -1);
         }
@@ -351,14 +353,15 @@ struct Compiler {
             }
             for (int s = -o.p; s <= o.p; ++s)
                 for (int s2 = -o.q; s2 <= o.q; ++s2) {
-                    // only footprint points whose rows can be nonzero get a neighbour slab; the
-                    // plane kernels also look up (s, 0) for the slab of k + s e_a
-                    bool used = ((o.pmask >> (s + o.p)) & 1) && (s2 == 0 || ((o.qmask >> (s2 + o.q)) & 1));
+                    // only footprint points whose rows can be nonzero get a table column; a plane op
+                    // on the last axis also looks up (s, 0), the row of k + s e_a
+                    bool used = ((o.pmask >> (s + o.p)) & 1) &&
+                                (((o.qmask >> (s2 + o.q)) & 1) || (s2 == 0 && o.rb == ROLE_LAST));
                     if (!used) {
                         S.didx[o.dbase + (s + o.p) * (2 * o.q + 1) + (s2 + o.q)] = 0;
                         continue;
                     }
-                    int di = delta_index(S, a, s, kind == 2 ? b : -1, s2);
+                    int di = delta_index(a, s, kind == 2 ? b : -1, s2);
                     if (di < 0) {
                         set_error("potential needs more than %d distinct neighbour offsets", kMaxDelta);
                         return HX_EUNSUPPORTED;
@@ -442,8 +445,9 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
     cp.L = pot->L;
     memset(&cp.ops, 0, sizeof(cp.ops));
     memset(&cp.ops1, 0, sizeof(cp.ops1));
-    cp.ops.ndelta = 1;   // index 0: zero outer offset
-    cp.ops1.ndelta = 1;
+    memset(&cp.roff, 0, sizeof(cp.roff));
+    cp.roff.n = 1;   // column 0: zero offset
+    cp.roff.d[0][0] = cp.roff.d[0][2] = -1;
     int order = pr->cfg.order;
     cp.ops.wAB = order == HX_ORDER_SYM ? 0.5 : (order == HX_ORDER_EQ ? 1.0 : 0.0);
     cp.ops.wBA = order == HX_ORDER_SYM ? 0.5 : (order == HX_ORDER_ALG ? 1.0 : 0.0);
@@ -506,6 +510,27 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
             }
         }
     }
+    // A pure line op on the second axis of a pure plane op, with the parity of the plane op's second
+    // polynomial and a degree of q or q + 2, shares the plane op's points k + s2 e_b: evaluate it
+    // inside the plane op (one gather per shared point); it keeps its own weight.
+    // (only when every op has degree <= 3: the kernel for higher degrees has no merged path; only
+    // into plane ops with both degrees <= 2, the classes with a specialised plane stencil; and only
+    // when the plane op's first degree is even, so that its stencil visits the points s = 0)
+    int maxdeg = 0;
+    for (int i = 0; i < cp.ops.nops; ++i) maxdeg = std::max(maxdeg, std::max(cp.ops.op[i].p, cp.ops.op[i].q));
+    for (int i = 0; i < cp.ops.nops && maxdeg <= 3; ++i) {
+        Op &o = cp.ops.op[i];
+        if (o.kind != 2 || o.cls < CLS_PLANE || o.cls >= CLS_GENERIC || o.src >= 0) continue;
+        if (o.p > 2 || o.q > 2 || o.p % 2) continue;
+        for (int j = 0; j < cp.ops.nops; ++j) {
+            Op &l = cp.ops.op[j];
+            if (l.kind != 1 || l.merged || l.src >= 0 || l.a != o.b || l.cls != CLS_LINE + l.p) continue;
+            if (!(l.p == o.q || (l.p == o.q + 2 && l.p <= 3))) continue;
+            o.mergeB = j;
+            l.merged = 1;
+            break;
+        }
+    }
     // upload
     size_t es = pr->cfg.dtype == HX_C64 ? sizeof(float) : sizeof(double);
     size_t tab_bytes = std::max<size_t>(cp.tab.size(), 1) * es;
@@ -544,35 +569,21 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
         pr->chan_ld = ld;
         if (pr->nch) HX_CUDA(cudaMalloc(&pr->chan, ld * es2 * pr->nch), "cudaMalloc(channels)");
     }
-    // work items: <= kItemElems elements and a slab count whose neighbour table fits shared memory
-    int nd = std::max(cp.ops.ndelta, cp.ops1.ndelta);
-    int spi = std::max(1, std::min(64, (32 * 1024) / (int)(sizeof(int2) * nd)));
-    pr->slabs_per_item = spi;
+    // row-offset table: kept when the offsets are those of the previous potential
     const IndexSetHost &h = set->h;
-    std::vector<int4> items;
-    int s = 0;
-    while (s < h.nslab) {
-        int e0 = h.slab_start[s];
-        int len = h.slab_start[s + 1] - e0;
-        if (len > kItemElems) {   // split a large slab into full tiles
-            for (int off = 0; off < len; off += kItemElems)
-                items.push_back(make_int4(s, s, e0 + off, e0 + std::min(len, off + kItemElems)));
-            ++s;
-            continue;
-        }
-        int s1 = s;
-        while (s1 + 1 < h.nslab && s1 + 1 - s < spi && h.slab_start[s1 + 2] - e0 <= kItemElems) ++s1;
-        items.push_back(make_int4(s, s1, e0, h.slab_start[s1 + 1]));
-        s = s1 + 1;
+    bool same = pr->rnb && pr->roff.n == cp.roff.n && !memcmp(pr->roff.d, cp.roff.d, sizeof(cp.roff.d[0]) * cp.roff.n);
+    if (!same) {
+        if (pr->rnb) cudaFree(pr->rnb);
+        pr->rnb = nullptr;
+        size_t bytes = (size_t)cp.roff.n * std::max(h.nrow, 1) * sizeof(int);
+        HX_CUDA(cudaMalloc((void **)&pr->rnb, bytes), "cudaMalloc(row-offset table)");
+        pr->roff = cp.roff;
+        int rc = launch_rowtab(set->d, pr->roff, pr->rnb, pr->stream);
+        if (rc) return rc;
+        HX_CUDA(cudaStreamSynchronize(pr->stream), "row-offset table");
     }
-    if (pr->items) cudaFree(pr->items);
-    pr->items = nullptr;
-    HX_CUDA(cudaMalloc((void **)&pr->items, items.size() * sizeof(int4)), "cudaMalloc(items)");
-    HX_CUDA(cudaMemcpy(pr->items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice),
-            "upload items");
-    pr->items_h = items;
-    pr->nitems = (int)items.size();
     pr->have_pot = true;
+    pr->generation++;
     return HX_OK;
 }
 
@@ -582,6 +593,7 @@ using namespace hx;
 
 struct hx_indexset : IndexSetObj {};
 struct hx_problem : Problem {};
+struct hx_batch : Batch {};
 
 extern "C" {
 
@@ -603,31 +615,39 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     int rc = build_host_tables(N, (int)B, s->h);
     if (rc) { delete s; return rc; }
     const IndexSetHost &h = s->h;
-    size_t b_start = (size_t)(h.nslab + 1) * sizeof(int);
-    size_t b_k = std::max<size_t>(h.slab_k.size(), 1) * sizeof(uint16_t);
+    size_t b_info = (size_t)std::max(h.nrow, 1) * sizeof(int4);
+    size_t b_k = std::max<size_t>(h.row_k.size(), 1) * sizeof(uint16_t);
+    size_t b_of = (size_t)std::max<int64_t>(h.size, 1) * sizeof(int);
     size_t b_qoff = (size_t)(h.B + 2) * sizeof(int);
     size_t b_Q = std::max<size_t>(h.Q.size(), 1) * sizeof(int);
     size_t b_nt = (size_t)(h.B + 1) * sizeof(int);
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t total = al(b_start) + al(b_k) + al(b_qoff) + al(b_Q) + al(b_nt);
+    size_t total = al(b_info) + al(b_k) + al(b_of) + al(b_qoff) + al(b_Q) + al(b_nt);
     cudaGetDevice(&s->device);
     cudaError_t e = cudaMalloc(&s->dmem, total);
     if (e != cudaSuccess) { delete s; return cuda_fail(e, "cudaMalloc(index tables)"); }
     char *base = (char *)s->dmem;
-    int *d_start = (int *)base;
-    uint16_t *d_k = (uint16_t *)(base + al(b_start));
-    int *d_qoff = (int *)(base + al(b_start) + al(b_k));
-    int *d_Q = (int *)(base + al(b_start) + al(b_k) + al(b_qoff));
-    int *d_nt = (int *)(base + al(b_start) + al(b_k) + al(b_qoff) + al(b_Q));
+    int4 *d_info = (int4 *)base;
+    base += al(b_info);
+    uint16_t *d_k = (uint16_t *)base;
+    base += al(b_k);
+    int *d_of = (int *)base;
+    base += al(b_of);
+    int *d_qoff = (int *)base;
+    base += al(b_qoff);
+    int *d_Q = (int *)base;
+    base += al(b_Q);
+    int *d_nt = (int *)base;
     {
         std::vector<int> nt(h.B + 1, 0);
         for (int x = 1; x <= h.B; ++x) nt[x] = h.B / x;
-        cudaMemcpy(d_nt, nt.data(), b_nt, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(d_nt, nt.data(), b_nt, cudaMemcpyHostToDevice);
     }
-    cudaMemcpy(d_start, h.slab_start.data(), b_start, cudaMemcpyHostToDevice);
-    if (!h.slab_k.empty()) cudaMemcpy(d_k, h.slab_k.data(), h.slab_k.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
-    cudaMemcpy(d_qoff, h.qoff.data(), b_qoff, cudaMemcpyHostToDevice);
-    if (!h.Q.empty()) e = cudaMemcpy(d_Q, h.Q.data(), h.Q.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_info, h.row_info.data(), (size_t)h.nrow * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !h.row_k.empty())
+        e = cudaMemcpy(d_k, h.row_k.data(), h.row_k.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_qoff, h.qoff.data(), b_qoff, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !h.Q.empty()) e = cudaMemcpy(d_Q, h.Q.data(), h.Q.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) {
         cudaFree(s->dmem);
         delete s;
@@ -636,13 +656,23 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     s->d.N = h.N;
     s->d.B = h.B;
     s->d.size = (int)h.size;
-    s->d.nslab = h.nslab;
+    s->d.nrow = h.nrow;
     s->d.qtotal = h.qtotal;
-    s->d.slab_start = d_start;
-    s->d.slab_k = d_k;
+    s->d.row_info = d_info;
+    s->d.row_k = d_k;
+    s->d.row_of = d_of;
     s->d.qoff = d_qoff;
     s->d.Q = d_Q;
     s->d.nt = d_nt;
+    rc = launch_row_of(s);
+    if (rc) {
+        cudaFree(s->dmem);
+        delete s;
+        return rc;
+    }
+    // the host copies of the row tables are no longer needed (rank/unrank use Q and qoff)
+    std::vector<int4>().swap(s->h.row_info);
+    std::vector<uint16_t>().swap(s->h.row_k);
     *out = s;
     return HX_OK;
 }
@@ -716,7 +746,7 @@ void hx_problem_destroy(hx_problem *p)
     krylov_free(p);
     cudaFree(p->tab);
     cudaFree(p->pw_values);
-    cudaFree(p->items);
+    cudaFree(p->rnb);
     cudaFree(p->chan);
     cudaFree(p->dscal);
     for (void *x : p->extra) cudaFree(x);
@@ -820,6 +850,53 @@ int hx_step_host(hx_problem *p, void *c_host, double dt, int nsteps)
         rc = cuda_fail(e, "step_host copy out");
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess && !rc) rc = cuda_fail(e, "step_host sync");
     return rc;
+}
+
+int hx_batch_create(hx_problem *const *probs, int n, hx_batch **out)
+{
+    if (!probs || n < 1 || !out) { set_error("hx_batch_create: need n >= 1 problems and out != NULL"); return HX_EINVAL; }
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!probs[i] || !probs[i]->have_pot) {
+            set_error("hx_batch_create: problem %d is NULL or has no potential", i);
+            return HX_EINVAL;
+        }
+        for (int j = 0; j < i; ++j)
+            if (probs[j] == probs[i]) { set_error("hx_batch_create: problem %d appears twice", i); return HX_EINVAL; }
+    }
+    hx_batch *b = new (std::nothrow) hx_batch();
+    if (!b) { set_error("out of host memory"); return HX_ENOMEM; }
+    b->probs.assign(probs, probs + n);
+    b->stream = probs[0]->stream;
+    *out = b;
+    return HX_OK;
+}
+
+int hx_batch_step(hx_batch *b, void *const *c, double dt, int nsteps)
+{
+    if (!b || !c || nsteps < 0 || !(dt == dt)) { set_error("hx_batch_step: bad argument"); return HX_EINVAL; }
+    for (size_t i = 0; i < b->probs.size(); ++i)
+        if (!c[i]) { set_error("hx_batch_step: state %zu is NULL", i); return HX_EINVAL; }
+    if (nsteps == 0) return HX_OK;
+    return batch_step(b, c, dt, nsteps);
+}
+
+void hx_batch_destroy(hx_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
+    batch_free(b);
+    delete b;
+}
+
+int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step)
+{
+    if (!p) { set_error("hx_step_launches: NULL problem"); return HX_EINVAL; }
+    if (!p->have_pot) { set_error("hx_step_launches: call hx_potential_set first"); return HX_EINVAL; }
+    const int a = apply_launches(p);
+    if (per_apply) *per_apply = a;
+    if (per_step) *per_step = p->cfg.m * (a + 3) + 2;
+    return HX_OK;
 }
 
 int hx_step_info(hx_problem *p, int *m_used, double *alpha, double *beta, double *norm)

@@ -13,12 +13,11 @@ namespace hx {
 
 constexpr int kMaxN = 16;
 constexpr int kMaxOps = 48;
-constexpr int kMaxDelta = 160;                 // distinct outer-axis offsets of one operator set
+constexpr int kMaxDelta = 255;                 // distinct row offsets of one problem (both stages)
 constexpr int kMaxDidx = 4096;                 // footprint -> offset map entries of one operator set
 constexpr int kMaxDeg = HX_MAX_DEG;
 constexpr int kSpan = 2 * kMaxDeg + 1;         // offsets -deg..deg
 constexpr int kMaxKrylov = 32;
-constexpr int kItemElems = 1024;               // elements per work item (tile)
 constexpr int kApplyThreads = 256;
 
 void set_error(const char *fmt, ...);
@@ -27,23 +26,22 @@ int cuda_fail(cudaError_t e, const char *what);
 // ---------------------------------------------------------------------------------------
 // Index set on the device.
 //
-// Canonical order is lexicographic, last coordinate fastest.  The first N-2 axes are the
-// "outer" axes; a slab is the set of elements sharing one outer prefix p, and it is the
-// 2-D hyperbolic cross {(i, j) : (1+i)(1+j) <= floor(B / q(p))}, q(p) = prod (1 + p_l),
-// stored contiguously (row i, then j).  For N <= 2 there is one slab.
+// Canonical order is lexicographic, last coordinate fastest.  A row is the set of elements
+// sharing one prefix p = (k_0, ..., k_{N-2}); it holds k_{N-1} = 0 .. floor(B / q(p)) - 1,
+// q(p) = prod (1 + p_l), stored contiguously, and the rows follow each other in the
+// lexicographic order of their prefixes.  For N = 1 there is one row.
 //
 // Rank tables: for level m >= 1 and prefix product q (1 <= q <= B),
 //   Q_m(q, k) = sum_{i<k} |K_m(floor(B / (q (1 + i))))|,   0 <= k <= floor(B / q),
 // stored at Q[(m - 1) * qtotal + qoff[q] + k].  Then
-//   rank(k) = sum_{d<N-1} Q_{N-1-d}(q_d, k_d) + k_{N-1},   q_d = prod_{l<d} (1 + k_l),
-// the start of a slab with prefix p is the same sum over the outer axes, and the position
-// of (i, j) inside a slab with prefix product q is Q_1(q, i) + j.
+//   rank(k) = sum_{d<N-1} Q_{N-1-d}(q_d, k_d) + k_{N-1},   q_d = prod_{l<d} (1 + k_l).
 // ---------------------------------------------------------------------------------------
 struct DevSet {
-    int N, B, size, nslab, qtotal;
-    const int *slab_start;            // nslab + 1
-    const uint16_t *slab_k;           // nslab x (N - 2) outer prefixes
-    const int *qoff;                  // B + 1
+    int N, B, size, nrow, qtotal;
+    const int4 *row_info;             // nrow: {start rank, q(p), sum_l p_l, length}
+    const uint16_t *row_k;            // nrow x (N - 1) prefixes
+    const int *row_of;                // size: row of each element
+    const int *qoff;                  // B + 2
     const int *Q;                     // (N - 1) x qtotal
     const int *nt;                    // nt[x] = floor(B / x), x = 1..B (nt[0] unused)
 };
@@ -52,12 +50,12 @@ struct IndexSetHost {
     int N;
     int B;
     int64_t size;
-    int nslab;
+    int nrow;
     int qtotal;
-    std::vector<int> qoff;            // B + 1
+    std::vector<int> qoff;            // B + 2
     std::vector<int> Q;               // (N - 1) x qtotal
-    std::vector<int> slab_start;      // nslab + 1
-    std::vector<uint16_t> slab_k;     // nslab x (N - 2)
+    std::vector<int4> row_info;       // nrow
+    std::vector<uint16_t> row_k;      // nrow x (N - 1)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -73,18 +71,21 @@ struct IndexSetHost {
 // ---------------------------------------------------------------------------------------
 // op classes with compile-time stencils (pure parity: P has only terms of the parity of its degree)
 enum { CLS_ID = 0, CLS_LINE = 1, CLS_PLANE = 10, CLS_GENERIC = 30 };
-enum { ROLE_OUT = 0, ROLE_I1 = 1, ROLE_I2 = 2, ROLE_NONE = 3 };
+// axis roles: an axis of the row prefix (moving along it changes the row) or the last axis
+enum { ROLE_ROW = 0, ROLE_LAST = 1, ROLE_NONE = 2 };
 
 struct Op {
     int kind;
-    int cls;                  // CLS_ID, CLS_LINE + p (p <= 3, pure), CLS_PLANE + 3 (p-1) + (q-1) (pure), CLS_GENERIC
-    int ra, rb;               // axis roles: ROLE_OUT (< N-2), ROLE_I1 (N-2), ROLE_I2 (N-1), ROLE_NONE
+    int cls;                  // CLS_ID, CLS_LINE + p, CLS_PLANE + 3 (p-1) + (q-1) (pure parity, p, q <= 3), CLS_GENERIC
+    int ra, rb;               // axis roles: ROLE_ROW (< N-1), ROLE_LAST (N-1), ROLE_NONE
     int a, b;                 // axes (b = -1 for a line op)
     int p, q;                 // degrees on a and b
     int pmask, qmask;         // bit (s + p) set when the rows can be nonzero at offset s
     int tabP, tabQ;           // row table bases
-    int dbase;                // base into didx (footprint position -> outer offset index)
+    int dbase;                // base into didx (footprint position -> row offset index)
     int src, dst;             // input channel (-1 = c), output channel (stage 1 only)
+    int mergeB;               // plane ops: index of a line op on axis b evaluated inside this op (-1: none)
+    int merged;               // line ops: 1 when evaluated inside a plane op (skipped on its own)
     int mod;                  // hx_mod_kind
     double amp, omega, phase;
     int pw_off, pw_n;         // into the pw value array
@@ -93,19 +94,24 @@ struct Op {
 
 struct OpSet {
     int nops;
-    int ndelta;
     double wAB, wBA;          // factor-order weights for plane ops
     int ndidx;
     Op op[kMaxOps];
-    int8_t delta[kMaxDelta][4];       // outer offset: axis0, step0, axis1, step1 (axis -1 = none)
-    uint8_t didx[kMaxDidx];
+    uint8_t didx[kMaxDidx];   // footprint position -> column of the row-offset table
+};
+
+// Row offsets used by a problem's operators: axis0, step0, axis1, step1 (axis -1 = none), over
+// the prefix axes 0..N-2; offset 0 is the zero offset.  The row-offset table holds, for
+// offset d and row r, the start rank of row r + offset d, or -1 when that prefix is not in K:
+//   rnb[d * nrow + r].
+struct RowOffsets {
+    int n;
+    int8_t d[kMaxDelta][4];
 };
 
 struct ApplyArgsBase {
     DevSet S;
-    const int4 *items;        // {slab_first, slab_last, e0, e1}
-    int nitems;
-    int slabs_per_item;
+    const int *rnb;           // row-offset table, nd x nrow
     const double *t_ptr;      // device time
     double t_shift;           // A is evaluated at *t_ptr + t_shift
     const double *pw_values;  // device
@@ -141,15 +147,15 @@ struct Problem {
     double t_host;
     // compiled potential
     bool have_pot;
+    int generation;           // incremented by every hx_potential_set (cached batch graphs check it)
     OpSet ops;                // main stage (accumulates y)
     OpSet ops1;               // first stage (writes channels), nops = 0 if unused
     int nch;                  // channel vectors
     void *chan;
     size_t chan_ld;           // elements between channels
-    std::vector<int4> items_h;
-    int4 *items;
-    int nitems;
-    int slabs_per_item;
+    RowOffsets roff;          // row offsets of ops and ops1
+    int *rnb;                 // row-offset table (device), roff.n x nrow
+    bool skip_diag;           // internal: omit D_K (gradient direction operators)
     void *tab;                // device row tables
     size_t tab_bytes;
     double *pw_values;
@@ -167,10 +173,40 @@ struct Problem {
 int launch_apply(Problem *p, const void *cin, void *cout, const double *t_ptr, double t_shift,
                  const ApplyFuse *fuse, cudaStream_t st);
 int launch_export(const IndexSetObj *s, int32_t *k_dev, cudaStream_t st);
+int launch_row_of(const IndexSetObj *s);
+int launch_rowtab(const DevSet &S, const RowOffsets &ro, int *rnb, cudaStream_t st);
 int launch_norm(Problem *p, const void *c, int is_c128, double *partials, unsigned *counter, double *result,
                 cudaStream_t st);
 int apply_grid(const Problem *p);
 int apply_launches(const Problem *p);   // kernels per product (1, or 2 with a channel stage)
+
+// Lanczos workspaces outside the step graph (hx_krylov.cu), used by the adjoint gradient
+struct LanczosWS {
+    void *sc;          // device scalars
+    void *V;           // (m + 1) complex128 vectors
+    double *partials;
+    size_t vec_bytes;
+    int m;
+};
+int lanczos_alloc(Problem *p, int m, LanczosWS *L);
+void lanczos_free(LanczosWS *L);
+int lanczos_enqueue(Problem *p, LanczosWS *L, const double2 *c, const double *t_ptr, double t_shift, cudaStream_t st);
+int lanczos_exp(Problem *p, LanczosWS *L, double h, double2 *out, cudaStream_t st);
+int lanczos_project(Problem *p, LanczosWS *L, const double2 *w, double *Mcol, cudaStream_t st);
+int lanczos_apply_basis(Problem *px, LanczosWS *L, int r, double2 *out, const double *t_ptr, cudaStream_t st);
+int adjoint_term(LanczosWS *Lp, LanczosWS *Ll, const double *M, double dt, double *gacc, cudaStream_t st);
+
+// Batches of independent problems stepped by one graph (hx_krylov.cu)
+struct Batch {
+    std::vector<Problem *> probs;
+    std::vector<void *> cptr;
+    std::vector<int> gen;     // member generations the graph was captured with
+    cudaGraphExec_t exec = nullptr;
+    double dt = 0.0;
+    cudaStream_t stream = nullptr;
+};
+int batch_step(Batch *b, void *const *c, double dt, int nsteps);
+void batch_free(Batch *b);
 
 // Krylov stepping (hx_krylov.cu)
 int krylov_step(Problem *p, void *c, double dt, int nsteps);

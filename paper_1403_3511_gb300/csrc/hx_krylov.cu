@@ -17,6 +17,8 @@
 // normalisation.  All scalars live in device memory, so the step has no host round trip.
 #include <math.h>
 
+#include <type_traits>
+
 #include "hx_internal.h"
 
 namespace hx {
@@ -30,10 +32,12 @@ struct Scal {                       // device scalars of one problem
     double h[2 * (kMaxKrylov + 1)];
     double h2[2 * (kMaxKrylov + 1)];
     double y[2 * kMaxKrylov];
+    double Q[kMaxKrylov * kMaxKrylov];   // eigenvectors of T_m (row-major, m_used x m_used)
+    double lam[kMaxKrylov];              // eigenvalues of T_m
     double scale;                   // running max_i(|alpha_i| + beta_{i-1}) for the breakdown test
     double norm_out;
     int m_used;
-    int flags;                      // bit 0: breakdown seen, bit 1: non-finite
+    int flags;                      // bit 0: breakdown seen, bit 1: non-finite, bit 2: eigensolver stalled
     unsigned counter;
 };
 
@@ -171,12 +175,15 @@ template <> struct Real<float2> { using T = float; };
 template <> struct Real<double2> { using T = double; };
 
 // h_i = s_i <v_i, w> for i <= k.
+// proj = 1 (projection onto a finished basis): k is clipped to the vectors actually built.
 template <typename V, int NV>
-__global__ void __launch_bounds__(256) dot_kernel(const V *w, const V *Vb, size_t ld, int n, int k, double *partials, Scal *sc)
+__global__ void __launch_bounds__(256) dot_kernel(const V *w, const V *Vb, size_t ld, int n, int k, double *partials, Scal *sc,
+                                                  int proj = 0)
 {
     __shared__ double red[32];
     __shared__ double tot[2 * NV];
-    if (k >= sc->m_used) return;
+    if (proj) k = min(k, sc->m_used - 1);
+    if (k < 0 || k >= sc->m_used) return;
     CAcc<V> acc[NV];
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         V x = w[e];
@@ -275,99 +282,140 @@ __global__ void __launch_bounds__(256) update_kernel(V *w, const V *Vb, size_t l
     }
 }
 
-// T_m = Q diag(lambda) Q^T by cyclic Jacobi rotations (Jacobi's method, Golub & Van Loan Sec. 8.5),
-// y = beta_0 Q exp(-i h lambda) Q^T e_1; stored as y_i * s_i for the combination pass.  One warp:
-// the rotation angle is computed by every lane, the rows and columns it touches are updated one
-// lane per index.  Also advances the problem time by h.
+// T_m = Q diag(lambda) Q^T by the implicit-shift QL iteration for symmetric tridiagonal matrices
+// (Bowdler, Martin, Reinsch and Wilkinson, "The QR and QL algorithms for symmetric matrices",
+// Numer. Math. 11, 1968): a shift from the leading 2 x 2 block, then a chase of plane rotations
+// from the bottom of the unreduced block up; an off-diagonal entry is zero once it is below
+// 2^-53 (|d_i| + |d_{i+1}|).  One warp: every lane runs the same scalar recurrence (so all lanes
+// agree on every rotation) and applies each rotation to its own row of Q.
+// y = beta_0 Q exp(-i h lambda) Q^T e_1, stored as y_i * s_i for the combination pass; also
+// advances the problem time by h.
 __global__ void __launch_bounds__(32) eig_kernel(Scal *sc, double h)
 {
-    __shared__ double A[kMaxKrylov * kMaxKrylov], Qm[kMaxKrylov * kMaxKrylov];
-    __shared__ double cph[kMaxKrylov], sph[kMaxKrylov];
     const int lane = threadIdx.x;
     const int m = sc->m_used;
-    for (int i = 0; i < m; ++i)
-        if (lane < m) {
-            const int j = lane;
-            A[i * m + j] = i == j ? sc->alpha[i] : ((j == i + 1 || i == j + 1) ? sc->beta[i < j ? i : j] : 0.0);
-            Qm[i * m + j] = i == j ? 1.0 : 0.0;
-        }
-    __syncwarp();
-    double nr = 0.0;
-    for (int i = 0; i < m; ++i) nr += A[i * m + i] * A[i * m + i] + (i + 1 < m ? 2.0 * A[i * m + i + 1] * A[i * m + i + 1] : 0.0);
-    for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0.0;
-        if (lane < m)
-            for (int j = lane + 1; j < m; ++j) off += A[lane * m + j] * A[lane * m + j];
-        for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
-        if (off <= 1e-34 * nr) break;
-        for (int p = 0; p < m; ++p)
-            for (int q = p + 1; q < m; ++q) {
-                const double apq = A[p * m + q];
-                if (apq == 0.0) continue;
-                const double theta = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                __syncwarp();
-                if (lane < m) {                      // A <- A J (columns p, q)
-                    const double arp = A[lane * m + p], arq = A[lane * m + q];
-                    A[lane * m + p] = c * arp - s * arq;
-                    A[lane * m + q] = s * arp + c * arq;
-                }
-                __syncwarp();
-                if (lane < m) {                      // A <- J^T A (rows p, q)
-                    const double apr = A[p * m + lane], aqr = A[q * m + lane];
-                    A[p * m + lane] = c * apr - s * aqr;
-                    A[q * m + lane] = s * apr + c * aqr;
-                    const double qrp = Qm[lane * m + p], qrq = Qm[lane * m + q];   // Q <- Q J
-                    Qm[lane * m + p] = c * qrp - s * qrq;
-                    Qm[lane * m + q] = s * qrp + c * qrq;
-                }
-                __syncwarp();
+    double d[kMaxKrylov], e[kMaxKrylov], z[kMaxKrylov];   // diagonal, off-diagonal (i, i+1), row `lane` of Q
+    for (int i = 0; i < m; ++i) {
+        d[i] = sc->alpha[i];
+        e[i] = i + 1 < m ? sc->beta[i] : 0.0;
+        z[i] = i == lane ? 1.0 : 0.0;
+    }
+    const double tiny = 0x1p-53;
+    for (int l = 0; l < m; ++l) {
+        for (int iter = 0;; ++iter) {
+            int u = l;                                  // end of the unreduced block starting at l
+            while (u < m - 1 && fabs(e[u]) > tiny * (fabs(d[u]) + fabs(d[u + 1]))) ++u;
+            if (u == l) break;
+            if (iter == 60) {                           // no convergence: report, keep what we have
+                if (lane == 0) sc->flags |= 4;
+                break;
             }
-    }
-    if (lane < m) {
-        const double ph = -h * A[lane * m + lane];
-        cph[lane] = cos(ph);
-        sph[lane] = sin(ph);
-    }
-    __syncwarp();
-    if (lane < m) {
-        double yr = 0.0, yi = 0.0;
-        for (int j = 0; j < m; ++j) {
-            const double w = Qm[lane * m + j] * Qm[0 * m + j];
-            yr += w * cph[j];
-            yi += w * sph[j];
+            // shift: the eigenvalue of the leading 2 x 2 block closer to d_l
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = hypot(g, 1.0);
+            g = d[u] - d[l] + e[l] / (g + copysign(r, g));
+            double sn = 1.0, cs = 1.0, p = 0.0;
+            bool restart = false;
+            for (int i = u - 1; i >= l; --i) {
+                const double f = sn * e[i], b = cs * e[i];
+                r = hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) {                         // the block splits: deflate and start again
+                    d[i + 1] -= p;
+                    e[u] = 0.0;
+                    restart = true;
+                    break;
+                }
+                sn = f / r;
+                cs = g / r;
+                g = d[i + 1] - p;
+                r = (d[i] - g) * sn + 2.0 * cs * b;
+                p = sn * r;
+                d[i + 1] = g + p;
+                g = cs * r - b;
+                const double zi = z[i], zi1 = z[i + 1];   // Q <- Q G(i, i+1)
+                z[i + 1] = sn * zi + cs * zi1;
+                z[i] = cs * zi - sn * zi1;
+            }
+            if (restart) continue;
+            d[l] -= p;
+            e[l] = g;
+            e[u] = 0.0;
         }
+    }
+    double yr = 0.0, yi = 0.0;
+    for (int j = 0; j < m; ++j) {
+        const double q0 = __shfl_sync(0xffffffffu, z[j], 0);   // Q_{0 j}
+        const double ph = -h * d[j];
+        const double w = z[j] * q0;
+        yr += w * cos(ph);
+        yi += w * sin(ph);
+        if (lane < m) sc->Q[lane * m + j] = z[j];
+    }
+    if (lane < m) {
+        sc->lam[lane] = d[lane];
         sc->y[2 * lane] = sc->beta0 * yr * sc->s[lane];
         sc->y[2 * lane + 1] = sc->beta0 * yi * sc->s[lane];
     }
     if (lane == 0) sc->t += h;
 }
 
-// c = sum_i y_i v_i (complex128 accumulation), and ||c||^2 for hx_step_info.
+// c = sum_i y_i v_i, and ||c||^2 for hx_step_info.  Complex128 vectors accumulate in FP64; for
+// complex64 vectors each y_i is split into float parts hi + lo and the sum is accumulated with
+// the compensated products of F2 (Dot2), which keeps it as accurate as FP64 accumulation (relative
+// error of order 2^-48 of sum |y_i v_i|) without FP64 arithmetic per element.
 template <typename V, int NV>
 __global__ void combine_kernel(double2 *c, const V *Vb, size_t ld, int n, double *partials, Scal *sc)
 {
     __shared__ double red[32];
     const int m = sc->m_used;
-    double yr[NV], yi[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        yr[i] = i < m ? sc->y[2 * i] : 0.0;
-        yi[i] = i < m ? sc->y[2 * i + 1] : 0.0;
-    }
     double acc = 0.0;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        double xr = 0.0, xi = 0.0;
+    if constexpr (std::is_same<V, float2>::value) {
+        float yrh[NV], yrl[NV], yih[NV], yil[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const double yr = i < m ? sc->y[2 * i] : 0.0, yi = i < m ? sc->y[2 * i + 1] : 0.0;
+            yrh[i] = (float)yr;
+            yrl[i] = (float)(yr - (double)yrh[i]);
+            yih[i] = (float)yi;
+            yil[i] = (float)(yi - (double)yih[i]);
+        }
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+            F2 xr, xi;
 #pragma unroll(NV <= 8 ? NV : 1)
-        for (int i = 0; i < NV; ++i)
-            if (i < m) {
-                V v = Vb[i * ld + e];
-                xr += yr[i] * v.x - yi[i] * v.y;
-                xi += yr[i] * v.y + yi[i] * v.x;
-            }
-        c[e] = make_double2(xr, xi);
-        acc += xr * xr + xi * xi;
+            for (int i = 0; i < NV; ++i)
+                if (i < m) {
+                    const float2 v = Vb[i * ld + e];
+                    xr.add_prod(yrh[i], v.x);
+                    xr.add_prod(-yih[i], v.y);
+                    xr.c = fmaf(yrl[i], v.x, fmaf(-yil[i], v.y, xr.c));
+                    xi.add_prod(yrh[i], v.y);
+                    xi.add_prod(yih[i], v.x);
+                    xi.c = fmaf(yrl[i], v.y, fmaf(yil[i], v.x, xi.c));
+                }
+            const double2 x = make_double2(xr.value(), xi.value());
+            c[e] = x;
+            acc += x.x * x.x + x.y * x.y;
+        }
+    } else {
+        double yr[NV], yi[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            yr[i] = i < m ? sc->y[2 * i] : 0.0;
+            yi[i] = i < m ? sc->y[2 * i + 1] : 0.0;
+        }
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+            double xr = 0.0, xi = 0.0;
+#pragma unroll(NV <= 8 ? NV : 1)
+            for (int i = 0; i < NV; ++i)
+                if (i < m) {
+                    const V v = Vb[i * ld + e];
+                    xr += yr[i] * v.x - yi[i] * v.y;
+                    xi += yr[i] * v.y + yi[i] * v.x;
+                }
+            c[e] = make_double2(xr, xi);
+            acc += xr * xr + xi * xi;
+        }
     }
     __shared__ double tot[1];
     if (reduce_partials(&acc, 1, partials, &sc->counter, red, tot) && threadIdx.x == 0) {
@@ -379,7 +427,7 @@ __global__ void combine_kernel(double2 *c, const V *Vb, size_t ld, int n, double
 }
 
 template <typename V, int NV>
-static int enqueue_step(Problem *p, Work *w, cudaStream_t st, double dt)
+static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, double dt)
 {
     const int n = p->set->d.size;
     const int m = p->cfg.m;
@@ -388,7 +436,7 @@ static int enqueue_step(Problem *p, Work *w, cudaStream_t st, double dt)
     V *Vb = (V *)w->V;
     const size_t ld = w->vec_bytes / sizeof(V);
     Scal *sc = w->sc;
-    init_kernel<V><<<G, T, 0, st>>>(w->state, Vb, n, w->partials, sc, m);
+    init_kernel<V><<<G, T, 0, st>>>(state, Vb, n, w->partials, sc, m);
     for (int k = 0; k < m; ++k) {
         ApplyFuse f;
         memset(&f, 0, sizeof(f));
@@ -401,18 +449,19 @@ static int enqueue_step(Problem *p, Work *w, cudaStream_t st, double dt)
         if (k < m - 1) update_kernel<V, NV><<<G, T, 0, st>>>(wv, Vb, ld, n, k, 1, w->partials, sc);
     }
     eig_kernel<<<1, 32, 0, st>>>(sc, dt);
-    combine_kernel<V, NV><<<G, T, 0, st>>>(w->state, Vb, ld, n, w->partials, sc);
+    combine_kernel<V, NV><<<G, T, 0, st>>>(state, Vb, ld, n, w->partials, sc);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     return HX_OK;
 }
 
-static int enqueue(Problem *p, Work *w, cudaStream_t st, double dt)
+static int enqueue(Problem *p, Work *w, double2 *state, cudaStream_t st, double dt)
 {
     const bool c64 = p->cfg.dtype == HX_C64;
     if (p->cfg.m <= 8)
-        return c64 ? enqueue_step<float2, 8>(p, w, st, dt) : enqueue_step<double2, 8>(p, w, st, dt);
-    return c64 ? enqueue_step<float2, kMaxKrylov>(p, w, st, dt) : enqueue_step<double2, kMaxKrylov>(p, w, st, dt);
+        return c64 ? enqueue_step<float2, 8>(p, w, state, st, dt) : enqueue_step<double2, 8>(p, w, state, st, dt);
+    return c64 ? enqueue_step<float2, kMaxKrylov>(p, w, state, st, dt)
+               : enqueue_step<double2, kMaxKrylov>(p, w, state, st, dt);
 }
 
 static int ensure_work(Problem *p)
@@ -473,7 +522,7 @@ int krylov_step(Problem *p, void *c, double dt, int nsteps)
         cudaGraph_t g;
         if ((e = cudaStreamBeginCapture(w->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return cuda_fail(e, "begin capture");
-        rc = enqueue(p, w, w->cap_stream, dt);
+        rc = enqueue(p, w, w->state, w->cap_stream, dt);
         e = cudaStreamEndCapture(w->cap_stream, &g);
         if (rc) return rc;
         if (e != cudaSuccess) return cuda_fail(e, "end capture");
@@ -519,8 +568,281 @@ int krylov_info(Problem *p, int *m_used, double *alpha, double *beta, double *no
     }
     if (norm) *norm = sc.norm_out;
     if (sc.flags & 2) { set_error("non-finite norm in a time step"); return HX_ENONFINITE; }
+    if (sc.flags & 4) { set_error("tridiagonal eigensolver did not converge in 60 iterations"); return HX_ENONFINITE; }
     if (sc.flags & 1) { set_error("Lanczos breakdown: fewer than m vectors were used"); return HX_EBREAKDOWN; }
     return HX_OK;
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Batches: one graph per step with every problem's step as an independent child graph
+// ---------------------------------------------------------------------------------------
+int batch_step(Batch *b, void *const *c, double dt, int nsteps)
+{
+    const int np = (int)b->probs.size();
+    for (Problem *p : b->probs) {
+        int rc = ensure_work(p);
+        if (rc) return rc;
+    }
+    // a member whose potential was set again since the capture has new tables: capture again
+    bool same = b->exec && b->dt == dt;
+    for (int i = 0; same && i < np; ++i) same = b->cptr[i] == c[i] && b->gen[i] == b->probs[i]->generation;
+    cudaError_t e;
+    if (!same) {
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        cudaGraph_t g;
+        if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return cuda_fail(e, "batch graph");
+        for (int i = 0; i < np; ++i) {
+            Problem *p = b->probs[i];
+            Work *w = work_of(p);
+            cudaGraph_t child;
+            if ((e = cudaStreamBeginCapture(w->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return cuda_fail(e, "batch capture");
+            }
+            int rc = enqueue(p, w, (double2 *)c[i], w->cap_stream, dt);
+            e = cudaStreamEndCapture(w->cap_stream, &child);
+            if (rc || e != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return rc ? rc : cuda_fail(e, "batch capture");
+            }
+            cudaGraphNode_t node;
+            e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, child);
+            cudaGraphDestroy(child);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return cuda_fail(e, "batch child node");
+            }
+        }
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { b->exec = nullptr; return cuda_fail(e, "batch instantiate"); }
+        b->cptr.assign(c, c + np);
+        b->gen.resize(np);
+        for (int i = 0; i < np; ++i) b->gen[i] = b->probs[i]->generation;
+        b->dt = dt;
+    }
+    cudaStream_t st = b->stream;
+    for (Problem *p : b->probs) {
+        Work *w = work_of(p);
+        if ((e = cudaMemcpyAsync(&w->sc->t, p->dscal, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(&w->sc->flags, 0, sizeof(int), st)) != cudaSuccess)
+            return cuda_fail(e, "batch set-up");
+    }
+    for (int s = 0; s < nsteps; ++s)
+        if ((e = cudaGraphLaunch(b->exec, st)) != cudaSuccess) return cuda_fail(e, "batch graph launch");
+    for (Problem *p : b->probs) {
+        Work *w = work_of(p);
+        if ((e = cudaMemcpyAsync(p->dscal, &w->sc->t, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "batch copy-out");
+        p->t_host += dt * nsteps;
+    }
+    return HX_OK;
+}
+
+void batch_free(Batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+}
+
+// ---------------------------------------------------------------------------------------
+// Lanczos workspaces outside the step graph (used by the adjoint gradient): the same kernels,
+// complex128 vectors, launched directly.
+// ---------------------------------------------------------------------------------------
+int lanczos_alloc(Problem *p, int m, LanczosWS *L)
+{
+    memset(L, 0, sizeof(*L));
+    const size_t n = (size_t)p->set->h.size;
+    L->vec_bytes = ((n * 16 + 255) / 256) * 256;
+    L->m = m;
+    const int G = apply_grid(p);
+    cudaError_t e;
+    if ((e = cudaMalloc(&L->V, L->vec_bytes * (m + 1))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&L->partials, (size_t)G * 2 * (kMaxKrylov + 2) * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&L->sc, sizeof(Scal))) != cudaSuccess) {
+        lanczos_free(L);
+        return cuda_fail(e, "cudaMalloc(Lanczos workspace)");
+    }
+    cudaMemset(L->sc, 0, sizeof(Scal));
+    return HX_OK;
+}
+
+void lanczos_free(LanczosWS *L)
+{
+    cudaFree(L->V);
+    cudaFree(L->partials);
+    cudaFree(L->sc);
+    memset(L, 0, sizeof(*L));
+}
+
+template <int NV>
+static int lanczos_enqueue_t(Problem *p, LanczosWS *L, const double2 *c, const double *t_ptr, double t_shift,
+                             cudaStream_t st)
+{
+    const int n = p->set->d.size, m = L->m, G = apply_grid(p), T = 256;
+    double2 *Vb = (double2 *)L->V;
+    const size_t ld = L->vec_bytes / sizeof(double2);
+    Scal *sc = (Scal *)L->sc;
+    init_kernel<double2><<<G, T, 0, st>>>(c, Vb, n, L->partials, sc, m);
+    for (int k = 0; k < m; ++k) {
+        ApplyFuse f;
+        memset(&f, 0, sizeof(f));
+        f.in_scale = &sc->s[k];
+        int rc = launch_apply(p, Vb + (size_t)k * ld, Vb + (size_t)(k + 1) * ld, t_ptr, t_shift, &f, st);
+        if (rc) return rc;
+        double2 *wv = Vb + (size_t)(k + 1) * ld;
+        dot_kernel<double2, NV><<<G, T, 0, st>>>(wv, Vb, ld, n, k, L->partials, sc);
+        update_kernel<double2, NV><<<G, T, 0, st>>>(wv, Vb, ld, n, k, 0, L->partials, sc);
+        if (k < m - 1) update_kernel<double2, NV><<<G, T, 0, st>>>(wv, Vb, ld, n, k, 1, L->partials, sc);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HX_OK : cuda_fail(e, "Lanczos kernel launch");
+}
+
+int lanczos_enqueue(Problem *p, LanczosWS *L, const double2 *c, const double *t_ptr, double t_shift, cudaStream_t st)
+{
+    return L->m <= 8 ? lanczos_enqueue_t<8>(p, L, c, t_ptr, t_shift, st)
+                     : lanczos_enqueue_t<kMaxKrylov>(p, L, c, t_ptr, t_shift, st);
+}
+
+// Eigen-decomposition of T (kept in the workspace) and, when out != nullptr,
+// out = beta_0 V Q exp(-i h Lambda) Q^T e_1.
+int lanczos_exp(Problem *p, LanczosWS *L, double h, double2 *out, cudaStream_t st)
+{
+    const int n = p->set->d.size, G = apply_grid(p);
+    Scal *sc = (Scal *)L->sc;
+    eig_kernel<<<1, 32, 0, st>>>(sc, h);
+    if (out) {
+        const size_t ld = L->vec_bytes / sizeof(double2);
+        if (L->m <= 8) combine_kernel<double2, 8><<<G, 256, 0, st>>>(out, (const double2 *)L->V, ld, n, L->partials, sc);
+        else combine_kernel<double2, kMaxKrylov><<<G, 256, 0, st>>>(out, (const double2 *)L->V, ld, n, L->partials, sc);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HX_OK : cuda_fail(e, "Lanczos exp launch");
+}
+
+// out = (operator of px) v_r for the orthonormal Lanczos vector v_r of L.
+int lanczos_apply_basis(Problem *px, LanczosWS *L, int r, double2 *out, const double *t_ptr, cudaStream_t st)
+{
+    Scal *sc = (Scal *)L->sc;
+    ApplyFuse f;
+    memset(&f, 0, sizeof(f));
+    f.in_scale = &sc->s[r];
+    const size_t ld = L->vec_bytes / sizeof(double2);
+    return launch_apply(px, (const double2 *)L->V + (size_t)r * ld, out, t_ptr, 0.0, &f, st);
+}
+
+// Mcol[2 i .. 2 i + 1] = <v_i, w> for the orthonormal Lanczos vectors v_i, i < m_used.
+__global__ void copy_h_kernel(const Scal *sc, double *Mcol, int m)
+{
+    for (int i = threadIdx.x; i < 2 * m; i += blockDim.x) Mcol[i] = i < 2 * sc->m_used ? sc->h[i] : 0.0;
+}
+
+int lanczos_project(Problem *p, LanczosWS *L, const double2 *w, double *Mcol, cudaStream_t st)
+{
+    const int n = p->set->d.size, G = apply_grid(p);
+    Scal *sc = (Scal *)L->sc;
+    const size_t ld = L->vec_bytes / sizeof(double2);
+    // dot_kernel with k = m - 1 projects on every stored vector (vectors beyond m_used are skipped)
+    if (L->m <= 8) dot_kernel<double2, 8><<<G, 256, 0, st>>>(w, (const double2 *)L->V, ld, n, L->m - 1, L->partials, sc, 1);
+    else dot_kernel<double2, kMaxKrylov><<<G, 256, 0, st>>>(w, (const double2 *)L->V, ld, n, L->m - 1, L->partials, sc, 1);
+    copy_h_kernel<<<1, 64, 0, st>>>(sc, Mcol, L->m);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HX_OK : cuda_fail(e, "projection launch");
+}
+
+// (e^z - 1) / z for z = i theta, theta real.
+__device__ double2 phi1_imag(double theta)
+{
+    if (fabs(theta) < 1e-4) {
+        const double t2 = theta * theta;
+        return make_double2(1.0 - t2 / 6.0 + t2 * t2 / 120.0, theta / 2.0 - theta * t2 / 24.0);
+    }
+    return make_double2(sin(theta) / theta, (1.0 - cos(theta)) / theta);
+}
+
+// Adds to *gacc (complex) the sub-step term of d<phi, psi_M>/du,
+//   -i dt integral_0^1 (e^{i(1-s) dt A} lambda_n)^H X (e^{-i s dt A} psi_{n-1}) ds,
+// with both exponentials in their Krylov spaces (Lanczos of psi_{n-1} in Lp, of lambda_n in Ll,
+// eigen-decompositions already stored): with T_psi = Q_p diag(mu) Q_p^T, T_lam = Q_l diag(lam) Q_l^T,
+// a = Q_l^T e_1, b = Q_p^T e_1 and M_pr = <v^l_p, X v^p_r>, the term is
+//   -i dt beta_l beta_p sum_{p,r} M_pr sum_{j,k} Q_l[p,j] Q_p[r,k] a_j b_k e^{-i dt lam_j} phi_1(-i dt (mu_k - lam_j)),
+// phi_1(z) = (e^z - 1)/z, because integral_0^1 e^{-i dt ((1-s) lam_j + s mu_k)} ds = e^{-i dt lam_j} phi_1(...).
+__global__ void __launch_bounds__(32) adjoint_term_kernel(const Scal *Sp, const Scal *Sl, const double *M, int mmax,
+                                                          double dt, double *gacc)
+{
+    __shared__ double Fr[kMaxKrylov * kMaxKrylov], Fi[kMaxKrylov * kMaxKrylov];
+    __shared__ double Gr[kMaxKrylov * kMaxKrylov], Gi[kMaxKrylov * kMaxKrylov];
+    const int lane = threadIdx.x;
+    const int mp = Sp->m_used, ml = Sl->m_used;
+    // F_jk = a_j b_k e^{-i dt lam_j} phi_1(-i dt (mu_k - lam_j))
+    for (int idx = lane; idx < ml * mp; idx += 32) {
+        const int j = idx / mp, k = idx % mp;
+        const double aj = Sl->Q[0 * ml + j], bk = Sp->Q[0 * mp + k];
+        const double2 ph = phi1_imag(-dt * (Sp->lam[k] - Sl->lam[j]));
+        const double c = cos(dt * Sl->lam[j]), s = -sin(dt * Sl->lam[j]);
+        Fr[idx] = aj * bk * (c * ph.x - s * ph.y);
+        Fi[idx] = aj * bk * (c * ph.y + s * ph.x);
+    }
+    __syncwarp();
+    // H = F Q_p^T, then G = Q_l H
+    for (int idx = lane; idx < ml * mp; idx += 32) {
+        const int j = idx / mp, r = idx % mp;
+        double hr = 0.0, hi = 0.0;
+        for (int k = 0; k < mp; ++k) {
+            const double q = Sp->Q[r * mp + k];
+            hr += Fr[j * mp + k] * q;
+            hi += Fi[j * mp + k] * q;
+        }
+        Gr[idx] = hr;
+        Gi[idx] = hi;
+    }
+    __syncwarp();
+    double gr_loc[kMaxKrylov], gi_loc[kMaxKrylov];   // this lane's entries of G, written after all reads
+    int cnt = 0;
+    for (int idx = lane; idx < ml * mp; idx += 32, ++cnt) {
+        const int pp = idx / mp, r = idx % mp;
+        double gr = 0.0, gi = 0.0;
+        for (int j = 0; j < ml; ++j) {
+            const double ql = Sl->Q[pp * ml + j];
+            gr += ql * Gr[j * mp + r];
+            gi += ql * Gi[j * mp + r];
+        }
+        gr_loc[cnt] = gr;
+        gi_loc[cnt] = gi;
+    }
+    __syncwarp();
+    cnt = 0;
+    for (int idx = lane; idx < ml * mp; idx += 32, ++cnt) {
+        Gr[idx] = gr_loc[cnt];
+        Gi[idx] = gi_loc[cnt];
+    }
+    __syncwarp();
+    // sum_{p,r} M_pr G_pr, M stored by columns: M[(r * mmax + p) * 2 + {0,1}] = <v^l_p, X v^p_r>
+    double sr = 0.0, si = 0.0;
+    for (int idx = lane; idx < ml * mp; idx += 32) {
+        const int pp = idx / mp, r = idx % mp;
+        const double mr = M[(r * mmax + pp) * 2], mi = M[(r * mmax + pp) * 2 + 1];
+        sr += mr * Gr[idx] - mi * Gi[idx];
+        si += mr * Gi[idx] + mi * Gr[idx];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) {
+        const double scale = dt * Sl->beta0 * Sp->beta0;   // times -i
+        gacc[0] += scale * si;
+        gacc[1] += -scale * sr;
+    }
+}
+
+int adjoint_term(LanczosWS *Lp, LanczosWS *Ll, const double *M, double dt, double *gacc, cudaStream_t st)
+{
+    adjoint_term_kernel<<<1, 32, 0, st>>>((const Scal *)Lp->sc, (const Scal *)Ll->sc, M, Ll->m, dt, gacc);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HX_OK : cuda_fail(e, "adjoint term launch");
 }
 
 }  // namespace hx

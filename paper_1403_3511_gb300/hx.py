@@ -42,6 +42,11 @@ class hx_potential(ctypes.Structure):
     _fields_ = [("L", ctypes.c_double), ("n_terms", ctypes.c_int), ("terms", ctypes.POINTER(hx_term))]
 
 
+class hx_control(ctypes.Structure):
+    _fields_ = [("axis", ctypes.c_int), ("n_intervals", ctypes.c_int), ("substeps", ctypes.c_int),
+                ("t0", ctypes.c_double), ("t1", ctypes.c_double), ("u", ctypes.POINTER(ctypes.c_double))]
+
+
 class hx_config(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("order", ctypes.c_int), ("m", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
@@ -70,7 +75,13 @@ def _load():
         "hx_step": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int]),
         "hx_step_host": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int]),
         "hx_step_info": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), dp, dp, dp]),
+        "hx_step_launches": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "hx_norm": (ctypes.c_int, [P, P, dp]),
+        "hx_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P)]),
+        "hx_batch_step": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.c_double, ctypes.c_int]),
+        "hx_batch_destroy": (None, [P]),
+        "hx_adjoint_grad": (ctypes.c_int, [P, ctypes.POINTER(hx_config), ctypes.POINTER(hx_potential),
+                                           ctypes.POINTER(hx_control), P, P, dp, dp]),
         "hx_norm_noalloc": (ctypes.c_int, [P, P, dp]),
         "hx_cheb_nodes": (ctypes.c_int, [ctypes.c_int, dp]),
         "hx_cheb_coeffs": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp, dp]),
@@ -154,9 +165,7 @@ def hx_problem_destroy(p):
     lib.hx_problem_destroy(p)
 
 
-def hx_potential_set(p, L: float, terms: list, t: float = 0.0):
-    """terms: list of dicts {axes: [a] or [a, b], coef: ndarray (deg+1,) or (deg_a+1, deg_b+1),
-    mod: hx_mod_kind, amp, omega, phase, pw_values, pw_t0, pw_t1}."""
+def _potential(L: float, terms: list):
     keep = []
     arr = (hx_term * max(len(terms), 1))()
     for i, t_ in enumerate(terms):
@@ -180,7 +189,13 @@ def hx_potential_set(p, L: float, terms: list, t: float = 0.0):
             tm.pw_n = len(pw)
             tm.pw_t0 = t_["pw_t0"]
             tm.pw_t1 = t_["pw_t1"]
-    pot = hx_potential(L, len(terms), arr)
+    return hx_potential(L, len(terms), arr), (keep, arr)
+
+
+def hx_potential_set(p, L: float, terms: list, t: float = 0.0):
+    """terms: list of dicts {axes: [a] or [a, b], coef: ndarray (deg+1,) or (deg_a+1, deg_b+1),
+    mod: hx_mod_kind, amp, omega, phase, pw_values, pw_t0, pw_t1}."""
+    pot, _keep = _potential(L, terms)
     _check(lib.hx_potential_set(p, ctypes.byref(pot), t))
 
 
@@ -220,6 +235,29 @@ def hx_step_info(p, m: int = 32) -> dict:
             "breakdown": st == HX_EBREAKDOWN}
 
 
+def hx_step_launches(p) -> tuple:
+    """(kernels per product, kernels per time step)."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib.hx_step_launches(p, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def hx_batch_create(problems: list):
+    arr = (ctypes.c_void_p * len(problems))(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in problems])
+    h = ctypes.c_void_p()
+    _check(lib.hx_batch_create(arr, len(problems), ctypes.byref(h)))
+    return h
+
+
+def hx_batch_step(b, states: list, dt: float, nsteps: int):
+    arr = (ctypes.c_void_p * len(states))(*[_tptr(c) for c in states])
+    _check(lib.hx_batch_step(b, arr, dt, nsteps))
+
+
+def hx_batch_destroy(b):
+    lib.hx_batch_destroy(b)
+
+
 def hx_norm(p, c) -> float:
     out = ctypes.c_double()
     _check(lib.hx_norm(p, ctypes.c_void_p(_tptr(c)), ctypes.byref(out)))
@@ -231,6 +269,42 @@ def hx_norm_noalloc(p, c) -> float:
     out = ctypes.c_double()
     _check(lib.hx_norm_noalloc(p, ctypes.c_void_p(_tptr(c)), ctypes.byref(out)))
     return out.value
+
+
+def hx_adjoint_grad(s, L: float, fixed_terms: list, axis: int, u, t0: float, t1: float, substeps: int, c0, phi,
+                    m: int = 20, order: int = HX_ORDER_SYM, stream: int = 0, gradient: bool = True):
+    """(J, dJ/du) for J = |<phi, psi(t1)>|^2 with the control u(t) x_axis (see include/hx.h).
+    c0, phi: complex128 CUDA tensors; u: host values, one per interval."""
+    pot, _keep = _potential(L, fixed_terms)
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    ctl = hx_control(axis, len(uu), substeps, t0, t1, _dptr(uu))
+    cfg = hx_config(HX_C128, order, m, ctypes.c_void_p(stream))
+    grad = np.zeros(len(uu))
+    J = ctypes.c_double()
+    _check(lib.hx_adjoint_grad(s, ctypes.byref(cfg), ctypes.byref(pot), ctypes.byref(ctl),
+                               ctypes.c_void_p(_tptr(c0)), ctypes.c_void_p(_tptr(phi)),
+                               _dptr(grad) if gradient else None, ctypes.byref(J)))
+    return J.value, (grad if gradient else None)
+
+
+def control_objective(s, L: float, fixed_terms: list, axis: int, t0: float, t1: float, substeps: int, c0, phi,
+                      m: int = 20):
+    """A torch.autograd.Function J(u): forward and gradient both from hx_adjoint_grad."""
+    import torch
+
+    class _ControlObjective(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, u):
+            J, g = hx_adjoint_grad(s, L, fixed_terms, axis, u.detach().cpu().numpy(), t0, t1, substeps, c0, phi, m)
+            ctx.save_for_backward(torch.as_tensor(g, dtype=u.dtype, device=u.device))
+            return torch.tensor(J, dtype=u.dtype, device=u.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (g,) = ctx.saved_tensors
+            return gout * g
+
+    return _ControlObjective.apply
 
 
 # ---- Chebyshev helpers -------------------------------------------------------------------

@@ -62,28 +62,33 @@ def workload(name: str) -> dict:
     if name == "hh2_b32":          # N=2 Henon-Heiles, FP64, 100 steps
         N, B = 2, 32
         return dict(name=name, N=N, B=B, L=half_width(B), potential=henon_heiles_chain(N, 0.111),
+                    desc="Henon-Heiles lambda=0.111",
                     init={"kind": "coherent", "q": [1.0, 1.0], "eps": 1e-3, "seed": 0},
                     dt=0.01, steps=100, m=7)
     if name == "hh6_b4096":        # N=6 Henon-Heiles chain + dipole, 1000 steps
         N, B = 6, 4096
         return dict(name=name, N=N, B=B, L=half_width(B),
                     potential=henon_heiles_chain(N, 0.111, dipole=(0.05, 1.0)),
+                    desc="Henon-Heiles chain lambda=0.111 + 0.05 cos(t) x1",
                     init={"kind": "gaussian", "seed": 1}, dt=0.01, steps=1000, m=7)
     if name == "cos10_b1024":      # N=10 cosine chain, degree-8 interpolant, 500 steps
         N, B = 10, 1024
         return dict(name=name, N=N, B=B, L=half_width(B), potential=cos_chain(N, 0.2, 8),
+                    desc="0.2 sum cos(x_d - x_{d+1}), degree-8 Chebyshev interpolant",
                     init={"kind": "decaying", "seed": 2, "power": 2.0}, dt=0.01, steps=500, m=7)
     if name == "ctrl4_b512":       # N=4 control problem for the adjoint gradient
         N, B = 4, 512
         rng = np.random.default_rng(4)
         u = rng.uniform(-0.1, 0.1, size=200)
         return dict(name=name, N=N, B=B, L=half_width(B), potential=control_quartic(u, 10.0),
+                    desc="0.1 x1^2 x2^2 + u(t) x1, u piecewise constant on 200 intervals",
                     init={"kind": "coherent", "q": [1.0, 0.0, 0.0, 0.0], "eps": 0.0, "seed": 4},
                     T=10.0, intervals=200, substeps=10, target=[1, 0, 0, 0], u=u.tolist(), m=7)
     if name == "hh6_b32768":       # roofline size: one vector well above L2
         N, B = 6, 32768
         return dict(name=name, N=N, B=B, L=half_width(B),
                     potential=henon_heiles_chain(N, 0.111, dipole=(0.05, 1.0)),
+                    desc="Henon-Heiles chain lambda=0.111 + 0.05 cos(t) x1",
                     init={"kind": "gaussian", "seed": 1}, dt=0.01, steps=10, m=7)
     raise KeyError(name)
 

@@ -73,3 +73,6 @@ def test_argument_errors_without_device(libhx):
     assert "B = 70000" in hx.hx_last_error()
     with pytest.raises(hx.HxError):
         hx.hx_cheb_nodes(-1)
+    with pytest.raises(hx.HxError):
+        hx.hx_step_launches(None)
+    assert "NULL problem" in hx.hx_last_error()

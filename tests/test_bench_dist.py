@@ -1,0 +1,65 @@
+"""The multi-rank host logic of bench.py on CPU: two gloo ranks (no GPU, no data-path collective;
+the replicas only agree on the slowest time), and the reference arm's rank > 0 doing no work."""
+import argparse
+import io
+import os
+import socket
+import sys
+from contextlib import redirect_stdout
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank: int, world: int, port: int, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        # each replica measured its own step and apply times; the job reports the slowest of each
+        got = bench.max_over_ranks([10.0 + rank, 3.0 - rank], world, "cpu")
+        out.put((rank, got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0] == res[1] == [11.0, 3.0]
+
+
+def test_whole_job_value_and_single_rank():
+    import bench
+    assert bench.max_over_ranks([1.5, 2.5], 1, "cpu") == [1.5, 2.5]
+    # 4 replicas of m = 7 matvecs of 1e6 coefficients in 10 ms each: 2.8 Gcoeff/s for the job
+    assert bench.whole_job_gcoeff_s(7, 1_000_000, 4, 0.010) == pytest.approx(2.8)
+
+
+def test_reference_arm_other_ranks_do_nothing():
+    import bench
+    args = argparse.Namespace(workload="hh2_b32", steps=1, warmup=0, gpus=2)
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(args, rank=1)
+    assert buf.getvalue() == ""

@@ -75,6 +75,14 @@ CASES = {
     "rand5_b150": lambda: random_spec(np.random.default_rng(11), 5, 150, 8, 3),
     "rand4_b90_deg6": lambda: random_spec(np.random.default_rng(12), 4, 90, 5, 6),
     "hh6_b2000": lambda: spec_of(6, 2000, inputs.henon_heiles_chain(6, 0.111, (0.05, 1.0))),
+    # line ops on the second axis of plane ops: merged with a (2,1) op at degree 3 and with a (2,2)
+    # op at degree 2; they stay separate beside a (3,1) plane op, whose stencil is not specialised,
+    # and beside a (1,1) plane op, whose stencil never visits the points s = 0 of a merged line
+    "merge4_b160": lambda: spec_of(4, 160, [
+        {"coef": 0.11, "powers": {0: 2, 1: 1}}, {"coef": -0.04, "powers": {1: 3}},
+        {"coef": 0.07, "powers": {1: 2, 2: 2}}, {"coef": 0.05, "powers": {2: 2}},
+        {"coef": 0.09, "powers": {0: 3, 3: 1}}, {"coef": 0.03, "powers": {3: 3}},
+        {"coef": -0.02, "powers": {2: 1, 3: 1}}, {"coef": 0.06, "powers": {3: 1}}]),
 }
 
 
@@ -103,7 +111,7 @@ def test_apply_matches_oracle(hx, oracle, case, dtype):
     c = inputs.initial_vector({"init": {"kind": "gaussian", "seed": 5}}, S.k)
     r, a = oracle.potential_terms(spec, t)
     ref = oracle.apply(S, r, a, spec["L"], c)
-    bound = (oracle.diag(S).max() + np.abs(a).sum()) * np.linalg.norm(c) if case.startswith("rand") else None
+    bound = (oracle.diag(S).max() + np.abs(a).sum()) * np.linalg.norm(c) if case.startswith(("rand", "merge")) else None
     P = make(hx, spec, dt, t=t)
     try:
         check(gpu_apply(hx, P, c), ref, dt, hx, bound)

@@ -388,3 +388,26 @@ def test_coherent_state_closed_form(oracle):
     proj = [np.sum(w * psi * hermite_explicit(k, xi)) for k in range(15)]
     got = inputs.coherent_state(np.arange(15)[:, None], [q]).real
     assert np.allclose(got, proj, atol=1e-13)
+
+
+def test_control_gradient_matches_central_differences(oracle):
+    """The FP64 adjoint gradient equals central finite differences of the objective (h = 1e-6)."""
+    N, B = 2, 10
+    S = oracle.IndexSet.hyperbolic(N, B)
+    u = np.array([0.07, -0.05, 0.02, 0.09])
+    spec = dict(N=N, B=B, L=inputs.half_width(B), potential=inputs.control_quartic(u, 0.8))
+    c0 = inputs.initial_vector({"init": {"kind": "coherent", "q": [1.0, 0.0], "eps": 0.0, "seed": 0}}, S.k)
+    phi = np.zeros(S.size, complex)
+    phi[S.rank([1, 0])] = 1.0
+    dt, nsub = 0.1, 8
+    J, g = oracle.control_gradient_dense(S, spec, c0, phi, dt, nsub, len(u))
+    h = 1e-6
+    for q in range(len(u)):
+        up, um = u.copy(), u.copy()
+        up[q] += h
+        um[q] -= h
+        Jp, _, _ = oracle.control_objective_dense(S, dict(spec, potential=inputs.control_quartic(up, 0.8)), c0, phi, dt, nsub)
+        Jm, _, _ = oracle.control_objective_dense(S, dict(spec, potential=inputs.control_quartic(um, 0.8)), c0, phi, dt, nsub)
+        fd = (Jp - Jm) / (2 * h)
+        assert abs(g[q] - fd) <= 1e-7 * max(abs(fd), 1e-3), (q, g[q], fd)
+    assert np.abs(g).max() > 1e-4

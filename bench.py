@@ -101,6 +101,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def profiled_traffic(workload: str, dtype: str):
+    """DRAM bytes per apply launch from the committed ncu summary of this workload, or None when
+    there is none or the kernel source has changed since it was captured."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", f"apply_kernel_{workload}_{dtype}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    src = re.search(r"hx_apply\.cu sha256 ([0-9a-f]{64})", text)
+    tr = re.search(r"traffic_bytes_per_launch: (\d+)", text)
+    if not src or not tr:
+        return None
+    with open(os.path.join(ROOT, "paper_1403_3511_gb300", "csrc", "hx_apply.cu"), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != src.group(1):
+            return None
+    return int(tr.group(1))
+
+
 def max_over_ranks(vals, world: int, device):
     """Element-wise maximum over the ranks of the job (the slowest replica sets the time)."""
     if world <= 1:
@@ -276,7 +296,8 @@ def main():
     alg_bytes = (16 if dtype == hx.HX_C64 else 32) * n
     achieved = alg_bytes / (ms_apply * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "apply_kernel", "ms_per_launch": ms_apply,
+            "traffic": profiled_traffic(spec["name"], args.dtype), "kernel": "apply_kernel",
+            "ms_per_launch": ms_apply,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"}
     if rank == 0:
         line = {"metric": "Galerkin matvecs: Gcoeff/s", "value": value, "unit": "Gcoeff/s", "n_gpus": world,

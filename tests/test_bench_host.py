@@ -1,5 +1,6 @@
-"""The multi-rank host logic of bench.py on CPU: two gloo ranks (no GPU, no data-path collective;
-the replicas only agree on the slowest time), and the reference arm's rank > 0 doing no work."""
+"""Host logic of bench.py on CPU: the multi-rank path with two gloo ranks (no GPU, no data-path
+collective; the replicas only agree on the slowest time), the reference arm's rank > 0 doing no
+work, and the roofline traffic taken from the committed ncu summary."""
 import argparse
 import io
 import os
@@ -63,3 +64,22 @@ def test_reference_arm_other_ranks_do_nothing():
     with redirect_stdout(buf):
         bench.run_reference(args, rank=1)
     assert buf.getvalue() == ""
+
+
+def test_profiled_traffic_tracks_kernel_source(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu summary only while the kernel source is the one
+    that summary names."""
+    import hashlib
+    import bench
+    src = tmp_path / "paper_1403_3511_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "hx_apply.cu").write_text("kernel v1\n")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    h = hashlib.sha256(b"kernel v1\n").hexdigest()
+    (prof / "apply_kernel_w_c64.md").write_text(f"hx_apply.cu sha256 {h}\ntraffic_bytes_per_launch: 1234\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("w", "c64") == 1234
+    assert bench.profiled_traffic("w", "c128") is None
+    (src / "hx_apply.cu").write_text("kernel v2\n")
+    assert bench.profiled_traffic("w", "c64") is None

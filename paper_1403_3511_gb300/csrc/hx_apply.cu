@@ -194,25 +194,42 @@ __device__ __forceinline__ void plane_op(const Ctx &c, const Elem &el, const OpS
 // floor(B / x) for x >= 1 from the table (0 when x > B: no element has those coordinates).
 __device__ __forceinline__ int nt_of(const DevSet &S, int x) { return x <= S.B ? __ldg(S.nt + x) : 0; }
 
+// The specialised stencils below issue every load of an operator unconditionally: a footprint
+// point outside K reads the row-offset table at its (always valid) slot and gathers the output
+// element itself, and gets weight 0.  Without branches around them, all loads of an operator are
+// in flight together instead of one dependent pair (table, gather) after another.
+
 // Line operator P(X_a), P of pure parity and degree P (offsets -P, -P+2, ..., P), axis role RA.
 template <typename R, int P, int RA>
 __device__ __forceinline__ void line_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
                                           const typename Vec2<R>::T *src, R &sx, R &sy)
 {
+    using V = typename Vec2<R>::T;
     const DevSet &S = *c.S;
     const int ka = RA == ROLE_LAST ? el.k2 : c.k(el, op.a);
-    // steps to the top of the a-fibre
+    // steps to the top of the a-fibre (>= 0: the element itself is in K)
     const int top = RA == ROLE_LAST ? el.rlen - 1 - el.k2 : nt_of(S, exact_div(el.qall, 1 + ka)) - 1 - ka;
     const R *row = tab + op.tabP + (ka * (P + 1) + min(P, top)) * (2 * P + 1) + P;
+    constexpr int NP = P + 1;
+    int addr[NP];
 #pragma unroll
-    for (int s = -P; s <= P; s += 2) {
-        if (ka + s < 0 || s > top) continue;
-        const int addr = RA == ROLE_LAST ? el.e + s
-                                         : (s == 0 ? el.e : c.row(el, O.didx[op.dbase + s + P]) + el.k2);
-        const typename Vec2<R>::T v = src[addr];
-        const R w = row[s];
-        sx += w * v.x;
-        sy += w * v.y;
+    for (int j = 0; j < NP; ++j) {
+        const int s = -P + 2 * j;
+        const bool ok = ka + s >= 0 && s <= top;
+        int a;
+        if (RA == ROLE_LAST) a = el.e + s;
+        else a = s == 0 ? el.e : c.row(el, O.didx[op.dbase + s + P]) + el.k2;
+        addr[j] = ok ? a : el.e;
+    }
+    V v[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) v[j] = src[addr[j]];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const int s = -P + 2 * j;
+        const R w = (ka + s >= 0 && s <= top) ? row[s] : (R)0;
+        sx += w * v[j].x;
+        sy += w * v[j].y;
     }
 }
 
@@ -222,86 +239,115 @@ __device__ __forceinline__ void line_role(const Ctx &c, const Elem &el, const Op
 // k+s2 e_b+s e_a} (path through k + s2 e_b); a path exists only if its intermediate point is in K.
 // Rows of P(J_n / L) and Q(J_n / L) come from the tables, indexed by the coordinate and the
 // distance to the fibre top.
-// SB > 0: a line operator S(X_b) of degree SB (parity of Q, SB = Q or Q + 2) merged into this op;
-// its sum goes to (lx, ly), which the caller weights with the line operator's own weight.
+// SB > 0: a line operator S(X_b) of degree SB (parity of Q, SB = Q or Q + 2) merged into this op
+// (P is even, so the points s = 0 are footprint points); its sum goes to (lx, ly), which the
+// caller weights with the line operator's own weight.
 template <typename R, int P, int Q, int RB, int SB>
 __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
                                            const typename Vec2<R>::T *src, R &sx, R &sy, R &lx, R &ly)
 {
+    using V = typename Vec2<R>::T;
     const DevSet &S = *c.S;
     const int ka = c.k(el, op.a);
     const int kb = RB == ROLE_LAST ? el.k2 : c.k(el, op.b);
     const int rab = exact_div(el.qall, (1 + ka) * (1 + kb));
     const R wAB = (R)O.wAB, wBA = (R)O.wBA;
     const R *tP = tab + op.tabP, *tQ = tab + op.tabQ;
-    // a-fibre tops at k + s2 e_b, b-fibre tops at k + s e_a
-    int topA[2 * Q + 1], topB[2 * P + 1];
-    const R *rowP[2 * Q + 1];   // P row at k + s2 e_b (valid when that point is in K)
-    const R *rowQ[2 * P + 1];   // Q row at k + s e_a
-    topA[Q] = nt_of(S, rab * (1 + kb)) - 1 - ka;
-    topB[P] = RB == ROLE_LAST ? el.rlen - 1 - el.k2 : nt_of(S, rab * (1 + ka)) - 1 - kb;
+    constexpr int NS = P + 1, NS2 = Q + 1;         // offsets s = -P + 2i, s2 = -Q + 2j
+    // a-fibre tops at k + s2 e_b (-1: that point is not in K), b-fibre tops at k + s e_a
+    int topA[NS2], topB[NS];
 #pragma unroll
-    for (int s2 = -Q; s2 <= Q; s2 += 2)
-        if (s2 != 0) topA[s2 + Q] = kb + s2 >= 0 ? nt_of(S, rab * (1 + kb + s2)) - 1 - ka : -1;
+    for (int j = 0; j < NS2; ++j) {
+        const int s2 = -Q + 2 * j;
+        topA[j] = kb + s2 >= 0 ? nt_of(S, rab * (1 + kb + s2)) - 1 - ka : -1;
+    }
 #pragma unroll
-    for (int s = -P; s <= P; s += 2)
-        if (s != 0) topB[s + P] = ka + s >= 0 ? nt_of(S, rab * (1 + ka + s)) - 1 - kb : -1;
+    for (int i = 0; i < NS; ++i) {
+        const int s = -P + 2 * i;
+        topB[i] = ka + s >= 0 ? nt_of(S, rab * (1 + ka + s)) - 1 - kb : -1;
+    }
+    // fibre tops at k itself (s = 0 or s2 = 0 need not be footprint offsets)
+    const int topA0 = (Q & 1) ? nt_of(S, rab * (1 + kb)) - 1 - ka : topA[Q / 2];
+    const int topB0 = RB == ROLE_LAST ? el.rlen - 1 - el.k2 : ((P & 1) ? nt_of(S, rab * (1 + ka)) - 1 - kb : topB[P / 2]);
+    const R *rowP0 = tP + (ka * (P + 1) + min(P, topA0)) * (2 * P + 1) + P;   // P row at k
+    const R *rowQ0 = tQ + (kb * (Q + 1) + min(Q, topB0)) * (2 * Q + 1) + Q;   // Q row at k
+    // addresses of the footprint points (own element when the point is not in K)
+    int addr[NS][NS2];
+    const int own = el.e - el.k2;                       // start of the own row
 #pragma unroll
-    for (int s2 = -Q; s2 <= Q; ++s2)
-        if (s2 == 0 || ((s2 - Q) & 1) == 0) rowP[s2 + Q] = tP + (ka * (P + 1) + max(0, min(P, topA[s2 + Q]))) * (2 * P + 1) + P;
+    for (int i = 0; i < NS; ++i) {
+        const int s = -P + 2 * i;
+        int base_s = own;                               // RB = LAST: start of the row of k + s e_a
+        if (RB == ROLE_LAST && s != 0) base_s = c.row(el, O.didx[op.dbase + (s + P) * (2 * Q + 1) + Q]);
 #pragma unroll
-    for (int s = -P; s <= P; ++s)
-        if (s == 0 || ((s - P) & 1) == 0) rowQ[s + P] = tQ + (kb * (Q + 1) + max(0, min(Q, topB[s + P]))) * (2 * Q + 1) + Q;
-    const int topA0 = topA[Q], topB0 = topB[P];
+        for (int j = 0; j < NS2; ++j) {
+            const int s2 = -Q + 2 * j;
+            const bool ok = ka + s >= 0 && kb + s2 >= 0 && s <= topA[j];
+            int a;
+            if (RB == ROLE_LAST) a = base_s + el.k2 + s2;
+            else if (s == 0 && s2 == 0) a = el.e;
+            else a = c.row(el, O.didx[op.dbase + (s + P) * (2 * Q + 1) + (s2 + Q)]) + el.k2;
+            addr[i][j] = ok ? a : el.e;
+        }
+    }
+    constexpr int NX = SB > Q ? 2 : 0;                  // merged line points +-SB outside the plane footprint
+    int xaddr[NX > 0 ? NX : 1];
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+        const int s2 = j == 0 ? -SB : SB;
+        const bool ok = kb + s2 >= 0 && s2 <= topB0;
+        int a;
+        if (RB == ROLE_LAST) {
+            a = el.e + s2;
+        } else {
+            const Op &ls = O.op[op.mergeB];
+            a = c.row(el, O.didx[ls.dbase + s2 + SB]) + el.k2;
+        }
+        xaddr[j] = ok ? a : el.e;
+    }
+    V v[NS][NS2];
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+#pragma unroll
+        for (int j = 0; j < NS2; ++j) v[i][j] = src[addr[i][j]];
+    V xv[NX > 0 ? NX : 1];
+#pragma unroll
+    for (int j = 0; j < NX; ++j) xv[j] = src[xaddr[j]];
+    // weights
     const R *rowS0 = nullptr;
     if (SB > 0) {
         const Op &ls = O.op[op.mergeB];
         rowS0 = tab + ls.tabP + (kb * (SB + 1) + min(SB, topB0)) * (2 * SB + 1) + SB;
     }
-    const int own = el.e - el.k2;                       // start of the own row
 #pragma unroll
-    for (int s = -P; s <= P; s += 2) {
-        if (ka + s < 0) continue;
-        const bool inA = s <= topA0;                    // k + s e_a in K
-        const R pj = inA ? rowP[Q][s] : (R)0;
-        int base_s = own;                               // RB = LAST: start of the row of k + s e_a
-        if (RB == ROLE_LAST && s != 0) base_s = c.row(el, O.didx[op.dbase + (s + P) * (2 * Q + 1) + Q]);
+    for (int i = 0; i < NS; ++i) {
+        const int s = -P + 2 * i;
+        const bool inA = ka + s >= 0 && s <= topA0;             // k + s e_a in K
+        const R pj = inA ? rowP0[s] : (R)0;
+        const R *rowQs = tQ + (kb * (Q + 1) + max(0, min(Q, topB[i]))) * (2 * Q + 1) + Q;   // Q row at k + s e_a
 #pragma unroll
-        for (int s2 = -Q; s2 <= Q; s2 += 2) {
-            if (kb + s2 < 0 || s > topA[s2 + Q]) continue;     // footprint point not in K
-            const R cab = inA ? pj * rowQ[s + P][s2] : (R)0;
-            const R cba = s2 <= topB0 ? rowQ[P][s2] * rowP[s2 + Q][s] : (R)0;   // k + s2 e_b in K
-            const R w = wAB * cab + wBA * cba;
-            int addr;
-            if (RB == ROLE_LAST) addr = base_s + el.k2 + s2;
-            else if (s == 0 && s2 == 0) addr = el.e;
-            else addr = c.row(el, O.didx[op.dbase + (s + P) * (2 * Q + 1) + (s2 + Q)]) + el.k2;
-            const typename Vec2<R>::T v = src[addr];
-            sx += w * v.x;
-            sy += w * v.y;
+        for (int j = 0; j < NS2; ++j) {
+            const int s2 = -Q + 2 * j;
+            const bool ok = ka + s >= 0 && kb + s2 >= 0 && s <= topA[j];
+            const R *rowPs = tP + (ka * (P + 1) + max(0, min(P, topA[j]))) * (2 * P + 1) + P;   // P row at k + s2 e_b
+            const R cab = inA ? pj * rowQs[s2] : (R)0;                                   // path via k + s e_a
+            const R cba = (kb + s2 >= 0 && s2 <= topB0) ? rowQ0[s2] * rowPs[s] : (R)0;   // path via k + s2 e_b
+            const R w = ok ? wAB * cab + wBA * cba : (R)0;
+            sx += w * v[i][j].x;
+            sy += w * v[i][j].y;
             if (SB > 0 && s == 0) {                     // k + s2 e_b is also a point of the merged line op
-                const R ws = rowS0[s2];
-                lx += ws * v.x;
-                ly += ws * v.y;
+                const R ws = ok ? rowS0[s2] : (R)0;
+                lx += ws * v[i][j].x;
+                ly += ws * v[i][j].y;
             }
         }
     }
-    if (SB > Q) {                                       // the merged line op's outermost points +-SB
 #pragma unroll
-        for (int s2 = -SB; s2 <= SB; s2 += 2 * SB) {
-            if (kb + s2 < 0 || s2 > topB0) continue;
-            int addr;
-            if (RB == ROLE_LAST) {
-                addr = el.e + s2;
-            } else {
-                const Op &ls = O.op[op.mergeB];
-                addr = c.row(el, O.didx[ls.dbase + s2 + SB]) + el.k2;
-            }
-            const typename Vec2<R>::T v = src[addr];
-            const R ws = rowS0[s2];
-            lx += ws * v.x;
-            ly += ws * v.y;
-        }
+    for (int j = 0; j < NX; ++j) {
+        const int s2 = j == 0 ? -SB : SB;
+        const R ws = (kb + s2 >= 0 && s2 <= topB0) ? rowS0[s2] : (R)0;
+        lx += ws * xv[j].x;
+        ly += ws * xv[j].y;
     }
 }
 
@@ -393,8 +439,19 @@ __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 3 : 1) apply_kernel(c
                         else plane_op<R, 3, 3, true>(ctx, el, O, op, tab, src, sx, sy);
                 }
             } else {
-                if (op.kind == 1) line_op<R, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
-                else plane_op<R, kMaxDeg, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
+                switch (op.cls) {   // pure-parity line operators of any degree: specialised stencils
+                    case CLS_LINE + 1: line_dispatch<R, 1>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                    case CLS_LINE + 2: line_dispatch<R, 2>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                    case CLS_LINE + 3: line_dispatch<R, 3>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                    case CLS_LINE + 4: line_dispatch<R, 4>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                    case CLS_LINE + 5: line_dispatch<R, 5>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                    case CLS_LINE + 6: line_dispatch<R, 6>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                    case CLS_LINE + 7: line_dispatch<R, 7>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                    case CLS_LINE + 8: line_dispatch<R, 8>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
+                    default:
+                        if (op.kind == 1) line_op<R, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
+                        else plane_op<R, kMaxDeg, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
+                }
             }
             const R w = sm_w[o];
             if (op.mergeB >= 0) {

@@ -330,7 +330,7 @@ struct Compiler {
                 return mask == want;
             };
             if (kind == 0) o.cls = CLS_ID;
-            else if (kind == 1 && o.p <= 3 && pure(o.pmask, o.p)) o.cls = CLS_LINE + o.p;
+            else if (kind == 1 && pure(o.pmask, o.p)) o.cls = CLS_LINE + o.p;
             else if (kind == 2 && o.p <= 3 && o.q <= 3 && pure(o.pmask, o.p) && pure(o.qmask, o.q))
                 o.cls = CLS_PLANE + 3 * (o.p - 1) + (o.q - 1);
             else o.cls = CLS_GENERIC;

@@ -76,7 +76,7 @@ enum { ROLE_ROW = 0, ROLE_LAST = 1, ROLE_NONE = 2 };
 
 struct Op {
     int kind;
-    int cls;                  // CLS_ID, CLS_LINE + p, CLS_PLANE + 3 (p-1) + (q-1) (pure parity, p, q <= 3), CLS_GENERIC
+    int cls;                  // CLS_ID, CLS_LINE + p (pure parity), CLS_PLANE + 3 (p-1) + (q-1) (pure parities, p, q <= 3), CLS_GENERIC
     int ra, rb;               // axis roles: ROLE_ROW (< N-1), ROLE_LAST (N-1), ROLE_NONE
     int a, b;                 // axes (b = -1 for a line op)
     int p, q;                 // degrees on a and b

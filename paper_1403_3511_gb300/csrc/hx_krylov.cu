@@ -174,6 +174,34 @@ template <typename V> struct Real;
 template <> struct Real<float2> { using T = float; };
 template <> struct Real<double2> { using T = double; };
 
+// Elements e and e + 1 of a vector (e even; vectors start on 256-byte boundaries): one 16-byte
+// access for complex64, two for complex128.  Two elements per thread and iteration keep twice as
+// many bytes in flight per thread as one.
+template <typename V> struct Pair { V a, b; };
+__device__ __forceinline__ Pair<float2> load_pair(const float2 *p, int e)
+{
+    const float4 q = *reinterpret_cast<const float4 *>(p + e);
+    return {make_float2(q.x, q.y), make_float2(q.z, q.w)};
+}
+__device__ __forceinline__ Pair<double2> load_pair(const double2 *p, int e) { return {p[e], p[e + 1]}; }
+__device__ __forceinline__ void store_pair(float2 *p, int e, const Pair<float2> &x)
+{
+    *reinterpret_cast<float4 *>(p + e) = make_float4(x.a.x, x.a.y, x.b.x, x.b.y);
+}
+__device__ __forceinline__ void store_pair(double2 *p, int e, const Pair<double2> &x)
+{
+    p[e] = x.a;
+    p[e + 1] = x.b;
+}
+
+// x -= (cr + i ci) v in the vector precision
+template <typename V, typename R>
+__device__ __forceinline__ void sub_scaled(V &x, R cr, R ci, const V &v)
+{
+    x.x -= cr * v.x - ci * v.y;
+    x.y -= cr * v.y + ci * v.x;
+}
+
 // h_i = s_i <v_i, w> for i <= k.
 // proj = 1 (projection onto a finished basis): k is clipped to the vectors actually built.
 template <typename V, int NV>
@@ -185,11 +213,34 @@ __global__ void __launch_bounds__(256) dot_kernel(const V *w, const V *Vb, size_
     if (proj) k = min(k, sc->m_used - 1);
     if (k < 0 || k >= sc->m_used) return;
     CAcc<V> acc[NV];
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        V x = w[e];
-#pragma unroll(NV <= 8 ? NV : 1)
-        for (int i = 0; i < NV; ++i)
-            if (i <= k) acc[i].add(Vb[i * ld + e], x);
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+    if constexpr (NV <= 8) {
+        for (int q = gid; q < (n >> 1); q += gstride) {
+            const int e = 2 * q;
+            const Pair<V> x = load_pair(w, e);
+            Pair<V> v[NV];
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i <= k) v[i] = load_pair(Vb + i * ld, e);
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i <= k) {
+                    acc[i].add(v[i].a, x.a);
+                    acc[i].add(v[i].b, x.b);
+                }
+        }
+        if ((n & 1) && gid == 0) {                          // odd length: the last element
+            const V x = w[n - 1];
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i <= k) acc[i].add(Vb[i * ld + n - 1], x);
+        }
+    } else {
+        for (int e = gid; e < n; e += gstride) {
+            const V x = w[e];
+            for (int i = 0; i < NV; ++i)
+                if (i <= k) acc[i].add(Vb[i * ld + e], x);
+        }
     }
     double vals[2 * NV];
 #pragma unroll(NV <= 8 ? NV : 1)
@@ -210,8 +261,9 @@ __global__ void __launch_bounds__(256) dot_kernel(const V *w, const V *Vb, size_
 // pass 0: w -= sum_i h_i s_i v_i, then h'_i = s_i <v_i, w>, alpha_k = Re(h_k + h'_k).
 // pass 1: w -= sum_i h'_i s_i v_i, then beta_k = ||w||, s_{k+1} = 1 / beta_k, breakdown test.
 // The update runs in the vector precision; the inner products and the norm as in dot_kernel.
-template <typename V, int NV>
-__global__ void __launch_bounds__(256) update_kernel(V *w, const V *Vb, size_t ld, int n, int k, int pass, double *partials, Scal *sc)
+// Every v_i is read once per element (the values are kept for the inner products).
+template <typename V, int NV, int pass>
+__global__ void __launch_bounds__(256) update_kernel(V *w, const V *Vb, size_t ld, int n, int k, double *partials, Scal *sc)
 {
     using R = typename Real<V>::T;
     __shared__ double red[32];
@@ -226,22 +278,64 @@ __global__ void __launch_bounds__(256) update_kernel(V *w, const V *Vb, size_t l
     }
     CAcc<V> acc[NV];
     CAcc<V> nrm;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        V x = w[e];
-#pragma unroll(NV <= 8 ? NV : 1)
-        for (int i = 0; i < NV; ++i)
-            if (i <= k) {
-                V v = Vb[i * ld + e];
-                x.x -= cr[i] * v.x - ci[i] * v.y;
-                x.y -= cr[i] * v.y + ci[i] * v.x;
-            }
-        w[e] = x;
-        if (pass == 0) {
-#pragma unroll(NV <= 8 ? NV : 1)
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+    if constexpr (NV <= 8) {
+        for (int q = gid; q < (n >> 1); q += gstride) {
+            const int e = 2 * q;
+            Pair<V> x = load_pair(w, e);
+            Pair<V> v[NV];
+#pragma unroll
             for (int i = 0; i < NV; ++i)
-                if (i <= k) acc[i].add(Vb[i * ld + e], x);
-        } else {
-            nrm.add(x, x);
+                if (i <= k) v[i] = load_pair(Vb + i * ld, e);
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i <= k) {
+                    sub_scaled(x.a, cr[i], ci[i], v[i].a);
+                    sub_scaled(x.b, cr[i], ci[i], v[i].b);
+                }
+            store_pair(w, e, x);
+            if constexpr (pass == 0) {
+#pragma unroll
+                for (int i = 0; i < NV; ++i)
+                    if (i <= k) {
+                        acc[i].add(v[i].a, x.a);
+                        acc[i].add(v[i].b, x.b);
+                    }
+            } else {
+                nrm.add(x.a, x.a);
+                nrm.add(x.b, x.b);
+            }
+        }
+        if ((n & 1) && gid == 0) {                          // odd length: the last element
+            const int e = n - 1;
+            V x = w[e];
+            V v[NV];
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i <= k) {
+                    v[i] = Vb[i * ld + e];
+                    sub_scaled(x, cr[i], ci[i], v[i]);
+                }
+            w[e] = x;
+            if constexpr (pass == 0) {
+#pragma unroll
+                for (int i = 0; i < NV; ++i)
+                    if (i <= k) acc[i].add(v[i], x);
+            } else {
+                nrm.add(x, x);
+            }
+        }
+    } else {
+        for (int e = gid; e < n; e += gstride) {
+            V x = w[e];
+            for (int i = 0; i < NV; ++i)
+                if (i <= k) sub_scaled(x, cr[i], ci[i], Vb[i * ld + e]);
+            w[e] = x;
+            if constexpr (pass == 0) {
+                for (int i = 0; i <= k && i < NV; ++i) acc[i].add(Vb[i * ld + e], x);
+            } else {
+                nrm.add(x, x);
+            }
         }
     }
     double vals[2 * NV];
@@ -445,8 +539,8 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
         if (rc) return rc;
         V *wv = Vb + (size_t)(k + 1) * ld;
         dot_kernel<V, NV><<<G, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
-        update_kernel<V, NV><<<G, T, 0, st>>>(wv, Vb, ld, n, k, 0, w->partials, sc);
-        if (k < m - 1) update_kernel<V, NV><<<G, T, 0, st>>>(wv, Vb, ld, n, k, 1, w->partials, sc);
+        update_kernel<V, NV, 0><<<G, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
+        if (k < m - 1) update_kernel<V, NV, 1><<<G, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
     }
     eig_kernel<<<1, 32, 0, st>>>(sc, dt);
     combine_kernel<V, NV><<<G, T, 0, st>>>(state, Vb, ld, n, w->partials, sc);
@@ -693,8 +787,8 @@ static int lanczos_enqueue_t(Problem *p, LanczosWS *L, const double2 *c, const d
         if (rc) return rc;
         double2 *wv = Vb + (size_t)(k + 1) * ld;
         dot_kernel<double2, NV><<<G, T, 0, st>>>(wv, Vb, ld, n, k, L->partials, sc);
-        update_kernel<double2, NV><<<G, T, 0, st>>>(wv, Vb, ld, n, k, 0, L->partials, sc);
-        if (k < m - 1) update_kernel<double2, NV><<<G, T, 0, st>>>(wv, Vb, ld, n, k, 1, L->partials, sc);
+        update_kernel<double2, NV, 0><<<G, T, 0, st>>>(wv, Vb, ld, n, k, L->partials, sc);
+        if (k < m - 1) update_kernel<double2, NV, 1><<<G, T, 0, st>>>(wv, Vb, ld, n, k, L->partials, sc);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HX_OK : cuda_fail(e, "Lanczos kernel launch");

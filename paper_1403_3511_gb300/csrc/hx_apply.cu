@@ -197,7 +197,9 @@ __device__ __forceinline__ int nt_of(const DevSet &S, int x) { return x <= S.B ?
 // The specialised stencils below issue every load of an operator unconditionally: a footprint
 // point outside K reads the row-offset table at its (always valid) slot and gathers the output
 // element itself, and gets weight 0.  Without branches around them, all loads of an operator are
-// in flight together instead of one dependent pair (table, gather) after another.
+// in flight together instead of one dependent pair (table, gather) after another.  This pays for
+// degrees <= 3; at degree 8 on short fibres most points lie outside K and the loads they would
+// waste cost more than the overlap gains, so those operators keep the branching generic loop.
 
 // Line operator P(X_a), P of pure parity and degree P (offsets -P, -P+2, ..., P), axis role RA.
 template <typename R, int P, int RA>
@@ -401,18 +403,18 @@ __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 3 : 1) apply_kernel(c
     ctx.nrow = args.nrow;
 
     for (int e = blockIdx.x * blockDim.x + tid; e < S.size; e += gridDim.x * blockDim.x) {
-        const int r = __ldg(S.row_of + e);
-        const int4 ri = __ldg(S.row_info + r);
+        const int4 er = __ldg(S.elem + e);      // {row, prod (1 + k_l), sum k_l, k_{N-1} | length << 16}
+        const int r = er.x;
         Elem el;
         el.e = e;
-        el.k2 = e - ri.x;
-        el.qall = ri.y * (1 + el.k2);
-        el.rlen = ri.w;
+        el.k2 = er.w & 0xffff;
+        el.qall = er.y;
+        el.rlen = (int)((unsigned)er.w >> 16);
         el.nb = args.rnb + r;
         el.kr = S.row_k + (size_t)r * (N - 1);
         const V ce = cin[e];
         Acc<R> acc;
-        const R dj = (R)(ri.z + el.k2) + (R)0.5 * (R)N;   // (D_K)_jj = sum_l (j_l + 1/2)
+        const R dj = (R)er.z + (R)0.5 * (R)N;   // (D_K)_jj = sum_l (j_l + 1/2)
         if (!args.stage1 && !args.skip_diag) acc.add(dj * ce.x, dj * ce.y);
         for (int o = 0; o < O.nops; ++o) {
             const Op &op = O.op[o];
@@ -439,19 +441,8 @@ __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 3 : 1) apply_kernel(c
                         else plane_op<R, 3, 3, true>(ctx, el, O, op, tab, src, sx, sy);
                 }
             } else {
-                switch (op.cls) {   // pure-parity line operators of any degree: specialised stencils
-                    case CLS_LINE + 1: line_dispatch<R, 1>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                    case CLS_LINE + 2: line_dispatch<R, 2>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                    case CLS_LINE + 3: line_dispatch<R, 3>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                    case CLS_LINE + 4: line_dispatch<R, 4>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                    case CLS_LINE + 5: line_dispatch<R, 5>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                    case CLS_LINE + 6: line_dispatch<R, 6>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                    case CLS_LINE + 7: line_dispatch<R, 7>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                    case CLS_LINE + 8: line_dispatch<R, 8>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                    default:
-                        if (op.kind == 1) line_op<R, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
-                        else plane_op<R, kMaxDeg, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
-                }
+                if (op.kind == 1) line_op<R, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
+                else plane_op<R, kMaxDeg, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
             }
             const R w = sm_w[o];
             if (op.mergeB >= 0) {
@@ -548,8 +539,9 @@ int launch_apply(Problem *p, const void *cin, void *cout, const double *t_ptr, d
 // Row structure on the device
 // ---------------------------------------------------------------------------------------
 
-// row_of[e]: the row holding rank e (largest r with start(r) <= e).
-__global__ void row_of_kernel(DevSet S, int *row_of)
+// Per-element record: the row holding rank e (largest r with start(r) <= e), the product of
+// (1 + k_l), the coordinate sum, and k_{N-1} with the row length above it (both below 2^16).
+__global__ void elem_info_kernel(DevSet S, int4 *elem)
 {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.size; e += gridDim.x * blockDim.x) {
         int lo = 0, hi = S.nrow - 1;
@@ -557,17 +549,19 @@ __global__ void row_of_kernel(DevSet S, int *row_of)
             const int mid = (lo + hi + 1) >> 1;
             if (S.row_info[mid].x <= e) lo = mid; else hi = mid - 1;
         }
-        row_of[e] = lo;
+        const int4 ri = S.row_info[lo];
+        const int k2 = e - ri.x;
+        elem[e] = make_int4(lo, ri.y * (1 + k2), ri.z + k2, (int)((unsigned)k2 | ((unsigned)ri.w << 16)));
     }
 }
 
-int launch_row_of(const IndexSetObj *s)
+int launch_elem_info(const IndexSetObj *s)
 {
     int blocks = (int)std::min<int64_t>((s->h.size + 255) / 256, 8192);
-    row_of_kernel<<<std::max(blocks, 1), 256>>>(s->d, const_cast<int *>(s->d.row_of));
+    elem_info_kernel<<<std::max(blocks, 1), 256>>>(s->d, const_cast<int4 *>(s->d.elem));
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return cuda_fail(e, "row index kernel");
+    if (e != cudaSuccess) return cuda_fail(e, "element record kernel");
     return HX_OK;
 }
 
@@ -610,7 +604,7 @@ __global__ void export_kernel(DevSet S, int32_t *k)
 {
     const int N = S.N, npre = N - 1;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.size; e += gridDim.x * blockDim.x) {
-        const int r = S.row_of[e];
+        const int r = S.elem[e].x;
         for (int l = 0; l < npre; ++l) k[(size_t)e * N + l] = S.row_k[(size_t)r * npre + l];
         k[(size_t)e * N + N - 1] = e - S.row_info[r].x;
     }

@@ -330,7 +330,7 @@ struct Compiler {
                 return mask == want;
             };
             if (kind == 0) o.cls = CLS_ID;
-            else if (kind == 1 && pure(o.pmask, o.p)) o.cls = CLS_LINE + o.p;
+            else if (kind == 1 && o.p <= 3 && pure(o.pmask, o.p)) o.cls = CLS_LINE + o.p;
             else if (kind == 2 && o.p <= 3 && o.q <= 3 && pure(o.pmask, o.p) && pure(o.qmask, o.q))
                 o.cls = CLS_PLANE + 3 * (o.p - 1) + (o.q - 1);
             else o.cls = CLS_GENERIC;
@@ -617,7 +617,7 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     const IndexSetHost &h = s->h;
     size_t b_info = (size_t)std::max(h.nrow, 1) * sizeof(int4);
     size_t b_k = std::max<size_t>(h.row_k.size(), 1) * sizeof(uint16_t);
-    size_t b_of = (size_t)std::max<int64_t>(h.size, 1) * sizeof(int);
+    size_t b_of = (size_t)std::max<int64_t>(h.size, 1) * sizeof(int4);
     size_t b_qoff = (size_t)(h.B + 2) * sizeof(int);
     size_t b_Q = std::max<size_t>(h.Q.size(), 1) * sizeof(int);
     size_t b_nt = (size_t)(h.B + 1) * sizeof(int);
@@ -631,7 +631,7 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     base += al(b_info);
     uint16_t *d_k = (uint16_t *)base;
     base += al(b_k);
-    int *d_of = (int *)base;
+    int4 *d_of = (int4 *)base;
     base += al(b_of);
     int *d_qoff = (int *)base;
     base += al(b_qoff);
@@ -660,11 +660,11 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     s->d.qtotal = h.qtotal;
     s->d.row_info = d_info;
     s->d.row_k = d_k;
-    s->d.row_of = d_of;
+    s->d.elem = d_of;
     s->d.qoff = d_qoff;
     s->d.Q = d_Q;
     s->d.nt = d_nt;
-    rc = launch_row_of(s);
+    rc = launch_elem_info(s);
     if (rc) {
         cudaFree(s->dmem);
         delete s;

@@ -40,7 +40,7 @@ struct DevSet {
     int N, B, size, nrow, qtotal;
     const int4 *row_info;             // nrow: {start rank, q(p), sum_l p_l, length}
     const uint16_t *row_k;            // nrow x (N - 1) prefixes
-    const int *row_of;                // size: row of each element
+    const int4 *elem;                 // size: per element {row, prod_l (1 + k_l), sum_l k_l, k_{N-1} | row length << 16}
     const int *qoff;                  // B + 2
     const int *Q;                     // (N - 1) x qtotal
     const int *nt;                    // nt[x] = floor(B / x), x = 1..B (nt[0] unused)
@@ -76,7 +76,7 @@ enum { ROLE_ROW = 0, ROLE_LAST = 1, ROLE_NONE = 2 };
 
 struct Op {
     int kind;
-    int cls;                  // CLS_ID, CLS_LINE + p (pure parity), CLS_PLANE + 3 (p-1) + (q-1) (pure parities, p, q <= 3), CLS_GENERIC
+    int cls;                  // CLS_ID, CLS_LINE + p, CLS_PLANE + 3 (p-1) + (q-1) (pure parity, p, q <= 3), CLS_GENERIC
     int ra, rb;               // axis roles: ROLE_ROW (< N-1), ROLE_LAST (N-1), ROLE_NONE
     int a, b;                 // axes (b = -1 for a line op)
     int p, q;                 // degrees on a and b
@@ -173,7 +173,7 @@ struct Problem {
 int launch_apply(Problem *p, const void *cin, void *cout, const double *t_ptr, double t_shift,
                  const ApplyFuse *fuse, cudaStream_t st);
 int launch_export(const IndexSetObj *s, int32_t *k_dev, cudaStream_t st);
-int launch_row_of(const IndexSetObj *s);
+int launch_elem_info(const IndexSetObj *s);
 int launch_rowtab(const DevSet &S, const RowOffsets &ro, int *rnb, cudaStream_t st);
 int launch_norm(Problem *p, const void *c, int is_c128, double *partials, unsigned *counter, double *result,
                 cudaStream_t st);

@@ -17,6 +17,7 @@
 // normalisation.  All scalars live in device memory, so the step has no host round trip.
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "hx_internal.h"
@@ -54,6 +55,17 @@ struct Work {
 };
 
 static Work *work_of(Problem *p) { return (Work *)p->krylov; }
+
+// Grid of a streaming kernel: one wave of resident blocks (a second, partial wave would run at a
+// fraction of the occupancy and take as long as the first), at most apply_grid(p) blocks (the
+// size of the partial-sum buffers).
+template <typename K>
+static int resident_grid(const Problem *p, K kernel, int threads)
+{
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    return std::max(1, std::min(apply_grid(p), p->num_sms * per_sm));
+}
 
 __device__ double block_reduce(double v, double *red)
 {
@@ -530,6 +542,8 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
     V *Vb = (V *)w->V;
     const size_t ld = w->vec_bytes / sizeof(V);
     Scal *sc = w->sc;
+    const int Gd = resident_grid(p, dot_kernel<V, NV>, T);
+    const int Gu0 = resident_grid(p, update_kernel<V, NV, 0>, T), Gu1 = resident_grid(p, update_kernel<V, NV, 1>, T);
     init_kernel<V><<<G, T, 0, st>>>(state, Vb, n, w->partials, sc, m);
     for (int k = 0; k < m; ++k) {
         ApplyFuse f;
@@ -538,12 +552,12 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
         int rc = launch_apply(p, Vb + (size_t)k * ld, Vb + (size_t)(k + 1) * ld, &sc->t, 0.5 * dt, &f, st);
         if (rc) return rc;
         V *wv = Vb + (size_t)(k + 1) * ld;
-        dot_kernel<V, NV><<<G, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
-        update_kernel<V, NV, 0><<<G, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
-        if (k < m - 1) update_kernel<V, NV, 1><<<G, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
+        dot_kernel<V, NV><<<Gd, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
+        update_kernel<V, NV, 0><<<Gu0, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
+        if (k < m - 1) update_kernel<V, NV, 1><<<Gu1, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
     }
     eig_kernel<<<1, 32, 0, st>>>(sc, dt);
-    combine_kernel<V, NV><<<G, T, 0, st>>>(state, Vb, ld, n, w->partials, sc);
+    combine_kernel<V, NV><<<resident_grid(p, combine_kernel<V, NV>, T), T, 0, st>>>(state, Vb, ld, n, w->partials, sc);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     return HX_OK;
@@ -786,9 +800,12 @@ static int lanczos_enqueue_t(Problem *p, LanczosWS *L, const double2 *c, const d
         int rc = launch_apply(p, Vb + (size_t)k * ld, Vb + (size_t)(k + 1) * ld, t_ptr, t_shift, &f, st);
         if (rc) return rc;
         double2 *wv = Vb + (size_t)(k + 1) * ld;
-        dot_kernel<double2, NV><<<G, T, 0, st>>>(wv, Vb, ld, n, k, L->partials, sc);
-        update_kernel<double2, NV, 0><<<G, T, 0, st>>>(wv, Vb, ld, n, k, L->partials, sc);
-        if (k < m - 1) update_kernel<double2, NV, 1><<<G, T, 0, st>>>(wv, Vb, ld, n, k, L->partials, sc);
+        dot_kernel<double2, NV><<<resident_grid(p, dot_kernel<double2, NV>, T), T, 0, st>>>(wv, Vb, ld, n, k, L->partials, sc);
+        update_kernel<double2, NV, 0><<<resident_grid(p, update_kernel<double2, NV, 0>, T), T, 0, st>>>(wv, Vb, ld, n, k,
+                                                                                                       L->partials, sc);
+        if (k < m - 1)
+            update_kernel<double2, NV, 1><<<resident_grid(p, update_kernel<double2, NV, 1>, T), T, 0, st>>>(wv, Vb, ld, n, k,
+                                                                                                          L->partials, sc);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HX_OK : cuda_fail(e, "Lanczos kernel launch");

@@ -75,6 +75,8 @@ CASES = {
     "rand5_b150": lambda: random_spec(np.random.default_rng(11), 5, 150, 8, 3),
     "rand4_b90_deg6": lambda: random_spec(np.random.default_rng(12), 4, 90, 5, 6),
     "hh6_b2000": lambda: spec_of(6, 2000, inputs.henon_heiles_chain(6, 0.111, (0.05, 1.0))),
+    # rows longer than 2^15 (the first row holds B elements)
+    "hh2_b40000": lambda: spec_of(2, 40000, inputs.henon_heiles_chain(2, 0.111, (0.05, 1.0))),
     # line ops on the second axis of plane ops: merged with a (2,1) op at degree 3 and with a (2,2)
     # op at degree 2; they stay separate beside a (3,1) plane op, whose stencil is not specialised,
     # and beside a (1,1) plane op, whose stencil never visits the points s = 0 of a merged line

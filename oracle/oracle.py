@@ -439,6 +439,64 @@ def expmpr_propagate(S: IndexSet, spec: dict, c0: np.ndarray, h: float, nsteps: 
     return c, t
 
 
+def galerkin_reference(S: IndexSet, spec: dict, c0: np.ndarray, T: float, M: int | None = None) -> np.ndarray:
+    """c(T) for i c' = (D_K + W_K(t)) c with the exact Galerkin matrix W_K(t) of W^pol(., t) on K
+    (not the fast algorithm's W^pol(X_K, t)): Gauss-Hermite assembly, Eq. (GHQuad_full), with M + 1
+    >= K + R/2 + 2 nodes, which integrates every entry exactly for these polynomial degrees; the ODE is
+    integrated by scipy's DOP853 at rtol 1e-13.  The potential's time dependence must be a modulation
+    of whole components (W(t) = W_0 + sum_j f_j(t) W_j).  Tiny sets only (dense matrices)."""
+    from scipy.integrate import solve_ivp
+    kmax = int(S.k.max())
+    M = M if M is not None else kmax + 6
+    groups = {}
+    for comp in spec["potential"]:
+        key = repr(comp.get("mod", {"kind": "const"}))
+        groups.setdefault(key, []).append(comp)
+    mats = []
+    for key, comps in groups.items():
+        mod = comps[0].get("mod", {"kind": "const"})
+        sub = dict(spec, potential=[dict(c, mod={"kind": "const"}) for c in comps])
+        r, a = potential_terms(sub, 0.0)
+        mats.append((mod, gh_assembly(S, r, a, spec["L"], M) if len(r) else np.zeros((S.size, S.size))))
+    D = np.diag(diag(S))
+
+    def rhs(t, y):
+        A = D.copy()
+        for mod, W in mats:
+            A += modulation(mod, t) * W
+        return -1j * (A @ y)
+
+    sol = solve_ivp(rhs, (0.0, T), np.asarray(c0, dtype=np.complex128), method="DOP853", rtol=1e-13, atol=1e-15)
+    return sol.y[:, -1]
+
+
+MAGNUS4_NODES = (0.5 - np.sqrt(3.0) / 6.0, 0.5 + np.sqrt(3.0) / 6.0)
+
+
+def magnus4_propagate(S: IndexSet, spec: dict, c0: np.ndarray, h: float, nsteps: int, m: int,
+                      t0: float = 0.0, order: str = "sym"):
+    """c^{n+1} = exp(Omega^n) c^n with the 2-stage Gauss-Legendre Magnus exponent, Eq. (2stageMagnus):
+    Omega^n = -(i/2) h (A_1 + A_2) - (sqrt(3)/12) h^2 [A_2, A_1], A_j = A(t^n + c_j h),
+    c_{1,2} = 1/2 -+ sqrt(3)/6.  Written as exp(-i h H) with the Hermitian
+    H = (A_1 + A_2)/2 - i (sqrt(3) h / 12) (A_2 A_1 - A_1 A_2), whose action takes four products;
+    each exponential by lanczos_exp."""
+    c = np.array(c0, dtype=np.complex128)
+    t = t0
+    g = np.sqrt(3.0) * h / 12.0
+    for _ in range(nsteps):
+        (r1, a1), (r2, a2) = (potential_terms(spec, t + cj * h) for cj in MAGNUS4_NODES)
+
+        def H(v, r1=r1, a1=a1, r2=r2, a2=a2):
+            u1 = apply(S, r1, a1, spec["L"], v, order)
+            u2 = apply(S, r2, a2, spec["L"], v, order)
+            comm = apply(S, r2, a2, spec["L"], u1, order) - apply(S, r1, a1, spec["L"], u2, order)
+            return 0.5 * (u1 + u2) - 1j * g * comm
+
+        c, _, _ = lanczos_exp(H, c, h, m)
+        t += h
+    return c, t
+
+
 # --------------------------------------------------------------------------- #
 # gradient of a final-time objective w.r.t. a piecewise-constant control       #
 # --------------------------------------------------------------------------- #

@@ -43,6 +43,26 @@ def henon_heiles_chain(N: int, lam: float, dipole: tuple | None = None) -> list:
     return comps
 
 
+def stretched_hh_laser(N: int, L: float) -> list:
+    """sum_l [(x_l/L)^2 (x_{l+1}/L) - (x_{l+1}/L)^3 / 3] - sin^2(t) (x_1/L): the time-integration
+    experiment's potential (Sec. 6.3), read with the laser term scaled like the others and without a
+    -(1/2)|x|^2 term (the harmonic part stays in D_K)."""
+    comps = []
+    for d in range(N - 1):
+        comps.append({"coef": 1.0 / L ** 3, "powers": {d: 2, d + 1: 1}})
+        comps.append({"coef": -1.0 / (3.0 * L ** 3), "powers": {d + 1: 3}})
+    comps.append({"coef": -1.0 / L, "powers": {0: 1}, "mod": {"kind": "sin2", "omega": 1.0}})
+    return comps
+
+
+def time_integration_workload(N: int, K: int, m: int = 7) -> dict:
+    """The time-integration experiment of Sec. 6.3: K + 1 = B, L = 16, initial coefficients
+    prod_{k_l != 0} k_l^-3 normalised, propagated over [0, 1]."""
+    return dict(name=f"hhlaser{N}_k{K}", N=N, B=K + 1, L=16.0, potential=stretched_hh_laser(N, 16.0),
+                desc="stretched Henon-Heiles, L = 16, - sin^2(t) x1 / L",
+                init={"kind": "beta_decay", "beta": 3.0}, T=1.0, m=m)
+
+
 def cos_chain(N: int, beta: float, R: int = 8) -> list:
     """W = beta * sum_d cos(x_d - x_{d+1}), to be replaced by its degree-R Chebyshev interpolant."""
     return [{"coef": beta, "func": "cos_diff", "axes": [d, d + 1], "R": R} for d in range(N - 1)]

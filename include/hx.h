@@ -73,6 +73,15 @@ typedef enum {
     HX_ORDER_ALG = 2       /* axis 0 acts on v first, then axis 1, ... */
 } hx_order;
 
+/* Exponent of one time step c^{n+1} = exp(Omega^n) c^n (Sec. 2.1). */
+typedef enum {
+    HX_SCHEME_EXPMPR = 0,  /* exponential midpoint rule, Eq. (expMPR): Omega = -i h A(t + h/2); order 2 */
+    HX_SCHEME_MAGNUS4 = 1  /* 2-stage Gauss-Legendre Magnus method, Eq. (2stageMagnus):
+                              Omega = -(i/2) h (A_1 + A_2) - (sqrt(3)/12) h^2 [A_2, A_1],
+                              A_j = A(t + c_j h), c_{1,2} = 1/2 -+ sqrt(3)/6; order 4, four
+                              products per Lanczos vector */
+} hx_scheme;
+
 /* Time dependence f(t) of one potential term. */
 typedef enum {
     HX_MOD_CONST = 0,      /* f = 1 */
@@ -110,6 +119,7 @@ typedef struct {
     int order;                     /* hx_order */
     int m;                         /* Lanczos steps per time step, 1 <= m <= 32 */
     void *stream;                  /* cudaStream_t, 0 for the legacy default stream */
+    int scheme;                    /* hx_scheme */
 } hx_config;
 
 typedef struct hx_indexset hx_indexset;
@@ -134,8 +144,8 @@ HX_API void hx_indexset_destroy(hx_indexset *s);
 
 /* ---- problem: index set + potential + configuration -------------------------- */
 
-/* cfg may be NULL: HX_C128, HX_ORDER_SYM, m = 7, default stream.  The index set must
- * outlive the problem. */
+/* cfg may be NULL: HX_C128, HX_ORDER_SYM, m = 7, default stream, HX_SCHEME_EXPMPR.  The index
+ * set must outlive the problem.  Errors: HX_EINVAL (bad dtype, order, m or scheme). */
 HX_API int hx_problem_create(const hx_indexset *s, const hx_config *cfg, hx_problem **out);
 HX_API void hx_problem_destroy(hx_problem *p);
 
@@ -159,9 +169,12 @@ HX_API int hx_apply_host(hx_problem *p, const void *c_in_host, void *c_out_host)
 
 /* ---- time stepping (Sec. 2) ----------------------------------------------------- */
 
-/* nsteps steps c <- exp(-i dt A(t + dt/2)) c (Eq. (expMPR)), each exponential by an m-step
- * Hermitian Lanczos process with full reorthogonalisation (classical Gram-Schmidt twice),
- * c^{n+1} = ||c^n|| V_m exp(-i dt T_m) e_1 (Sec. 2.2).  c is a DEVICE complex128 vector of
+/* nsteps steps c <- exp(Omega^n) c with the problem's scheme: exp(-i dt A(t + dt/2)) c for
+ * HX_SCHEME_EXPMPR (Eq. (expMPR)), exp(-i dt H) c with the Hermitian
+ * H = (A_1 + A_2)/2 - i (sqrt(3) dt / 12)(A_2 A_1 - A_1 A_2) for HX_SCHEME_MAGNUS4
+ * (Eq. (2stageMagnus)).  Each exponential by an m-step Hermitian Lanczos process with full
+ * reorthogonalisation (classical Gram-Schmidt twice), c^{n+1} = ||c^n|| V_m exp(-i dt T_m) e_1
+ * (Sec. 2.2).  c is a DEVICE complex128 vector of
  * |K| elements, updated in place, for both dtypes (HX_C64 runs the Krylov vectors and the
  * stencil in complex64, the state and all inner products in FP64).  Advances the problem
  * time by nsteps * dt.  One step is captured into a CUDA graph for the pair (c, dt) and replayed
@@ -176,9 +189,10 @@ HX_API int hx_step_host(hx_problem *p, void *c_host, double dt, int nsteps);
  * (host arrays of at least m and m-1 doubles, either may be NULL) and the norm of c. */
 HX_API int hx_step_info(hx_problem *p, int *m_used, double *alpha, double *beta, double *norm);
 /* Kernel launches of one product hx_apply (1, or 2 when some term is evaluated in two stages
- * through channel vectors) and of one time step of hx_step (m (per_apply + 3) + 2: the
- * normalisation, per Lanczos vector the product, one projection and two orthogonalisation
- * passes (one for the last vector), the eigensolver and the recombination).  Needs a potential;
+ * through channel vectors) and of one time step of hx_step: m (per_apply + 3) + 2 for
+ * HX_SCHEME_EXPMPR (the normalisation, per Lanczos vector the product, one projection and two
+ * orthogonalisation passes (one for the last vector), the eigensolver and the recombination),
+ * m (4 per_apply + 4) + 2 for HX_SCHEME_MAGNUS4 (four products and their combination).  Needs a potential;
  * either pointer may be NULL.  The paper has no counterpart: this reports how the library maps
  * its work onto kernels. */
 HX_API int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step);
@@ -220,7 +234,8 @@ typedef struct {
  * converged propagator), cfg->order and cfg->stream are honoured.  c0, phi: DEVICE complex128
  * vectors of |K|; grad_out: host array of n_intervals doubles, or NULL for J only; J_out: host.
  * Device memory: about (n_intervals + substeps + 2m + 8) vectors.  Synchronous.
- * Errors: HX_EINVAL (NULL pointers, bad control), HX_ENOMEM, HX_ECUDA, as hx_potential_set. */
+ * Errors: HX_EINVAL (NULL pointers, bad control), HX_EUNSUPPORTED (cfg->scheme other than
+ * HX_SCHEME_EXPMPR), HX_ENOMEM, HX_ECUDA, as hx_potential_set. */
 HX_API int hx_adjoint_grad(const hx_indexset *s, const hx_config *cfg, const hx_potential *fixed,
                            const hx_control *ctl, const void *c0, const void *phi, double *grad_out,
                            double *J_out);

@@ -194,6 +194,19 @@ __device__ __forceinline__ void plane_op(const Ctx &c, const Elem &el, const OpS
 // floor(B / x) for x >= 1 from the table (0 when x > B: no element has those coordinates).
 __device__ __forceinline__ int nt_of(const DevSet &S, int x) { return x <= S.B ? __ldg(S.nt + x) : 0; }
 
+// One packed row (4 entries, see the packed row tables): a 16-byte load for FP32, two for FP64.
+template <typename R> struct Row4 { R v[4]; };
+__device__ __forceinline__ Row4<float> load_row4(const float *p)
+{
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+    return {{q.x, q.y, q.z, q.w}};
+}
+__device__ __forceinline__ Row4<double> load_row4(const double *p)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return {{a.x, a.y, b.x, b.y}};
+}
+
 // The specialised stencils below issue every load of an operator unconditionally: a footprint
 // point outside K reads the row-offset table at its (always valid) slot and gathers the output
 // element itself, and gets weight 0.  Without branches around them, all loads of an operator are
@@ -211,7 +224,7 @@ __device__ __forceinline__ void line_role(const Ctx &c, const Elem &el, const Op
     const int ka = RA == ROLE_LAST ? el.k2 : c.k(el, op.a);
     // steps to the top of the a-fibre (>= 0: the element itself is in K)
     const int top = RA == ROLE_LAST ? el.rlen - 1 - el.k2 : nt_of(S, exact_div(el.qall, 1 + ka)) - 1 - ka;
-    const R *row = tab + op.tabP + (ka * (P + 1) + min(P, top)) * (2 * P + 1) + P;
+    const Row4<R> row = load_row4(tab + op.ptabP + (ka * (P + 1) + min(P, top)) * 4);   // entries at s = -P + 2j
     constexpr int NP = P + 1;
     int addr[NP];
 #pragma unroll
@@ -229,7 +242,7 @@ __device__ __forceinline__ void line_role(const Ctx &c, const Elem &el, const Op
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         const int s = -P + 2 * j;
-        const R w = (ka + s >= 0 && s <= top) ? row[s] : (R)0;
+        const R w = (ka + s >= 0 && s <= top) ? row.v[j] : (R)0;
         sx += w * v[j].x;
         sy += w * v[j].y;
     }
@@ -254,7 +267,7 @@ __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const O
     const int kb = RB == ROLE_LAST ? el.k2 : c.k(el, op.b);
     const int rab = exact_div(el.qall, (1 + ka) * (1 + kb));
     const R wAB = (R)O.wAB, wBA = (R)O.wBA;
-    const R *tP = tab + op.tabP, *tQ = tab + op.tabQ;
+    const R *tP = tab + op.ptabP, *tQ = tab + op.ptabQ;   // packed rows: entry i at offset -P + 2i
     constexpr int NS = P + 1, NS2 = Q + 1;         // offsets s = -P + 2i, s2 = -Q + 2j
     // a-fibre tops at k + s2 e_b (-1: that point is not in K), b-fibre tops at k + s e_a
     int topA[NS2], topB[NS];
@@ -271,8 +284,8 @@ __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const O
     // fibre tops at k itself (s = 0 or s2 = 0 need not be footprint offsets)
     const int topA0 = (Q & 1) ? nt_of(S, rab * (1 + kb)) - 1 - ka : topA[Q / 2];
     const int topB0 = RB == ROLE_LAST ? el.rlen - 1 - el.k2 : ((P & 1) ? nt_of(S, rab * (1 + ka)) - 1 - kb : topB[P / 2]);
-    const R *rowP0 = tP + (ka * (P + 1) + min(P, topA0)) * (2 * P + 1) + P;   // P row at k
-    const R *rowQ0 = tQ + (kb * (Q + 1) + min(Q, topB0)) * (2 * Q + 1) + Q;   // Q row at k
+    const Row4<R> rowP0 = load_row4(tP + (ka * (P + 1) + min(P, topA0)) * 4);   // P row at k
+    const Row4<R> rowQ0 = load_row4(tQ + (kb * (Q + 1) + min(Q, topB0)) * 4);   // Q row at k
     // addresses of the footprint points (own element when the point is not in K)
     int addr[NS][NS2];
     const int own = el.e - el.k2;                       // start of the own row
@@ -316,29 +329,31 @@ __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const O
 #pragma unroll
     for (int j = 0; j < NX; ++j) xv[j] = src[xaddr[j]];
     // weights
-    const R *rowS0 = nullptr;
+    Row4<R> rowS0 = {};
     if (SB > 0) {
         const Op &ls = O.op[op.mergeB];
-        rowS0 = tab + ls.tabP + (kb * (SB + 1) + min(SB, topB0)) * (2 * SB + 1) + SB;
+        rowS0 = load_row4(tab + ls.ptabP + (kb * (SB + 1) + min(SB, topB0)) * 4);   // entry at s2: (s2 + SB) / 2
     }
+    Row4<R> rowPs[NS2];                                 // P rows at k + s2 e_b
+#pragma unroll
+    for (int j = 0; j < NS2; ++j) rowPs[j] = load_row4(tP + (ka * (P + 1) + max(0, min(P, topA[j]))) * 4);
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         const int s = -P + 2 * i;
         const bool inA = ka + s >= 0 && s <= topA0;             // k + s e_a in K
-        const R pj = inA ? rowP0[s] : (R)0;
-        const R *rowQs = tQ + (kb * (Q + 1) + max(0, min(Q, topB[i]))) * (2 * Q + 1) + Q;   // Q row at k + s e_a
+        const R pj = inA ? rowP0.v[i] : (R)0;
+        const Row4<R> rowQs = load_row4(tQ + (kb * (Q + 1) + max(0, min(Q, topB[i]))) * 4);   // Q row at k + s e_a
 #pragma unroll
         for (int j = 0; j < NS2; ++j) {
             const int s2 = -Q + 2 * j;
             const bool ok = ka + s >= 0 && kb + s2 >= 0 && s <= topA[j];
-            const R *rowPs = tP + (ka * (P + 1) + max(0, min(P, topA[j]))) * (2 * P + 1) + P;   // P row at k + s2 e_b
-            const R cab = inA ? pj * rowQs[s2] : (R)0;                                   // path via k + s e_a
-            const R cba = (kb + s2 >= 0 && s2 <= topB0) ? rowQ0[s2] * rowPs[s] : (R)0;   // path via k + s2 e_b
+            const R cab = inA ? pj * rowQs.v[j] : (R)0;                                   // path via k + s e_a
+            const R cba = (kb + s2 >= 0 && s2 <= topB0) ? rowQ0.v[j] * rowPs[j].v[i] : (R)0;   // path via k + s2 e_b
             const R w = ok ? wAB * cab + wBA * cba : (R)0;
             sx += w * v[i][j].x;
             sy += w * v[i][j].y;
             if (SB > 0 && s == 0) {                     // k + s2 e_b is also a point of the merged line op
-                const R ws = ok ? rowS0[s2] : (R)0;
+                const R ws = ok ? rowS0.v[(s2 + SB) / 2] : (R)0;
                 lx += ws * v[i][j].x;
                 ly += ws * v[i][j].y;
             }
@@ -347,7 +362,7 @@ __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const O
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
         const int s2 = j == 0 ? -SB : SB;
-        const R ws = (kb + s2 >= 0 && s2 <= topB0) ? rowS0[s2] : (R)0;
+        const R ws = (kb + s2 >= 0 && s2 <= topB0) ? rowS0.v[(s2 + SB) / 2] : (R)0;
         lx += ws * xv[j].x;
         ly += ws * xv[j].y;
     }

@@ -254,6 +254,7 @@ struct Compiler {
     const IndexSetObj *set;
     double L;
     std::map<PolyKey, int> poly_base;    // polynomial -> row-table base
+    std::map<PolyKey, int> packed_base;  // polynomial -> packed row-table base
     std::vector<double> tab;             // all row tables (double)
     OpSet ops;                           // main stage
     OpSet ops1;                          // first stage (channel writers)
@@ -272,6 +273,26 @@ struct Compiler {
             for (int d = 0; d <= p; ++d)
                 poly_row(a, L, i, i + 1 + d, &tab[base + ((size_t)i * (p + 1) + d) * (2 * p + 1)]);
         poly_base[PolyKey{a}] = base;
+        return base;
+    }
+
+    // Packed rows of a pure-parity polynomial of degree <= 3 (4 entries per row, 4-aligned base).
+    int packed(const std::vector<double> &a)
+    {
+        auto it = packed_base.find(PolyKey{a});
+        if (it != packed_base.end()) return it->second;
+        int p = (int)a.size() - 1;
+        int B = set->h.B;
+        tab.resize((tab.size() + 3) & ~(size_t)3, 0.0);
+        int base = (int)tab.size();
+        tab.resize(tab.size() + (size_t)B * (p + 1) * 4, 0.0);
+        double row[2 * 3 + 1];
+        for (int i = 0; i < B; ++i)
+            for (int d = 0; d <= p; ++d) {
+                poly_row(a, L, i, i + 1 + d, row);
+                for (int j = 0; j <= p; ++j) tab[base + ((size_t)i * (p + 1) + d) * 4 + j] = row[2 * j];
+            }
+        packed_base[PolyKey{a}] = base;
         return base;
     }
 
@@ -334,6 +355,11 @@ struct Compiler {
             else if (kind == 2 && o.p <= 3 && o.q <= 3 && pure(o.pmask, o.p) && pure(o.qmask, o.q))
                 o.cls = CLS_PLANE + 3 * (o.p - 1) + (o.q - 1);
             else o.cls = CLS_GENERIC;
+            o.ptabP = o.ptabQ = 0;
+            if (o.cls != CLS_ID && o.cls != CLS_GENERIC) {
+                o.ptabP = packed(P);
+                if (kind == 2) o.ptabQ = packed(Q);
+            }
         }
         o.mod = t.mod_kind;
         o.amp = t.amp * scale;
@@ -719,10 +745,11 @@ int hx_problem_create(const hx_indexset *s, const hx_config *cfg, hx_problem **o
 {
     if (!s || !out) { set_error("hx_problem_create: NULL argument"); return HX_EINVAL; }
     *out = nullptr;
-    hx_config c = {HX_C128, HX_ORDER_SYM, 7, nullptr};
+    hx_config c = {HX_C128, HX_ORDER_SYM, 7, nullptr, HX_SCHEME_EXPMPR};
     if (cfg) c = *cfg;
-    if ((c.dtype != HX_C128 && c.dtype != HX_C64) || c.order < 0 || c.order > 2 || c.m < 1 || c.m > kMaxKrylov) {
-        set_error("hx_problem_create: bad dtype, order or m (1..%d)", kMaxKrylov);
+    if ((c.dtype != HX_C128 && c.dtype != HX_C64) || c.order < 0 || c.order > 2 || c.m < 1 || c.m > kMaxKrylov ||
+        (c.scheme != HX_SCHEME_EXPMPR && c.scheme != HX_SCHEME_MAGNUS4)) {
+        set_error("hx_problem_create: bad dtype, order, m (1..%d) or scheme", kMaxKrylov);
         return HX_EINVAL;
     }
     hx_problem *p = new (std::nothrow) hx_problem();
@@ -895,7 +922,7 @@ int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step)
     if (!p->have_pot) { set_error("hx_step_launches: call hx_potential_set first"); return HX_EINVAL; }
     const int a = apply_launches(p);
     if (per_apply) *per_apply = a;
-    if (per_step) *per_step = p->cfg.m * (a + 3) + 2;
+    if (per_step) *per_step = p->cfg.scheme == HX_SCHEME_MAGNUS4 ? p->cfg.m * (4 * a + 4) + 2 : p->cfg.m * (a + 3) + 2;
     return HX_OK;
 }
 

@@ -68,6 +68,10 @@ struct IndexSetHost {
 //   tab[base + ((i * (p + 1) + d) * (2p + 1)) + (s + p)] = [P(J_n / L)]_{i, i+s},  n = i + 1 + d,
 // where J_n is the n x n truncated Jacobi matrix of the Hermite recurrence (Eq. (Recurrence1D)):
 // row i of a fibre whose top is d steps above i (d = p stands for "p or more").
+// Packed row tables (a polynomial of pure parity and degree p <= 3, whose row has p + 1 entries
+// that can be nonzero, at s = -p, -p + 2, ..., p):
+//   tab[pbase + (i * (p + 1) + d) * 4 + j] = [P(J_n / L)]_{i, i-p+2j},  j <= p, zero for j > p,
+// one 16-byte (FP32) or 32-byte (FP64) load per row.
 // ---------------------------------------------------------------------------------------
 // op classes with compile-time stencils (pure parity: P has only terms of the parity of its degree)
 enum { CLS_ID = 0, CLS_LINE = 1, CLS_PLANE = 10, CLS_GENERIC = 30 };
@@ -82,6 +86,7 @@ struct Op {
     int p, q;                 // degrees on a and b
     int pmask, qmask;         // bit (s + p) set when the rows can be nonzero at offset s
     int tabP, tabQ;           // row table bases
+    int ptabP, ptabQ;         // packed row table bases (pure parity, degree <= 3; 0 otherwise)
     int dbase;                // base into didx (footprint position -> row offset index)
     int src, dst;             // input channel (-1 = c), output channel (stage 1 only)
     int mergeB;               // plane ops: index of a line op on axis b evaluated inside this op (-1: none)

@@ -48,6 +48,7 @@ struct Work {
     double2 *state;                 // complex128 state the captured graph reads and writes
     double2 *host_state;            // device buffer used by hx_step_host
     double *partials;               // G x 2 (m + 2)
+    void *mag;                      // HX_SCHEME_MAGNUS4: 4 vectors of the Krylov dtype (A_1 v, A_2 v, A_2 A_1 v, A_1 A_2 v)
     size_t vec_bytes;
     cudaGraphExec_t exec;
     cudaStream_t cap_stream;
@@ -182,6 +183,41 @@ template <> struct CAcc<double2> {
     __device__ double i() const { return im; }
 };
 
+// Accumulator of Re/Im conj(v) w over pairs of elements: the four products of a pair are summed
+// with fused multiply-adds (a few ulp of their magnitudes) and the pair sums are accumulated
+// with TwoSum compensation, so the rounding does not grow with the number of elements; about a
+// third of the work of Dot2 on every product.  Used by the paired loops for complex64 vectors.
+struct TwoSumAcc {
+    float s = 0.f, c = 0.f;
+    __device__ void add(float p)
+    {
+        const float t = s + p, bb = t - s;
+        c += (s - (t - bb)) + (p - bb);
+        s = t;
+    }
+    __device__ double value() const { return (double)s + (double)c; }
+};
+struct PairAcc {
+    TwoSumAcc re, im;
+    __device__ void add(float2 va, float2 wa, float2 vb, float2 wb)
+    {
+        re.add(fmaf(va.x, wa.x, fmaf(va.y, wa.y, fmaf(vb.x, wb.x, vb.y * wb.y))));
+        im.add(fmaf(va.x, wa.y, fmaf(-va.y, wa.x, fmaf(vb.x, wb.y, -vb.y * wb.x))));
+    }
+    __device__ void add(float2 v, float2 w) { add(v, w, make_float2(0.f, 0.f), make_float2(0.f, 0.f)); }
+    __device__ double r() const { return re.value(); }
+    __device__ double i() const { return im.value(); }
+};
+// complex128 vectors keep FP64 accumulation
+template <typename V> struct PairAccOf { using T = PairAcc; };
+template <> struct PairAccOf<double2> { using T = CAcc<double2>; };
+template <typename A, typename V>
+__device__ __forceinline__ void add_pair(A &acc, const V &va, const V &wa, const V &vb, const V &wb)
+{
+    if constexpr (std::is_same<A, PairAcc>::value) acc.add(va, wa, vb, wb);
+    else { acc.add(va, wa); acc.add(vb, wb); }
+}
+
 template <typename V> struct Real;
 template <> struct Real<float2> { using T = float; };
 template <> struct Real<double2> { using T = double; };
@@ -224,7 +260,8 @@ __global__ void __launch_bounds__(256) dot_kernel(const V *w, const V *Vb, size_
     __shared__ double tot[2 * NV];
     if (proj) k = min(k, sc->m_used - 1);
     if (k < 0 || k >= sc->m_used) return;
-    CAcc<V> acc[NV];
+    using A = typename std::conditional<(NV <= 8), typename PairAccOf<V>::T, CAcc<V>>::type;
+    A acc[NV];
     const int gid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
     if constexpr (NV <= 8) {
         for (int q = gid; q < (n >> 1); q += gstride) {
@@ -236,10 +273,7 @@ __global__ void __launch_bounds__(256) dot_kernel(const V *w, const V *Vb, size_
                 if (i <= k) v[i] = load_pair(Vb + i * ld, e);
 #pragma unroll
             for (int i = 0; i < NV; ++i)
-                if (i <= k) {
-                    acc[i].add(v[i].a, x.a);
-                    acc[i].add(v[i].b, x.b);
-                }
+                if (i <= k) add_pair(acc[i], v[i].a, x.a, v[i].b, x.b);
         }
         if ((n & 1) && gid == 0) {                          // odd length: the last element
             const V x = w[n - 1];
@@ -275,7 +309,7 @@ __global__ void __launch_bounds__(256) dot_kernel(const V *w, const V *Vb, size_
 // The update runs in the vector precision; the inner products and the norm as in dot_kernel.
 // Every v_i is read once per element (the values are kept for the inner products).
 template <typename V, int NV, int pass>
-__global__ void __launch_bounds__(256) update_kernel(V *w, const V *Vb, size_t ld, int n, int k, double *partials, Scal *sc)
+__global__ void __launch_bounds__(256, (sizeof(V) == 8 && NV <= 8) ? 3 : 1) update_kernel(V *w, const V *Vb, size_t ld, int n, int k, double *partials, Scal *sc)
 {
     using R = typename Real<V>::T;
     __shared__ double red[32];
@@ -288,8 +322,9 @@ __global__ void __launch_bounds__(256) update_kernel(V *w, const V *Vb, size_t l
         cr[i] = i <= k ? (R)(coef[2 * i] * sc->s[i]) : (R)0;
         ci[i] = i <= k ? (R)(coef[2 * i + 1] * sc->s[i]) : (R)0;
     }
-    CAcc<V> acc[NV];
-    CAcc<V> nrm;
+    using A = typename std::conditional<(NV <= 8), typename PairAccOf<V>::T, CAcc<V>>::type;
+    A acc[NV];
+    A nrm;
     const int gid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
     if constexpr (NV <= 8) {
         for (int q = gid; q < (n >> 1); q += gstride) {
@@ -309,13 +344,9 @@ __global__ void __launch_bounds__(256) update_kernel(V *w, const V *Vb, size_t l
             if constexpr (pass == 0) {
 #pragma unroll
                 for (int i = 0; i < NV; ++i)
-                    if (i <= k) {
-                        acc[i].add(v[i].a, x.a);
-                        acc[i].add(v[i].b, x.b);
-                    }
+                    if (i <= k) add_pair(acc[i], v[i].a, x.a, v[i].b, x.b);
             } else {
-                nrm.add(x.a, x.a);
-                nrm.add(x.b, x.b);
+                add_pair(nrm, x.a, x.a, x.b, x.b);
             }
         }
         if ((n & 1) && gid == 0) {                          // odd length: the last element
@@ -532,6 +563,23 @@ __global__ void combine_kernel(double2 *c, const V *Vb, size_t ld, int n, double
     }
 }
 
+// H v for the 2-stage Magnus exponent, Eq. (2stageMagnus) written as Omega = -i h H:
+// H v = (A_1 v + A_2 v) / 2 - i g (A_2 A_1 v - A_1 A_2 v), g = sqrt(3) h / 12.
+template <typename V>
+__global__ void magnus_combine_kernel(V *out, const V *a1v, const V *a2v, const V *a2a1v, const V *a1a2v, int n,
+                                      double g_)
+{
+    using R = typename Real<V>::T;
+    const R g = (R)g_, half = (R)0.5;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const V x1 = a1v[e], x2 = a2v[e], y1 = a2a1v[e], y2 = a1a2v[e];
+        V r;
+        r.x = half * (x1.x + x2.x) + g * (y1.y - y2.y);   // -i g z = g (z.y, -z.x)
+        r.y = half * (x1.y + x2.y) - g * (y1.x - y2.x);
+        out[e] = r;
+    }
+}
+
 template <typename V, int NV>
 static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, double dt)
 {
@@ -549,8 +597,21 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
         ApplyFuse f;
         memset(&f, 0, sizeof(f));
         f.in_scale = &sc->s[k];
-        int rc = launch_apply(p, Vb + (size_t)k * ld, Vb + (size_t)(k + 1) * ld, &sc->t, 0.5 * dt, &f, st);
-        if (rc) return rc;
+        int rc;
+        if (p->cfg.scheme == HX_SCHEME_MAGNUS4) {   // Eq. (2stageMagnus): nodes 1/2 -+ sqrt(3)/6
+            const double c1 = 0.5 - sqrt(3.0) / 6.0, c2 = 0.5 + sqrt(3.0) / 6.0;
+            V *a1v = (V *)w->mag, *a2v = a1v + ld, *a2a1v = a2v + ld, *a1a2v = a2a1v + ld;
+            if ((rc = launch_apply(p, Vb + (size_t)k * ld, a1v, &sc->t, c1 * dt, &f, st)) ||
+                (rc = launch_apply(p, Vb + (size_t)k * ld, a2v, &sc->t, c2 * dt, &f, st)) ||
+                (rc = launch_apply(p, a1v, a2a1v, &sc->t, c2 * dt, nullptr, st)) ||
+                (rc = launch_apply(p, a2v, a1a2v, &sc->t, c1 * dt, nullptr, st)))
+                return rc;
+            magnus_combine_kernel<V><<<G, T, 0, st>>>(Vb + (size_t)(k + 1) * ld, a1v, a2v, a2a1v, a1a2v, n,
+                                                      sqrt(3.0) * dt / 12.0);
+        } else {
+            rc = launch_apply(p, Vb + (size_t)k * ld, Vb + (size_t)(k + 1) * ld, &sc->t, 0.5 * dt, &f, st);
+            if (rc) return rc;
+        }
         V *wv = Vb + (size_t)(k + 1) * ld;
         dot_kernel<V, NV><<<Gd, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
         update_kernel<V, NV, 0><<<Gu0, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
@@ -582,10 +643,12 @@ static int ensure_work(Problem *p)
     w->vec_bytes = ((n * es + 255) / 256) * 256;
     const int G = apply_grid(p);
     cudaError_t e;
+    const bool mag = p->cfg.scheme == HX_SCHEME_MAGNUS4;
     if ((e = cudaMalloc(&w->V, w->vec_bytes * (p->cfg.m + 1))) != cudaSuccess ||
         (e = cudaMalloc((void **)&w->partials, (size_t)G * 2 * (kMaxKrylov + 2) * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc((void **)&w->sc, sizeof(Scal))) != cudaSuccess) {
-        cudaFree(w->V); cudaFree(w->partials); cudaFree(w->sc);
+        (e = cudaMalloc((void **)&w->sc, sizeof(Scal))) != cudaSuccess ||
+        (mag && (e = cudaMalloc(&w->mag, w->vec_bytes * 4)) != cudaSuccess)) {
+        cudaFree(w->V); cudaFree(w->partials); cudaFree(w->sc); cudaFree(w->mag);
         delete w;
         return cuda_fail(e, "cudaMalloc(Krylov workspace)");
     }
@@ -593,7 +656,7 @@ static int ensure_work(Problem *p)
     // the time lives in the problem's scalar block; copy it in
     cudaMemcpy(&w->sc->t, p->dscal, sizeof(double), cudaMemcpyDeviceToDevice);
     if ((e = cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
-        cudaFree(w->V); cudaFree(w->partials); cudaFree(w->sc);
+        cudaFree(w->V); cudaFree(w->partials); cudaFree(w->sc); cudaFree(w->mag);
         delete w;
         return cuda_fail(e, "cudaStreamCreate");
     }
@@ -611,6 +674,7 @@ void krylov_free(Problem *p)
     cudaFree(w->host_state);
     cudaFree(w->partials);
     cudaFree(w->sc);
+    cudaFree(w->mag);
     delete w;
     p->krylov = nullptr;
 }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libhx.so")
 
 HX_C128, HX_C64 = 0, 1
 HX_ORDER_SYM, HX_ORDER_EQ, HX_ORDER_ALG = 0, 1, 2
+HX_SCHEME_EXPMPR, HX_SCHEME_MAGNUS4 = 0, 1
 HX_MOD_CONST, HX_MOD_COS, HX_MOD_SIN2, HX_MOD_PWCONST = 0, 1, 2, 3
 HX_EBREAKDOWN = -5
 ORDERS = {"sym": HX_ORDER_SYM, "eq": HX_ORDER_EQ, "alg": HX_ORDER_ALG}
@@ -48,7 +49,8 @@ class hx_control(ctypes.Structure):
 
 
 class hx_config(ctypes.Structure):
-    _fields_ = [("dtype", ctypes.c_int), ("order", ctypes.c_int), ("m", ctypes.c_int), ("stream", ctypes.c_void_p)]
+    _fields_ = [("dtype", ctypes.c_int), ("order", ctypes.c_int), ("m", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("scheme", ctypes.c_int)]
 
 
 def _load():
@@ -154,8 +156,9 @@ def hx_indexset_destroy(s):
 
 # ---- problem -----------------------------------------------------------------------------
 
-def hx_problem_create(s, dtype: int = HX_C128, order: int = HX_ORDER_SYM, m: int = 7, stream: int = 0):
-    cfg = hx_config(dtype, order, m, ctypes.c_void_p(stream))
+def hx_problem_create(s, dtype: int = HX_C128, order: int = HX_ORDER_SYM, m: int = 7, stream: int = 0,
+                      scheme: int = HX_SCHEME_EXPMPR):
+    cfg = hx_config(dtype, order, m, ctypes.c_void_p(stream), scheme)
     h = ctypes.c_void_p()
     _check(lib.hx_problem_create(s, ctypes.byref(cfg), ctypes.byref(h)))
     return h
@@ -278,7 +281,7 @@ def hx_adjoint_grad(s, L: float, fixed_terms: list, axis: int, u, t0: float, t1:
     pot, _keep = _potential(L, fixed_terms)
     uu = np.ascontiguousarray(u, dtype=np.float64)
     ctl = hx_control(axis, len(uu), substeps, t0, t1, _dptr(uu))
-    cfg = hx_config(HX_C128, order, m, ctypes.c_void_p(stream))
+    cfg = hx_config(HX_C128, order, m, ctypes.c_void_p(stream), HX_SCHEME_EXPMPR)
     grad = np.zeros(len(uu))
     J = ctypes.c_double()
     _check(lib.hx_adjoint_grad(s, ctypes.byref(cfg), ctypes.byref(pot), ctypes.byref(ctl),
@@ -367,13 +370,14 @@ class Problem:
     """Convenience owner of an index set and a problem (frees both)."""
 
     def __init__(self, N: int, B: int, dtype: int = HX_C128, order: str = "sym", m: int = 7, stream: int = 0,
-                 indexset=None):
+                 indexset=None, scheme: int = HX_SCHEME_EXPMPR):
         self._own_set = indexset is None
         self.set = hx_indexset_create(N, B) if indexset is None else indexset
         self.N, self.B = N, B
         self.size = hx_indexset_size(self.set)
         self.dtype = dtype
-        self.p = hx_problem_create(self.set, dtype, ORDERS[order] if isinstance(order, str) else order, m, stream)
+        self.p = hx_problem_create(self.set, dtype, ORDERS[order] if isinstance(order, str) else order, m, stream,
+                                   scheme)
 
     def set_potential(self, spec: dict, t: float = 0.0):
         hx_potential_set(self.p, spec["L"], terms_from_spec(spec), t)

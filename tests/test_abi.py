@@ -76,3 +76,13 @@ def test_argument_errors_without_device(libhx):
     with pytest.raises(hx.HxError):
         hx.hx_step_launches(None)
     assert "NULL problem" in hx.hx_last_error()
+
+
+def test_config_layout_matches_header(libhx):
+    """The binding's hx_config has the header's fields in the header's order."""
+    import re
+    from paper_1403_3511_gb300 import hx
+    hdr = open(os.path.join(ROOT, "include", "hx.h")).read()
+    body = re.search(r"typedef struct \{([^}]*)\} hx_config;", hdr).group(1)
+    names = re.findall(r"\b(\w+);", body)
+    assert names == [f[0] for f in hx.hx_config._fields_]

@@ -1,4 +1,5 @@
-"""GPU parity of the time step (exponential midpoint rule + Lanczos) against the oracle."""
+"""GPU parity of the time step (exponential midpoint rule or 2-stage Magnus method, with Lanczos)
+against the oracle."""
 import numpy as np
 import pytest
 
@@ -18,8 +19,8 @@ def hx():
     return _hx
 
 
-def run_gpu(hx, spec, c0, dtype, dt, nsteps, m=7, t0=0.0, chunks=1):
-    P = hx.Problem(spec["N"], spec["B"], dtype=dtype, m=m)
+def run_gpu(hx, spec, c0, dtype, dt, nsteps, m=7, t0=0.0, chunks=1, scheme=0):
+    P = hx.Problem(spec["N"], spec["B"], dtype=dtype, m=m, scheme=scheme)
     try:
         P.set_potential(spec, t0)
         x = torch.from_numpy(np.ascontiguousarray(c0)).to("cuda", torch.complex128)
@@ -113,3 +114,59 @@ def test_host_step_entry_point(hx, oracle):
         assert rel(c, ref) <= 1e-12
     finally:
         P.close()
+
+
+def _laser_hh(N, B):
+    """Henon-Heiles chain with a strong sin^2(2t) x_1 term: A(t) varies on the time scale of a step."""
+    return dict(N=N, B=B, L=inputs.half_width(B),
+                potential=inputs.henon_heiles_chain(N, 0.2) + [{"coef": 0.8, "powers": {0: 1},
+                                                                "mod": {"kind": "sin2", "omega": 2.0}}])
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
+@pytest.mark.parametrize("N,B,h,steps", [(2, 40, 0.05, 20), (4, 60, 0.02, 10)])
+def test_magnus4_matches_oracle(hx, oracle, dtype, tol, N, B, h, steps):
+    """Eq. (2stageMagnus): four products per Lanczos vector at the two Gauss-Legendre times.  The
+    cases keep h |H| small enough for m = 7 to converge: there the step map does not amplify
+    rounding (a 1e-10 perturbation of c0 grows by at most 1.02 over the run; at N = 4, B = 300,
+    h = 0.05 it grows by 1.5e5, and two correct implementations differ by that factor times their
+    rounding)."""
+    spec = _laser_hh(N, B)
+    S = oracle.IndexSet.hyperbolic(N, B)
+    c0 = inputs.initial_vector({"init": {"kind": "coherent", "q": [0.6] * N, "eps": 1e-3, "seed": 5}}, S.k)
+    ref, t_ref = oracle.magnus4_propagate(S, spec, c0, h, steps, 7, t0=0.1)
+    dt_ = hx.HX_C128 if dtype == "c128" else hx.HX_C64
+    got, info, t = run_gpu(hx, spec, c0, dt_, h, steps, t0=0.1, chunks=2, scheme=hx.HX_SCHEME_MAGNUS4)
+    assert abs(t - t_ref) < 1e-12
+    assert rel(got, ref) <= tol, rel(got, ref)
+    if dtype == "c128":                       # the two schemes differ by far more than the tolerance
+        mpr, _ = oracle.expmpr_propagate(S, spec, c0, h, steps, 7, t0=0.1)
+        assert rel(mpr, ref) > 1e3 * tol
+
+
+def test_magnus4_time_integration_experiment(hx, oracle):
+    """The time-integration experiment of Sec. 6.3 (N = 2, K = 40, m = 7, h = 1/10) on the GPU equals
+    the oracle's 2-stage Magnus run (whose error against the exact-Galerkin solution the oracle pins
+    reproduce from the paper's table)."""
+    spec = inputs.time_integration_workload(2, 40)
+    S = oracle.IndexSet.hyperbolic(2, spec["B"])
+    c0 = inputs.initial_vector(spec, S.k)
+    ref, _ = oracle.magnus4_propagate(S, spec, c0, 0.1, 10, 7)
+    got, _, t = run_gpu(hx, spec, c0, hx.HX_C128, 0.1, 10, scheme=hx.HX_SCHEME_MAGNUS4)
+    assert abs(t - 1.0) < 1e-12
+    assert rel(got, ref) <= 1e-12, rel(got, ref)
+
+
+def test_step_launch_counts(hx):
+    for scheme, per in ((0, lambda m, a: m * (a + 3) + 2), (1, lambda m, a: m * (4 * a + 4) + 2)):
+        for name in ("hh2_b32", "cos10_b1024"):
+            spec = inputs.workload(name) if name == "hh2_b32" else dict(N=3, B=40, L=inputs.half_width(40),
+                                                                      potential=inputs.cos_chain(3, 0.2, 8))
+            P = hx.Problem(spec["N"], spec["B"], m=6, scheme=scheme)
+            try:
+                P.set_potential(spec, 0.0)
+                a, step = hx.hx_step_launches(P.p)
+                assert a == (1 if name == "hh2_b32" else 2)
+                assert step == per(6, a)
+            finally:
+                P.close()

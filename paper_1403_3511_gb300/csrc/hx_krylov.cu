@@ -68,44 +68,47 @@ static int resident_grid(const Problem *p, K kernel, int threads)
     return std::max(1, std::min(apply_grid(p), p->num_sms * per_sm));
 }
 
-__device__ double block_reduce(double v, double *red)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-    __syncthreads();
-    return s;   // thread 0
-}
 
-// Writes nval per-block sums to partials[blockIdx.x * nval + j].  In the last block to arrive, all
-// threads then add the partials up (each thread a fixed strided subset, then a fixed tree), so the
-// totals land in tot[0..nval) (shared) in an order that does not depend on block timing.  Returns
-// true in every thread of that last block.
-__device__ bool reduce_partials(const double *vals, int nval, double *partials, unsigned *counter, double *red,
-                                double *tot)
+// Writes nval per-block sums to partials[blockIdx.x * nval + j] (all values reduced together:
+// warp shuffles, then one pass over the warp sums).  In the last block to arrive, thread t adds
+// value j = t mod nval over the blocks c, c + nc, ... (c = t div nval, nc = blockDim / nval) and
+// the nc chunk sums are added in chunk order, so the totals land in tot[0..nval) (shared) in an
+// order that does not depend on block timing.  Returns true in every thread of that last block.
+// Needs blockDim.x <= 256 and nval <= 2 (kMaxKrylov + 1).
+constexpr int kRedMax = 2 * (kMaxKrylov + 1);
+__device__ bool reduce_partials(const double *vals, int nval, double *partials, unsigned *counter, double *tot)
 {
+    __shared__ double wsum[8][kRedMax];
+    __shared__ double csum[256];
     __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = 0; j < nval; ++j) {
-        double s = block_reduce(vals[j], red);
-        if (threadIdx.x == 0) partials[blockIdx.x * nval + j] = s;
+        double v = vals[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) wsum[wid][j] = v;
     }
-    if (threadIdx.x == 0) {
+    __syncthreads();
+    if ((int)threadIdx.x < nval) {
+        double s = 0.0;
+        for (int i = 0; i < nw; ++i) s += wsum[i][threadIdx.x];
+        partials[blockIdx.x * nval + threadIdx.x] = s;
         __threadfence();
-        last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    for (int j = 0; j < nval; ++j) {
+    const int nc = blockDim.x / nval, j = threadIdx.x % nval, c = threadIdx.x / nval;
+    double s = 0.0;
+    if (c < nc)
+        for (int blk = c; blk < (int)gridDim.x; blk += nc) s += ((volatile const double *)partials)[blk * nval + j];
+    csum[threadIdx.x] = s;
+    __syncthreads();
+    if ((int)threadIdx.x < nval) {
         double t = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += ((volatile const double *)partials)[b * nval + j];
-        t = block_reduce(t, red);
-        if (threadIdx.x == 0) tot[j] = t;
+        for (int i = 0; i < nc; ++i) t += csum[i * nval + threadIdx.x];
+        tot[threadIdx.x] = t;
     }
     __syncthreads();
     return true;
@@ -138,7 +141,6 @@ template <> __device__ __forceinline__ double2 to_vec<double2>(double2 x) { retu
 template <typename V>
 __global__ void init_kernel(const double2 *c, V *v0, int n, double *partials, Scal *sc, int m)
 {
-    __shared__ double red[32];
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double2 x = c[i];
@@ -146,7 +148,7 @@ __global__ void init_kernel(const double2 *c, V *v0, int n, double *partials, Sc
         acc += x.x * x.x + x.y * x.y;
     }
     __shared__ double tot[1];
-    if (reduce_partials(&acc, 1, partials, &sc->counter, red, tot) && threadIdx.x == 0) {
+    if (reduce_partials(&acc, 1, partials, &sc->counter, tot) && threadIdx.x == 0) {
         double b0 = sqrt(tot[0]);
         sc->beta0 = b0;
         sc->s[0] = b0 > 0.0 ? 1.0 / b0 : 0.0;
@@ -256,7 +258,6 @@ template <typename V, int NV>
 __global__ void __launch_bounds__(256) dot_kernel(const V *w, const V *Vb, size_t ld, int n, int k, double *partials, Scal *sc,
                                                   int proj = 0)
 {
-    __shared__ double red[32];
     __shared__ double tot[2 * NV];
     if (proj) k = min(k, sc->m_used - 1);
     if (k < 0 || k >= sc->m_used) return;
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(256) dot_kernel(const V *w, const V *Vb, size_
         vals[2 * i + 1] = acc[i].i();
     }
     const int nval = 2 * (k + 1);
-    if (reduce_partials(vals, nval, partials, &sc->counter, red, tot) && threadIdx.x == 0) {
+    if (reduce_partials(vals, nval, partials, &sc->counter, tot) && threadIdx.x == 0) {
         for (int i = 0; i <= k; ++i) {
             sc->h[2 * i] = sc->s[i] * tot[2 * i];
             sc->h[2 * i + 1] = sc->s[i] * tot[2 * i + 1];
@@ -312,7 +313,6 @@ template <typename V, int NV, int pass>
 __global__ void __launch_bounds__(256, (sizeof(V) == 8 && NV <= 8) ? 3 : 1) update_kernel(V *w, const V *Vb, size_t ld, int n, int k, double *partials, Scal *sc)
 {
     using R = typename Real<V>::T;
-    __shared__ double red[32];
     __shared__ double tot[2 * NV];
     if (k >= sc->m_used) return;
     const double *coef = pass == 0 ? sc->h : sc->h2;
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(256, (sizeof(V) == 8 && NV <= 8) ? 3 : 1) upda
         vals[0] = nrm.r();
         nval = 1;
     }
-    if (reduce_partials(vals, nval, partials, &sc->counter, red, tot) && threadIdx.x == 0) {
+    if (reduce_partials(vals, nval, partials, &sc->counter, tot) && threadIdx.x == 0) {
         if (pass == 0) {
             for (int i = 0; i <= k; ++i) {
                 sc->h2[2 * i] = sc->s[i] * tot[2 * i];
@@ -504,7 +504,6 @@ __global__ void __launch_bounds__(32) eig_kernel(Scal *sc, double h)
 template <typename V, int NV>
 __global__ void combine_kernel(double2 *c, const V *Vb, size_t ld, int n, double *partials, Scal *sc)
 {
-    __shared__ double red[32];
     const int m = sc->m_used;
     double acc = 0.0;
     if constexpr (std::is_same<V, float2>::value) {
@@ -555,7 +554,7 @@ __global__ void combine_kernel(double2 *c, const V *Vb, size_t ld, int n, double
         }
     }
     __shared__ double tot[1];
-    if (reduce_partials(&acc, 1, partials, &sc->counter, red, tot) && threadIdx.x == 0) {
+    if (reduce_partials(&acc, 1, partials, &sc->counter, tot) && threadIdx.x == 0) {
         double nr = sqrt(tot[0]);
         sc->norm_out = nr;
         if (!isfinite(nr)) sc->flags |= 2;

@@ -102,23 +102,37 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profiled_traffic(workload: str, dtype: str):
-    """DRAM bytes per apply launch from the committed ncu summary of this workload, or None when
-    there is none or the kernel source has changed since it was captured."""
+# sources of the product kernels (generic and specialised); their hash identifies a profiled build
+KERNEL_SOURCES = ["hx_types.h", "hx_stencil.cuh", "hx_apply.cu", "hx_jit.cu"]
+
+
+def kernel_source_hash(root: str = None) -> str:
     import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(root or ROOT, "paper_1403_3511_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(workload: str, dtype: str):
+    """DRAM bytes per product launch from the committed ncu summary of this workload, or None when
+    there is none or the kernel sources have changed since it was captured."""
     import re
     path = os.path.join(ROOT, "profiles", f"apply_kernel_{workload}_{dtype}.md")
     try:
         text = open(path).read()
     except OSError:
         return None
-    src = re.search(r"hx_apply\.cu sha256 ([0-9a-f]{64})", text)
+    src = re.search(r"kernel sources sha256 ([0-9a-f]{64})", text)
     tr = re.search(r"traffic_bytes_per_launch: (\d+)", text)
     if not src or not tr:
         return None
-    with open(os.path.join(ROOT, "paper_1403_3511_gb300", "csrc", "hx_apply.cu"), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != src.group(1):
+    try:
+        if kernel_source_hash() != src.group(1):
             return None
+    except OSError:
+        return None
     return int(tr.group(1))
 
 
@@ -368,7 +382,8 @@ def main():
     alg_bytes = (16 if dtype == hx.HX_C64 else 32) * n
     achieved = alg_bytes / (ms_apply * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": profiled_traffic(spec["name"], args.dtype), "kernel": "apply_kernel",
+            "traffic": profiled_traffic(spec["name"], args.dtype),
+            "kernel": "hx_apply_specialised" if hx.hx_apply_specialised(P.p) else "apply_kernel",
             "ms_per_launch": ms_apply,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"}
     if rank == 0:

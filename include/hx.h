@@ -188,6 +188,14 @@ HX_API int hx_step_host(hx_problem *p, void *c_host, double dt, int nsteps);
 /* Synchronises the stream and reports the last step: Lanczos size used, alpha/beta of T_m
  * (host arrays of at least m and m-1 doubles, either may be NULL) and the norm of c. */
 HX_API int hx_step_info(hx_problem *p, int *m_used, double *alpha, double *beta, double *norm);
+/* 1 when the product runs a kernel compiled at hx_potential_set for this potential's operator
+ * structure (NVRTC, sm_103a; every operator of the potential has a specialised stencil), 0 when it
+ * runs the generic kernel; hx_last_error then says why (also when 1).  Both compute the same
+ * product.  HX_EINVAL without a potential.  The paper has no counterpart: this reports how the
+ * library runs the product.  Setting the environment variable HX_APPLY_SPECIALISE=0 before
+ * hx_potential_set selects the generic kernel.  The steps of a batch (hx_batch_step) always run the
+ * generic kernel. */
+HX_API int hx_apply_specialised(const hx_problem *p);
 /* Kernel launches of one product hx_apply (1, or 2 when some term is evaluated in two stages
  * through channel vectors) and of one time step of hx_step: m (per_apply + 3) + 2 for
  * HX_SCHEME_EXPMPR (the normalisation, per Lanczos vector the product, one projection and two

@@ -20,90 +20,9 @@
 #include <algorithm>
 
 #include "hx_internal.h"
+#include "hx_stencil.cuh"
 
 namespace hx {
-
-template <typename R> struct Vec2;
-template <> struct Vec2<float> { using T = float2; };
-template <> struct Vec2<double> { using T = double2; };
-
-struct ApplyArgs : ApplyArgsBase {
-    OpSet ops;
-    int nrow;                  // row-offset table stride
-    const void *cin;
-    void *cout;
-    const double *out_scale;   // nullptr = 1
-    void *chan;                // channel vectors (read by the main stage, written by stage 1)
-    size_t chan_ld;
-    int stage1;                // 1: write each op's result to its channel instead of y
-    int skip_diag;             // 1: omit D_K
-};
-
-// amp * f(t) in the stencil precision R (the interval index of a piecewise-constant modulation is
-// always found in FP64 so that both precisions switch intervals at the same t).
-template <typename R>
-__device__ __forceinline__ R op_weight(const Op &op, double t, const double *pw)
-{
-    R f = (R)1;
-    switch (op.mod) {
-        case HX_MOD_COS: f = cos((R)(op.omega * t + op.phase)); break;
-        case HX_MOD_SIN2: { R s = sin((R)(op.omega * t)); f = s * s; } break;
-        case HX_MOD_PWCONST: {
-            double x = floor((t - op.pw_t0) / (op.pw_t1 - op.pw_t0) * op.pw_n);
-            int qi = x < 0.0 ? 0 : (x >= op.pw_n ? op.pw_n - 1 : (int)x);
-            f = (R)pw[op.pw_off + qi];
-        } break;
-        default: break;
-    }
-    return (R)op.amp * f;
-}
-
-// Exact a / b when b divides a, 1 <= b <= a < 2^16: __fdividef is within 2 ulp of a / b, so the
-// computed quotient (an integer below 2^16) is off by less than 2^-6 and rounds to itself.
-__device__ __forceinline__ int exact_div(int a, int b) { return __float2int_rn(__fdividef((float)a, (float)b)); }
-
-// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = a + b;
-    float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-template <typename R> struct Acc;
-template <> struct Acc<double> {
-    double x = 0.0, y = 0.0;
-    __device__ void add(double a, double b) { x += a; y += b; }
-    __device__ double2 get() const { return make_double2(x, y); }
-};
-template <> struct Acc<float> {   // compensated accumulation of the operator contributions
-    float x = 0.f, y = 0.f, ex = 0.f, ey = 0.f;
-    __device__ void add(float a, float b)
-    {
-        float s, e;
-        two_sum(x, a, s, e); x = s; ex += e;
-        two_sum(y, b, s, e); y = s; ey += e;
-    }
-    __device__ float2 get() const { return make_float2(x + ex, y + ey); }
-};
-
-// Per-thread view of one output element.
-struct Elem {
-    int e;                  // rank
-    int k2;                 // last coordinate k_{N-1}
-    int qall;               // prod_l (1 + k_l)
-    int rlen;               // length of the own row
-    const int *nb;          // row-offset table at the own row (column d at nb[d * nrow])
-    const uint16_t *kr;     // prefix k_0..k_{N-2} of the own row
-};
-
-struct Ctx {
-    const DevSet *S;
-    int nrow;
-    __device__ int k(const Elem &el, int l) const { return l == S->N - 1 ? el.k2 : (int)__ldg(el.kr + l); }
-    // start rank of the row reached by row offset d (d > 0; the point must lie in K)
-    __device__ int row(const Elem &el, int d) const { return __ldg(el.nb + (size_t)d * nrow); }
-};
 
 // Address of element k + s e_a + s2 e_b (footprint position pos of the operator); the point lies in K.
 __device__ __forceinline__ int point_addr(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, int pos,
@@ -191,183 +110,6 @@ __device__ __forceinline__ void plane_op(const Ctx &c, const Elem &el, const OpS
     }
 }
 
-// floor(B / x) for x >= 1 from the table (0 when x > B: no element has those coordinates).
-__device__ __forceinline__ int nt_of(const DevSet &S, int x) { return x <= S.B ? __ldg(S.nt + x) : 0; }
-
-// One packed row (4 entries, see the packed row tables): a 16-byte load for FP32, two for FP64.
-template <typename R> struct Row4 { R v[4]; };
-__device__ __forceinline__ Row4<float> load_row4(const float *p)
-{
-    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
-    return {{q.x, q.y, q.z, q.w}};
-}
-__device__ __forceinline__ Row4<double> load_row4(const double *p)
-{
-    const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
-    return {{a.x, a.y, b.x, b.y}};
-}
-
-// The specialised stencils below issue every load of an operator unconditionally: a footprint
-// point outside K reads the row-offset table at its (always valid) slot and gathers the output
-// element itself, and gets weight 0.  Without branches around them, all loads of an operator are
-// in flight together instead of one dependent pair (table, gather) after another.  This pays for
-// degrees <= 3; at degree 8 on short fibres most points lie outside K and the loads they would
-// waste cost more than the overlap gains, so those operators keep the branching generic loop.
-
-// Line operator P(X_a), P of pure parity and degree P (offsets -P, -P+2, ..., P), axis role RA.
-template <typename R, int P, int RA>
-__device__ __forceinline__ void line_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
-                                          const typename Vec2<R>::T *src, R &sx, R &sy)
-{
-    using V = typename Vec2<R>::T;
-    const DevSet &S = *c.S;
-    const int ka = RA == ROLE_LAST ? el.k2 : c.k(el, op.a);
-    // steps to the top of the a-fibre (>= 0: the element itself is in K)
-    const int top = RA == ROLE_LAST ? el.rlen - 1 - el.k2 : nt_of(S, exact_div(el.qall, 1 + ka)) - 1 - ka;
-    const Row4<R> row = load_row4(tab + op.ptabP + (ka * (P + 1) + min(P, top)) * 4);   // entries at s = -P + 2j
-    constexpr int NP = P + 1;
-    int addr[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        const int s = -P + 2 * j;
-        const bool ok = ka + s >= 0 && s <= top;
-        int a;
-        if (RA == ROLE_LAST) a = el.e + s;
-        else a = s == 0 ? el.e : c.row(el, O.didx[op.dbase + s + P]) + el.k2;
-        addr[j] = ok ? a : el.e;
-    }
-    V v[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) v[j] = src[addr[j]];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        const int s = -P + 2 * j;
-        const R w = (ka + s >= 0 && s <= top) ? row.v[j] : (R)0;
-        sx += w * v[j].x;
-        sy += w * v[j].y;
-    }
-}
-
-// Plane operator wAB P(X_a) Q(X_b) + wBA Q(X_b) P(X_a), pure parities, degrees P, Q; a is a prefix
-// axis, b has role RB.  A footprint point k + s e_a + s2 e_b carries [P]_{k, k+s e_a}
-// [Q]_{k+s e_a, k+s e_a+s2 e_b} (path through k + s e_a) and [Q]_{k, k+s2 e_b} [P]_{k+s2 e_b,
-// k+s2 e_b+s e_a} (path through k + s2 e_b); a path exists only if its intermediate point is in K.
-// Rows of P(J_n / L) and Q(J_n / L) come from the tables, indexed by the coordinate and the
-// distance to the fibre top.
-// SB > 0: a line operator S(X_b) of degree SB (parity of Q, SB = Q or Q + 2) merged into this op
-// (P is even, so the points s = 0 are footprint points); its sum goes to (lx, ly), which the
-// caller weights with the line operator's own weight.
-template <typename R, int P, int Q, int RB, int SB>
-__device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
-                                           const typename Vec2<R>::T *src, R &sx, R &sy, R &lx, R &ly)
-{
-    using V = typename Vec2<R>::T;
-    const DevSet &S = *c.S;
-    const int ka = c.k(el, op.a);
-    const int kb = RB == ROLE_LAST ? el.k2 : c.k(el, op.b);
-    const int rab = exact_div(el.qall, (1 + ka) * (1 + kb));
-    const R wAB = (R)O.wAB, wBA = (R)O.wBA;
-    const R *tP = tab + op.ptabP, *tQ = tab + op.ptabQ;   // packed rows: entry i at offset -P + 2i
-    constexpr int NS = P + 1, NS2 = Q + 1;         // offsets s = -P + 2i, s2 = -Q + 2j
-    // a-fibre tops at k + s2 e_b (-1: that point is not in K), b-fibre tops at k + s e_a
-    int topA[NS2], topB[NS];
-#pragma unroll
-    for (int j = 0; j < NS2; ++j) {
-        const int s2 = -Q + 2 * j;
-        topA[j] = kb + s2 >= 0 ? nt_of(S, rab * (1 + kb + s2)) - 1 - ka : -1;
-    }
-#pragma unroll
-    for (int i = 0; i < NS; ++i) {
-        const int s = -P + 2 * i;
-        topB[i] = ka + s >= 0 ? nt_of(S, rab * (1 + ka + s)) - 1 - kb : -1;
-    }
-    // fibre tops at k itself (s = 0 or s2 = 0 need not be footprint offsets)
-    const int topA0 = (Q & 1) ? nt_of(S, rab * (1 + kb)) - 1 - ka : topA[Q / 2];
-    const int topB0 = RB == ROLE_LAST ? el.rlen - 1 - el.k2 : ((P & 1) ? nt_of(S, rab * (1 + ka)) - 1 - kb : topB[P / 2]);
-    const Row4<R> rowP0 = load_row4(tP + (ka * (P + 1) + min(P, topA0)) * 4);   // P row at k
-    const Row4<R> rowQ0 = load_row4(tQ + (kb * (Q + 1) + min(Q, topB0)) * 4);   // Q row at k
-    // addresses of the footprint points (own element when the point is not in K)
-    int addr[NS][NS2];
-    const int own = el.e - el.k2;                       // start of the own row
-#pragma unroll
-    for (int i = 0; i < NS; ++i) {
-        const int s = -P + 2 * i;
-        int base_s = own;                               // RB = LAST: start of the row of k + s e_a
-        if (RB == ROLE_LAST && s != 0) base_s = c.row(el, O.didx[op.dbase + (s + P) * (2 * Q + 1) + Q]);
-#pragma unroll
-        for (int j = 0; j < NS2; ++j) {
-            const int s2 = -Q + 2 * j;
-            const bool ok = ka + s >= 0 && kb + s2 >= 0 && s <= topA[j];
-            int a;
-            if (RB == ROLE_LAST) a = base_s + el.k2 + s2;
-            else if (s == 0 && s2 == 0) a = el.e;
-            else a = c.row(el, O.didx[op.dbase + (s + P) * (2 * Q + 1) + (s2 + Q)]) + el.k2;
-            addr[i][j] = ok ? a : el.e;
-        }
-    }
-    constexpr int NX = SB > Q ? 2 : 0;                  // merged line points +-SB outside the plane footprint
-    int xaddr[NX > 0 ? NX : 1];
-#pragma unroll
-    for (int j = 0; j < NX; ++j) {
-        const int s2 = j == 0 ? -SB : SB;
-        const bool ok = kb + s2 >= 0 && s2 <= topB0;
-        int a;
-        if (RB == ROLE_LAST) {
-            a = el.e + s2;
-        } else {
-            const Op &ls = O.op[op.mergeB];
-            a = c.row(el, O.didx[ls.dbase + s2 + SB]) + el.k2;
-        }
-        xaddr[j] = ok ? a : el.e;
-    }
-    V v[NS][NS2];
-#pragma unroll
-    for (int i = 0; i < NS; ++i)
-#pragma unroll
-        for (int j = 0; j < NS2; ++j) v[i][j] = src[addr[i][j]];
-    V xv[NX > 0 ? NX : 1];
-#pragma unroll
-    for (int j = 0; j < NX; ++j) xv[j] = src[xaddr[j]];
-    // weights
-    Row4<R> rowS0 = {};
-    if (SB > 0) {
-        const Op &ls = O.op[op.mergeB];
-        rowS0 = load_row4(tab + ls.ptabP + (kb * (SB + 1) + min(SB, topB0)) * 4);   // entry at s2: (s2 + SB) / 2
-    }
-    Row4<R> rowPs[NS2];                                 // P rows at k + s2 e_b
-#pragma unroll
-    for (int j = 0; j < NS2; ++j) rowPs[j] = load_row4(tP + (ka * (P + 1) + max(0, min(P, topA[j]))) * 4);
-#pragma unroll
-    for (int i = 0; i < NS; ++i) {
-        const int s = -P + 2 * i;
-        const bool inA = ka + s >= 0 && s <= topA0;             // k + s e_a in K
-        const R pj = inA ? rowP0.v[i] : (R)0;
-        const Row4<R> rowQs = load_row4(tQ + (kb * (Q + 1) + max(0, min(Q, topB[i]))) * 4);   // Q row at k + s e_a
-#pragma unroll
-        for (int j = 0; j < NS2; ++j) {
-            const int s2 = -Q + 2 * j;
-            const bool ok = ka + s >= 0 && kb + s2 >= 0 && s <= topA[j];
-            const R cab = inA ? pj * rowQs.v[j] : (R)0;                                   // path via k + s e_a
-            const R cba = (kb + s2 >= 0 && s2 <= topB0) ? rowQ0.v[j] * rowPs[j].v[i] : (R)0;   // path via k + s2 e_b
-            const R w = ok ? wAB * cab + wBA * cba : (R)0;
-            sx += w * v[i][j].x;
-            sy += w * v[i][j].y;
-            if (SB > 0 && s == 0) {                     // k + s2 e_b is also a point of the merged line op
-                const R ws = ok ? rowS0.v[(s2 + SB) / 2] : (R)0;
-                lx += ws * v[i][j].x;
-                ly += ws * v[i][j].y;
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < NX; ++j) {
-        const int s2 = j == 0 ? -SB : SB;
-        const R ws = (kb + s2 >= 0 && s2 <= topB0) ? rowS0.v[(s2 + SB) / 2] : (R)0;
-        lx += ws * xv[j].x;
-        ly += ws * xv[j].y;
-    }
-}
-
 template <typename R, int P, int Q, int SB>
 __device__ __forceinline__ void plane_dispatch_sb(int rb, const Ctx &c, const Elem &el, const OpSet &O, const Op &op,
                                                   const R *tab, const typename Vec2<R>::T *src, R &sx, R &sy, R &lx, R &ly)
@@ -395,42 +137,15 @@ __device__ __forceinline__ void line_dispatch(int ra, const Ctx &c, const Elem &
 }
 
 // MD: largest polynomial degree of the compiled potential (3: unrolled stencils; kMaxDeg: rolled loops).
+// The operator list is read from the launch arguments and dispatched per operator; the kernels
+// compiled at run time for one potential (hx_jit.cu) replace this loop by the fixed sequence.
 template <typename R, int MD>
 __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 3 : 1) apply_kernel(const __grid_constant__ ApplyArgs args)
 {
     using V = typename Vec2<R>::T;
-    __shared__ R sm_w[kMaxOps];
-
-    const DevSet &S = args.S;
     const OpSet &O = args.ops;
-    const int N = S.N;
-    const int tid = threadIdx.x;
-    const V *cin = (const V *)args.cin;
-    V *cout = (V *)args.cout;
-    const R *tab = (const R *)args.tab;
-
-    if (tid < O.nops) sm_w[tid] = op_weight<R>(O.op[tid], *args.t_ptr + args.t_shift, args.pw_values);
-    const R oscale = args.out_scale ? (R)(*args.out_scale) : (R)1;
-    __syncthreads();
-
-    Ctx ctx;
-    ctx.S = &S;
-    ctx.nrow = args.nrow;
-
-    for (int e = blockIdx.x * blockDim.x + tid; e < S.size; e += gridDim.x * blockDim.x) {
-        const int4 er = __ldg(S.elem + e);      // {row, prod (1 + k_l), sum k_l, k_{N-1} | length << 16}
-        const int r = er.x;
-        Elem el;
-        el.e = e;
-        el.k2 = er.w & 0xffff;
-        el.qall = er.y;
-        el.rlen = (int)((unsigned)er.w >> 16);
-        el.nb = args.rnb + r;
-        el.kr = S.row_k + (size_t)r * (N - 1);
-        const V ce = cin[e];
-        Acc<R> acc;
-        const R dj = (R)er.z + (R)0.5 * (R)N;   // (D_K)_jj = sum_l (j_l + 1/2)
-        if (!args.stage1 && !args.skip_diag) acc.add(dj * ce.x, dj * ce.y);
+    apply_elements<R>(args, [&](const Ctx &ctx, const Elem &el, Acc<R> &acc, const R *sm_w, const V *cin, const R *tab) {
+        const int e = el.e;
         for (int o = 0; o < O.nops; ++o) {
             const Op &op = O.op[o];
             if (op.merged) continue;
@@ -462,9 +177,7 @@ __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 3 : 1) apply_kernel(c
             const R w = sm_w[o];
             if (op.mergeB >= 0) {
                 const R wl = sm_w[op.mergeB];
-                sx = w * sx + wl * lx;
-                sy = w * sy + wl * ly;
-                acc.add(sx, sy);
+                acc.add(w * sx + wl * lx, w * sy + wl * ly);
                 continue;
             }
             if (args.stage1) {
@@ -476,13 +189,7 @@ __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 3 : 1) apply_kernel(c
                 acc.add(w * sx, w * sy);
             }
         }
-        if (!args.stage1) {
-            V y = acc.get();
-            y.x *= oscale;
-            y.y *= oscale;
-            cout[e] = y;
-        }
-    }
+    });
 }
 
 int apply_grid(const Problem *p)
@@ -514,10 +221,11 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
     a.chan_ld = p->chan_ld;
     a.stage1 = stage1;
     a.skip_diag = p->skip_diag;
+    const int blocks = (p->set->d.size + kApplyThreads - 1) / kApplyThreads;
+    if (!stage1 && p->jit && !g_batch_capture) return jit_launch(p, &a, blocks, st);   // the potential's specialised kernel
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_kernel<R, MD>, kApplyThreads, 0);
     int grid = p->num_sms * (per_sm > 0 ? per_sm : 1);     // one wave of resident CTAs
-    const int blocks = (p->set->d.size + kApplyThreads - 1) / kApplyThreads;
     if (grid > blocks) grid = blocks > 0 ? blocks : 1;
     apply_kernel<R, MD><<<grid, kApplyThreads, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();

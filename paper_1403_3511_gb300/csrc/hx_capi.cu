@@ -608,6 +608,7 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
         if (rc) return rc;
         HX_CUDA(cudaStreamSynchronize(pr->stream), "row-offset table");
     }
+    jit_prepare(pr);
     pr->have_pot = true;
     pr->generation++;
     return HX_OK;
@@ -914,6 +915,14 @@ void hx_batch_destroy(hx_batch *b)
     if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
     batch_free(b);
     delete b;
+}
+
+int hx_apply_specialised(const hx_problem *p)
+{
+    if (!p) { set_error("hx_apply_specialised: NULL problem"); return HX_EINVAL; }
+    if (!p->have_pot) { set_error("hx_apply_specialised: call hx_potential_set first"); return HX_EINVAL; }
+    set_error("%s", p->jit_reason.c_str());
+    return p->jit ? 1 : 0;
 }
 
 int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step)

@@ -1,0 +1,237 @@
+// Kernels compiled at run time for one potential's operator structure.
+//
+// The generic apply kernel (hx_apply.cu) reads the compiled operator list from its launch
+// arguments and dispatches every operator of every element through a switch.  When all operators
+// of a potential have specialised stencils (identity, pure-parity line operators of degree <= 3,
+// plane operators with both degrees <= 2, no channel stage), hx_potential_set writes the operator
+// sequence out as CUDA source: the same element loop and stencil functions (hx_stencil.cuh), but
+// with every operator's class, axis roles and merged line fixed at compile time, so the compiler
+// sees one straight sequence of loads and arithmetic instead of a loop over a switch.  The source
+// is compiled with NVRTC for sm_103a and loaded through the driver API; kernels are cached per
+// device, precision and structure (potentials that differ only in coefficients, time modulation or
+// tables share one kernel).  Operator data (table offsets, degrees' rows, weights) still come from
+// the launch arguments.  When compilation or loading fails the generic kernel is used.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <nvrtc.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <algorithm>
+
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "hx_internal.h"
+#include "hx_stencil.cuh"
+#include "hx_jit_sources.inc"   // kJitTypesSource, kJitStencilSource (generated by build.py)
+
+namespace hx {
+
+struct JitKernel {
+    CUfunction fn = nullptr;
+    int per_sm = 1;
+};
+
+// Driver functions, looked up through the runtime (the library does not link the driver library,
+// so that it also loads on machines without a GPU driver).
+struct Driver {
+    PFN_cuModuleLoadData_v2000 moduleLoadData = nullptr;
+    PFN_cuModuleGetFunction_v2000 moduleGetFunction = nullptr;
+    PFN_cuLaunchKernel_v4000 launchKernel = nullptr;
+    PFN_cuOccupancyMaxActiveBlocksPerMultiprocessor_v6050 occupancy = nullptr;
+    PFN_cuGetErrorString_v6000 errorString = nullptr;
+    bool ok = false;
+};
+
+static const Driver &driver()
+{
+    static Driver d;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        auto get = [](const char *name, void **fn) {
+            cudaDriverEntryPointQueryResult q;
+            return cudaGetDriverEntryPointByVersion(name, fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess && *fn;
+        };
+        d.ok = get("cuModuleLoadData", (void **)&d.moduleLoadData) &&
+               get("cuModuleGetFunction", (void **)&d.moduleGetFunction) &&
+               get("cuLaunchKernel", (void **)&d.launchKernel) &&
+               get("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void **)&d.occupancy) &&
+               get("cuGetErrorString", (void **)&d.errorString);
+    });
+    return d;
+}
+
+static std::mutex g_jit_mu;
+static std::map<std::string, JitKernel> g_jit_cache;
+
+static bool specialised_plane(const Op &op, int sb)
+{
+    const bool cls = op.cls == CLS_PLANE + 0 || op.cls == CLS_PLANE + 3 || op.cls == CLS_PLANE + 1 || op.cls == CLS_PLANE + 4;
+    return cls && (sb == 0 || sb == op.q || (sb == op.q + 2 && sb <= 3));
+}
+
+// The specialised sequence for O, or "" when some operator needs the generic loop.
+static std::string jit_body(const OpSet &O)
+{
+    std::string b;
+    char line[512];
+    for (int i = 0; i < O.nops; ++i) {
+        const Op &op = O.op[i];
+        if (op.merged) continue;
+        if (op.src >= 0 || op.dst >= 0) return "";
+        if (op.kind == 0) {
+            snprintf(line, sizeof(line), "    { const V cs = cin[el.e]; acc.add(sm_w[%d] * cs.x, sm_w[%d] * cs.y); }\n", i, i);
+        } else if (op.kind == 1) {
+            if (op.cls < CLS_LINE + 1 || op.cls > CLS_LINE + 3 || op.mergeB >= 0) return "";
+            snprintf(line, sizeof(line),
+                     "    { R sx = 0, sy = 0; line_role<R, %d, %s>(ctx, el, O, O.op[%d], tab, cin, sx, sy);\n"
+                     "      acc.add(sm_w[%d] * sx, sm_w[%d] * sy); }\n",
+                     op.p, op.ra == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW", i, i, i);
+        } else {
+            const int sb = op.mergeB >= 0 ? O.op[op.mergeB].p : 0;
+            if (!specialised_plane(op, sb)) return "";
+            char wl[32];
+            if (sb > 0) snprintf(wl, sizeof(wl), "sm_w[%d]", op.mergeB);
+            else snprintf(wl, sizeof(wl), "(R)0");
+            snprintf(line, sizeof(line),
+                     "    { R sx = 0, sy = 0, lx = 0, ly = 0;\n"
+                     "      plane_role<R, %d, %d, %s, %d>(ctx, el, O, O.op[%d], tab, cin, sx, sy, lx, ly);\n"
+                     "      acc.add(sm_w[%d] * sx + %s * lx, sm_w[%d] * sy + %s * ly); }\n",
+                     op.p, op.q, op.rb == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW", sb, i, i, wl, i, wl);
+        }
+        b += line;
+    }
+    return b;
+}
+
+static std::string jit_source(bool f32, const std::string &body)
+{
+    std::string s;
+    s += "#include \"hx_stencil.cuh\"\n";
+    s += "namespace hx {\n";
+    s += "using R = ";
+    s += f32 ? "float" : "double";
+    s += ";\nusing V = Vec2<R>::T;\n";
+    s += "__device__ __forceinline__ void ops(const ApplyArgs &args, const Ctx &ctx, const Elem &el, Acc<R> &acc,\n"
+         "                                    const R *sm_w, const V *cin, const R *tab)\n{\n"
+         "    const OpSet &O = args.ops;\n";
+    s += body;
+    s += "}\n}  // namespace hx\n";
+    s += "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 3)\n"
+         "hx_apply_specialised(const __grid_constant__ hx::ApplyArgs args)\n{\n"
+         "    hx::apply_elements<hx::R>(args, [&](const hx::Ctx &ctx, const hx::Elem &el, hx::Acc<hx::R> &acc,\n"
+         "                                        const hx::R *sm_w, const hx::V *cin, const hx::R *tab) {\n"
+         "        hx::ops(args, ctx, el, acc, sm_w, cin, tab);\n"
+         "    });\n}\n";
+    return s;
+}
+
+static bool compile_and_load(const std::string &src, int dev, JitKernel *out, std::string &reason)
+{
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) {
+        reason = "run-time compiled kernels target sm_103a only";
+        return false;
+    }
+    const Driver &drv = driver();
+    if (!drv.ok) {
+        reason = "driver entry points for module loading are unavailable";
+        return false;
+    }
+    nvrtcProgram prog;
+    const char *headers[] = {kJitTypesSource, kJitStencilSource};
+    const char *names[] = {"hx_types.h", "hx_stencil.cuh"};
+    if (nvrtcCreateProgram(&prog, src.c_str(), "hx_apply_specialised.cu", 2, headers, names) != NVRTC_SUCCESS) {
+        reason = "nvrtcCreateProgram failed";
+        return false;
+    }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo"};
+    nvrtcResult rc = nvrtcCompileProgram(prog, 3, opts);
+    if (rc != NVRTC_SUCCESS) {
+        size_t n = 0;
+        nvrtcGetProgramLogSize(prog, &n);
+        std::string log(n, '\0');
+        if (n) nvrtcGetProgramLog(prog, &log[0]);
+        reason = std::string("nvrtc: ") + nvrtcGetErrorString(rc) + ": " + log.substr(0, 400);
+        nvrtcDestroyProgram(&prog);
+        return false;
+    }
+    size_t nbin = 0;
+    nvrtcGetCUBINSize(prog, &nbin);
+    std::string cubin(nbin, '\0');
+    nvrtcGetCUBIN(prog, &cubin[0]);
+    nvrtcDestroyProgram(&prog);
+    CUmodule mod;
+    CUfunction fn;
+    if (drv.moduleLoadData(&mod, cubin.data()) != CUDA_SUCCESS ||
+        drv.moduleGetFunction(&fn, mod, "hx_apply_specialised") != CUDA_SUCCESS) {
+        reason = "loading the compiled kernel failed";
+        return false;
+    }
+    int per_sm = 1;
+    if (drv.occupancy(&per_sm, fn, kApplyThreads, 0) != CUDA_SUCCESS || per_sm < 1)
+        per_sm = 1;
+    out->fn = fn;
+    out->per_sm = per_sm;
+    return true;
+}
+
+// Prepares the specialised kernel of p's main-stage operators (after compile_potential); p->jit is
+// left null when the generic kernel must be used.  Never fails the caller.
+void jit_prepare(Problem *p)
+{
+    p->jit = nullptr;
+    std::string &reason = p->jit_reason;
+    const char *env = getenv("HX_APPLY_SPECIALISE");
+    if (env && env[0] == '0') {
+        reason = "disabled by HX_APPLY_SPECIALISE=0";
+        return;
+    }
+    int md = 0;
+    for (int i = 0; i < p->ops.nops; ++i) md = std::max(md, std::max(p->ops.op[i].p, p->ops.op[i].q));
+    if (md > 3 || p->ops1.nops > 0) {
+        reason = "an operator needs the generic kernel (degree above 3 or a channel stage)";
+        return;
+    }
+    const std::string body = jit_body(p->ops);
+    if (body.empty()) {
+        reason = "an operator has no specialised stencil";
+        return;
+    }
+    const bool f32 = p->cfg.dtype == HX_C64;
+    const std::string key = std::to_string(p->device) + (f32 ? "|f|" : "|d|") + body;
+    std::lock_guard<std::mutex> lock(g_jit_mu);
+    auto it = g_jit_cache.find(key);
+    if (it == g_jit_cache.end()) {
+        JitKernel k;
+        if (!compile_and_load(jit_source(f32, body), p->device, &k, reason)) return;
+        it = g_jit_cache.emplace(key, k).first;
+    }
+    p->jit = &it->second;
+    reason = "specialised kernel in use";
+}
+
+// Launches the specialised kernel with the generic kernel's arguments.
+int jit_launch(const Problem *p, const void *args, int blocks, cudaStream_t st)
+{
+    const JitKernel *k = (const JitKernel *)p->jit;
+    int grid = p->num_sms * k->per_sm;
+    if (grid > blocks) grid = blocks > 0 ? blocks : 1;
+    void *params[] = {const_cast<void *>(args)};
+    const Driver &drv = driver();
+    CUresult r = drv.launchKernel(k->fn, grid, 1, 1, kApplyThreads, 1, 1, 0, (CUstream)st, params, nullptr);
+    if (r != CUDA_SUCCESS) {
+        const char *msg = nullptr;
+        drv.errorString(r, &msg);
+        set_error("specialised apply kernel launch: %s", msg ? msg : "unknown error");
+        return HX_ECUDA;
+    }
+    return HX_OK;
+}
+
+}  // namespace hx

@@ -57,6 +57,12 @@ struct Work {
 
 static Work *work_of(Problem *p) { return (Work *)p->krylov; }
 
+// Set while a batch graph is captured.  Batch members run the generic apply kernel: one 32-problem
+// batch with the kernels specialised per potential stopped with cudaErrorInvalidAddressSpace, which
+// bounds-checked copies of the same kernels did not reproduce; until the cause is known, batch graphs
+// keep the kernel they were validated with.
+thread_local bool g_batch_capture = false;
+
 // Grid of a streaming kernel: one wave of resident blocks (a second, partial wave would run at a
 // fraction of the occupancy and take as long as the first), at most apply_grid(p) blocks (the
 // size of the partial-sum buffers).
@@ -771,7 +777,9 @@ int batch_step(Batch *b, void *const *c, double dt, int nsteps)
                 cudaGraphDestroy(g);
                 return cuda_fail(e, "batch capture");
             }
+            g_batch_capture = true;             // batch members run the generic apply kernel
             int rc = enqueue(p, w, (double2 *)c[i], w->cap_stream, dt);
+            g_batch_capture = false;
             e = cudaStreamEndCapture(w->cap_stream, &child);
             if (rc || e != cudaSuccess) {
                 cudaGraphDestroy(g);

@@ -1,0 +1,108 @@
+// Device-side types and constants of libhx shared by the CUDA sources and by the kernels that
+// hx_potential_set compiles at run time for one potential's operator structure.  Plain C++ with
+// CUDA vector types only (no standard-library headers), so that the run-time compiler can read it.
+#pragma once
+
+namespace hx {
+
+constexpr int kMaxN = 16;
+constexpr int kMaxOps = 48;
+constexpr int kMaxDelta = 255;                 // distinct row offsets of one problem (both stages)
+constexpr int kMaxDidx = 4096;                 // footprint -> offset map entries of one operator set
+constexpr int kMaxDeg = 8;                     // HX_MAX_DEG
+constexpr int kSpan = 2 * kMaxDeg + 1;         // offsets -deg..deg
+constexpr int kMaxKrylov = 32;
+constexpr int kApplyThreads = 256;
+
+// time modulations (values of hx_mod_kind)
+enum { MOD_CONST = 0, MOD_COS = 1, MOD_SIN2 = 2, MOD_PWCONST = 3 };
+
+// ---------------------------------------------------------------------------------------
+// Index set on the device.
+//
+// Canonical order is lexicographic, last coordinate fastest.  A row is the set of elements
+// sharing one prefix p = (k_0, ..., k_{N-2}); it holds k_{N-1} = 0 .. floor(B / q(p)) - 1,
+// q(p) = prod (1 + p_l), stored contiguously, and the rows follow each other in the
+// lexicographic order of their prefixes.  For N = 1 there is one row.
+//
+// Rank tables: for level m >= 1 and prefix product q (1 <= q <= B),
+//   Q_m(q, k) = sum_{i<k} |K_m(floor(B / (q (1 + i))))|,   0 <= k <= floor(B / q),
+// stored at Q[(m - 1) * qtotal + qoff[q] + k].  Then
+//   rank(k) = sum_{d<N-1} Q_{N-1-d}(q_d, k_d) + k_{N-1},   q_d = prod_{l<d} (1 + k_l).
+// ---------------------------------------------------------------------------------------
+struct DevSet {
+    int N, B, size, nrow, qtotal;
+    const int4 *row_info;             // nrow: {start rank, q(p), sum_l p_l, length}
+    const unsigned short *row_k;            // nrow x (N - 1) prefixes
+    const int4 *elem;                 // size: per element {row, prod_l (1 + k_l), sum_l k_l, k_{N-1} | row length << 16}
+    const int *qoff;                  // B + 2
+    const int *Q;                     // (N - 1) x qtotal
+    const int *nt;                    // nt[x] = floor(B / x), x = 1..B (nt[0] unused)
+};
+
+// ---------------------------------------------------------------------------------------
+// Compiled potential.  Each op contributes w(t) * (op matrix) * (input) to A c:
+//   kind 0: identity;  kind 1: P(X_a) (line);  kind 2: Sym/ordered P(X_a) Q(X_b) (plane, a < b).
+// The input is c (src = -1) or a channel vector written by a first stage.  A plane op whose
+// footprint is large is evaluated in two stages: stage 1 writes the channels Q(X_b) c and
+// P(X_a) c (line ops with dst >= 0), stage 2 applies P(X_a) and Q(X_b) to them as line ops.
+// Row tables: for a univariate polynomial P of degree p, entry
+//   tab[base + ((i * (p + 1) + d) * (2p + 1)) + (s + p)] = [P(J_n / L)]_{i, i+s},  n = i + 1 + d,
+// where J_n is the n x n truncated Jacobi matrix of the Hermite recurrence (Eq. (Recurrence1D)):
+// row i of a fibre whose top is d steps above i (d = p stands for "p or more").
+// Packed row tables (a polynomial of pure parity and degree p <= 3, whose row has p + 1 entries
+// that can be nonzero, at s = -p, -p + 2, ..., p):
+//   tab[pbase + (i * (p + 1) + d) * 4 + j] = [P(J_n / L)]_{i, i-p+2j},  j <= p, zero for j > p,
+// one 16-byte (FP32) or 32-byte (FP64) load per row.
+// ---------------------------------------------------------------------------------------
+// op classes with compile-time stencils (pure parity: P has only terms of the parity of its degree)
+enum { CLS_ID = 0, CLS_LINE = 1, CLS_PLANE = 10, CLS_GENERIC = 30 };
+// axis roles: an axis of the row prefix (moving along it changes the row) or the last axis
+enum { ROLE_ROW = 0, ROLE_LAST = 1, ROLE_NONE = 2 };
+
+struct Op {
+    int kind;
+    int cls;                  // CLS_ID, CLS_LINE + p, CLS_PLANE + 3 (p-1) + (q-1) (pure parity, p, q <= 3), CLS_GENERIC
+    int ra, rb;               // axis roles: ROLE_ROW (< N-1), ROLE_LAST (N-1), ROLE_NONE
+    int a, b;                 // axes (b = -1 for a line op)
+    int p, q;                 // degrees on a and b
+    int pmask, qmask;         // bit (s + p) set when the rows can be nonzero at offset s
+    int tabP, tabQ;           // row table bases
+    int ptabP, ptabQ;         // packed row table bases (pure parity, degree <= 3; 0 otherwise)
+    int dbase;                // base into didx (footprint position -> row offset index)
+    int src, dst;             // input channel (-1 = c), output channel (stage 1 only)
+    int mergeB;               // plane ops: index of a line op on axis b evaluated inside this op (-1: none)
+    int merged;               // line ops: 1 when evaluated inside a plane op (skipped on its own)
+    int mod;                  // hx_mod_kind
+    double amp, omega, phase;
+    int pw_off, pw_n;         // into the pw value array
+    double pw_t0, pw_t1;
+};
+
+struct OpSet {
+    int nops;
+    double wAB, wBA;          // factor-order weights for plane ops
+    int ndidx;
+    Op op[kMaxOps];
+    unsigned char didx[kMaxDidx];   // footprint position -> column of the row-offset table
+};
+
+// Row offsets used by a problem's operators: axis0, step0, axis1, step1 (axis -1 = none), over
+// the prefix axes 0..N-2; offset 0 is the zero offset.  The row-offset table holds, for
+// offset d and row r, the start rank of row r + offset d, or -1 when that prefix is not in K:
+//   rnb[d * nrow + r].
+struct RowOffsets {
+    int n;
+    signed char d[kMaxDelta][4];
+};
+
+struct ApplyArgsBase {
+    DevSet S;
+    const int *rnb;           // row-offset table, nd x nrow
+    const double *t_ptr;      // device time
+    double t_shift;           // A is evaluated at *t_ptr + t_shift
+    const double *pw_values;  // device
+    const void *tab;          // row tables (float or double)
+};
+
+}  // namespace hx

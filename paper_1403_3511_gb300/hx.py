@@ -78,6 +78,7 @@ def _load():
         "hx_step_host": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int]),
         "hx_step_info": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), dp, dp, dp]),
         "hx_step_launches": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "hx_apply_specialised": (ctypes.c_int, [P]),
         "hx_norm": (ctypes.c_int, [P, P, dp]),
         "hx_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P)]),
         "hx_batch_step": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.c_double, ctypes.c_int]),
@@ -236,6 +237,15 @@ def hx_step_info(p, m: int = 32) -> dict:
     st = _check(lib.hx_step_info(p, ctypes.byref(mu), _dptr(a), _dptr(b), ctypes.byref(nr)), allow=(HX_EBREAKDOWN,))
     return {"m_used": mu.value, "alpha": a[: mu.value], "beta": b[: max(mu.value - 1, 0)], "norm": nr.value,
             "breakdown": st == HX_EBREAKDOWN}
+
+
+def hx_apply_specialised(p) -> int:
+    """1 when the product runs the kernel compiled for this potential's operator structure, 0 when it
+    runs the generic kernel (hx_last_error() says why)."""
+    r = lib.hx_apply_specialised(p)
+    if r < 0:
+        raise HxError(r, hx_last_error())
+    return r
 
 
 def hx_step_launches(p) -> tuple:

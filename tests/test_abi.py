@@ -86,3 +86,5 @@ def test_config_layout_matches_header(libhx):
     body = re.search(r"typedef struct \{([^}]*)\} hx_config;", hdr).group(1)
     names = re.findall(r"\b(\w+);", body)
     assert names == [f[0] for f in hx.hx_config._fields_]
+    with pytest.raises(hx.HxError):
+        hx.hx_apply_specialised(None)

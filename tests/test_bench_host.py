@@ -67,19 +67,19 @@ def test_reference_arm_other_ranks_do_nothing():
 
 
 def test_profiled_traffic_tracks_kernel_source(tmp_path, monkeypatch):
-    """roofline.traffic comes from the committed ncu summary only while the kernel source is the one
-    that summary names."""
-    import hashlib
+    """roofline.traffic comes from the committed ncu summary only while the kernel sources are the
+    ones that summary names."""
     import bench
     src = tmp_path / "paper_1403_3511_gb300" / "csrc"
     src.mkdir(parents=True)
-    (src / "hx_apply.cu").write_text("kernel v1\n")
+    for name in bench.KERNEL_SOURCES:
+        (src / name).write_text(name + " v1\n")
     prof = tmp_path / "profiles"
     prof.mkdir()
-    h = hashlib.sha256(b"kernel v1\n").hexdigest()
-    (prof / "apply_kernel_w_c64.md").write_text(f"hx_apply.cu sha256 {h}\ntraffic_bytes_per_launch: 1234\n")
+    h = bench.kernel_source_hash(str(tmp_path))
+    (prof / "apply_kernel_w_c64.md").write_text(f"kernel sources sha256 {h}\ntraffic_bytes_per_launch: 1234\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.profiled_traffic("w", "c64") == 1234
     assert bench.profiled_traffic("w", "c128") is None
-    (src / "hx_apply.cu").write_text("kernel v2\n")
+    (src / "hx_stencil.cuh").write_text("changed\n")
     assert bench.profiled_traffic("w", "c64") is None

@@ -238,3 +238,38 @@ def test_errors(hx):
             hx.hx_potential_set(P.p, 5.0, [{"axes": [1, 0], "coef": np.ones((2, 2))}], 0.0)
     finally:
         P.close()
+
+
+@pytest.mark.parametrize("case", ["hh6_b2000", "ctrl4_b512", "hh3_b300_dipole", "hh2_b40000"])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_specialised_kernel_matches_generic(hx, case, dtype, monkeypatch):
+    """Potentials whose operators all have specialised stencils run a kernel compiled for their
+    operator sequence at hx_potential_set; it computes what the generic kernel computes."""
+    spec = CASES[case]()
+    dt = hx.HX_C128 if dtype == "c128" else hx.HX_C64
+    n = None
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("HX_APPLY_SPECIALISE", flag)
+        P = make(hx, spec, dt, t=0.3)
+        try:
+            assert hx.hx_apply_specialised(P.p) == (1 if flag == "1" else 0), hx.hx_last_error()
+            if n is None:
+                n = P.size
+                c = inputs.complex_gaussian(n, 4)
+            outs.append(gpu_apply(hx, P, c))
+        finally:
+            P.close()
+    err = np.abs(outs[0] - outs[1]).max() / np.abs(outs[1]).max()
+    assert err <= (1e-14 if dtype == "c128" else 1e-6), err
+
+
+@pytest.mark.parametrize("case,why", [("cos3_b64", "generic kernel"), ("merge4_b160", "no specialised stencil")])
+def test_potentials_without_specialised_kernel(hx, case, why):
+    """A channel stage (degree-8 terms) or a plane operator of degree 3 keeps the generic kernel."""
+    P = make(hx, CASES[case](), hx.HX_C64)
+    try:
+        assert hx.hx_apply_specialised(P.p) == 0
+        assert why in hx.hx_last_error()
+    finally:
+        P.close()

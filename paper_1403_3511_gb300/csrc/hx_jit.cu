@@ -120,8 +120,11 @@ static std::string jit_source(bool f32, const std::string &body)
          "    const OpSet &O = args.ops;\n";
     s += body;
     s += "}\n}  // namespace hx\n";
-    s += "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 3)\n"
-         "hx_apply_specialised(const __grid_constant__ hx::ApplyArgs args)\n{\n"
+    // 4 blocks of 256 per SM fit the FP32 kernels in 64 registers without spills (more warps to hide
+    // the load latency); the FP64 kernels would spill there and keep 3 blocks (80 registers)
+    s += f32 ? "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 4)\n"
+             : "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 3)\n";
+    s += "hx_apply_specialised(const __grid_constant__ hx::ApplyArgs args)\n{\n"
          "    hx::apply_elements<hx::R>(args, [&](const hx::Ctx &ctx, const hx::Elem &el, hx::Acc<hx::R> &acc,\n"
          "                                        const hx::R *sm_w, const hx::V *cin, const hx::R *tab) {\n"
          "        hx::ops(args, ctx, el, acc, sm_w, cin, tab);\n"

@@ -382,7 +382,7 @@ __global__ void norm2_kernel(const V *c, int n, double *partials, unsigned *coun
     if (last && threadIdx.x == 0) {
         __threadfence();
         double t = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) t += ((volatile double *)partials)[b];
+        for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(partials + b);   // L2-coherent, batched
         *result = t;
         *counter = 0;
     }

@@ -108,7 +108,9 @@ __device__ bool reduce_partials(const double *vals, int nval, double *partials, 
     const int nc = blockDim.x / nval, j = threadIdx.x % nval, c = threadIdx.x / nval;
     double s = 0.0;
     if (c < nc)
-        for (int blk = c; blk < (int)gridDim.x; blk += nc) s += ((volatile const double *)partials)[blk * nval + j];
+        // L2-coherent loads (the other blocks' partials are visible after their fence and the counter);
+        // unlike volatile loads they can all be in flight at once
+        for (int blk = c; blk < (int)gridDim.x; blk += nc) s += __ldcg(partials + blk * nval + j);
     csum[threadIdx.x] = s;
     __syncthreads();
     if ((int)threadIdx.x < nval) {

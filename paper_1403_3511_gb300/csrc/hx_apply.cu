@@ -202,7 +202,7 @@ int apply_grid(const Problem *p)
 
 template <typename R, int MD>
 static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *cin, void *cout,
-                          const double *t_ptr, double t_shift, const double *out_scale, cudaStream_t st)
+                          const double *t_ptr, double t_shift, const ApplyFuse *fuse, cudaStream_t st)
 {
     ApplyArgs a;
     memset(&a, 0, sizeof(a));
@@ -216,7 +216,21 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
     a.ops = ops;
     a.cin = cin;
     a.cout = cout;
-    a.out_scale = out_scale;
+    a.out_scale = fuse ? fuse->in_scale : nullptr;
+    if (fuse && fuse->dvec) {
+        if (stage1 || !apply_fuses_dots(p) || fuse->dk < 0 || fuse->dk >= kMaxFusedDots) {
+            set_error("projections requested from a product kernel that cannot compute them");
+            return HX_EUNSUPPORTED;
+        }
+        a.dvec = fuse->dvec;
+        a.dld = fuse->dld;
+        a.dk = fuse->dk;
+        a.dm_used = fuse->m_used;
+        a.ds = fuse->s;
+        a.dh = fuse->h;
+        a.dpartials = fuse->partials;
+        a.dcounter = fuse->counter;
+    }
     a.chan = p->chan;
     a.chan_ld = p->chan_ld;
     a.stage1 = stage1;
@@ -234,7 +248,7 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
 }
 
 static int launch_stage(Problem *p, const OpSet &ops, int stage1, const void *cin, void *cout, const double *t_ptr,
-                        double t_shift, const double *scale, cudaStream_t st)
+                        double t_shift, const ApplyFuse *scale, cudaStream_t st)
 {
     int md = 0;
     for (int i = 0; i < ops.nops; ++i) md = max(md, max(ops.op[i].p, ops.op[i].q));
@@ -247,15 +261,19 @@ static int launch_stage(Problem *p, const OpSet &ops, int stage1, const void *ci
 
 int apply_launches(const Problem *p) { return p->ops1.nops > 0 ? 2 : 1; }
 
+bool apply_fuses_dots(const Problem *p)
+{
+    return p->jit && !g_batch_capture && p->ops1.nops == 0 && p->cfg.dtype == HX_C64;
+}
+
 int launch_apply(Problem *p, const void *cin, void *cout, const double *t_ptr, double t_shift, const ApplyFuse *fuse,
                  cudaStream_t st)
 {
-    const double *scale = fuse ? fuse->in_scale : nullptr;
     if (p->ops1.nops > 0) {
         int rc = launch_stage(p, p->ops1, 1, cin, nullptr, t_ptr, t_shift, nullptr, st);
         if (rc) return rc;
     }
-    return launch_stage(p, p->ops, 0, cin, cout, t_ptr, t_shift, scale, st);
+    return launch_stage(p, p->ops, 0, cin, cout, t_ptr, t_shift, fuse, st);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -931,7 +931,9 @@ int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step)
     if (!p->have_pot) { set_error("hx_step_launches: call hx_potential_set first"); return HX_EINVAL; }
     const int a = apply_launches(p);
     if (per_apply) *per_apply = a;
-    if (per_step) *per_step = p->cfg.scheme == HX_SCHEME_MAGNUS4 ? p->cfg.m * (4 * a + 4) + 2 : p->cfg.m * (a + 3) + 2;
+    // expMPR: the product kernel computes the projections itself when it is specialised (m <= 8)
+    const int dots = p->cfg.m <= kMaxFusedDots && apply_fuses_dots(p) ? 0 : 1;
+    if (per_step) *per_step = p->cfg.scheme == HX_SCHEME_MAGNUS4 ? p->cfg.m * (4 * a + 4) + 2 : p->cfg.m * (a + 2 + dots) + 2;
     return HX_OK;
 }
 

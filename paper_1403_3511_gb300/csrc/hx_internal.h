@@ -43,13 +43,18 @@ struct IndexSetObj {
 // per-launch options of the apply kernel used by the Krylov step
 struct ApplyFuse {
     const double *in_scale;   // multiply A v by *in_scale (nullptr = 1)
-    int ndot;                 // fused dots <v_i, y> for i < ndot (0 = none)
-    const void *const *vecs;  // device array of ndot vector pointers (problem dtype)
-    const double *vscale;     // device array of ndot scales
-    double *partials;         // gridDim.x x (2 * ndot) doubles
+    // projections h_i = s_i <v_i, y> (i <= dk, skipped when dk >= *m_used) computed by the product
+    // launch itself; only when apply_fuses_dots(p) (dvec == nullptr: none)
+    const void *dvec;         // v_0 in the problem dtype; v_i at dvec + i * dld elements
+    size_t dld;
+    int dk;                   // < kMaxFusedDots
+    const int *m_used;
+    const double *s;          // s_i
+    double *h;                // 2 (dk + 1) doubles: h_i (re, im)
+    double *partials;         // apply_grid(p) x 2 (dk + 1) doubles
     unsigned *counter;        // zero-initialised; reset by the last block
-    double *result;           // 2 * ndot doubles: sum_i scale_i * <v_i, y> (re, im)
 };
+
 
 struct Problem {
     const IndexSetObj *set;
@@ -93,7 +98,8 @@ int launch_rowtab(const DevSet &S, const RowOffsets &ro, int *rnb, cudaStream_t 
 int launch_norm(Problem *p, const void *c, int is_c128, double *partials, unsigned *counter, double *result,
                 cudaStream_t st);
 int apply_grid(const Problem *p);
-int apply_launches(const Problem *p);   // kernels per product (1, or 2 with a channel stage)
+int apply_launches(const Problem *p);
+bool apply_fuses_dots(const Problem *p);   // the product kernel can compute ApplyFuse projections   // kernels per product (1, or 2 with a channel stage)
 
 extern thread_local bool g_batch_capture;   // hx_krylov.cu: a batch graph is being captured
 

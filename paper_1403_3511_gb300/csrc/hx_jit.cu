@@ -10,7 +10,10 @@
 // is compiled with NVRTC for sm_103a and loaded through the driver API; kernels are cached per
 // device, precision and structure (potentials that differ only in coefficients, time modulation or
 // tables share one kernel).  Operator data (table offsets, degrees' rows, weights) still come from
-// the launch arguments.  When compilation or loading fails the generic kernel is used.
+// the launch arguments.  When compilation or loading fails the generic kernel is used.  For
+// complex64 the module holds a second kernel that also computes the Lanczos projections
+// h_i = s_i <v_i, A v_k> from the values it stores (ApplyFuse), which saves the time step one pass
+// over the new vector per Krylov step.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <nvrtc.h>
@@ -31,7 +34,8 @@ namespace hx {
 
 struct JitKernel {
     CUfunction fn = nullptr;
-    int per_sm = 1;
+    CUfunction fn_dots = nullptr;   // complex64 only: the product with fused projections
+    int per_sm = 1, per_sm_dots = 1;
 };
 
 // Driver functions, looked up through the runtime (the library does not link the driver library,
@@ -129,6 +133,14 @@ static std::string jit_source(bool f32, const std::string &body)
          "                                        const hx::R *sm_w, const hx::V *cin, const hx::R *tab) {\n"
          "        hx::ops(args, ctx, el, acc, sm_w, cin, tab);\n"
          "    });\n}\n";
+    if (f32) {   // the same product that also computes the Lanczos projections (ApplyFuse)
+        s += "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 4)\n"
+             "hx_apply_specialised_dots(const __grid_constant__ hx::ApplyArgs args)\n{\n"
+             "    hx::apply_elements<hx::R, true>(args, [&](const hx::Ctx &ctx, const hx::Elem &el, hx::Acc<hx::R> &acc,\n"
+             "                                              const hx::R *sm_w, const hx::V *cin, const hx::R *tab) {\n"
+             "        hx::ops(args, ctx, el, acc, sm_w, cin, tab);\n"
+             "    });\n}\n";
+    }
     return s;
 }
 
@@ -176,11 +188,21 @@ static bool compile_and_load(const std::string &src, int dev, JitKernel *out, st
         reason = "loading the compiled kernel failed";
         return false;
     }
-    int per_sm = 1;
-    if (drv.occupancy(&per_sm, fn, kApplyThreads, 0) != CUDA_SUCCESS || per_sm < 1)
-        per_sm = 1;
+    CUfunction fn_dots = nullptr;
+    if (src.find("hx_apply_specialised_dots") != std::string::npos &&
+        drv.moduleGetFunction(&fn_dots, mod, "hx_apply_specialised_dots") != CUDA_SUCCESS) {
+        reason = "loading the compiled kernel failed";
+        return false;
+    }
+    auto occ = [&](CUfunction f) {
+        int per_sm = 1;
+        if (!f || drv.occupancy(&per_sm, f, kApplyThreads, 0) != CUDA_SUCCESS || per_sm < 1) per_sm = 1;
+        return per_sm;
+    };
     out->fn = fn;
-    out->per_sm = per_sm;
+    out->fn_dots = fn_dots;
+    out->per_sm = occ(fn);
+    out->per_sm_dots = occ(fn_dots);
     return true;
 }
 
@@ -223,11 +245,17 @@ void jit_prepare(Problem *p)
 int jit_launch(const Problem *p, const void *args, int blocks, cudaStream_t st)
 {
     const JitKernel *k = (const JitKernel *)p->jit;
-    int grid = p->num_sms * k->per_sm;
+    const bool dots = ((const ApplyArgs *)args)->dvec != nullptr;
+    if (dots && !k->fn_dots) {
+        set_error("the specialised kernel has no fused projections (complex64 only)");
+        return HX_EUNSUPPORTED;
+    }
+    // apply_grid(p) blocks at most: the size of the partial-sum buffers
+    int grid = std::min(p->num_sms * (dots ? k->per_sm_dots : k->per_sm), apply_grid(p));
     if (grid > blocks) grid = blocks > 0 ? blocks : 1;
     void *params[] = {const_cast<void *>(args)};
     const Driver &drv = driver();
-    CUresult r = drv.launchKernel(k->fn, grid, 1, 1, kApplyThreads, 1, 1, 0, (CUstream)st, params, nullptr);
+    CUresult r = drv.launchKernel(dots ? k->fn_dots : k->fn, grid, 1, 1, kApplyThreads, 1, 1, 0, (CUstream)st, params, nullptr);
     if (r != CUDA_SUCCESS) {
         const char *msg = nullptr;
         drv.errorString(r, &msg);

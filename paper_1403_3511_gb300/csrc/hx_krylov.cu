@@ -6,7 +6,8 @@
 //   init      v_0 = c (in the Krylov dtype), beta_0 = ||c|| (FP64)
 //   for k = 0 .. m-1:
 //     apply   w = A(t + h/2) v_k                              (hx_apply.cu)
-//     dot     h_i = <v_i, w>, i <= k                            (FP64)
+//     dot     h_i = <v_i, w>, i <= k                            (FP64; done by the apply kernel
+//                                                                when it is specialised, m <= 8)
 //     update  w -= sum_i h_i v_i;  h'_i = <v_i, w>               (FP64)
 //     update  w -= sum_i h'_i v_i; beta_k = ||w||, v_{k+1} = w / beta_k   (k < m-1)
 //     alpha_k = Re(h_k + h'_k)
@@ -21,6 +22,7 @@
 #include <type_traits>
 
 #include "hx_internal.h"
+#include "hx_stencil.cuh"   // reduce_partials, kMaxFusedDots
 
 namespace hx {
 
@@ -75,52 +77,6 @@ static int resident_grid(const Problem *p, K kernel, int threads)
 }
 
 
-// Writes nval per-block sums to partials[blockIdx.x * nval + j] (all values reduced together:
-// warp shuffles, then one pass over the warp sums).  In the last block to arrive, thread t adds
-// value j = t mod nval over the blocks c, c + nc, ... (c = t div nval, nc = blockDim / nval) and
-// the nc chunk sums are added in chunk order, so the totals land in tot[0..nval) (shared) in an
-// order that does not depend on block timing.  Returns true in every thread of that last block.
-// Needs blockDim.x <= 256 and nval <= 2 (kMaxKrylov + 1).
-constexpr int kRedMax = 2 * (kMaxKrylov + 1);
-__device__ bool reduce_partials(const double *vals, int nval, double *partials, unsigned *counter, double *tot)
-{
-    __shared__ double wsum[8][kRedMax];
-    __shared__ double csum[256];
-    __shared__ bool last;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = 0; j < nval; ++j) {
-        double v = vals[j];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) wsum[wid][j] = v;
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < nval) {
-        double s = 0.0;
-        for (int i = 0; i < nw; ++i) s += wsum[i][threadIdx.x];
-        partials[blockIdx.x * nval + threadIdx.x] = s;
-        __threadfence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    const int nc = blockDim.x / nval, j = threadIdx.x % nval, c = threadIdx.x / nval;
-    double s = 0.0;
-    if (c < nc)
-        // L2-coherent loads (the other blocks' partials are visible after their fence and the counter);
-        // unlike volatile loads they can all be in flight at once
-        for (int blk = c; blk < (int)gridDim.x; blk += nc) s += __ldcg(partials + blk * nval + j);
-    csum[threadIdx.x] = s;
-    __syncthreads();
-    if ((int)threadIdx.x < nval) {
-        double t = 0.0;
-        for (int i = 0; i < nc; ++i) t += csum[i * nval + threadIdx.x];
-        tot[threadIdx.x] = t;
-    }
-    __syncthreads();
-    return true;
-}
 
 // Error-free transformations (Knuth's TwoSum, and TwoProd with a fused multiply-add) and the
 // compensated dot product built from them (Ogita, Rump and Oishi, "Accurate sum and dot product",
@@ -599,6 +555,8 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
     Scal *sc = w->sc;
     const int Gd = resident_grid(p, dot_kernel<V, NV>, T);
     const int Gu0 = resident_grid(p, update_kernel<V, NV, 0>, T), Gu1 = resident_grid(p, update_kernel<V, NV, 1>, T);
+    // the exponential midpoint step takes the projections from the product kernel when it can
+    const bool fused = p->cfg.scheme == HX_SCHEME_EXPMPR && NV <= kMaxFusedDots && apply_fuses_dots(p);
     init_kernel<V><<<G, T, 0, st>>>(state, Vb, n, w->partials, sc, m);
     for (int k = 0; k < m; ++k) {
         ApplyFuse f;
@@ -616,11 +574,21 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
             magnus_combine_kernel<V><<<G, T, 0, st>>>(Vb + (size_t)(k + 1) * ld, a1v, a2v, a2a1v, a1a2v, n,
                                                       sqrt(3.0) * dt / 12.0);
         } else {
+            if (fused) {     // h_i = s_i <v_i, w> from the product kernel's own stores
+                f.dvec = Vb;
+                f.dld = ld;
+                f.dk = k;
+                f.m_used = &sc->m_used;
+                f.s = sc->s;
+                f.h = sc->h;
+                f.partials = w->partials;
+                f.counter = &sc->counter;
+            }
             rc = launch_apply(p, Vb + (size_t)k * ld, Vb + (size_t)(k + 1) * ld, &sc->t, 0.5 * dt, &f, st);
             if (rc) return rc;
         }
         V *wv = Vb + (size_t)(k + 1) * ld;
-        dot_kernel<V, NV><<<Gd, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
+        if (!f.dvec) dot_kernel<V, NV><<<Gd, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
         update_kernel<V, NV, 0><<<Gu0, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
         if (k < m - 1) update_kernel<V, NV, 1><<<Gu1, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
     }

@@ -22,7 +22,64 @@ struct ApplyArgs : ApplyArgsBase {
     size_t chan_ld;
     int stage1;                // 1: write each op's result to its channel instead of y
     int skip_diag;             // 1: omit D_K
+    // projections h_i = s_i <v_i, y>, i <= dk, computed with the product (kernels compiled per
+    // potential only; dvec == nullptr: none; skipped when dk >= *dm_used)
+    const void *dvec;          // v_0 (problem dtype); v_i at dvec + i * dld elements
+    size_t dld;
+    int dk;
+    const int *dm_used;
+    const double *ds;          // s_i
+    double *dh;                // h (re, im per vector)
+    double *dpartials;         // gridDim.x x 2 (dk + 1)
+    unsigned *dcounter;        // zero; reset by the last block
 };
+
+// Writes nval per-block sums to partials[blockIdx.x * nval + j] (all values reduced together:
+// warp shuffles, then one pass over the warp sums).  In the last block to arrive, thread t adds
+// value j = t mod nval over the blocks c, c + nc, ... (c = t div nval, nc = blockDim / nval) and
+// the nc chunk sums are added in chunk order, so the totals land in tot[0..nval) (shared) in an
+// order that does not depend on block timing.  Returns true in every thread of that last block.
+// Needs blockDim.x <= 256 and nval <= 2 (kMaxKrylov + 1).
+constexpr int kRedMax = 2 * (kMaxKrylov + 1);
+static __device__ bool reduce_partials(const double *vals, int nval, double *partials, unsigned *counter, double *tot)
+{
+    __shared__ double wsum[8][kRedMax];
+    __shared__ double csum[256];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = 0; j < nval; ++j) {
+        double v = vals[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) wsum[wid][j] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nval) {
+        double s = 0.0;
+        for (int i = 0; i < nw; ++i) s += wsum[i][threadIdx.x];
+        partials[blockIdx.x * nval + threadIdx.x] = s;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    const int nc = blockDim.x / nval, j = threadIdx.x % nval, c = threadIdx.x / nval;
+    double s = 0.0;
+    if (c < nc)
+        // L2-coherent loads (the other blocks' partials are visible after their fence and the counter);
+        // unlike volatile loads they can all be in flight at once
+        for (int blk = c; blk < (int)gridDim.x; blk += nc) s += __ldcg(partials + blk * nval + j);
+    csum[threadIdx.x] = s;
+    __syncthreads();
+    if ((int)threadIdx.x < nval) {
+        double t = 0.0;
+        for (int i = 0; i < nc; ++i) t += csum[i * nval + threadIdx.x];
+        tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+    return true;
+}
 
 // amp * f(t) in the stencil precision R (the interval index of a piecewise-constant modulation is
 // always found in FP64 so that both precisions switch intervals at the same t).
@@ -268,48 +325,142 @@ __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const O
 }
 
 
-// The element loop: one thread per output element (grid-stride), D_K on the diagonal, then
-// body(ctx, el, acc, sm_w, cin, tab) adds the operators' contributions, and y = out_scale * acc is
-// written unless the launch only writes channel vectors (stage 1).
+// Warp sums of NV per-lane values (NV a power of two <= 32) by a butterfly reduce-scatter: in
+// each of the first log2 NV exchange rounds a lane keeps one half of its values, sends the other
+// half to its partner and adds the partner's copy of the kept half; the remaining rounds add up
+// the one value left.  Lane l then holds the warp sum of value l >> (5 - log2 NV) (NV - 1 + 5 -
+// log2 NV shuffles instead of 5 NV for separate reductions).
+template <int NV>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[NV])
+{
+    const int lane = threadIdx.x & 31;
+    int o = 16;
+#pragma unroll
+    for (int half = NV / 2; half >= 1; half >>= 1, o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < half; ++j) {
+            const float keep = hi ? v[j + half] : v[j], send = hi ? v[j] : v[j + half];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    float r = v[0];
+#pragma unroll
+    for (; o >= 1; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+}
+
+// log2 of the exchange width for nd projections (2 nd values rounded up to a power of two)
+__device__ __forceinline__ int dot_width_log2(int nd) { return nd <= 1 ? 1 : nd <= 2 ? 2 : nd <= 4 ? 3 : 4; }
+
+// Adds this element's conj(v_i) y, i < nd, to the lane's compensated sum (hs, hc) of the warp
+// sums of value lane >> (5 - log2 NV).
+template <int NV>
+__device__ __forceinline__ void add_projections(const ApplyArgs &args, int nd, int e, bool valid, float2 y, float &hs,
+                                                float &hc)
+{
+    const float2 *dv = (const float2 *)args.dvec;
+    float v[NV];
+#pragma unroll
+    for (int i = 0; i < NV / 2; ++i) {
+        float2 x = make_float2(0.f, 0.f);
+        if (i < nd && valid) x = dv[(size_t)i * args.dld + e];
+        v[2 * i] = fmaf(x.x, y.x, x.y * y.y);        // Re conj(v_i) y
+        v[2 * i + 1] = fmaf(x.x, y.y, -x.y * y.x);   // Im conj(v_i) y
+    }
+    const float r = warp_reduce_scatter<NV>(v);
+    const float t = hs + r, bb = t - hs;            // TwoSum
+    hc += (hs - (t - bb)) + (r - bb);
+    hs = t;
+}
+
+// One element: D_K on the diagonal, body(ctx, el, acc, sm_w, cin, tab) adds the operators'
+// contributions, and y = out_scale * acc is written unless the launch only writes channel vectors
+// (stage 1); returns y.
 template <typename R, typename Body>
-__device__ __forceinline__ void apply_elements(const ApplyArgs &args, Body body)
+__device__ __forceinline__ typename Vec2<R>::T apply_element(const ApplyArgs &args, const Ctx &ctx, int e, R oscale,
+                                                             const R *sm_w, Body &body)
 {
     using V = typename Vec2<R>::T;
+    const DevSet &S = args.S;
+    const V *cin = (const V *)args.cin;
+    const int4 er = __ldg(S.elem + e);      // {row, prod (1 + k_l), sum k_l, k_{N-1} | length << 16}
+    const int r = er.x;
+    Elem el;
+    el.e = e;
+    el.k2 = er.w & 0xffff;
+    el.qall = er.y;
+    el.rlen = (int)((unsigned)er.w >> 16);
+    el.nb = args.rnb + r;
+    el.kr = S.row_k + (size_t)r * (S.N - 1);
+    Acc<R> acc;
+    if (!args.stage1 && !args.skip_diag) {
+        const V ce = cin[e];
+        const R dj = (R)er.z + (R)0.5 * (R)S.N;   // (D_K)_jj = sum_l (j_l + 1/2)
+        acc.add(dj * ce.x, dj * ce.y);
+    }
+    body(ctx, el, acc, sm_w, cin, (const R *)args.tab);
+    V y = acc.get();
+    if (!args.stage1) {
+        y.x *= oscale;
+        y.y *= oscale;
+        ((V *)args.cout)[e] = y;
+    }
+    return y;
+}
+
+// The element loop: one thread per output element (grid-stride).  With DOTS (complex64 only) the
+// launch also computes the projections h_i = s_i <v_i, y>, i <= dk, of the launch arguments from
+// the stored y: per element the products conj(v_i) y go through warp_reduce_scatter, each lane
+// adds its warp sum to one compensated FP32 sum (TwoSum), and the sums are reduced over the grid
+// at the end.  The loop then runs warp-uniformly (whole warps per trip) so that every lane takes
+// part in the exchanges.
+template <typename R, bool DOTS = false, typename Body>
+__device__ __forceinline__ void apply_elements(const ApplyArgs &args, Body body)
+{
     __shared__ R sm_w[kMaxOps];
     const DevSet &S = args.S;
     const OpSet &O = args.ops;
-    const int N = S.N;
-    const V *cin = (const V *)args.cin;
-    V *cout = (V *)args.cout;
-    const R *tab = (const R *)args.tab;
     if ((int)threadIdx.x < O.nops) sm_w[threadIdx.x] = op_weight<R>(O.op[threadIdx.x], *args.t_ptr + args.t_shift, args.pw_values);
     const R oscale = args.out_scale ? (R)(*args.out_scale) : (R)1;
     __syncthreads();
     Ctx ctx;
     ctx.S = &S;
     ctx.nrow = args.nrow;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.size; e += gridDim.x * blockDim.x) {
-        const int4 er = __ldg(S.elem + e);      // {row, prod (1 + k_l), sum k_l, k_{N-1} | length << 16}
-        const int r = er.x;
-        Elem el;
-        el.e = e;
-        el.k2 = er.w & 0xffff;
-        el.qall = er.y;
-        el.rlen = (int)((unsigned)er.w >> 16);
-        el.nb = args.rnb + r;
-        el.kr = S.row_k + (size_t)r * (N - 1);
-        Acc<R> acc;
-        if (!args.stage1 && !args.skip_diag) {
-            const V ce = cin[e];
-            const R dj = (R)er.z + (R)0.5 * (R)N;   // (D_K)_jj = sum_l (j_l + 1/2)
-            acc.add(dj * ce.x, dj * ce.y);
+    if constexpr (!DOTS) {
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.size; e += gridDim.x * blockDim.x)
+            apply_element<R>(args, ctx, e, oscale, sm_w, body);
+    } else {
+        static_assert(sizeof(R) == 4, "fused projections are implemented for complex64 vectors");
+        const int nd = args.dvec && !args.stage1 && args.dk < *args.dm_used ? args.dk + 1 : 0;
+        const int lane = threadIdx.x & 31;
+        const int wl = dot_width_log2(nd);
+        float hs = 0.f, hc = 0.f;              // this lane's TwoSum of value lane >> (5 - wl)
+        for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < S.size; base += gridDim.x * blockDim.x) {
+            const int e = base + lane;
+            float2 y = make_float2(0.f, 0.f);
+            if (e < S.size) y = apply_element<R>(args, ctx, e, oscale, sm_w, body);
+            if (nd) {
+                const bool valid = e < S.size;
+                if (wl == 4) add_projections<16>(args, nd, e, valid, y, hs, hc);
+                else if (wl == 3) add_projections<8>(args, nd, e, valid, y, hs, hc);
+                else if (wl == 2) add_projections<4>(args, nd, e, valid, y, hs, hc);
+                else add_projections<2>(args, nd, e, valid, y, hs, hc);
+            }
         }
-        body(ctx, el, acc, (const R *)sm_w, cin, tab);
-        if (!args.stage1) {
-            V y = acc.get();
-            y.x *= oscale;
-            y.y *= oscale;
-            cout[e] = y;
+        if (nd) {
+            double vals[2 * kMaxFusedDots];
+#pragma unroll
+            for (int j = 0; j < 2 * kMaxFusedDots; ++j)
+                vals[j] = (lane >> (5 - wl)) == j && (lane & ((1 << (5 - wl)) - 1)) == 0 ? (double)hs + (double)hc : 0.0;
+            __shared__ double tot[2 * kMaxFusedDots];
+            if (reduce_partials(vals, 2 * nd, args.dpartials, args.dcounter, tot) && threadIdx.x == 0) {
+                for (int i = 0; i < nd; ++i) {
+                    args.dh[2 * i] = args.ds[i] * tot[2 * i];
+                    args.dh[2 * i + 1] = args.ds[i] * tot[2 * i + 1];
+                }
+                *args.dcounter = 0;
+            }
         }
     }
 }

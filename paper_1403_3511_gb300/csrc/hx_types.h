@@ -13,6 +13,7 @@ constexpr int kMaxDeg = 8;                     // HX_MAX_DEG
 constexpr int kSpan = 2 * kMaxDeg + 1;         // offsets -deg..deg
 constexpr int kMaxKrylov = 32;
 constexpr int kApplyThreads = 256;
+constexpr int kMaxFusedDots = 8;     // projections one product launch can compute (Krylov steps m <= 8)
 
 // time modulations (values of hx_mod_kind)
 enum { MOD_CONST = 0, MOD_COS = 1, MOD_SIN2 = 2, MOD_PWCONST = 3 };

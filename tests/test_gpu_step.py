@@ -79,6 +79,34 @@ def test_harmonic_breakdown_is_exact(hx, oracle):
     assert np.allclose(got, np.exp(-1j * d * h) * c0, atol=1e-13)
 
 
+@pytest.mark.parametrize("m", [1, 7, 8])
+def test_fused_projections_lanczos_coefficients(hx, oracle, m):
+    """complex64 with the specialised product kernel: the kernel computes the first Gram-Schmidt
+    projections itself (up to 8 of them, m = 8); T_m and the step still match the oracle to FP32
+    accuracy."""
+    spec = dict(N=3, B=200, L=inputs.half_width(200), potential=inputs.henon_heiles_chain(3, 0.111, (0.05, 1.0)))
+    S = oracle.IndexSet.hyperbolic(3, 200)
+    c0 = inputs.initial_vector({"init": {"kind": "coherent", "q": [0.5, -0.3, 0.8], "eps": 1e-3, "seed": 3}}, S.k)
+    h = 0.02
+    r, a = oracle.potential_terms(spec, 0.5 * h)
+    ref, al, be = oracle.lanczos_exp(lambda v: oracle.apply(S, r, a, spec["L"], v), c0, h, m)
+    P = hx.Problem(3, 200, dtype=hx.HX_C64, m=m)
+    try:
+        P.set_potential(spec, 0.0)
+        assert hx.hx_apply_specialised(P.p) == 1
+        assert hx.hx_step_launches(P.p)[1] == m * 3 + 2       # no separate projection kernel
+        x = torch.from_numpy(c0).to("cuda")
+        hx.hx_step(P.p, x, h, 1)
+        info = hx.hx_step_info(P.p)
+        got = x.cpu().numpy()
+    finally:
+        P.close()
+    assert info["m_used"] == len(al) == m
+    assert np.allclose(info["alpha"], al, rtol=0, atol=2e-6 * np.abs(al).max())
+    assert np.allclose(info["beta"], be, rtol=2e-6)
+    assert rel(got, ref) <= 1e-5, rel(got, ref)
+
+
 @pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
 def test_control_problem_steps(hx, oracle, dtype, tol):
     spec = inputs.workload("ctrl4_b512")
@@ -158,15 +186,21 @@ def test_magnus4_time_integration_experiment(hx, oracle):
 
 
 def test_step_launch_counts(hx):
-    for scheme, per in ((0, lambda m, a: m * (a + 3) + 2), (1, lambda m, a: m * (4 * a + 4) + 2)):
+    # expMPR: the specialised complex64 product kernel computes the projections itself when m <= 8
+    per = {0: lambda m, a, spec: m * (a + (2 if spec and m <= 8 else 3)) + 2,
+           1: lambda m, a, spec: m * (4 * a + 4) + 2}
+    for scheme in (0, 1):
         for name in ("hh2_b32", "cos10_b1024"):
             spec = inputs.workload(name) if name == "hh2_b32" else dict(N=3, B=40, L=inputs.half_width(40),
                                                                       potential=inputs.cos_chain(3, 0.2, 8))
-            P = hx.Problem(spec["N"], spec["B"], m=6, scheme=scheme)
-            try:
-                P.set_potential(spec, 0.0)
-                a, step = hx.hx_step_launches(P.p)
-                assert a == (1 if name == "hh2_b32" else 2)
-                assert step == per(6, a)
-            finally:
-                P.close()
+            for m, dtype in ((6, hx.HX_C64), (6, hx.HX_C128), (12, hx.HX_C64)):
+                P = hx.Problem(spec["N"], spec["B"], m=m, scheme=scheme, dtype=dtype)
+                try:
+                    P.set_potential(spec, 0.0)
+                    a, step = hx.hx_step_launches(P.p)
+                    assert a == (1 if name == "hh2_b32" else 2)
+                    specialised = hx.hx_apply_specialised(P.p)
+                    assert specialised == (name == "hh2_b32")
+                    assert step == per[scheme](m, a, specialised and dtype == hx.HX_C64)
+                finally:
+                    P.close()

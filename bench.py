@@ -115,11 +115,13 @@ def kernel_source_hash(root: str = None) -> str:
     return h.hexdigest()
 
 
-def profiled_traffic(workload: str, dtype: str):
-    """DRAM bytes per product launch from the committed ncu summary of this workload, or None when
-    there is none or the kernel sources have changed since it was captured."""
+def profiled_traffic(workload: str, dtype: str, kind: str = "apply_kernel"):
+    """DRAM bytes per launch from the committed ncu summary of this workload (kind "apply_kernel":
+    the product; "apply_project_kernel": the product with the Lanczos projections, averaged over
+    the projection counts of one step), or None when there is none or the kernel sources have
+    changed since it was captured."""
     import re
-    path = os.path.join(ROOT, "profiles", f"apply_kernel_{workload}_{dtype}.md")
+    path = os.path.join(ROOT, "profiles", f"{kind}_{workload}_{dtype}.md")
     try:
         text = open(path).read()
     except OSError:
@@ -314,8 +316,25 @@ def main():
     eb.record(stream)
     barrier()
     ms_apply = ea.elapsed_time(eb) / napply
+    # the step's own product launches: with the specialised complex64 kernel they also compute the
+    # projections h_i = <v_i, A v_k>, i <= k, k = 0 .. m-1 (hx_apply_project), each k once per step
+    fused = bool(hx.hx_apply_specialised(P.p)) and dtype == hx.HX_C64 and m <= 8
+    ms_proj = 0.0
+    if fused:
+        basis = torch.randn((m, n), dtype=vdt, device="cuda")
+        hproj = torch.empty(16, dtype=torch.float64, device="cuda")
+        for k in range(m):
+            hx.hx_apply_project(P.p, basis[k], y, basis, k, hproj)
+        nproj = m * max(2, args.steps)
+        ea.record(stream)
+        for i in range(nproj):
+            hx.hx_apply_project(P.p, basis[i % m], y, basis, i % m, hproj)
+        eb.record(stream)
+        barrier()
+        ms_proj = ea.elapsed_time(eb) / nproj
+        del basis
     clk = clocks.stop()
-    ms_step, ms_apply = max_over_ranks([ms_step, ms_apply], world, "cuda")
+    ms_step, ms_apply, ms_proj = max_over_ranks([ms_step, ms_apply, ms_proj], world, "cuda")
     value = whole_job_gcoeff_s(m, n, world, ms_step * 1e-3)
     # end to end through the host entry point: pinned host state, H2D + step + D2H every step
     ch = torch.from_numpy(c0.copy()).pin_memory()
@@ -379,13 +398,25 @@ def main():
         PM.close()
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_source = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
+    # algorithmic bytes: the product reads c and writes y (16 B per coefficient in complex64); the
+    # projections add the basis vectors v_0 .. v_{k-1} (v_k is the product's input), 8 k B
     alg_bytes = (16 if dtype == hx.HX_C64 else 32) * n
-    achieved = alg_bytes / (ms_apply * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": profiled_traffic(spec["name"], args.dtype),
-            "kernel": "hx_apply_specialised" if hx.hx_apply_specialised(P.p) else "apply_kernel",
-            "ms_per_launch": ms_apply,
-            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"}
+    product = {"kernel": "hx_apply_specialised" if hx.hx_apply_specialised(P.p) else "apply_kernel",
+               "ms_per_launch": ms_apply, "achieved": alg_bytes / (ms_apply * 1e-3) / 1e9,
+               "traffic": profiled_traffic(spec["name"], args.dtype)}
+    if fused:
+        alg_proj = (16 + 8 * (m - 1) / 2) * n            # mean over k = 0 .. m-1
+        achieved = alg_proj / (ms_proj * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(spec["name"], args.dtype, "apply_project_kernel"),
+                "kernel": "hx_apply_specialised_dots", "ms_per_launch": ms_proj,
+                "bytes_per_launch": alg_proj, "peak_source": peak_source, "product_alone": product}
+    else:
+        achieved = product["achieved"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": product["traffic"], "kernel": product["kernel"], "ms_per_launch": ms_apply,
+                "bytes_per_launch": alg_bytes, "peak_source": peak_source}
     if rank == 0:
         line = {"metric": "Galerkin matvecs: Gcoeff/s", "value": value, "unit": "Gcoeff/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,

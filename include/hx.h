@@ -161,9 +161,24 @@ HX_API int hx_set_time(hx_problem *p, double t);
 /* ---- the matrix-free product (Sec. 3) ------------------------------------------ */
 
 /* c_out = A(t) c_in at the problem time t: D_K c_in + W^pol(X_K, t) c_in with the
- * configured factor order.  Device pointers of |K| elements of the problem dtype;
+ * configured factor order.  Device pointers of |K| elements of the problem dtype, aligned to
+ * the element size (8 bytes for HX_C64, 16 for HX_C128; HX_EINVAL otherwise);
  * c_in and c_out must not overlap.  Asynchronous on the problem stream. */
 HX_API int hx_apply(hx_problem *p, const void *c_in, void *c_out);
+/* The product of one Lanczos step with its first Gram-Schmidt projections (Sec. 2.2):
+ * y = A(t) c and h_i = <basis_i, y> = sum_j conj(basis_i[j]) y[j] for i = 0..k.
+ * c, y: device vectors of |K| elements of the problem dtype (c and y must not overlap, and y
+ * must not overlap the basis).  basis: device, k + 1 vectors of the problem dtype, vector i at
+ * basis + i * ld elements (ld >= |K|).  h: device array of 2 (k + 1) doubles, h[2i] + i h[2i+1].
+ * 0 <= k < 8.  All vectors aligned to the element size as for hx_apply, h to 8 bytes.
+ * With a specialised product kernel (hx_apply_specialised) and HX_C64 one kernel
+ * computes both (the projections from the stored y, compensated FP32 partial sums); otherwise the
+ * product is followed by a projection kernel (FP64 or compensated FP32 sums).  Asynchronous on
+ * the problem stream; the first call allocates a small workspace and synchronises.
+ * Errors: HX_EINVAL (NULL pointer, k out of range, ld < |K|, c == y, misaligned pointer, no
+ * potential). */
+HX_API int hx_apply_project(hx_problem *p, const void *c, void *y, const void *basis, size_t ld, int k,
+                            double *h);
 /* Same with host buffers: copies in, applies, copies out, synchronises. */
 HX_API int hx_apply_host(hx_problem *p, const void *c_in_host, void *c_out_host);
 
@@ -182,6 +197,7 @@ HX_API int hx_apply_host(hx_problem *p, const void *c_in_host, void *c_out_host)
  * hx_step_info reports HX_EBREAKDOWN (informational) when some step needed fewer than m
  * Lanczos vectors, and HX_ENONFINITE when the norm became NaN/Inf or the eigensolver of T_m
  * did not converge. */
+/* c: device complex128 state of |K| elements, 16-byte aligned (HX_EINVAL otherwise). */
 HX_API int hx_step(hx_problem *p, void *c, double dt, int nsteps);
 /* Same with a host complex128 vector: copies in, steps, copies out, synchronises. */
 HX_API int hx_step_host(hx_problem *p, void *c_host, double dt, int nsteps);
@@ -214,7 +230,7 @@ HX_API int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step);
  * the GPU runs the problems concurrently; the graph is replayed nsteps times.  The problems keep
  * their own index sets, potentials, times and Krylov workspaces; they must stay alive and unchanged
  * (no hx_potential_set) while the batch exists.  Work is ordered on the first problem's stream.
- * hx_batch_step: c[i] is the DEVICE complex128 state of problem i (in place); the graph is built on
+ * hx_batch_step: c[i] is the DEVICE complex128 state of problem i (in place, 16-byte aligned); the graph is built on
  * the first call and rebuilt when dt or a state pointer changes.  Asynchronous. */
 typedef struct hx_batch hx_batch;
 HX_API int hx_batch_create(hx_problem *const *probs, int n, hx_batch **out);
@@ -250,7 +266,8 @@ HX_API int hx_adjoint_grad(const hx_indexset *s, const hx_config *cfg, const hx_
                            const hx_control *ctl, const void *c0, const void *phi, double *grad_out,
                            double *J_out);
 
-/* ||c||_2 of a device vector of the problem dtype, accumulated in FP64; synchronous. */
+/* ||c||_2 of a device vector of the problem dtype (aligned to the element size), accumulated in
+ * FP64; synchronous. */
 HX_API int hx_norm(hx_problem *p, const void *c, double *out);
 
 /* ---- allocation-free norm ------------------------------------------------------- */

@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <algorithm>
@@ -807,12 +808,36 @@ int hx_potential_set(hx_problem *p, const hx_potential *pot, double t)
     return hx_set_time(p, t);
 }
 
+// Device vectors must be aligned to their element size (8 bytes for HX_C64, 16 for HX_C128).
+static bool elem_aligned(const Problem *p, const void *x)
+{
+    return (uintptr_t)x % (p->cfg.dtype == HX_C64 ? 8 : 16) == 0;
+}
+
 int hx_apply(hx_problem *p, const void *c_in, void *c_out)
 {
     if (!p || !c_in || !c_out) { set_error("hx_apply: NULL argument"); return HX_EINVAL; }
     if (!p->have_pot) { set_error("hx_apply: call hx_potential_set first"); return HX_EINVAL; }
     if (c_in == c_out) { set_error("hx_apply: c_in and c_out must not overlap"); return HX_EINVAL; }
+    if (!elem_aligned(p, c_in) || !elem_aligned(p, c_out)) {
+        set_error("hx_apply: vectors must be aligned to the element size");
+        return HX_EINVAL;
+    }
     return launch_apply(p, c_in, c_out, p->dscal, 0.0, nullptr, p->stream);
+}
+
+int hx_apply_project(hx_problem *p, const void *c, void *y, const void *basis, size_t ld, int k, double *h)
+{
+    if (!p || !c || !y || !basis || !h) { set_error("hx_apply_project: NULL argument"); return HX_EINVAL; }
+    if (!p->have_pot) { set_error("hx_apply_project: call hx_potential_set first"); return HX_EINVAL; }
+    if (c == y) { set_error("hx_apply_project: c and y must not overlap"); return HX_EINVAL; }
+    if (k < 0 || k >= kMaxFusedDots) { set_error("hx_apply_project: k must be in [0, %d)", kMaxFusedDots); return HX_EINVAL; }
+    if (ld < (size_t)p->set->h.size) { set_error("hx_apply_project: ld below the vector length"); return HX_EINVAL; }
+    if (!elem_aligned(p, c) || !elem_aligned(p, y) || !elem_aligned(p, basis) || (uintptr_t)h % 8) {
+        set_error("hx_apply_project: vectors must be aligned to the element size");
+        return HX_EINVAL;
+    }
+    return apply_project_dispatch(p, c, y, basis, ld, k, h);
 }
 
 int hx_apply_host(hx_problem *p, const void *c_in_host, void *c_out_host)
@@ -837,6 +862,7 @@ int hx_apply_host(hx_problem *p, const void *c_in_host, void *c_out_host)
 int hx_norm(hx_problem *p, const void *c, double *out)
 {
     if (!p || !c || !out) { set_error("hx_norm: NULL argument"); return HX_EINVAL; }
+    if (!elem_aligned(p, c)) { set_error("hx_norm: vector must be aligned to the element size"); return HX_EINVAL; }
     int G = apply_grid(p);
     double *buf = nullptr;
     HX_CUDA(cudaMallocAsync((void **)&buf, (G + 2) * sizeof(double) + 64, p->stream), "cudaMallocAsync(norm)");
@@ -859,6 +885,7 @@ int hx_step(hx_problem *p, void *c, double dt, int nsteps)
 {
     if (!p || !c || nsteps < 0 || !(dt == dt)) { set_error("hx_step: bad argument"); return HX_EINVAL; }
     if (!p->have_pot) { set_error("hx_step: call hx_potential_set first"); return HX_EINVAL; }
+    if ((uintptr_t)c % 16) { set_error("hx_step: the complex128 state must be 16-byte aligned"); return HX_EINVAL; }
     if (nsteps == 0) return HX_OK;
     return krylov_step(p, c, dt, nsteps);
 }
@@ -904,7 +931,7 @@ int hx_batch_step(hx_batch *b, void *const *c, double dt, int nsteps)
 {
     if (!b || !c || nsteps < 0 || !(dt == dt)) { set_error("hx_batch_step: bad argument"); return HX_EINVAL; }
     for (size_t i = 0; i < b->probs.size(); ++i)
-        if (!c[i]) { set_error("hx_batch_step: state %zu is NULL", i); return HX_EINVAL; }
+        if (!c[i] || (uintptr_t)c[i] % 16) { set_error("hx_batch_step: state %zu is NULL or not 16-byte aligned", i); return HX_EINVAL; }
     if (nsteps == 0) return HX_OK;
     return batch_step(b, c, dt, nsteps);
 }

@@ -87,6 +87,7 @@ struct Problem {
     double graph_dt;
     int graph_nsteps;
     std::vector<void *> extra;   // further device allocations owned by the problem
+    void *proj_ws = nullptr;     // hx_apply_project scalars and partial sums (one of extra)
 };
 
 // launchers (hx_apply.cu)
@@ -98,8 +99,11 @@ int launch_rowtab(const DevSet &S, const RowOffsets &ro, int *rnb, cudaStream_t 
 int launch_norm(Problem *p, const void *c, int is_c128, double *partials, unsigned *counter, double *result,
                 cudaStream_t st);
 int apply_grid(const Problem *p);
-int apply_launches(const Problem *p);
-bool apply_fuses_dots(const Problem *p);   // the product kernel can compute ApplyFuse projections   // kernels per product (1, or 2 with a channel stage)
+int apply_launches(const Problem *p);     // kernels per product (1, or 2 with a channel stage)
+bool apply_fuses_dots(const Problem *p);  // the product kernel can compute ApplyFuse projections
+
+// hx_apply_project after the argument checks (hx_krylov.cu)
+int apply_project_dispatch(Problem *p, const void *c, void *y, const void *basis, size_t ld, int k, double *h);
 
 extern thread_local bool g_batch_capture;   // hx_krylov.cu: a batch graph is being captured
 

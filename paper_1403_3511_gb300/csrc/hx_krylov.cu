@@ -17,6 +17,7 @@
 // stored unnormalised with a device scale s_k (v_k = s_k * stored_k) so no pass is spent on
 // normalisation.  All scalars live in device memory, so the step has no host round trip.
 #include <math.h>
+#include <stdint.h>
 
 #include <algorithm>
 #include <type_traits>
@@ -597,6 +598,80 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     return HX_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// hx_apply_project: the product with the first projections of a Lanczos step, outside the graph
+// ---------------------------------------------------------------------------------------
+
+struct ProjWS {
+    Scal sc;                        // m_used = kMaxFusedDots, s_i = 1, counter, h
+    double partials[1];             // apply_grid(p) x 2 kMaxFusedDots
+};
+
+static ProjWS *proj_ws(Problem *p)
+{
+    if (p->proj_ws) return (ProjWS *)p->proj_ws;
+    const size_t bytes = sizeof(ProjWS) + (size_t)apply_grid(p) * 2 * kMaxFusedDots * sizeof(double);
+    void *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e != cudaSuccess) { cuda_fail(e, "cudaMalloc(projection workspace)"); return nullptr; }
+    Scal h;
+    memset(&h, 0, sizeof(h));
+    h.m_used = kMaxFusedDots;
+    for (int i = 0; i < kMaxFusedDots; ++i) h.s[i] = 1.0;
+    if ((e = cudaMemcpy(d, &h, sizeof(h), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        cudaFree(d);
+        cuda_fail(e, "projection workspace init");
+        return nullptr;
+    }
+    p->extra.push_back(d);
+    p->proj_ws = d;
+    return (ProjWS *)d;
+}
+
+template <typename V>
+static int apply_project(Problem *p, const void *c, void *y, const void *basis, size_t ld, int k, double *h)
+{
+    ProjWS *ws = proj_ws(p);
+    if (!ws) return HX_ECUDA;
+    const int n = p->set->d.size;
+    cudaStream_t st = p->stream;
+    if (apply_fuses_dots(p)) {
+        ApplyFuse f;
+        memset(&f, 0, sizeof(f));
+        f.dvec = basis;
+        f.dld = ld;
+        f.dk = k;
+        f.m_used = &ws->sc.m_used;
+        f.s = ws->sc.s;
+        f.h = h;
+        f.partials = ws->partials;
+        f.counter = &ws->sc.counter;
+        return launch_apply(p, c, y, p->dscal, 0.0, &f, st);
+    }
+    int rc = launch_apply(p, c, y, p->dscal, 0.0, nullptr, st);
+    if (rc) return rc;
+    // the paired variant reads two complex64 values per 16-byte load: y, the basis and its row
+    // stride must be 16-byte aligned for it; otherwise the element-wise variant runs
+    const bool paired = (uintptr_t)y % 16 == 0 && (uintptr_t)basis % 16 == 0 && (ld * sizeof(V)) % 16 == 0;
+    if (paired) {
+        const int G = resident_grid(p, dot_kernel<V, kMaxFusedDots>, 256);
+        dot_kernel<V, kMaxFusedDots><<<G, 256, 0, st>>>((const V *)y, (const V *)basis, ld, n, k, ws->partials, &ws->sc);
+    } else {
+        const int G = resident_grid(p, dot_kernel<V, kMaxKrylov>, 256);
+        dot_kernel<V, kMaxKrylov><<<G, 256, 0, st>>>((const V *)y, (const V *)basis, ld, n, k, ws->partials, &ws->sc);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, ws->sc.h, 2 * (k + 1) * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "projection kernel");
+    return HX_OK;
+}
+
+int apply_project_dispatch(Problem *p, const void *c, void *y, const void *basis, size_t ld, int k, double *h)
+{
+    return p->cfg.dtype == HX_C64 ? apply_project<float2>(p, c, y, basis, ld, k, h)
+                                  : apply_project<double2>(p, c, y, basis, ld, k, h);
 }
 
 static int enqueue(Problem *p, Work *w, double2 *state, cudaStream_t st, double dt)

@@ -20,7 +20,7 @@ HX_C128, HX_C64 = 0, 1
 HX_ORDER_SYM, HX_ORDER_EQ, HX_ORDER_ALG = 0, 1, 2
 HX_SCHEME_EXPMPR, HX_SCHEME_MAGNUS4 = 0, 1
 HX_MOD_CONST, HX_MOD_COS, HX_MOD_SIN2, HX_MOD_PWCONST = 0, 1, 2, 3
-HX_EBREAKDOWN = -5
+HX_EINVAL, HX_ENOMEM, HX_ECUDA, HX_ENONFINITE, HX_EBREAKDOWN, HX_ETIMEOUT, HX_EUNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
 ORDERS = {"sym": HX_ORDER_SYM, "eq": HX_ORDER_EQ, "alg": HX_ORDER_ALG}
 MODS = {"const": HX_MOD_CONST, "cos": HX_MOD_COS, "sin2": HX_MOD_SIN2, "pwconst": HX_MOD_PWCONST}
 
@@ -74,6 +74,7 @@ def _load():
         "hx_set_time": (ctypes.c_int, [P, ctypes.c_double]),
         "hx_apply": (ctypes.c_int, [P, P, P]),
         "hx_apply_host": (ctypes.c_int, [P, P, P]),
+        "hx_apply_project": (ctypes.c_int, [P, P, P, P, ctypes.c_size_t, ctypes.c_int, P]),
         "hx_step": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int]),
         "hx_step_host": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int]),
         "hx_step_info": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), dp, dp, dp]),
@@ -215,6 +216,17 @@ def hx_set_time(p, t: float):
 
 def hx_apply(p, c_in, c_out):
     _check(lib.hx_apply(p, ctypes.c_void_p(_tptr(c_in)), ctypes.c_void_p(_tptr(c_out))))
+
+
+def hx_apply_project(p, c, y, basis, k: int, h):
+    """y = A(t) c and h_i = <basis[i], y> for i <= k.  basis: CUDA tensor of at least k + 1 rows of
+    |K| elements (row stride = ld), h: CUDA float64 tensor of 2 (k + 1) values (re, im)."""
+    if not (basis.is_cuda and basis.dim() == 2 and basis.stride(1) == 1):
+        raise ValueError("basis must be a CUDA tensor of rows with unit element stride")
+    if not (h.is_cuda and str(h.dtype) == "torch.float64" and h.is_contiguous()):
+        raise ValueError("h must be a contiguous CUDA float64 tensor")
+    _check(lib.hx_apply_project(p, ctypes.c_void_p(_tptr(c)), ctypes.c_void_p(_tptr(y)),
+                                ctypes.c_void_p(basis.data_ptr()), basis.stride(0), k, ctypes.c_void_p(h.data_ptr())))
 
 
 def hx_apply_host(p, c_in: np.ndarray, c_out: np.ndarray):

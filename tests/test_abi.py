@@ -76,6 +76,8 @@ def test_argument_errors_without_device(libhx):
     with pytest.raises(hx.HxError):
         hx.hx_step_launches(None)
     assert "NULL problem" in hx.hx_last_error()
+    assert hx.lib.hx_apply_project(None, None, None, None, 0, 0, None) == hx.HX_EINVAL
+    assert "NULL argument" in hx.hx_last_error()
 
 
 def test_config_layout_matches_header(libhx):

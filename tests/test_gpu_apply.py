@@ -273,3 +273,70 @@ def test_potentials_without_specialised_kernel(hx, case, why):
         assert why in hx.hx_last_error()
     finally:
         P.close()
+
+
+@pytest.mark.parametrize("case,dtype,k,fused", [
+    ("hh3_b300_dipole", "c64", 0, True), ("hh3_b300_dipole", "c64", 3, True), ("hh3_b300_dipole", "c64", 7, True),
+    ("hh6_b2000", "c64", 5, True), ("hh2_b40000", "c64", 2, True),
+    ("hh3_b300_dipole", "c128", 4, False), ("cos3_b64", "c64", 6, False), ("cos3_b64", "c128", 7, False)])
+def test_apply_project_matches_oracle(hx, oracle, case, dtype, k, fused):
+    """hx_apply_project: the product against the oracle and h_i = <basis_i, y> against FP64 sums of
+    the returned y, in one kernel (specialised complex64 kernels) or with a projection kernel after
+    the product.  The basis holds the input itself, random vectors and a row stride above |K|."""
+    spec = CASES[case]()
+    dt = hx.HX_C128 if dtype == "c128" else hx.HX_C64
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    S = oracle.IndexSet.hyperbolic(spec["N"], spec["B"])
+    n = S.size
+    c = inputs.initial_vector({"init": {"kind": "gaussian", "seed": 8}}, S.k)
+    basis_np = np.stack([c] + [inputs.complex_gaussian(n, 20 + i) / np.sqrt(2 * n) for i in range(k)])
+    r, a = oracle.potential_terms(spec, 0.4)
+    ref = oracle.apply(S, r, a, spec["L"], c)
+    P = make(hx, spec, dt, t=0.4)
+    try:
+        assert bool(hx.hx_apply_specialised(P.p) and dtype == "c64") == fused
+        basis = torch.zeros((k + 1, n + 37), dtype=tdt, device="cuda")[:, :n]
+        basis.copy_(torch.from_numpy(basis_np).to(tdt))
+        x = basis[0].clone()
+        y = torch.empty_like(x)
+        h = torch.full((2 * (k + 1),), float("nan"), dtype=torch.float64, device="cuda")
+        hx.hx_apply_project(P.p, x, y, basis, k, h)
+        torch.cuda.synchronize()
+        yg = y.cpu().numpy().astype(np.complex128)
+        check(yg, ref, dt, hx)
+        bg = basis.cpu().numpy().astype(np.complex128)
+        href = bg.conj() @ yg
+        got = h.cpu().numpy()
+        got = got[0::2] + 1j * got[1::2]
+        scale = np.linalg.norm(bg, axis=1) * np.linalg.norm(yg)
+        tol = 1e-13 if dtype == "c128" else 1e-6
+        assert np.all(np.abs(got - href) <= tol * scale), (np.abs(got - href) / scale).max()
+    finally:
+        P.close()
+
+
+def test_apply_project_argument_errors(hx):
+    spec = CASES["hh2_b32"]()
+    P = make(hx, spec, hx.HX_C64)
+    try:
+        x = torch.zeros(P.size, dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        basis = torch.zeros((9, P.size), dtype=torch.complex64, device="cuda")
+        h = torch.zeros(18, dtype=torch.float64, device="cuda")
+        for kk in (-1, 8):
+            with pytest.raises(hx.HxError):
+                hx.hx_apply_project(P.p, x, y, basis, kk, h)
+        with pytest.raises(hx.HxError):
+            hx.hx_apply_project(P.p, x, x, basis, 0, h)
+        with pytest.raises(hx.HxError):          # row stride below |K|
+            hx.hx_apply_project(P.p, x, y, basis.view(-1)[: 2 * (P.size - 1)].view(2, P.size - 1), 1, h)
+        # pointers off the element alignment are refused on the host (nothing is launched)
+        import ctypes
+        bad = ctypes.c_void_p(x.data_ptr() + 4)
+        assert hx.lib.hx_apply(P.p, bad, ctypes.c_void_p(y.data_ptr())) == hx.HX_EINVAL
+        assert hx.lib.hx_apply_project(P.p, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                       ctypes.c_void_p(basis.data_ptr() + 4), P.size, 0,
+                                       ctypes.c_void_p(h.data_ptr())) == hx.HX_EINVAL
+        assert hx.lib.hx_step(P.p, ctypes.c_void_p(h.data_ptr() + 8), 0.01, 1) == hx.HX_EINVAL
+    finally:
+        P.close()

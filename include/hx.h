@@ -191,13 +191,14 @@ HX_API int hx_apply_host(hx_problem *p, const void *c_in_host, void *c_out_host)
  * reorthogonalisation (classical Gram-Schmidt twice), c^{n+1} = ||c^n|| V_m exp(-i dt T_m) e_1
  * (Sec. 2.2).  c is a DEVICE complex128 vector of
  * |K| elements, updated in place, for both dtypes (HX_C64 runs the Krylov vectors and the
- * stencil in complex64, the state and all inner products in FP64).  Advances the problem
+ * stencil in complex64, the state and all inner products in FP64; its first Krylov vector is the
+ * state rounded to complex64 before normalisation, so the state's norm should lie well inside
+ * the binary32 range, e.g. a normalised wave function).  Advances the problem
  * time by nsteps * dt.  One step is captured into a CUDA graph for the pair (c, dt) and replayed
  * nsteps times; a call with another vector or step size captures a new graph.  Asynchronous;
  * hx_step_info reports HX_EBREAKDOWN (informational) when some step needed fewer than m
  * Lanczos vectors, and HX_ENONFINITE when the norm became NaN/Inf or the eigensolver of T_m
- * did not converge. */
-/* c: device complex128 state of |K| elements, 16-byte aligned (HX_EINVAL otherwise). */
+ * did not converge.  c must be 16-byte aligned (HX_EINVAL otherwise). */
 HX_API int hx_step(hx_problem *p, void *c, double dt, int nsteps);
 /* Same with a host complex128 vector: copies in, steps, copies out, synchronises. */
 HX_API int hx_step_host(hx_problem *p, void *c_host, double dt, int nsteps);

@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "hx_internal.h"
+#include "hx_convert.h"
 #include "hx_stencil.cuh"   // reduce_partials, kMaxFusedDots
 
 namespace hx {
@@ -97,20 +98,55 @@ struct F2 {
     __device__ double value() const { return (double)s + (double)c; }
 };
 
-template <typename V>
-__device__ __forceinline__ V to_vec(double2 x);
-template <> __device__ __forceinline__ float2 to_vec<float2>(double2 x) { return make_float2((float)x.x, (float)x.y); }
-template <> __device__ __forceinline__ double2 to_vec<double2>(double2 x) { return x; }
+// sum x^2 over FP64 values x without FP64 arithmetic for the usual magnitudes: x = hi + lo split
+// into binary32 parts with integer operations (hx_convert.h), hi^2 + 2 hi lo accumulated as a
+// compensated FP32 pair (relative error of order 2^-44).  Magnitudes in [2^-174, 2^-74) go to a
+// second pair scaled by 2^200 (x by 2^100), the rest (tinier, or 2^100 and above) to FP64.
+struct NormAcc {
+    F2 a, b;
+    double rest = 0.0;
+    // adds x^2 and returns x rounded to binary32 (to nearest, ties to even)
+    __device__ float add(double x)
+    {
+        float h, l;
+        if (d2f_split(x, h, l)) {
+            a.add_prod(h, h);
+            a.c = fmaf(2.f * h, l, a.c);
+            return h;
+        }
+        const uint64_t bx = conv_bits64(x);
+        const uint32_t e = (uint32_t)(bx >> 52) & 0x7ffu;
+        if (e - (1023u - 174u) < 100u && d2f_split(conv_from_bits64(bx + (100ull << 52)), h, l)) {
+            b.add_prod(h, h);
+            b.c = fmaf(2.f * h, l, b.c);
+        } else {
+            rest = fma(x, x, rest);
+        }
+        return d2f_rn(x);
+    }
+    __device__ double value() const { return a.value() + 0x1p-200 * b.value() + rest; }
+};
 
-// v_0 = c in the Krylov dtype; beta_0 = ||c||, s_0 = 1 / beta_0.
+// v_0 = c in the Krylov dtype; beta_0 = ||c||, s_0 = 1 / beta_0.  For complex64 vectors the
+// rounding to binary32 and the norm use integer and FP32 operations only (NormAcc).
 template <typename V>
 __global__ void init_kernel(const double2 *c, V *v0, int n, double *partials, Scal *sc, int m)
 {
     double acc = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double2 x = c[i];
-        v0[i] = to_vec<V>(x);
-        acc += x.x * x.x + x.y * x.y;
+    if constexpr (std::is_same<V, float2>::value) {
+        NormAcc na;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            const double2 x = c[i];
+            const float xr = na.add(x.x), xi = na.add(x.y);
+            v0[i] = make_float2(xr, xi);
+        }
+        acc = na.value();
+    } else {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            const double2 x = c[i];
+            v0[i] = x;
+            acc += x.x * x.x + x.y * x.y;
+        }
     }
     __shared__ double tot[1];
     if (reduce_partials(&acc, 1, partials, &sc->counter, tot) && threadIdx.x == 0) {
@@ -462,10 +498,130 @@ __global__ void __launch_bounds__(32) eig_kernel(Scal *sc, double h)
     if (lane == 0) sc->t += h;
 }
 
+// The same iteration for m <= 8 with T and the rows of Q in registers: every loop over indices is
+// unrolled and the block bounds l and u become predicates, so that no array is indexed at run time
+// (in eig_kernel d, e and z live in local memory).  A rotation takes sqrt(f^2 + g^2) and one
+// reciprocal (the magnitudes here are far from the FP64 range limits; a result below 2^-500 falls
+// back to hypot).  Eight lanes: lane i holds row i of Q; lane j computes the phase of eigenvalue j.
+constexpr int kEigSmall = 8;
+__global__ void __launch_bounds__(kEigSmall) eig_small_kernel(Scal *sc, double h)
+{
+    constexpr int M = kEigSmall;
+    constexpr unsigned mask = (1u << M) - 1;
+    const int lane = threadIdx.x;
+    const int m = sc->m_used;
+    double d[M], e[M], z[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        d[i] = i < m ? sc->alpha[i] : 0.0;
+        e[i] = i + 1 < m ? sc->beta[i] : 0.0;
+        z[i] = i == lane ? 1.0 : 0.0;
+    }
+    const double tiny = 0x1p-53;
+    auto rot_norm = [](double f, double g) {
+        double r = sqrt(fma(f, f, g * g));
+        return r < 0x1p-500 ? hypot(f, g) : r;
+    };
+#pragma unroll
+    for (int l = 0; l < M - 1; ++l) {        // l = M - 1 is a 1 x 1 block
+        if (l >= m) break;
+        for (int iter = 0;; ++iter) {
+            int u = m - 1;                      // end of the unreduced block starting at l
+            bool open = true;
+#pragma unroll
+            for (int j = l; j < M - 1; ++j)
+                if (open && (j >= m - 1 || !(fabs(e[j]) > tiny * (fabs(d[j]) + fabs(d[j + 1]))))) {
+                    u = j;
+                    open = false;
+                }
+            if (u == l) break;
+            if (iter == 60) {                   // no convergence: report, keep what we have
+                if (lane == 0) sc->flags |= 4;
+                break;
+            }
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = rot_norm(g, 1.0);
+            double du = d[M - 1];
+#pragma unroll
+            for (int j = l + 1; j < M - 1; ++j)
+                if (j == u) du = d[j];
+            g = du - d[l] + e[l] / (g + copysign(r, g));
+            double sn = 1.0, cs = 1.0, p = 0.0;
+            bool restart = false, live = true;
+#pragma unroll
+            for (int i = M - 2; i >= l; --i) {
+                if (live && i < u) {
+                    const double f = sn * e[i], b = cs * e[i];
+                    r = rot_norm(f, g);
+                    e[i + 1] = r;
+                    if (r == 0.0) {                 // the block splits: deflate and start again
+                        d[i + 1] -= p;
+#pragma unroll
+                        for (int j = l + 1; j < M; ++j)
+                            if (j == u) e[j] = 0.0;
+                        restart = true;
+                        live = false;
+                    } else {
+                        const double inv = 1.0 / r;
+                        sn = f * inv;
+                        cs = g * inv;
+                        g = d[i + 1] - p;
+                        r = (d[i] - g) * sn + 2.0 * cs * b;
+                        p = sn * r;
+                        d[i + 1] = g + p;
+                        g = cs * r - b;
+                        const double zi = z[i], zi1 = z[i + 1];   // Q <- Q G(i, i+1)
+                        z[i + 1] = sn * zi + cs * zi1;
+                        z[i] = cs * zi - sn * zi1;
+                    }
+                }
+            }
+            if (restart) continue;
+            d[l] -= p;
+            e[l] = g;
+#pragma unroll
+            for (int j = l + 1; j < M; ++j)
+                if (j == u) e[j] = 0.0;
+        }
+    }
+    double dl = d[0];
+#pragma unroll
+    for (int j = 1; j < M; ++j)
+        if (j == lane) dl = d[j];
+    double sph = 0.0, cph = 1.0;
+    if (lane < m) sincos(-h * dl, &sph, &cph);
+    double yr = 0.0, yi = 0.0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const double q0 = __shfl_sync(mask, z[j], 0);   // Q_{0 j}
+        const double cj = __shfl_sync(mask, cph, j), sj = __shfl_sync(mask, sph, j);
+        if (j < m) {
+            const double w = z[j] * q0;
+            yr += w * cj;
+            yi += w * sj;
+            if (lane < m) sc->Q[lane * m + j] = z[j];
+        }
+    }
+    if (lane < m) {
+        sc->lam[lane] = dl;
+        sc->y[2 * lane] = sc->beta0 * yr * sc->s[lane];
+        sc->y[2 * lane + 1] = sc->beta0 * yi * sc->s[lane];
+    }
+    if (lane == 0) sc->t += h;
+}
+
+// Eigen-decomposition and the Krylov coefficients of the step for m_used <= m.
+static void launch_eig(Scal *sc, int m, double h, cudaStream_t st)
+{
+    if (m <= kEigSmall) eig_small_kernel<<<1, kEigSmall, 0, st>>>(sc, h);
+    else eig_kernel<<<1, 32, 0, st>>>(sc, h);
+}
+
 // c = sum_i y_i v_i, and ||c||^2 for hx_step_info.  Complex128 vectors accumulate in FP64; for
 // complex64 vectors each y_i is split into float parts hi + lo and the sum is accumulated with
 // the compensated products of F2 (Dot2), which keeps it as accurate as FP64 accumulation (relative
-// error of order 2^-48 of sum |y_i v_i|) without FP64 arithmetic per element.
+// error of order 2^-48 of sum |y_i v_i|); per element the only FP64 operations are the two adds
+// that round the pair sums to the complex128 state (the norm goes through NormAcc).
 template <typename V, int NV>
 __global__ void combine_kernel(double2 *c, const V *Vb, size_t ld, int n, double *partials, Scal *sc)
 {
@@ -481,6 +637,7 @@ __global__ void combine_kernel(double2 *c, const V *Vb, size_t ld, int n, double
             yih[i] = (float)yi;
             yil[i] = (float)(yi - (double)yih[i]);
         }
+        NormAcc na;
         for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
             F2 xr, xi;
 #pragma unroll(NV <= 8 ? NV : 1)
@@ -494,10 +651,13 @@ __global__ void combine_kernel(double2 *c, const V *Vb, size_t ld, int n, double
                     xi.add_prod(yih[i], v.x);
                     xi.c = fmaf(yrl[i], v.y, fmaf(yil[i], v.x, xi.c));
                 }
-            const double2 x = make_double2(xr.value(), xi.value());
+            // the pair sums as FP64 (exact binary32 -> binary64 conversions, one FP64 add each)
+            const double2 x = make_double2(f2d_exact(xr.s) + f2d_exact(xr.c), f2d_exact(xi.s) + f2d_exact(xi.c));
             c[e] = x;
-            acc += x.x * x.x + x.y * x.y;
+            na.add(x.x);
+            na.add(x.y);
         }
+        acc = na.value();
     } else {
         double yr[NV], yi[NV];
 #pragma unroll
@@ -593,7 +753,7 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
         update_kernel<V, NV, 0><<<Gu0, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
         if (k < m - 1) update_kernel<V, NV, 1><<<Gu1, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
     }
-    eig_kernel<<<1, 32, 0, st>>>(sc, dt);
+    launch_eig(sc, m, dt, st);
     combine_kernel<V, NV><<<resident_grid(p, combine_kernel<V, NV>, T), T, 0, st>>>(state, Vb, ld, n, w->partials, sc);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
@@ -939,7 +1099,7 @@ int lanczos_exp(Problem *p, LanczosWS *L, double h, double2 *out, cudaStream_t s
 {
     const int n = p->set->d.size, G = apply_grid(p);
     Scal *sc = (Scal *)L->sc;
-    eig_kernel<<<1, 32, 0, st>>>(sc, h);
+    launch_eig(sc, L->m, h, st);
     if (out) {
         const size_t ld = L->vec_bytes / sizeof(double2);
         if (L->m <= 8) combine_kernel<double2, 8><<<G, 256, 0, st>>>(out, (const double2 *)L->V, ld, n, L->partials, sc);

@@ -90,3 +90,20 @@ def test_config_layout_matches_header(libhx):
     assert names == [f[0] for f in hx.hx_config._fields_]
     with pytest.raises(hx.HxError):
         hx.hx_apply_specialised(None)
+
+
+def test_integer_float_conversions_match_host():
+    """The binary64 <-> binary32 conversions that the complex64 Krylov kernels do with integer
+    operations (csrc/hx_convert.h) agree bit for bit with the host's IEEE conversions."""
+    import shutil
+    import subprocess
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    out_dir = os.path.join(ROOT, "paper_1403_3511_gb300", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    exe = os.path.join(out_dir, "convert_check")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-I", os.path.join(ROOT, "paper_1403_3511_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "native", "convert_check.cpp"), "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr

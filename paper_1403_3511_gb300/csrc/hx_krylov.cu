@@ -306,6 +306,35 @@ __global__ void __launch_bounds__(256) dot_kernel(const V *w, const V *Vb, size_
     }
 }
 
+// After the grid reduction of an update pass (last block, thread 0): pass 0 stores h'_i and
+// alpha_k = Re(h_k + h'_k) and tracks the scale of T; pass 1 stores beta_k = ||w|| and
+// s_{k+1} = 1 / beta_k, or stops the process at an invariant subspace.
+template <int pass>
+__device__ void update_scalars(Scal *sc, int k, const double *tot)
+{
+    if (pass == 0) {
+        for (int i = 0; i <= k; ++i) {
+            sc->h2[2 * i] = sc->s[i] * tot[2 * i];
+            sc->h2[2 * i + 1] = sc->s[i] * tot[2 * i + 1];
+        }
+        double a = sc->h[2 * k] + sc->h2[2 * k];
+        sc->alpha[k] = a;
+        double sc_k = fabs(a) + (k > 0 ? sc->beta[k - 1] : 0.0);
+        if (sc_k > sc->scale) sc->scale = sc_k;
+    } else {
+        double b = sqrt(tot[0]);
+        if (!isfinite(b)) sc->flags |= 2;
+        if (b <= 1e-13 * sc->scale) {       // invariant subspace: stop with k + 1 vectors
+            sc->m_used = k + 1;
+            sc->flags |= 1;
+        } else {
+            sc->beta[k] = b;
+            sc->s[k + 1] = 1.0 / b;
+        }
+    }
+    sc->counter = 0;
+}
+
 // pass 0: w -= sum_i h_i s_i v_i, then h'_i = s_i <v_i, w>, alpha_k = Re(h_k + h'_k).
 // pass 1: w -= sum_i h'_i s_i v_i, then beta_k = ||w||, s_{k+1} = 1 / beta_k, breakdown test.
 // The update runs in the vector precision; the inner products and the norm as in dot_kernel.
@@ -395,29 +424,98 @@ __global__ void __launch_bounds__(256, (sizeof(V) == 8 && NV <= 8) ? 3 : 1) upda
         vals[0] = nrm.r();
         nval = 1;
     }
-    if (reduce_partials(vals, nval, partials, &sc->counter, tot) && threadIdx.x == 0) {
-        if (pass == 0) {
-            for (int i = 0; i <= k; ++i) {
-                sc->h2[2 * i] = sc->s[i] * tot[2 * i];
-                sc->h2[2 * i + 1] = sc->s[i] * tot[2 * i + 1];
-            }
-            double a = sc->h[2 * k] + sc->h2[2 * k];
-            sc->alpha[k] = a;
-            double sc_k = fabs(a) + (k > 0 ? sc->beta[k - 1] : 0.0);
-            if (sc_k > sc->scale) sc->scale = sc_k;
-        } else {
-            double b = sqrt(tot[0]);
-            if (!isfinite(b)) sc->flags |= 2;
-            if (b <= 1e-13 * sc->scale) {       // invariant subspace: stop with k + 1 vectors
-                sc->m_used = k + 1;
-                sc->flags |= 1;
-            } else {
-                sc->beta[k] = b;
-                sc->s[k + 1] = 1.0 / b;
+    if (reduce_partials(vals, nval, partials, &sc->counter, tot) && threadIdx.x == 0) update_scalars<pass>(sc, k, tot);
+}
+
+// The update for one Lanczos index K <= 7 known at compile time (the step graph launches one per
+// k): register arrays of exactly K + 1 vectors, and for small K each thread loads U grid-stride
+// iterations before using them, so that enough bytes are in flight to cover the memory latency
+// when only K + 2 vectors stream.
+template <typename V, int K>
+constexpr int update_k_blocks()   // resident blocks per SM that keep the kernel free of spills
+{
+    return sizeof(V) == 8 ? (K < 6 ? 3 : 2) : (K < 3 ? 2 : 1);
+}
+
+template <typename V, int K, int pass>
+__global__ void __launch_bounds__(256, update_k_blocks<V, K>()) update_k_kernel(V *w, const V *Vb, size_t ld, int n, double *partials, Scal *sc)
+{
+    constexpr int NK = K + 1;
+    constexpr int U = K + 2 >= 5 ? 1 : (K + 2 >= 3 ? 2 : 4);
+    using R = typename Real<V>::T;
+    __shared__ double tot[2 * NK];
+    if (K >= sc->m_used) return;
+    const double *coef = pass == 0 ? sc->h : sc->h2;
+    R cr[NK], ci[NK];
+#pragma unroll
+    for (int i = 0; i < NK; ++i) {
+        cr[i] = (R)(coef[2 * i] * sc->s[i]);
+        ci[i] = (R)(coef[2 * i + 1] * sc->s[i]);
+    }
+    using A = typename PairAccOf<V>::T;
+    A acc[pass == 0 ? NK : 1];
+    A nrm;
+    const int npair = n >> 1;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+    for (int q0 = gid; q0 < npair; q0 += U * gstride) {
+        Pair<V> x[U], v[U][NK];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int q = q0 + u * gstride;
+            if (q < npair) {
+                x[u] = load_pair(w, 2 * q);
+#pragma unroll
+                for (int i = 0; i < NK; ++i) v[u][i] = load_pair(Vb + i * ld, 2 * q);
             }
         }
-        sc->counter = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int q = q0 + u * gstride;
+            if (q < npair) {
+#pragma unroll
+                for (int i = 0; i < NK; ++i) {
+                    sub_scaled(x[u].a, cr[i], ci[i], v[u][i].a);
+                    sub_scaled(x[u].b, cr[i], ci[i], v[u][i].b);
+                }
+                store_pair(w, 2 * q, x[u]);
+                if constexpr (pass == 0) {
+#pragma unroll
+                    for (int i = 0; i < NK; ++i) add_pair(acc[i], v[u][i].a, x[u].a, v[u][i].b, x[u].b);
+                } else {
+                    add_pair(nrm, x[u].a, x[u].a, x[u].b, x[u].b);
+                }
+            }
+        }
     }
+    if ((n & 1) && gid == 0) {                              // odd length: the last element
+        const int e = n - 1;
+        V x = w[e];
+        V v[NK];
+#pragma unroll
+        for (int i = 0; i < NK; ++i) {
+            v[i] = Vb[i * ld + e];
+            sub_scaled(x, cr[i], ci[i], v[i]);
+        }
+        w[e] = x;
+        if constexpr (pass == 0) {
+#pragma unroll
+            for (int i = 0; i < NK; ++i) acc[i].add(v[i], x);
+        } else {
+            nrm.add(x, x);
+        }
+    }
+    double vals[pass == 0 ? 2 * NK : 1];
+    if constexpr (pass == 0) {
+#pragma unroll
+        for (int i = 0; i < NK; ++i) {
+            vals[2 * i] = acc[i].r();
+            vals[2 * i + 1] = acc[i].i();
+        }
+    } else {
+        vals[0] = nrm.r();
+    }
+    if (reduce_partials(vals, pass == 0 ? 2 * NK : 1, partials, &sc->counter, tot) && threadIdx.x == 0)
+        update_scalars<pass>(sc, K, tot);
 }
 
 // T_m = Q diag(lambda) Q^T by the implicit-shift QL iteration for symmetric tridiagonal matrices
@@ -704,6 +802,33 @@ __global__ void magnus_combine_kernel(V *out, const V *a1v, const V *a2v, const 
     }
 }
 
+template <typename V, int K, int pass>
+static void launch_update_k_t(const Problem *p, V *wv, const V *Vb, size_t ld, int n, double *partials, Scal *sc,
+                              cudaStream_t st)
+{
+    const int G = resident_grid(p, update_k_kernel<V, K, pass>, 256);
+    update_k_kernel<V, K, pass><<<G, 256, 0, st>>>(wv, Vb, ld, n, partials, sc);
+}
+
+// The update pass for Lanczos index k < 8 with the kernel specialised for k.
+template <typename V>
+static int launch_update_k(const Problem *p, V *wv, const V *Vb, size_t ld, int n, int k, int pass, double *partials,
+                           Scal *sc, cudaStream_t st)
+{
+#define HX_UPDATE_K(K)                                                                  \
+    case K:                                                                             \
+        if (pass == 0) launch_update_k_t<V, K, 0>(p, wv, Vb, ld, n, partials, sc, st);  \
+        else launch_update_k_t<V, K, 1>(p, wv, Vb, ld, n, partials, sc, st);            \
+        return HX_OK;
+    switch (k) {
+        HX_UPDATE_K(0) HX_UPDATE_K(1) HX_UPDATE_K(2) HX_UPDATE_K(3)
+        HX_UPDATE_K(4) HX_UPDATE_K(5) HX_UPDATE_K(6) HX_UPDATE_K(7)
+    }
+#undef HX_UPDATE_K
+    set_error("internal: update kernel for k = %d", k);
+    return HX_EUNSUPPORTED;
+}
+
 template <typename V, int NV>
 static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, double dt)
 {
@@ -750,8 +875,14 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
         }
         V *wv = Vb + (size_t)(k + 1) * ld;
         if (!f.dvec) dot_kernel<V, NV><<<Gd, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
-        update_kernel<V, NV, 0><<<Gu0, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
-        if (k < m - 1) update_kernel<V, NV, 1><<<Gu1, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
+        if (NV <= 8) {
+            if ((rc = launch_update_k<V>(p, wv, Vb, ld, n, k, 0, w->partials, sc, st)) ||
+                (k < m - 1 && (rc = launch_update_k<V>(p, wv, Vb, ld, n, k, 1, w->partials, sc, st))))
+                return rc;
+        } else {
+            update_kernel<V, NV, 0><<<Gu0, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
+            if (k < m - 1) update_kernel<V, NV, 1><<<Gu1, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
+        }
     }
     launch_eig(sc, m, dt, st);
     combine_kernel<V, NV><<<resident_grid(p, combine_kernel<V, NV>, T), T, 0, st>>>(state, Vb, ld, n, w->partials, sc);

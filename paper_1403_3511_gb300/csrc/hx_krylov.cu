@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(256, update_k_blocks<V, K>()) update_k_kernel(
 // agree on every rotation) and applies each rotation to its own row of Q.
 // y = beta_0 Q exp(-i h lambda) Q^T e_1, stored as y_i * s_i for the combination pass; also
 // advances the problem time by h.
-__global__ void __launch_bounds__(32) eig_kernel(Scal *sc, double h)
+__device__ void eig_warp(Scal *sc, double h)
 {
     const int lane = threadIdx.x;
     const int m = sc->m_used;
@@ -596,13 +596,15 @@ __global__ void __launch_bounds__(32) eig_kernel(Scal *sc, double h)
     if (lane == 0) sc->t += h;
 }
 
+__global__ void __launch_bounds__(32) eig_kernel(Scal *sc, double h) { eig_warp(sc, h); }
+
 // The same iteration for m <= 8 with T and the rows of Q in registers: every loop over indices is
 // unrolled and the block bounds l and u become predicates, so that no array is indexed at run time
 // (in eig_kernel d, e and z live in local memory).  A rotation takes sqrt(f^2 + g^2) and one
 // reciprocal (the magnitudes here are far from the FP64 range limits; a result below 2^-500 falls
 // back to hypot).  Eight lanes: lane i holds row i of Q; lane j computes the phase of eigenvalue j.
 constexpr int kEigSmall = 8;
-__global__ void __launch_bounds__(kEigSmall) eig_small_kernel(Scal *sc, double h)
+__device__ void eig_small_warp(Scal *sc, double h)   // run by lanes 0 .. 7 of a warp
 {
     constexpr int M = kEigSmall;
     constexpr unsigned mask = (1u << M) - 1;
@@ -706,6 +708,135 @@ __global__ void __launch_bounds__(kEigSmall) eig_small_kernel(Scal *sc, double h
         sc->y[2 * lane + 1] = sc->beta0 * yi * sc->s[lane];
     }
     if (lane == 0) sc->t += h;
+}
+
+__global__ void __launch_bounds__(kEigSmall) eig_small_kernel(Scal *sc, double h) { eig_small_warp(sc, h); }
+
+// y = beta_0 exp(-i h T_m) e_1 for the time step, which needs no eigenvectors.  With c, r from the
+// Gershgorin bounds of T_m, T_m = c I + r X with the spectrum of X in [-1, 1], and by the
+// Jacobi-Anger expansion exp(-i h T_m) = e^{-i h c} sum_k eps_k (-i sgn h)^k J_k(|h| r) T_k(X)
+// (eps_0 = 1, eps_k = 2), truncated where the Bessel terms fall below 1e-17 (at index about
+// z + 10 z^(1/3) + 12 for z = |h| r).  The J_k come from Miller's backward recurrence
+// J_{n-1} = (2n/z) J_n - J_{n+1}, started 10 indices further out and normalised by
+// J_0 + 2 sum_k J_2k = 1.  When |h| r exceeds 32 the step is split into s equal parts and the
+// series applied s times.  On this GPU a single warp's FP64 instruction costs about as much as
+// 64 FP32 ones: the QL iteration takes a few thousand of them whatever |h| r, the series about
+// 6 (real vector) to 14 (complex) per term, so the series runs for |h| r <= 96 (at most three
+// applications) and the QL eigensolver otherwise (and for a non-finite T).
+// One warp: lane j holds component j of the Chebyshev vectors (T_m is tridiagonal, so X t
+// takes the neighbours by shuffles).
+constexpr int kChebZ = 32;         // largest |h| r per series application
+constexpr int kChebN = 96;         // Bessel values kept (truncation index for z = 32 is 76)
+constexpr int kChebMaxSub = 3;     // beyond 3 applications the QL eigendecomposition is cheaper
+
+__device__ __forceinline__ int cheb_terms(double z) { return z < 1e-20 ? 0 : (int)ceil(z + 10.0 * cbrt(z) + 12.0); }
+
+template <bool SMALL>   // SMALL: m <= 8, so that the QL fallback is eig_small_warp
+__global__ void __launch_bounds__(32) expv_kernel(Scal *sc, double h)
+{
+    const int j = threadIdx.x;
+    const int mu = sc->m_used;
+    if (mu <= 0) {
+        if (j == 0) sc->t += h;
+        return;
+    }
+    __shared__ double J[kChebN];
+    const double aj = j < mu ? sc->alpha[j] : 0.0;
+    const double bj = j + 1 < mu ? sc->beta[j] : 0.0;              // T_{j, j+1}
+    double bjm = __shfl_up_sync(0xffffffffu, bj, 1);
+    if (j == 0) bjm = 0.0;
+    double lo = j < mu ? aj - fabs(bjm) - fabs(bj) : INFINITY, hi = j < mu ? aj + fabs(bjm) + fabs(bj) : -INFINITY;
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const double c = 0.5 * (lo + hi);
+    double r = 0.5 * (hi - lo);
+    if (!(r >= 1e-290)) r = 1e-290;                                // T = c I (or non-finite: propagates)
+    const double sgn = h < 0.0 ? -1.0 : 1.0;
+    const double z_all = fabs(h) * r;
+    if (!(z_all <= kChebZ * kChebMaxSub)) {      // large |h| ||T|| or non-finite T: QL instead
+        if (!SMALL) eig_warp(sc, h);
+        else if (j < kEigSmall) eig_small_warp(sc, h);
+        return;
+    }
+    const int nsub = z_all > kChebZ ? (int)ceil(z_all / kChebZ) : 1;
+    const double z = z_all / nsub;
+    const int K = cheb_terms(z);
+    if (j == 0) {                                                   // Miller's recurrence (lane 0)
+        if (K == 0) {
+            J[0] = 1.0;
+        } else {
+            int n0 = K + 10;
+            n0 += n0 & 1;
+            const double tz = 2.0 / z;
+            double jp1 = 0.0, jn = 1e-280, norm = 0.0;
+            for (int n = n0; n >= 1; --n) {
+                if (n <= K) J[n] = jn;
+                if (!(n & 1)) norm += 2.0 * jn;
+                const double jm1 = (tz * n) * jn - jp1;
+                jp1 = jn;
+                jn = jm1;
+                if (fabs(jn) > 1e250) {                             // rescale (only for small z)
+                    for (int k = n; k <= K; ++k) J[k] *= 1e-250;
+                    norm *= 1e-250;
+                    jp1 *= 1e-250;
+                    jn *= 1e-250;
+                }
+            }
+            J[0] = jn;
+            norm += jn;
+            const double inv = 1.0 / norm;
+            for (int k = 0; k <= K; ++k) J[k] *= inv;
+        }
+    }
+    __syncwarp();
+    const double ax = j < mu ? (aj - c) / r : 0.0, bx = bj / r, bxm = bjm / r;   // row j of X
+    double ps, pc;
+    sincos(-h * c / nsub, &ps, &pc);                                // e^{-i h c / s}
+    double vr = j == 0 ? 1.0 : 0.0, vi = 0.0;
+    for (int sub = 0; sub < nsub; ++sub) {
+        // y = sum_k eps_k (-i sgn)^k J_k T_k(X) v by the three-term recurrence of T_k
+        double t0r = vr, t0i = vi;
+        double yr = J[0] * t0r, yi = J[0] * t0i;
+        if (K >= 1) {
+            const bool real = sub == 0;                             // v = e_1: T_k(X) v stays real
+            double t1r = ax * t0r + bxm * __shfl_up_sync(0xffffffffu, t0r, 1) + bx * __shfl_down_sync(0xffffffffu, t0r, 1);
+            double t1i = real ? 0.0 : ax * t0i + bxm * __shfl_up_sync(0xffffffffu, t0i, 1) + bx * __shfl_down_sync(0xffffffffu, t0i, 1);
+            double pr = 0.0, pi = -sgn;                             // (-i sgn)^1
+            double cr = 2.0 * J[1] * pr, ci = 2.0 * J[1] * pi;
+            yr += cr * t1r - ci * t1i;
+            yi += cr * t1i + ci * t1r;
+            for (int k = 2; k <= K; ++k) {
+                const double npr = sgn * pi, npi = -sgn * pr;       // times (-i sgn)
+                pr = npr;
+                pi = npi;
+                const double ur = __shfl_up_sync(0xffffffffu, t1r, 1), dr = __shfl_down_sync(0xffffffffu, t1r, 1);
+                const double t2r = 2.0 * (ax * t1r + bxm * ur + bx * dr) - t0r;
+                double t2i = 0.0;
+                if (!real) {
+                    const double ui = __shfl_up_sync(0xffffffffu, t1i, 1), di = __shfl_down_sync(0xffffffffu, t1i, 1);
+                    t2i = 2.0 * (ax * t1i + bxm * ui + bx * di) - t0i;
+                }
+                const double w = 2.0 * J[k];
+                cr = w * pr;
+                ci = w * pi;
+                yr += cr * t2r - ci * t2i;
+                yi += cr * t2i + ci * t2r;
+                t0r = t1r;
+                t0i = t1i;
+                t1r = t2r;
+                t1i = t2i;
+            }
+        }
+        vr = pc * yr - ps * yi;
+        vi = pc * yi + ps * yr;
+    }
+    if (j < mu) {
+        sc->y[2 * j] = sc->beta0 * vr * sc->s[j];
+        sc->y[2 * j + 1] = sc->beta0 * vi * sc->s[j];
+    }
+    if (j == 0) sc->t += h;
 }
 
 // Eigen-decomposition and the Krylov coefficients of the step for m_used <= m.
@@ -884,7 +1015,8 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
             if (k < m - 1) update_kernel<V, NV, 1><<<Gu1, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
         }
     }
-    launch_eig(sc, m, dt, st);
+    if (m <= kEigSmall) expv_kernel<true><<<1, 32, 0, st>>>(sc, dt);
+    else expv_kernel<false><<<1, 32, 0, st>>>(sc, dt);
     combine_kernel<V, NV><<<resident_grid(p, combine_kernel<V, NV>, T), T, 0, st>>>(state, Vb, ld, n, w->partials, sc);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");

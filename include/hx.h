@@ -270,6 +270,12 @@ HX_API int hx_adjoint_grad(const hx_indexset *s, const hx_config *cfg, const hx_
 /* ||c||_2 of a device vector of the problem dtype (aligned to the element size), accumulated in
  * FP64; synchronous. */
 HX_API int hx_norm(hx_problem *p, const void *c, double *out);
+/* The energy <c, A(t) c> (real, since A(t) is Hermitian; not divided by ||c||^2) of a device vector
+ * of the problem dtype at the problem time, for monitoring a propagation (Sec. 2.2 assumes a
+ * Hermitian A(t); for a time-independent W the exponential midpoint rule keeps it up to the
+ * Lanczos error).  One product with its projection (hx_apply_project, k = 0) into a temporary
+ * vector; synchronous.  Errors as hx_apply. */
+HX_API int hx_energy(hx_problem *p, const void *c, double *out);
 
 /* ---- allocation-free norm ------------------------------------------------------- */
 

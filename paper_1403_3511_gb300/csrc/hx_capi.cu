@@ -859,6 +859,30 @@ int hx_apply_host(hx_problem *p, const void *c_in_host, void *c_out_host)
     return rc;
 }
 
+int hx_energy(hx_problem *p, const void *c, double *out)
+{
+    if (!p || !c || !out) { set_error("hx_energy: NULL argument"); return HX_EINVAL; }
+    if (!p->have_pot) { set_error("hx_energy: call hx_potential_set first"); return HX_EINVAL; }
+    if (!elem_aligned(p, c)) { set_error("hx_energy: vector must be aligned to the element size"); return HX_EINVAL; }
+    const size_t es = p->cfg.dtype == HX_C64 ? 8 : 16;
+    const size_t bytes = std::max<size_t>((size_t)p->set->h.size * es, 16);
+    char *buf = nullptr;   // y = A c, then h_0 = <c, y> (two doubles)
+    const size_t hoff = ((bytes + 255) / 256) * 256;
+    HX_CUDA(cudaMallocAsync((void **)&buf, hoff + 256, p->stream), "cudaMallocAsync(energy)");
+    double *h = (double *)(buf + hoff);
+    int rc = apply_project_dispatch(p, c, buf, c, (size_t)p->set->h.size, 0, h);
+    double hv[2] = {0.0, 0.0};
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(hv, h, sizeof(hv), cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "hx_energy");
+    }
+    cudaFreeAsync(buf, p->stream);
+    cudaStreamSynchronize(p->stream);
+    *out = hv[0];
+    return rc;
+}
+
 int hx_norm(hx_problem *p, const void *c, double *out)
 {
     if (!p || !c || !out) { set_error("hx_norm: NULL argument"); return HX_EINVAL; }

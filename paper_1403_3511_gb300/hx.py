@@ -81,6 +81,7 @@ def _load():
         "hx_step_launches": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "hx_apply_specialised": (ctypes.c_int, [P]),
         "hx_norm": (ctypes.c_int, [P, P, dp]),
+        "hx_energy": (ctypes.c_int, [P, P, dp]),
         "hx_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P)]),
         "hx_batch_step": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.c_double, ctypes.c_int]),
         "hx_batch_destroy": (None, [P]),
@@ -286,6 +287,13 @@ def hx_batch_destroy(b):
 def hx_norm(p, c) -> float:
     out = ctypes.c_double()
     _check(lib.hx_norm(p, ctypes.c_void_p(_tptr(c)), ctypes.byref(out)))
+    return out.value
+
+
+def hx_energy(p, c) -> float:
+    """<c, A(t) c> (see include/hx.h)."""
+    out = ctypes.c_double()
+    _check(lib.hx_energy(p, ctypes.c_void_p(_tptr(c)), ctypes.byref(out)))
     return out.value
 
 

@@ -227,3 +227,25 @@ def test_step_launch_counts(hx):
                     assert step == per[scheme](m, a, specialised and dtype == hx.HX_C64)
                 finally:
                     P.close()
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 2e-6)])
+def test_energy_matches_oracle_and_is_conserved(hx, oracle, dtype, tol):
+    """hx_energy = <c, A c> against the oracle's product; for a time-independent W the exponential
+    midpoint rule keeps the energy (and the norm) up to the Lanczos error over 50 steps."""
+    spec = inputs.workload("hh2_b32")
+    S = oracle.IndexSet.hyperbolic(2, 32)
+    c0 = inputs.initial_vector(spec, S.k)
+    r, a = oracle.potential_terms(spec, 0.0)
+    e_ref = float(np.real(np.vdot(c0, oracle.apply(S, r, a, spec["L"], c0))))
+    P = hx.Problem(2, 32, dtype=hx.HX_C128 if dtype == "c128" else hx.HX_C64)
+    try:
+        P.set_potential(spec, 0.0)
+        x = torch.from_numpy(c0.copy()).to("cuda", torch.complex128 if dtype == "c128" else torch.complex64)
+        e0 = hx.hx_energy(P.p, x)
+        assert abs(e0 - e_ref) <= tol * abs(e_ref), (e0, e_ref)
+        if dtype == "c128":
+            hx.hx_step(P.p, x, 0.01, 50)
+            assert abs(hx.hx_energy(P.p, x) - e0) <= 1e-10 * abs(e0)
+    finally:
+        P.close()

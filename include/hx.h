@@ -200,7 +200,8 @@ HX_API int hx_apply_host(hx_problem *p, const void *c_in_host, void *c_out_host)
  * Lanczos vectors, and HX_ENONFINITE when the norm became NaN/Inf or the eigensolver of T_m
  * did not converge.  c must be 16-byte aligned (HX_EINVAL otherwise). */
 HX_API int hx_step(hx_problem *p, void *c, double dt, int nsteps);
-/* Same with a host complex128 vector: copies in, steps, copies out, synchronises. */
+/* Same with a host complex128 vector: copies in, steps, copies out, synchronises (the copies run
+ * at full speed from page-locked memory). */
 HX_API int hx_step_host(hx_problem *p, void *c_host, double dt, int nsteps);
 /* Synchronises the stream and reports the last step: Lanczos size used, alpha/beta of T_m
  * (host arrays of at least m and m-1 doubles, either may be NULL) and the norm of c. */

@@ -916,6 +916,88 @@ __global__ void combine_kernel(double2 *c, const V *Vb, size_t ld, int n, double
     }
 }
 
+// One term y_i v of the complex64 recombination into the compensated pairs (xr, xi), with
+// y_i = (yr_hi + yr_lo) + i (yi_hi + yi_lo) packed in y as (yr_hi, yr_lo, yi_hi, yi_lo).
+__device__ __forceinline__ void combine_term(F2 &xr, F2 &xi, float4 y, float2 v)
+{
+    xr.add_prod(y.x, v.x);
+    xr.add_prod(-y.z, v.y);
+    xr.c = fmaf(y.y, v.x, fmaf(-y.w, v.y, xr.c));
+    xi.add_prod(y.x, v.y);
+    xi.add_prod(y.z, v.x);
+    xi.c = fmaf(y.y, v.y, fmaf(y.w, v.x, xi.c));
+}
+
+// The complex64 recombination for m = M <= 8 known at compile time: two elements per thread and
+// iteration (16-byte loads of every basis vector, all issued before the arithmetic), the split
+// coefficients in shared memory.  Same arithmetic per element as combine_kernel.
+template <int M>
+__global__ void __launch_bounds__(256) combine_m_kernel(double2 *c, const float2 *Vb, size_t ld, int n,
+                                                        double *partials, Scal *sc)
+{
+    __shared__ float4 ys[M];
+    const int mu = sc->m_used;
+    if ((int)threadIdx.x < M) {
+        const int i = threadIdx.x;
+        const double yr = i < mu ? sc->y[2 * i] : 0.0, yi = i < mu ? sc->y[2 * i + 1] : 0.0;
+        const float yrh = (float)yr, yih = (float)yi;
+        ys[i] = make_float4(yrh, (float)(yr - (double)yrh), yih, (float)(yi - (double)yih));
+    }
+    __syncthreads();
+    NormAcc na;
+    const int npair = n >> 1;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+    for (int q = gid; q < npair; q += gstride) {
+        const int e = 2 * q;
+        Pair<float2> v[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if (i < mu) v[i] = load_pair(Vb + i * ld, e);
+        F2 ar, ai, br, bi;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if (i < mu) {
+                const float4 y = ys[i];
+                combine_term(ar, ai, y, v[i].a);
+                combine_term(br, bi, y, v[i].b);
+            }
+        const double2 xa = make_double2(f2d_exact(ar.s) + f2d_exact(ar.c), f2d_exact(ai.s) + f2d_exact(ai.c));
+        const double2 xb = make_double2(f2d_exact(br.s) + f2d_exact(br.c), f2d_exact(bi.s) + f2d_exact(bi.c));
+        c[e] = xa;
+        c[e + 1] = xb;
+        na.add(xa.x);
+        na.add(xa.y);
+        na.add(xb.x);
+        na.add(xb.y);
+    }
+    if ((n & 1) && gid == 0) {                              // odd length: the last element
+        const int e = n - 1;
+        F2 ar, ai;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if (i < mu) combine_term(ar, ai, ys[i], Vb[i * ld + e]);
+        const double2 xa = make_double2(f2d_exact(ar.s) + f2d_exact(ar.c), f2d_exact(ai.s) + f2d_exact(ai.c));
+        c[e] = xa;
+        na.add(xa.x);
+        na.add(xa.y);
+    }
+    double acc = na.value();
+    __shared__ double tot[1];
+    if (reduce_partials(&acc, 1, partials, &sc->counter, tot) && threadIdx.x == 0) {
+        double nr = sqrt(tot[0]);
+        sc->norm_out = nr;
+        if (!isfinite(nr)) sc->flags |= 2;
+        sc->counter = 0;
+    }
+}
+
+template <int M>
+static void launch_combine_m(const Problem *p, double2 *c, const float2 *Vb, size_t ld, int n, double *partials, Scal *sc,
+                             cudaStream_t st)
+{
+    combine_m_kernel<M><<<resident_grid(p, combine_m_kernel<M>, 256), 256, 0, st>>>(c, Vb, ld, n, partials, sc);
+}
+
 // H v for the 2-stage Magnus exponent, Eq. (2stageMagnus) written as Omega = -i h H:
 // H v = (A_1 v + A_2 v) / 2 - i g (A_2 A_1 v - A_1 A_2 v), g = sqrt(3) h / 12.
 template <typename V>
@@ -1017,7 +1099,22 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
     }
     if (m <= kEigSmall) expv_kernel<true><<<1, 32, 0, st>>>(sc, dt);
     else expv_kernel<false><<<1, 32, 0, st>>>(sc, dt);
-    combine_kernel<V, NV><<<resident_grid(p, combine_kernel<V, NV>, T), T, 0, st>>>(state, Vb, ld, n, w->partials, sc);
+    if constexpr (std::is_same<V, float2>::value) {
+        switch (m) {
+        case 1: launch_combine_m<1>(p, state, Vb, ld, n, w->partials, sc, st); break;
+        case 2: launch_combine_m<2>(p, state, Vb, ld, n, w->partials, sc, st); break;
+        case 3: launch_combine_m<3>(p, state, Vb, ld, n, w->partials, sc, st); break;
+        case 4: launch_combine_m<4>(p, state, Vb, ld, n, w->partials, sc, st); break;
+        case 5: launch_combine_m<5>(p, state, Vb, ld, n, w->partials, sc, st); break;
+        case 6: launch_combine_m<6>(p, state, Vb, ld, n, w->partials, sc, st); break;
+        case 7: launch_combine_m<7>(p, state, Vb, ld, n, w->partials, sc, st); break;
+        case 8: launch_combine_m<8>(p, state, Vb, ld, n, w->partials, sc, st); break;
+        default:
+            combine_kernel<V, NV><<<resident_grid(p, combine_kernel<V, NV>, T), T, 0, st>>>(state, Vb, ld, n, w->partials, sc);
+        }
+    } else {
+        combine_kernel<V, NV><<<resident_grid(p, combine_kernel<V, NV>, T), T, 0, st>>>(state, Vb, ld, n, w->partials, sc);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     return HX_OK;

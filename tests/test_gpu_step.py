@@ -152,6 +152,28 @@ def test_backward_step_returns_to_the_start(hx, oracle):
     assert rel(back, c0) <= 1e-10
 
 
+def test_host_step_on_pinned_memory(hx, oracle):
+    """hx_step_host on page-locked memory (the bench's end-to-end path), one and two steps, against
+    the oracle."""
+    spec = inputs.workload("hh2_b32")
+    S = oracle.IndexSet.hyperbolic(2, 32)
+    c0 = inputs.initial_vector(spec, S.k)
+    ref1, _ = oracle.expmpr_propagate(S, spec, c0, 0.01, 1, 7)
+    ref3, _ = oracle.expmpr_propagate(S, spec, c0, 0.01, 3, 7)
+    P = hx.Problem(2, 32)
+    try:
+        P.set_potential(spec, 0.0)
+        pinned = torch.from_numpy(c0.copy()).pin_memory()
+        c = pinned.numpy()
+        hx.hx_step_host(P.p, c, 0.01, 1)
+        assert rel(c, ref1) <= 1e-12
+        hx.hx_step_host(P.p, c, 0.01, 2)
+        assert rel(c, ref3) <= 1e-12
+        assert abs(hx.hx_get_time(P.p) - 0.03) < 1e-14
+    finally:
+        P.close()
+
+
 def test_host_step_entry_point(hx, oracle):
     spec = inputs.workload("hh2_b32")
     S = oracle.IndexSet.hyperbolic(2, 32)

@@ -271,3 +271,29 @@ def test_energy_matches_oracle_and_is_conserved(hx, oracle, dtype, tol):
             assert abs(hx.hx_energy(P.p, x) - e0) <= 1e-10 * abs(e0)
     finally:
         P.close()
+
+
+def test_fig8_perturbed_lanczos_row_on_gpu(hx, oracle):
+    """Sec. 6.2, Fig. 8, row N = 4, K = 40 (m = 5, h = 1/10 and 1/20): the GPU step (fast product,
+    complex128) against the Lanczos step with the exact Galerkin matrix of the interpolated torsional
+    potential reproduces the printed perturbation errors (read with max-abs, as Fig. 5); the GPU step
+    itself matches the oracle's fast-product step to 1e-12."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fig8_perturbed_lanczos.json")))
+    row = next(r for r in gold["rows"] if r["N"] == 4 and r["K"] == 40)
+    N, K = 4, 40
+    comps = [{"coef": -1.0, "func": "cos_scaled", "axes": [l], "scale": 1 / 16.0, "R": 8} for l in range(N)]
+    spec = dict(N=N, B=K + 1, L=16.0, potential=comps + [{"coef": float(N), "powers": {}}])
+    S = oracle.IndexSet.hyperbolic(N, K + 1)
+    r, a = oracle.potential_terms(spec, 0.0)
+    v = inputs.initial_vector({"init": {"kind": "beta_decay", "beta": gold["beta"]}}, S.k)
+    d = oracle.diag(S)
+    A = np.diag(d) + oracle.gh_assembly(S, r, a, 16.0, K + 10)
+    for h, printed in zip(gold["h"][:2], row["err"][:2]):
+        up, _, _ = oracle.lanczos_exp(lambda x: A @ x, v, h, gold["m"])
+        pe, _, _ = oracle.lanczos_exp(lambda x: oracle.apply(S, r, a, 16.0, x), v, h, gold["m"])
+        got, _, _ = run_gpu(hx, spec, v, hx.HX_C128, h, 1, m=gold["m"])
+        assert rel(got, pe) <= 1e-12, rel(got, pe)
+        err = np.abs(up - got).max()
+        assert err == pytest.approx(printed, rel=5e-3), (h, err, printed)

@@ -474,3 +474,43 @@ def test_time_integration_table(oracle):
     c, _ = oracle.magnus4_propagate(S, spec, c0, 0.025, 40, 7)
     plateau = np.abs(c - ref).max()
     assert 1.0 < plateau / rows[2, 7, 40, "magnus4"][-1] < 1.6
+
+
+# --------------------------------------------------------------------------- #
+# perturbed Lanczos (Sec. 6.2)                                                 #
+# --------------------------------------------------------------------------- #
+
+def test_fig8_perturbed_lanczos_soft_pin(oracle):
+    """Sec. 6.2, Fig. 8: the error of an m = 5 Lanczos step when the fast algorithm replaces the
+    exact Galerkin product, read with the unperturbed A = D_K + (exact Galerkin matrix of the
+    interpolated W), v_k = prod max(k_l, 1)^-3 normalised, and max-abs (the norm that reproduces
+    Fig. 5).  The N = 4 row is reproduced (0.2 %), N = 3 to 4 %, the N = 2 rows within a factor 1.6
+    (a soft pin); linear in h (each halving of h halves the error to 8 %; the printed ratios run from
+    1.99 to 2.105); smaller for larger K at N = 2 and larger for larger N at K = 40, as printed."""
+    gold = json.load(open(os.path.join(GOLDEN, "fig8_perturbed_lanczos.json")))
+    m, beta = gold["m"], gold["beta"]
+    first = {}
+    for row in gold["rows"]:
+        N, K = row["N"], row["K"]
+        S = oracle.IndexSet.hyperbolic(N, K + 1)
+        r, a = oracle.potential_terms(torsional_spec(N), 0.0)
+        r = np.vstack([r, np.zeros((1, N), np.int32)])
+        a = np.append(a, float(N))
+        v = inputs.initial_vector({"init": {"kind": "beta_decay", "beta": beta}}, S.k)
+        d = oracle.diag(S)
+        A = np.diag(d) + oracle.gh_assembly(S, r, a, 16.0, K + 10)      # exact for this polynomial
+        errs = []
+        for h in gold["h"]:
+            up, _, _ = oracle.lanczos_exp(lambda x: A @ x, v, h, m)
+            pe, _, _ = oracle.lanczos_exp(lambda x: d * x + oracle.fast_algorithm(S, r, a, 16.0, x), v, h, m)
+            errs.append(np.abs(up - pe).max())
+        # N = 4 reproduces the printed row to 0.2 %, N = 3 to 4 %; the N = 2 rows come out a constant
+        # factor 1.10 ... 1.41 above theirs
+        tol = {4: 1.005, 3: 1.05}.get(N, 1.6)
+        for e, p in zip(errs, row["err"]):
+            assert p / tol <= e <= p * tol, (N, K, e, p)
+        for e0, e1 in zip(errs, errs[1:]):
+            assert e0 / e1 == pytest.approx(2.0, rel=0.08)     # printed ratios: 1.99 ... 2.105
+        first[(N, K)] = errs[0]
+    assert first[(2, 10)] > first[(2, 20)] > first[(2, 30)] > first[(2, 40)]
+    assert first[(2, 40)] < first[(3, 40)] < first[(4, 40)]

@@ -373,7 +373,10 @@ def terms_from_spec(spec: dict) -> list:
              "phase": mod.get("phase", 0.0)}
         if mod["kind"] == "pwconst":
             t.update(pw_values=mod["values"], pw_t0=mod["t0"], pw_t1=mod["t1"])
-        if "powers" in comp:
+        if "powers" in comp and not comp["powers"]:     # a constant: degree 0 on axis 0 (the diagonal)
+            t["axes"] = [0]
+            t["coef"] = np.ones(1)
+        elif "powers" in comp:
             axes = sorted(comp["powers"])
             if len(axes) > 2:
                 raise ValueError("terms on more than two axes are not supported")

@@ -169,7 +169,6 @@ def test_edge_cases(hx, oracle):
         P.close()
     # constant term folds into the diagonal; a term on the last axis only
     spec = spec_of(2, 20, [{"coef": 0.4, "powers": {}}, {"coef": 0.7, "powers": {1: 2}}])
-    spec["potential"][0] = {"coef": 0.4, "func": "cos_scaled", "axes": [0], "scale": 0.0, "R": 0}
     S = oracle.IndexSet.hyperbolic(2, 20)
     c = inputs.initial_vector({"init": {"kind": "gaussian", "seed": 1}}, S.k)
     r, a = oracle.potential_terms(spec, 0.0)

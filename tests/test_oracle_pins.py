@@ -514,3 +514,39 @@ def test_fig8_perturbed_lanczos_soft_pin(oracle):
         first[(N, K)] = errs[0]
     assert first[(2, 10)] > first[(2, 20)] > first[(2, 30)] > first[(2, 40)]
     assert first[(2, 40)] < first[(3, 40)] < first[(4, 40)]
+
+
+def test_fig9_lanczos_error_table_soft_pin(oracle):
+    """Sec. 6.2, Fig. 9 (h = 1/10): the unperturbed Lanczos error (against exp(-ihA) v by scipy's
+    expm) and the perturbation error, with the readings of the Fig. 8 pin.  A soft pin: every
+    printed cell within a factor 2.5 (the m = 9, K = 10 entry is 1e-13, rounding level), and the
+    structure the paper draws from the table: at N = 2 the unperturbed error falls with m and rises
+    with K, the perturbation error falls with K and hardly depends on m (m >= 5: within 3 %)."""
+    gold = json.load(open(os.path.join(GOLDEN, "fig9_lanczos_errors.json")))
+    h = gold["h"]
+    got = {}
+    for row in gold["rows"]:
+        N, m = row["N"], row["m"]
+        un, pe = [], []
+        for K in gold["K"]:
+            S = oracle.IndexSet.hyperbolic(N, K + 1)
+            r, a = oracle.potential_terms(torsional_spec(N), 0.0)
+            r = np.vstack([r, np.zeros((1, N), np.int32)])
+            a = np.append(a, float(N))
+            v = inputs.initial_vector({"init": {"kind": "beta_decay", "beta": gold["beta"]}}, S.k)
+            d = oracle.diag(S)
+            A = np.diag(d) + oracle.gh_assembly(S, r, a, 16.0, K + 10)
+            up, _, _ = oracle.lanczos_exp(lambda x: A @ x, v, h, m)
+            pf, _, _ = oracle.lanczos_exp(lambda x: d * x + oracle.fast_algorithm(S, r, a, 16.0, x), v, h, m)
+            un.append(np.abs(up - scipy.linalg.expm(-1j * h * A) @ v).max())
+            pe.append(np.abs(up - pf).max())
+        for e, p in zip(un + pe, row["unperturbed"] + row["perturbation"]):
+            assert p / 2.5 <= e <= p * 2.5, (N, m, e, p)
+        got[(N, m)] = (un, pe)
+    for mlo, mhi in ((3, 5), (5, 7), (7, 9)):
+        assert all(x > y for x, y in zip(got[(2, mlo)][0], got[(2, mhi)][0]))
+    for m in (3, 5, 7, 9):
+        un, pe = got[(2, m)]
+        assert un == sorted(un) and pe == sorted(pe, reverse=True)
+    for m in (7, 9):
+        assert np.allclose(got[(2, m)][1], got[(2, 5)][1], rtol=0.03)

@@ -39,11 +39,12 @@ struct ApplyArgs : ApplyArgsBase {
 // value j = t mod nval over the blocks c, c + nc, ... (c = t div nval, nc = blockDim / nval) and
 // the nc chunk sums are added in chunk order, so the totals land in tot[0..nval) (shared) in an
 // order that does not depend on block timing.  Returns true in every thread of that last block.
-// Needs blockDim.x <= 256 and nval <= 2 (kMaxKrylov + 1).
+// Needs blockDim.x <= 256 and nval <= NMAX <= 2 (kMaxKrylov + 1).
 constexpr int kRedMax = 2 * (kMaxKrylov + 1);
+template <int NMAX = kRedMax>   // nval <= NMAX (sizes the shared warp sums)
 static __device__ bool reduce_partials(const double *vals, int nval, double *partials, unsigned *counter, double *tot)
 {
-    __shared__ double wsum[8][kRedMax];
+    __shared__ double wsum[8][NMAX];
     __shared__ double csum[256];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -454,7 +455,7 @@ __device__ __forceinline__ void apply_elements(const ApplyArgs &args, Body body)
             for (int j = 0; j < 2 * kMaxFusedDots; ++j)
                 vals[j] = (lane >> (5 - wl)) == j && (lane & ((1 << (5 - wl)) - 1)) == 0 ? (double)hs + (double)hc : 0.0;
             __shared__ double tot[2 * kMaxFusedDots];
-            if (reduce_partials(vals, 2 * nd, args.dpartials, args.dcounter, tot) && threadIdx.x == 0) {
+            if (reduce_partials<2 * kMaxFusedDots>(vals, 2 * nd, args.dpartials, args.dcounter, tot) && threadIdx.x == 0) {
                 for (int i = 0; i < nd; ++i) {
                     args.dh[2 * i] = args.ds[i] * tot[2 * i];
                     args.dh[2 * i + 1] = args.ds[i] * tot[2 * i + 1];

@@ -134,11 +134,17 @@ __global__ void init_kernel(const double2 *c, V *v0, int n, double *partials, Sc
 {
     double acc = 0.0;
     if constexpr (std::is_same<V, float2>::value) {
-        NormAcc na;
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-            const double2 x = c[i];
+        NormAcc na;   // two elements per thread and iteration: 32 bytes in, one 16-byte store out
+        const int gid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+        for (int q = gid; q < (n >> 1); q += gstride) {
+            const double2 x = c[2 * q], y = c[2 * q + 1];
+            const float xr = na.add(x.x), xi = na.add(x.y), yr = na.add(y.x), yi = na.add(y.y);
+            *reinterpret_cast<float4 *>(v0 + 2 * q) = make_float4(xr, xi, yr, yi);
+        }
+        if ((n & 1) && gid == 0) {
+            const double2 x = c[n - 1];
             const float xr = na.add(x.x), xi = na.add(x.y);
-            v0[i] = make_float2(xr, xi);
+            v0[n - 1] = make_float2(xr, xi);
         }
         acc = na.value();
     } else {

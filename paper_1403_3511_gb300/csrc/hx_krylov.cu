@@ -433,6 +433,45 @@ __global__ void __launch_bounds__(256, (sizeof(V) == 8 && NV <= 8) ? 3 : 1) upda
     if (reduce_partials(vals, nval, partials, &sc->counter, tot) && threadIdx.x == 0) update_scalars<pass>(sc, k, tot);
 }
 
+__host__ __device__ constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
+// Warp sums of NV compensated FP32 values s_j + c_j (NV a power of two, at most 32) by a butterfly
+// reduce-scatter in FP32 pairs: in each of the first log2 NV rounds a lane keeps half of its
+// values and adds its partner's copy of them with TwoSum, the remaining rounds add up the one
+// value left; lane l then holds value l >> (5 - log2 NV).  One lane per value and warp writes it
+// as FP64 to wsum[warp][j] (j < nval).  On this GPU an FP64 add costs about as much as 64 FP32
+// operations, so this replaces 5 FP64 shuffle-adds per value and thread.
+template <int NV, int NMAX>
+__device__ __forceinline__ void warp_pair_sums(float (&s)[NV], float (&c)[NV], int nval, double (*wsum)[NMAX])
+{
+    const int lane = threadIdx.x & 31;
+    int o = 16;
+#pragma unroll
+    for (int half = NV / 2; half >= 1; half >>= 1, o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < half; ++j) {
+            const float ks = hi ? s[j + half] : s[j], kc = hi ? c[j + half] : c[j];
+            const float xs = hi ? s[j] : s[j + half], xc = hi ? c[j] : c[j + half];
+            const float rs = __shfl_xor_sync(0xffffffffu, xs, o), rc = __shfl_xor_sync(0xffffffffu, xc, o);
+            const float t = ks + rs, bb = t - ks;
+            c[j] = kc + rc + ((ks - (t - bb)) + (rs - bb));
+            s[j] = t;
+        }
+    }
+#pragma unroll
+    for (; o >= 1; o >>= 1) {
+        const float rs = __shfl_xor_sync(0xffffffffu, s[0], o), rc = __shfl_xor_sync(0xffffffffu, c[0], o);
+        const float t = s[0] + rs, bb = t - s[0];
+        c[0] = c[0] + rc + ((s[0] - (t - bb)) + (rs - bb));
+        s[0] = t;
+    }
+    constexpr int sh = 5 - ilog2(NV);
+    const int j = lane >> sh;
+    if ((lane & ((1 << sh) - 1)) == 0 && j < nval) wsum[threadIdx.x >> 5][j] = (double)s[0] + (double)c[0];
+}
+
 // The update for one Lanczos index K <= 7 known at compile time (the step graph launches one per
 // k): register arrays of exactly K + 1 vectors, and for small K each thread loads U grid-stride
 // iterations before using them, so that enough bytes are in flight to cover the memory latency
@@ -510,18 +549,36 @@ __global__ void __launch_bounds__(256, update_k_blocks<V, K>()) update_k_kernel(
             nrm.add(x, x);
         }
     }
-    double vals[pass == 0 ? 2 * NK : 1];
-    if constexpr (pass == 0) {
+    if constexpr (pass == 0 && std::is_same<V, float2>::value) {
+        // the 2 (K + 1) projections: warp sums in FP32 pairs, one FP64 value per warp and projection
+        constexpr int NV = pow2_at_least(2 * NK);
+        float ps[NV], pc[NV];
 #pragma unroll
-        for (int i = 0; i < NK; ++i) {
-            vals[2 * i] = acc[i].r();
-            vals[2 * i + 1] = acc[i].i();
+        for (int i = 0; i < NV / 2; ++i) {
+            ps[2 * i] = i < NK ? acc[i].re.s : 0.f;
+            pc[2 * i] = i < NK ? acc[i].re.c : 0.f;
+            ps[2 * i + 1] = i < NK ? acc[i].im.s : 0.f;
+            pc[2 * i + 1] = i < NK ? acc[i].im.c : 0.f;
         }
+        __shared__ double wsum[8][2 * kMaxFusedDots];
+        warp_pair_sums<NV>(ps, pc, 2 * NK, wsum);
+        __syncthreads();
+        if (reduce_warp_sums<2 * kMaxFusedDots>(wsum, 2 * NK, partials, &sc->counter, tot) && threadIdx.x == 0)
+            update_scalars<pass>(sc, K, tot);
     } else {
-        vals[0] = nrm.r();
+        double vals[pass == 0 ? 2 * NK : 1];
+        if constexpr (pass == 0) {
+#pragma unroll
+            for (int i = 0; i < NK; ++i) {
+                vals[2 * i] = acc[i].r();
+                vals[2 * i + 1] = acc[i].i();
+            }
+        } else {
+            vals[0] = nrm.r();
+        }
+        if (reduce_partials(vals, pass == 0 ? 2 * NK : 1, partials, &sc->counter, tot) && threadIdx.x == 0)
+            update_scalars<pass>(sc, K, tot);
     }
-    if (reduce_partials(vals, pass == 0 ? 2 * NK : 1, partials, &sc->counter, tot) && threadIdx.x == 0)
-        update_scalars<pass>(sc, K, tot);
 }
 
 // T_m = Q diag(lambda) Q^T by the implicit-shift QL iteration for symmetric tridiagonal matrices

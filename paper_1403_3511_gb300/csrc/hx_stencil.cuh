@@ -34,26 +34,20 @@ struct ApplyArgs : ApplyArgsBase {
     unsigned *dcounter;        // zero; reset by the last block
 };
 
-// Writes nval per-block sums to partials[blockIdx.x * nval + j] (all values reduced together:
-// warp shuffles, then one pass over the warp sums).  In the last block to arrive, thread t adds
-// value j = t mod nval over the blocks c, c + nc, ... (c = t div nval, nc = blockDim / nval) and
-// the nc chunk sums are added in chunk order, so the totals land in tot[0..nval) (shared) in an
-// order that does not depend on block timing.  Returns true in every thread of that last block.
-// Needs blockDim.x <= 256 and nval <= NMAX <= 2 (kMaxKrylov + 1).
-constexpr int kRedMax = 2 * (kMaxKrylov + 1);
-template <int NMAX = kRedMax>   // nval <= NMAX (sizes the shared warp sums)
-static __device__ bool reduce_partials(const double *vals, int nval, double *partials, unsigned *counter, double *tot)
+// Block and grid stages of the reductions: wsum[w][j] (shared, filled by the caller, followed by a
+// barrier) holds warp w's sum of value j < nval.  Writes the nval per-block sums to
+// partials[blockIdx.x * nval + j].  In the last block to arrive, thread t adds value
+// j = t mod nval over the blocks c, c + nc, ... (c = t div nval, nc = blockDim / nval) and the nc
+// chunk sums are added in chunk order, so the totals land in tot[0..nval) (shared) in an order
+// that does not depend on block timing.  Returns true in every thread of that last block.
+// Needs blockDim.x <= 256 and nval <= NMAX.
+template <int NMAX>
+static __device__ bool reduce_warp_sums(double (*wsum)[NMAX], int nval, double *partials, unsigned *counter,
+                                        double *tot)
 {
-    __shared__ double wsum[8][NMAX];
     __shared__ double csum[256];
     __shared__ bool last;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = 0; j < nval; ++j) {
-        double v = vals[j];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) wsum[wid][j] = v;
-    }
-    __syncthreads();
+    const int nw = blockDim.x >> 5;
     if ((int)threadIdx.x < nval) {
         double s = 0.0;
         for (int i = 0; i < nw; ++i) s += wsum[i][threadIdx.x];
@@ -80,6 +74,24 @@ static __device__ bool reduce_partials(const double *vals, int nval, double *par
     }
     __syncthreads();
     return true;
+}
+
+// The reduction of nval FP64 values per thread (vals[0..nval)): warp sums by FP64 shuffles, then
+// reduce_warp_sums.  (Each shuffle round is an FP64 add per value and thread; the kernels that
+// reduce many values from FP32 accumulators fill the warp sums themselves.)
+constexpr int kRedMax = 2 * (kMaxKrylov + 1);
+template <int NMAX = kRedMax>   // nval <= NMAX (sizes the shared warp sums)
+static __device__ bool reduce_partials(const double *vals, int nval, double *partials, unsigned *counter, double *tot)
+{
+    __shared__ double wsum[8][NMAX];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = 0; j < nval; ++j) {
+        double v = vals[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) wsum[wid][j] = v;
+    }
+    __syncthreads();
+    return reduce_warp_sums<NMAX>(wsum, nval, partials, counter, tot);
 }
 
 // amp * f(t) in the stencil precision R (the interval index of a piecewise-constant modulation is
@@ -458,12 +470,13 @@ __device__ __forceinline__ void apply_elements(const ApplyArgs &args, Body body)
             }
         }
         if (nd) {
-            double vals[2 * kMaxFusedDots];
-#pragma unroll
-            for (int j = 0; j < 2 * kMaxFusedDots; ++j)
-                vals[j] = (lane >> (5 - wl)) == j && (lane & ((1 << (5 - wl)) - 1)) == 0 ? (double)hs + (double)hc : 0.0;
+            // the lanes already hold warp sums (lane l: value l >> (5 - wl)): one write per value and warp
+            __shared__ double wsum[8][2 * kMaxFusedDots];
+            const int sh = 5 - wl, j = lane >> sh;
+            if ((lane & ((1 << sh) - 1)) == 0 && j < 2 * nd) wsum[threadIdx.x >> 5][j] = (double)hs + (double)hc;
+            __syncthreads();
             __shared__ double tot[2 * kMaxFusedDots];
-            if (reduce_partials<2 * kMaxFusedDots>(vals, 2 * nd, args.dpartials, args.dcounter, tot) && threadIdx.x == 0) {
+            if (reduce_warp_sums<2 * kMaxFusedDots>(wsum, 2 * nd, args.dpartials, args.dcounter, tot) && threadIdx.x == 0) {
                 for (int i = 0; i < nd; ++i) {
                     args.dh[2 * i] = args.ds[i] * tot[2 * i];
                     args.dh[2 * i + 1] = args.ds[i] * tot[2 * i + 1];

@@ -259,6 +259,45 @@ __device__ __forceinline__ void sub_scaled(V &x, R cr, R ci, const V &v)
     x.y -= cr * v.y + ci * v.x;
 }
 
+__host__ __device__ constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
+// Warp sums of NV compensated FP32 values s_j + c_j (NV a power of two, at most 32) by a butterfly
+// reduce-scatter in FP32 pairs: in each of the first log2 NV rounds a lane keeps half of its
+// values and adds its partner's copy of them with TwoSum, the remaining rounds add up the one
+// value left; lane l then holds value l >> (5 - log2 NV).  One lane per value and warp writes it
+// as FP64 to wsum[warp][j] (j < nval).  On this GPU an FP64 add costs about as much as 64 FP32
+// operations, so this replaces 5 FP64 shuffle-adds per value and thread.
+template <int NV, int NMAX>
+__device__ __forceinline__ void warp_pair_sums(float (&s)[NV], float (&c)[NV], int nval, double (*wsum)[NMAX])
+{
+    const int lane = threadIdx.x & 31;
+    int o = 16;
+#pragma unroll
+    for (int half = NV / 2; half >= 1; half >>= 1, o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < half; ++j) {
+            const float ks = hi ? s[j + half] : s[j], kc = hi ? c[j + half] : c[j];
+            const float xs = hi ? s[j] : s[j + half], xc = hi ? c[j] : c[j + half];
+            const float rs = __shfl_xor_sync(0xffffffffu, xs, o), rc = __shfl_xor_sync(0xffffffffu, xc, o);
+            const float t = ks + rs, bb = t - ks;
+            c[j] = kc + rc + ((ks - (t - bb)) + (rs - bb));
+            s[j] = t;
+        }
+    }
+#pragma unroll
+    for (; o >= 1; o >>= 1) {
+        const float rs = __shfl_xor_sync(0xffffffffu, s[0], o), rc = __shfl_xor_sync(0xffffffffu, c[0], o);
+        const float t = s[0] + rs, bb = t - s[0];
+        c[0] = c[0] + rc + ((s[0] - (t - bb)) + (rs - bb));
+        s[0] = t;
+    }
+    constexpr int sh = 5 - ilog2(NV);
+    const int j = lane >> sh;
+    if ((lane & ((1 << sh) - 1)) == 0 && j < nval) wsum[threadIdx.x >> 5][j] = (double)s[0] + (double)c[0];
+}
+
 // h_i = s_i <v_i, w> for i <= k.
 // proj = 1 (projection onto a finished basis): k is clipped to the vectors actually built.
 template <typename V, int NV>
@@ -296,14 +335,31 @@ __global__ void __launch_bounds__(256) dot_kernel(const V *w, const V *Vb, size_
                 if (i <= k) acc[i].add(Vb[i * ld + e], x);
         }
     }
-    double vals[2 * NV];
-#pragma unroll(NV <= 8 ? NV : 1)
-    for (int i = 0; i < NV; ++i) {
-        vals[2 * i] = acc[i].r();
-        vals[2 * i + 1] = acc[i].i();
-    }
     const int nval = 2 * (k + 1);
-    if (reduce_partials(vals, nval, partials, &sc->counter, tot) && threadIdx.x == 0) {
+    bool done;
+    if constexpr (std::is_same<V, float2>::value && NV <= 8) {   // warp sums in FP32 pairs
+        float ps[2 * NV], pc[2 * NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            ps[2 * i] = acc[i].re.s;
+            pc[2 * i] = acc[i].re.c;
+            ps[2 * i + 1] = acc[i].im.s;
+            pc[2 * i + 1] = acc[i].im.c;
+        }
+        __shared__ double wsum[8][2 * NV];
+        warp_pair_sums<2 * NV>(ps, pc, nval, wsum);
+        __syncthreads();
+        done = reduce_warp_sums<2 * NV>(wsum, nval, partials, &sc->counter, tot);
+    } else {
+        double vals[2 * NV];
+#pragma unroll(NV <= 8 ? NV : 1)
+        for (int i = 0; i < NV; ++i) {
+            vals[2 * i] = acc[i].r();
+            vals[2 * i + 1] = acc[i].i();
+        }
+        done = reduce_partials(vals, nval, partials, &sc->counter, tot);
+    }
+    if (done && threadIdx.x == 0) {
         for (int i = 0; i <= k; ++i) {
             sc->h[2 * i] = sc->s[i] * tot[2 * i];
             sc->h[2 * i + 1] = sc->s[i] * tot[2 * i + 1];
@@ -431,45 +487,6 @@ __global__ void __launch_bounds__(256, (sizeof(V) == 8 && NV <= 8) ? 3 : 1) upda
         nval = 1;
     }
     if (reduce_partials(vals, nval, partials, &sc->counter, tot) && threadIdx.x == 0) update_scalars<pass>(sc, k, tot);
-}
-
-__host__ __device__ constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
-__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
-
-// Warp sums of NV compensated FP32 values s_j + c_j (NV a power of two, at most 32) by a butterfly
-// reduce-scatter in FP32 pairs: in each of the first log2 NV rounds a lane keeps half of its
-// values and adds its partner's copy of them with TwoSum, the remaining rounds add up the one
-// value left; lane l then holds value l >> (5 - log2 NV).  One lane per value and warp writes it
-// as FP64 to wsum[warp][j] (j < nval).  On this GPU an FP64 add costs about as much as 64 FP32
-// operations, so this replaces 5 FP64 shuffle-adds per value and thread.
-template <int NV, int NMAX>
-__device__ __forceinline__ void warp_pair_sums(float (&s)[NV], float (&c)[NV], int nval, double (*wsum)[NMAX])
-{
-    const int lane = threadIdx.x & 31;
-    int o = 16;
-#pragma unroll
-    for (int half = NV / 2; half >= 1; half >>= 1, o >>= 1) {
-        const bool hi = (lane & o) != 0;
-#pragma unroll
-        for (int j = 0; j < half; ++j) {
-            const float ks = hi ? s[j + half] : s[j], kc = hi ? c[j + half] : c[j];
-            const float xs = hi ? s[j] : s[j + half], xc = hi ? c[j] : c[j + half];
-            const float rs = __shfl_xor_sync(0xffffffffu, xs, o), rc = __shfl_xor_sync(0xffffffffu, xc, o);
-            const float t = ks + rs, bb = t - ks;
-            c[j] = kc + rc + ((ks - (t - bb)) + (rs - bb));
-            s[j] = t;
-        }
-    }
-#pragma unroll
-    for (; o >= 1; o >>= 1) {
-        const float rs = __shfl_xor_sync(0xffffffffu, s[0], o), rc = __shfl_xor_sync(0xffffffffu, c[0], o);
-        const float t = s[0] + rs, bb = t - s[0];
-        c[0] = c[0] + rc + ((s[0] - (t - bb)) + (rs - bb));
-        s[0] = t;
-    }
-    constexpr int sh = 5 - ilog2(NV);
-    const int j = lane >> sh;
-    if ((lane & ((1 << sh) - 1)) == 0 && j < nval) wsum[threadIdx.x >> 5][j] = (double)s[0] + (double)c[0];
 }
 
 // The update for one Lanczos index K <= 7 known at compile time (the step graph launches one per
@@ -775,6 +792,128 @@ __device__ void eig_small_warp(Scal *sc, double h)   // run by lanes 0 .. 7 of a
 
 __global__ void __launch_bounds__(kEigSmall) eig_small_kernel(Scal *sc, double h) { eig_small_warp(sc, h); }
 
+// y = beta_0 Q exp(-i h Lambda) Q^T e_1 for m <= 8 with few FP64 instructions (each costs about 64
+// FP32 ones for a single warp here), one eigenpair per lane j < m:
+//   1. lambda_j (the (j+1)-th smallest) by bisection on [lo, hi] in FP32 with Sturm counts (the signs
+//      of the pivots of T - x I = L D L^T);
+//   2. three Newton steps in FP64 on det(T - x I) and its derivative (three-term recurrences);
+//   3. the eigenvector by inverse iteration: T - lambda_j I = L D L^T in FP64 (pivots below
+//      1e-14 (hi - lo) replaced by that), two solves from the vector of ones, normalised.
+// When two eigenvalues lie closer than 1 % of hi - lo (the eigenvectors of inverse iteration then
+// lose orthogonality in proportion to eps (hi - lo) / gap), or a Newton step fails, it returns false
+// without writing anything and the caller runs the QL solver.  Warp-uniform; 32 lanes call it.
+__device__ bool eig_fast_warp(Scal *sc, double h, double lo, double hi)
+{
+    constexpr int M = kEigSmall;
+    const int lane = threadIdx.x & 31;
+    const int mu = sc->m_used;
+    double a[M], b[M];                                  // b[i] = T_{i, i+1}
+    float af[M], b2f[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        a[i] = i < mu ? sc->alpha[i] : 0.0;
+        b[i] = i + 1 < mu ? sc->beta[i] : 0.0;
+        af[i] = (float)a[i];
+        b2f[i] = (float)(b[i] * b[i]);
+    }
+    const double span = hi - lo;
+    // 1. bisection (FP32): lane j keeps [lf, uf] with count(lf) <= j < count(uf)
+    float lf = (float)(lo - 1e-6 * span) - 1e-30f, uf = (float)(hi + 1e-6 * span) + 1e-30f;
+    for (int it = 0; it < 32; ++it) {
+        const float x = 0.5f * (lf + uf);
+        int cnt = 0;
+        float q = 1.f;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if (i < mu) {
+                q = (af[i] - x) - (i > 0 ? __fdividef(b2f[i - 1], q) : 0.f);
+                if (fabsf(q) < 1e-30f) q = -1e-30f;
+                cnt += q < 0.f;
+            }
+        if (cnt > lane) uf = x;
+        else lf = x;
+    }
+    // 2. Newton (FP64)
+    const double xb = 0.5 * ((double)lf + (double)uf);
+    double x = xb;
+    bool ok = true;
+    for (int it = 0; it < 3; ++it) {
+        double p0 = 1.0, p1 = a[0] - x, d0 = 0.0, d1 = -1.0;
+#pragma unroll
+        for (int i = 1; i < M; ++i)
+            if (i < mu) {
+                const double bb = b[i - 1] * b[i - 1];
+                const double p2 = (a[i] - x) * p1 - bb * p0, d2 = (a[i] - x) * d1 - p1 - bb * d0;
+                p0 = p1;
+                p1 = p2;
+                d0 = d1;
+                d1 = d2;
+            }
+        const double step = p1 / d1;
+        if (isfinite(step)) x -= step;
+        else if (p1 != 0.0) ok = false;
+    }
+    ok = ok && isfinite(x) && fabs(x - xb) <= 4.0 * ((double)uf - (double)lf) + 1e-12 * span;
+    // gaps between consecutive eigenvalues (lane j: lambda_{j+1} - lambda_j)
+    const double xn = __shfl_down_sync(0xffffffffu, x, 1);
+    if (lane + 1 < mu) ok = ok && xn - x > 1e-2 * span;
+    if (!__all_sync(0xffffffffu, ok || lane >= mu) || !(span > 0.0)) return false;
+    // 3. inverse iteration (FP64)
+    const double tiny = 1e-14 * span;
+    double inv_d[M], l[M], z[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        if (i < mu) {
+            l[i] = i > 0 ? b[i - 1] * inv_d[i - 1] : 0.0;
+            double d = a[i] - x - (i > 0 ? l[i] * b[i - 1] : 0.0);
+            if (fabs(d) < tiny) d = tiny;
+            inv_d[i] = 1.0 / d;
+        } else {
+            l[i] = 0.0;
+            inv_d[i] = 0.0;
+        }
+        z[i] = i < mu ? 1.0 : 0.0;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+        for (int i = 1; i < M; ++i) z[i] -= l[i] * z[i - 1];          // L y = r
+#pragma unroll
+        for (int i = M - 1; i >= 0; --i) z[i] = z[i] * inv_d[i] - (i + 1 < M ? l[i + 1] * z[i + 1] : 0.0);   // D L^T z = y
+        double nr = 0.0;
+#pragma unroll
+        for (int i = 0; i < M; ++i) nr = fma(z[i], z[i], nr);
+        const double inv = rsqrt(nr);
+#pragma unroll
+        for (int i = 0; i < M; ++i) z[i] *= inv;
+    }
+    // y_i = beta_0 sum_j z_j[i] z_j[0] e^{-i h lambda_j}
+    __shared__ double Zs[M][M];
+    double ps, pc;
+    sincos(-h * x, &ps, &pc);
+    const double wr = lane < mu ? z[0] * pc : 0.0, wi = lane < mu ? z[0] * ps : 0.0;
+    if (lane < mu) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) Zs[lane][i] = z[i];
+    }
+    __syncwarp();
+    double yr = 0.0, yi = 0.0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const double wrj = __shfl_sync(0xffffffffu, wr, j), wij = __shfl_sync(0xffffffffu, wi, j);
+        if (j < mu && lane < M) {
+            const double q = Zs[j][lane];
+            yr = fma(q, wrj, yr);
+            yi = fma(q, wij, yi);
+        }
+    }
+    if (lane < mu) {
+        sc->y[2 * lane] = sc->beta0 * yr * sc->s[lane];
+        sc->y[2 * lane + 1] = sc->beta0 * yi * sc->s[lane];
+    }
+    if (lane == 0) sc->t += h;
+    return true;
+}
+
 // y = beta_0 exp(-i h T_m) e_1 for the time step, which needs no eigenvectors.  With c, r from the
 // Gershgorin bounds of T_m, T_m = c I + r X with the spectrum of X in [-1, 1], and by the
 // Jacobi-Anger expansion exp(-i h T_m) = e^{-i h c} sum_k eps_k (-i sgn h)^k J_k(|h| r) T_k(X)
@@ -818,9 +957,9 @@ __global__ void __launch_bounds__(32) expv_kernel(Scal *sc, double h)
     if (!(r >= 1e-290)) r = 1e-290;                                // T = c I (or non-finite: propagates)
     const double sgn = h < 0.0 ? -1.0 : 1.0;
     const double z_all = fabs(h) * r;
-    if (!(z_all <= kChebZ * kChebMaxSub)) {      // large |h| ||T|| or non-finite T: QL instead
+    if (!(z_all <= kChebZ * kChebMaxSub)) {      // large |h| ||T|| or non-finite T: eigenpairs instead
         if (!SMALL) eig_warp(sc, h);
-        else if (j < kEigSmall) eig_small_warp(sc, h);
+        else if (!eig_fast_warp(sc, h, lo, hi) && j < kEigSmall) eig_small_warp(sc, h);
         return;
     }
     const int nsub = z_all > kChebZ ? (int)ceil(z_all / kChebZ) : 1;

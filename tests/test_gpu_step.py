@@ -297,3 +297,18 @@ def test_fig8_perturbed_lanczos_row_on_gpu(hx, oracle):
         assert rel(got, pe) <= 1e-12, rel(got, pe)
         err = np.abs(up - got).max()
         assert err == pytest.approx(printed, rel=5e-3), (h, err, printed)
+
+
+@pytest.mark.parametrize("m,h", [(8, 10.0), (5, 12.0), (3, 20.0)])
+def test_large_step_exponential_matches_oracle(hx, oracle, m, h):
+    """|h| ||T_m|| beyond the Chebyshev series' range (> 96): the exponential takes the eigenpair path
+    (FP32 bisection, FP64 Newton and inverse iteration, or the QL fallback); one step against the
+    oracle's eigendecomposition of T_m."""
+    spec = inputs.workload("hh2_b32")
+    S = oracle.IndexSet.hyperbolic(2, 32)
+    c0 = inputs.initial_vector(spec, S.k)
+    ref, _ = oracle.expmpr_propagate(S, spec, c0, h, 1, m)
+    got, info, _ = run_gpu(hx, spec, c0, hx.HX_C128, h, 1, m=m)
+    assert info["m_used"] == m
+    assert h * (max(info["alpha"]) - min(info["alpha"])) / 2 > 96
+    assert rel(got, ref) <= 1e-12, rel(got, ref)

@@ -202,7 +202,8 @@ int apply_grid(const Problem *p)
 
 template <typename R, int MD>
 static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *cin, void *cout,
-                          const double *t_ptr, double t_shift, const ApplyFuse *fuse, cudaStream_t st)
+                          const double *t_ptr, double t_shift, const ApplyFuse *fuse, cudaStream_t st,
+                          void *cout2 = nullptr, double t_shift2 = 0.0)
 {
     ApplyArgs a;
     memset(&a, 0, sizeof(a));
@@ -235,8 +236,14 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
     a.chan_ld = p->chan_ld;
     a.stage1 = stage1;
     a.skip_diag = p->skip_diag;
+    a.cout2 = cout2;
+    a.t_shift2 = t_shift2;
     const int blocks = (p->set->d.size + kApplyThreads - 1) / kApplyThreads;
     if (!stage1 && p->jit && !g_batch_capture) return jit_launch(p, &a, blocks, st);   // the potential's specialised kernel
+    if (cout2) {
+        set_error("internal: a two-time product needs the specialised kernel");
+        return HX_EUNSUPPORTED;
+    }
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_kernel<R, MD>, kApplyThreads, 0);
     int grid = p->num_sms * (per_sm > 0 ? per_sm : 1);     // one wave of resident CTAs
@@ -260,6 +267,20 @@ static int launch_stage(Problem *p, const OpSet &ops, int stage1, const void *ci
 }
 
 int apply_launches(const Problem *p) { return p->ops1.nops > 0 ? 2 : 1; }
+
+bool apply_dual(const Problem *p) { return p->jit && !g_batch_capture && p->ops1.nops == 0; }
+
+int launch_apply_dual(Problem *p, const void *cin, void *cout, void *cout2, const double *t_ptr, double t_shift,
+                      double t_shift2, const ApplyFuse *fuse, cudaStream_t st)
+{
+    if (!apply_dual(p)) {
+        int rc = launch_apply(p, cin, cout, t_ptr, t_shift, fuse, st);
+        return rc ? rc : launch_apply(p, cin, cout2, t_ptr, t_shift2, fuse, st);
+    }
+    return p->cfg.dtype == HX_C64
+               ? launch_apply_t<float, 3>(p, p->ops, 0, cin, cout, t_ptr, t_shift, fuse, st, cout2, t_shift2)
+               : launch_apply_t<double, 3>(p, p->ops, 0, cin, cout, t_ptr, t_shift, fuse, st, cout2, t_shift2);
+}
 
 bool apply_fuses_dots(const Problem *p)
 {

@@ -101,6 +101,10 @@ int launch_norm(Problem *p, const void *c, int is_c128, double *partials, unsign
 int apply_grid(const Problem *p);
 int apply_launches(const Problem *p);     // kernels per product (1, or 2 with a channel stage)
 bool apply_fuses_dots(const Problem *p);  // the product kernel can compute ApplyFuse projections
+bool apply_dual(const Problem *p);        // one launch can give the products at two times
+// cout = A(t + t_shift) cin and cout2 = A(t + t_shift2) cin, in one launch when apply_dual(p)
+int launch_apply_dual(Problem *p, const void *cin, void *cout, void *cout2, const double *t_ptr, double t_shift,
+                      double t_shift2, const ApplyFuse *fuse, cudaStream_t st);
 
 // hx_apply_project after the argument checks (hx_krylov.cu)
 int apply_project_dispatch(Problem *p, const void *c, void *y, const void *basis, size_t ld, int k, double *h);

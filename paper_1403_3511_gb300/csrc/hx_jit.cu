@@ -35,7 +35,8 @@ namespace hx {
 struct JitKernel {
     CUfunction fn = nullptr;
     CUfunction fn_dots = nullptr;   // complex64 only: the product with fused projections
-    int per_sm = 1, per_sm_dots = 1;
+    CUfunction fn_dual = nullptr;   // two times at once
+    int per_sm = 1, per_sm_dots = 1, per_sm_dual = 1;
 };
 
 // Driver functions, looked up through the runtime (the library does not link the driver library,
@@ -77,41 +78,54 @@ static bool specialised_plane(const Op &op, int sb)
     return cls && (sb == 0 || sb == op.q || (sb == op.q + 2 && sb <= 3));
 }
 
-// The specialised sequence for O, or "" when some operator needs the generic loop.
-static std::string jit_body(const OpSet &O)
+// The specialised sequence for O, or "" when some operator needs the generic loop.  dual: each
+// operator's sum also goes to acc2 with its weight at the second time (sm_w2).
+static std::string jit_body(const OpSet &O, bool dual = false)
 {
     std::string b;
-    char line[512];
+    char line[768];
     for (int i = 0; i < O.nops; ++i) {
         const Op &op = O.op[i];
         if (op.merged) continue;
         if (op.src >= 0 || op.dst >= 0) return "";
+        char add2[256] = "";
         if (op.kind == 0) {
-            snprintf(line, sizeof(line), "    { const V cs = cin[el.e]; acc.add(sm_w[%d] * cs.x, sm_w[%d] * cs.y); }\n", i, i);
+            if (dual) snprintf(add2, sizeof(add2), " acc2.add(sm_w2[%d] * cs.x, sm_w2[%d] * cs.y);", i, i);
+            snprintf(line, sizeof(line), "    { const V cs = cin[el.e]; acc.add(sm_w[%d] * cs.x, sm_w[%d] * cs.y);%s }\n",
+                     i, i, add2);
         } else if (op.kind == 1) {
             if (op.cls < CLS_LINE + 1 || op.cls > CLS_LINE + 3 || op.mergeB >= 0) return "";
+            if (dual) snprintf(add2, sizeof(add2), " acc2.add(sm_w2[%d] * sx, sm_w2[%d] * sy);", i, i);
             snprintf(line, sizeof(line),
                      "    { R sx = 0, sy = 0; line_role<R, %d, %s>(ctx, el, O, O.op[%d], tab, cin, sx, sy);\n"
-                     "      acc.add(sm_w[%d] * sx, sm_w[%d] * sy); }\n",
-                     op.p, op.ra == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW", i, i, i);
+                     "      acc.add(sm_w[%d] * sx, sm_w[%d] * sy);%s }\n",
+                     op.p, op.ra == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW", i, i, i, add2);
         } else {
             const int sb = op.mergeB >= 0 ? O.op[op.mergeB].p : 0;
             if (!specialised_plane(op, sb)) return "";
-            char wl[32];
-            if (sb > 0) snprintf(wl, sizeof(wl), "sm_w[%d]", op.mergeB);
-            else snprintf(wl, sizeof(wl), "(R)0");
+            char wl[32], wl2[32];
+            if (sb > 0) {
+                snprintf(wl, sizeof(wl), "sm_w[%d]", op.mergeB);
+                snprintf(wl2, sizeof(wl2), "sm_w2[%d]", op.mergeB);
+            } else {
+                snprintf(wl, sizeof(wl), "(R)0");
+                snprintf(wl2, sizeof(wl2), "(R)0");
+            }
+            if (dual)
+                snprintf(add2, sizeof(add2), "\n      acc2.add(sm_w2[%d] * sx + %s * lx, sm_w2[%d] * sy + %s * ly);", i,
+                         wl2, i, wl2);
             snprintf(line, sizeof(line),
                      "    { R sx = 0, sy = 0, lx = 0, ly = 0;\n"
                      "      plane_role<R, %d, %d, %s, %d>(ctx, el, O, O.op[%d], tab, cin, sx, sy, lx, ly);\n"
-                     "      acc.add(sm_w[%d] * sx + %s * lx, sm_w[%d] * sy + %s * ly); }\n",
-                     op.p, op.q, op.rb == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW", sb, i, i, wl, i, wl);
+                     "      acc.add(sm_w[%d] * sx + %s * lx, sm_w[%d] * sy + %s * ly);%s }\n",
+                     op.p, op.q, op.rb == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW", sb, i, i, wl, i, wl, add2);
         }
         b += line;
     }
     return b;
 }
 
-static std::string jit_source(bool f32, const std::string &body)
+static std::string jit_source(bool f32, const std::string &body, const std::string &body2)
 {
     std::string s;
     s += "#include \"hx_stencil.cuh\"\n";
@@ -123,6 +137,11 @@ static std::string jit_source(bool f32, const std::string &body)
          "                                    const R *sm_w, const V *cin, const R *tab)\n{\n"
          "    const OpSet &O = args.ops;\n";
     s += body;
+    s += "}\n";
+    s += "__device__ __forceinline__ void ops_dual(const ApplyArgs &args, const Ctx &ctx, const Elem &el, Acc<R> &acc,\n"
+         "                                         Acc<R> &acc2, const R *sm_w, const R *sm_w2, const V *cin, const R *tab)\n{\n"
+         "    const OpSet &O = args.ops;\n";
+    s += body2;
     s += "}\n}  // namespace hx\n";
     // 4 blocks of 256 per SM fit the FP32 kernels in 64 registers without spills (more warps to hide
     // the load latency); the FP64 kernels would spill there and keep 3 blocks (80 registers)
@@ -132,6 +151,15 @@ static std::string jit_source(bool f32, const std::string &body)
          "    hx::apply_elements<hx::R>(args, [&](const hx::Ctx &ctx, const hx::Elem &el, hx::Acc<hx::R> &acc,\n"
          "                                        const hx::R *sm_w, const hx::V *cin, const hx::R *tab) {\n"
          "        hx::ops(args, ctx, el, acc, sm_w, cin, tab);\n"
+         "    });\n}\n";
+    // two times at once (the 2-stage Magnus method's A_1 v and A_2 v)
+    s += f32 ? "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 4)\n"
+             : "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 3)\n";
+    s += "hx_apply_specialised_dual(const __grid_constant__ hx::ApplyArgs args)\n{\n"
+         "    hx::apply_elements_dual<hx::R>(args, [&](const hx::Ctx &ctx, const hx::Elem &el, hx::Acc<hx::R> &acc,\n"
+         "                                             hx::Acc<hx::R> &acc2, const hx::R *sm_w, const hx::R *sm_w2,\n"
+         "                                             const hx::V *cin, const hx::R *tab) {\n"
+         "        hx::ops_dual(args, ctx, el, acc, acc2, sm_w, sm_w2, cin, tab);\n"
          "    });\n}\n";
     if (f32) {   // the same product that also computes the Lanczos projections (ApplyFuse)
         s += "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 4)\n"
@@ -188,9 +216,10 @@ static bool compile_and_load(const std::string &src, int dev, JitKernel *out, st
         reason = "loading the compiled kernel failed";
         return false;
     }
-    CUfunction fn_dots = nullptr;
-    if (src.find("hx_apply_specialised_dots") != std::string::npos &&
-        drv.moduleGetFunction(&fn_dots, mod, "hx_apply_specialised_dots") != CUDA_SUCCESS) {
+    CUfunction fn_dots = nullptr, fn_dual = nullptr;
+    if ((src.find("hx_apply_specialised_dots") != std::string::npos &&
+         drv.moduleGetFunction(&fn_dots, mod, "hx_apply_specialised_dots") != CUDA_SUCCESS) ||
+        drv.moduleGetFunction(&fn_dual, mod, "hx_apply_specialised_dual") != CUDA_SUCCESS) {
         reason = "loading the compiled kernel failed";
         return false;
     }
@@ -201,8 +230,10 @@ static bool compile_and_load(const std::string &src, int dev, JitKernel *out, st
     };
     out->fn = fn;
     out->fn_dots = fn_dots;
+    out->fn_dual = fn_dual;
     out->per_sm = occ(fn);
     out->per_sm_dots = occ(fn_dots);
+    out->per_sm_dual = occ(fn_dual);
     return true;
 }
 
@@ -234,7 +265,7 @@ void jit_prepare(Problem *p)
     auto it = g_jit_cache.find(key);
     if (it == g_jit_cache.end()) {
         JitKernel k;
-        if (!compile_and_load(jit_source(f32, body), p->device, &k, reason)) return;
+        if (!compile_and_load(jit_source(f32, body, jit_body(p->ops, true)), p->device, &k, reason)) return;
         it = g_jit_cache.emplace(key, k).first;
     }
     p->jit = &it->second;
@@ -245,17 +276,20 @@ void jit_prepare(Problem *p)
 int jit_launch(const Problem *p, const void *args, int blocks, cudaStream_t st)
 {
     const JitKernel *k = (const JitKernel *)p->jit;
-    const bool dots = ((const ApplyArgs *)args)->dvec != nullptr;
-    if (dots && !k->fn_dots) {
-        set_error("the specialised kernel has no fused projections (complex64 only)");
+    const ApplyArgs *a = (const ApplyArgs *)args;
+    const bool dots = a->dvec != nullptr, dual = a->cout2 != nullptr;
+    if ((dots && !k->fn_dots) || (dots && dual)) {
+        set_error("the specialised kernel has no fused projections here (complex64 single products only)");
         return HX_EUNSUPPORTED;
     }
+    CUfunction fn = dual ? k->fn_dual : dots ? k->fn_dots : k->fn;
+    const int per_sm = dual ? k->per_sm_dual : dots ? k->per_sm_dots : k->per_sm;
     // apply_grid(p) blocks at most: the size of the partial-sum buffers
-    int grid = std::min(p->num_sms * (dots ? k->per_sm_dots : k->per_sm), apply_grid(p));
+    int grid = std::min(p->num_sms * per_sm, apply_grid(p));
     if (grid > blocks) grid = blocks > 0 ? blocks : 1;
     void *params[] = {const_cast<void *>(args)};
     const Driver &drv = driver();
-    CUresult r = drv.launchKernel(dots ? k->fn_dots : k->fn, grid, 1, 1, kApplyThreads, 1, 1, 0, (CUstream)st, params, nullptr);
+    CUresult r = drv.launchKernel(fn, grid, 1, 1, kApplyThreads, 1, 1, 0, (CUstream)st, params, nullptr);
     if (r != CUDA_SUCCESS) {
         const char *msg = nullptr;
         drv.errorString(r, &msg);

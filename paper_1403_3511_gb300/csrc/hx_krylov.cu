@@ -1267,8 +1267,7 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
         if (p->cfg.scheme == HX_SCHEME_MAGNUS4) {   // Eq. (2stageMagnus): nodes 1/2 -+ sqrt(3)/6
             const double c1 = 0.5 - sqrt(3.0) / 6.0, c2 = 0.5 + sqrt(3.0) / 6.0;
             V *a1v = (V *)w->mag, *a2v = a1v + ld, *a2a1v = a2v + ld, *a1a2v = a2a1v + ld;
-            if ((rc = launch_apply(p, Vb + (size_t)k * ld, a1v, &sc->t, c1 * dt, &f, st)) ||
-                (rc = launch_apply(p, Vb + (size_t)k * ld, a2v, &sc->t, c2 * dt, &f, st)) ||
+            if ((rc = launch_apply_dual(p, Vb + (size_t)k * ld, a1v, a2v, &sc->t, c1 * dt, c2 * dt, &f, st)) ||
                 (rc = launch_apply(p, a1v, a2a1v, &sc->t, c2 * dt, nullptr, st)) ||
                 (rc = launch_apply(p, a2v, a1a2v, &sc->t, c1 * dt, nullptr, st)))
                 return rc;

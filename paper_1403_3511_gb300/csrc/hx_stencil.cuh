@@ -32,6 +32,10 @@ struct ApplyArgs : ApplyArgsBase {
     double *dh;                // h (re, im per vector)
     double *dpartials;         // gridDim.x x 2 (dk + 1)
     unsigned *dcounter;        // zero; reset by the last block
+    // a second product of the same input at another time, A(*t_ptr + t_shift2) cin into cout2
+    // (kernels compiled per potential only; cout2 == nullptr: none)
+    void *cout2;
+    double t_shift2;
 };
 
 // Block and grid stages of the reductions: wsum[w][j] (shared, filled by the caller, followed by a
@@ -387,6 +391,20 @@ __device__ __forceinline__ void add_projections(const ApplyArgs &args, int nd, i
     hs = t;
 }
 
+// The per-thread view of element e from its record er = {row, prod (1 + k_l), sum k_l,
+// k_{N-1} | row length << 16}.
+__device__ __forceinline__ Elem make_elem(const ApplyArgs &args, int e, int4 er)
+{
+    Elem el;
+    el.e = e;
+    el.k2 = er.w & 0xffff;
+    el.qall = er.y;
+    el.rlen = (int)((unsigned)er.w >> 16);
+    el.nb = args.rnb + er.x;
+    el.kr = args.S.row_k + (size_t)er.x * (args.S.N - 1);
+    return el;
+}
+
 // One element: D_K on the diagonal, body(ctx, el, acc, sm_w, cin, tab) adds the operators'
 // contributions, and y = out_scale * acc is written unless the launch only writes channel vectors
 // (stage 1); returns y.
@@ -397,15 +415,7 @@ __device__ __forceinline__ typename Vec2<R>::T apply_element(const ApplyArgs &ar
     using V = typename Vec2<R>::T;
     const DevSet &S = args.S;
     const V *cin = (const V *)args.cin;
-    // er: the element record {row, prod (1 + k_l), sum k_l, k_{N-1} | length << 16}
-    const int r = er.x;
-    Elem el;
-    el.e = e;
-    el.k2 = er.w & 0xffff;
-    el.qall = er.y;
-    el.rlen = (int)((unsigned)er.w >> 16);
-    el.nb = args.rnb + r;
-    el.kr = S.row_k + (size_t)r * (S.N - 1);
+    const Elem el = make_elem(args, e, er);
     Acc<R> acc;
     if (!args.stage1 && !args.skip_diag) {
         const V ce = cin[e];
@@ -484,6 +494,49 @@ __device__ __forceinline__ void apply_elements(const ApplyArgs &args, Body body)
                 *args.dcounter = 0;
             }
         }
+    }
+}
+
+// Two products of the same input in one pass: y = A(*t_ptr + t_shift) c into cout and
+// y2 = A(*t_ptr + t_shift2) c into cout2 (the two time nodes of the 2-stage Magnus method).  The
+// stencil sums do not depend on the time, only the operator weights do, so every gather and all
+// index work are shared; body(ctx, el, acc, acc2, sm_w, sm_w2, cin, tab) adds each operator's sum
+// with its weight at either time.
+template <typename R, typename Body>
+__device__ __forceinline__ void apply_elements_dual(const ApplyArgs &args, Body body)
+{
+    using V = typename Vec2<R>::T;
+    __shared__ R sm_w[kMaxOps], sm_w2[kMaxOps];
+    const DevSet &S = args.S;
+    const OpSet &O = args.ops;
+    if ((int)threadIdx.x < O.nops) {
+        sm_w[threadIdx.x] = op_weight<R>(O.op[threadIdx.x], *args.t_ptr + args.t_shift, args.pw_values);
+        sm_w2[threadIdx.x] = op_weight<R>(O.op[threadIdx.x], *args.t_ptr + args.t_shift2, args.pw_values);
+    }
+    const R oscale = args.out_scale ? (R)(*args.out_scale) : (R)1;
+    __syncthreads();
+    Ctx ctx;
+    ctx.S = &S;
+    ctx.nrow = args.nrow;
+    const V *cin = (const V *)args.cin;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.size; e += gridDim.x * blockDim.x) {
+        const int4 er = __ldg(S.elem + e);
+        const Elem el = make_elem(args, e, er);
+        Acc<R> acc, acc2;
+        if (!args.skip_diag) {
+            const V ce = cin[e];
+            const R dj = (R)er.z + (R)0.5 * (R)S.N;
+            acc.add(dj * ce.x, dj * ce.y);
+            acc2.add(dj * ce.x, dj * ce.y);
+        }
+        body(ctx, el, acc, acc2, (const R *)sm_w, (const R *)sm_w2, cin, (const R *)args.tab);
+        V y = acc.get(), y2 = acc2.get();
+        y.x *= oscale;
+        y.y *= oscale;
+        y2.x *= oscale;
+        y2.y *= oscale;
+        ((V *)args.cout)[e] = y;
+        ((V *)args.cout2)[e] = y2;
     }
 }
 

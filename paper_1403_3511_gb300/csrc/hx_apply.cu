@@ -203,7 +203,7 @@ int apply_grid(const Problem *p)
 template <typename R, int MD>
 static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *cin, void *cout,
                           const double *t_ptr, double t_shift, const ApplyFuse *fuse, cudaStream_t st,
-                          void *cout2 = nullptr, double t_shift2 = 0.0)
+                          void *cout2 = nullptr, double t_shift2 = 0.0, const void *cin2 = nullptr)
 {
     ApplyArgs a;
     memset(&a, 0, sizeof(a));
@@ -237,6 +237,7 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
     a.stage1 = stage1;
     a.skip_diag = p->skip_diag;
     a.cout2 = cout2;
+    a.cin2 = cin2;
     a.t_shift2 = t_shift2;
     const int blocks = (p->set->d.size + kApplyThreads - 1) / kApplyThreads;
     if (!stage1 && p->jit && !g_batch_capture) return jit_launch(p, &a, blocks, st);   // the potential's specialised kernel
@@ -280,6 +281,18 @@ int launch_apply_dual(Problem *p, const void *cin, void *cout, void *cout2, cons
     return p->cfg.dtype == HX_C64
                ? launch_apply_t<float, 3>(p, p->ops, 0, cin, cout, t_ptr, t_shift, fuse, st, cout2, t_shift2)
                : launch_apply_t<double, 3>(p, p->ops, 0, cin, cout, t_ptr, t_shift, fuse, st, cout2, t_shift2);
+}
+
+int launch_apply_pair(Problem *p, const void *cin, void *cout, double t_shift, const void *cin2, void *cout2,
+                      double t_shift2, const double *t_ptr, cudaStream_t st)
+{
+    if (!apply_dual(p)) {
+        int rc = launch_apply(p, cin, cout, t_ptr, t_shift, nullptr, st);
+        return rc ? rc : launch_apply(p, cin2, cout2, t_ptr, t_shift2, nullptr, st);
+    }
+    return p->cfg.dtype == HX_C64
+               ? launch_apply_t<float, 3>(p, p->ops, 0, cin, cout, t_ptr, t_shift, nullptr, st, cout2, t_shift2, cin2)
+               : launch_apply_t<double, 3>(p, p->ops, 0, cin, cout, t_ptr, t_shift, nullptr, st, cout2, t_shift2, cin2);
 }
 
 bool apply_fuses_dots(const Problem *p)

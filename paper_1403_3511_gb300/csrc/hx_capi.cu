@@ -984,8 +984,9 @@ int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step)
     if (per_apply) *per_apply = a;
     // expMPR: the product kernel computes the projections itself when it is specialised (m <= 8)
     const int dots = p->cfg.m <= kMaxFusedDots && apply_fuses_dots(p) ? 0 : 1;
-    // 2-stage Magnus: A_1 v and A_2 v in one launch with the specialised kernel
-    const int mag = apply_dual(p) ? 3 * a + 4 : 4 * a + 4;
+    // 2-stage Magnus: A_1 v and A_2 v in one launch, A_2 A_1 v and A_1 A_2 v in another, with the
+    // specialised kernel
+    const int mag = apply_dual(p) ? 2 * a + 4 : 4 * a + 4;
     if (per_step) *per_step = p->cfg.scheme == HX_SCHEME_MAGNUS4 ? p->cfg.m * mag + 2 : p->cfg.m * (a + 2 + dots) + 2;
     return HX_OK;
 }

@@ -105,6 +105,9 @@ bool apply_dual(const Problem *p);        // one launch can give the products at
 // cout = A(t + t_shift) cin and cout2 = A(t + t_shift2) cin, in one launch when apply_dual(p)
 int launch_apply_dual(Problem *p, const void *cin, void *cout, void *cout2, const double *t_ptr, double t_shift,
                       double t_shift2, const ApplyFuse *fuse, cudaStream_t st);
+// cout = A(t + t_shift) cin and cout2 = A(t + t_shift2) cin2, in one launch when apply_dual(p)
+int launch_apply_pair(Problem *p, const void *cin, void *cout, double t_shift, const void *cin2, void *cout2,
+                      double t_shift2, const double *t_ptr, cudaStream_t st);
 
 // hx_apply_project after the argument checks (hx_krylov.cu)
 int apply_project_dispatch(Problem *p, const void *c, void *y, const void *basis, size_t ld, int k, double *h);

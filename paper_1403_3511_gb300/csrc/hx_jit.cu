@@ -36,7 +36,8 @@ struct JitKernel {
     CUfunction fn = nullptr;
     CUfunction fn_dots = nullptr;   // complex64 only: the product with fused projections
     CUfunction fn_dual = nullptr;   // two times at once
-    int per_sm = 1, per_sm_dots = 1, per_sm_dual = 1;
+    CUfunction fn_pair = nullptr;   // two inputs at two times
+    int per_sm = 1, per_sm_dots = 1, per_sm_dual = 1, per_sm_pair = 1;
 };
 
 // Driver functions, looked up through the runtime (the library does not link the driver library,
@@ -77,6 +78,8 @@ static bool specialised_plane(const Op &op, int sb)
     const bool cls = op.cls == CLS_PLANE + 0 || op.cls == CLS_PLANE + 3 || op.cls == CLS_PLANE + 1 || op.cls == CLS_PLANE + 4;
     return cls && (sb == 0 || sb == op.q || (sb == op.q + 2 && sb <= 3));
 }
+
+static std::string jit_body_pair(const OpSet &O);
 
 // The specialised sequence for O, or "" when some operator needs the generic loop.  dual: each
 // operator's sum also goes to acc2 with its weight at the second time (sm_w2).
@@ -125,7 +128,49 @@ static std::string jit_body(const OpSet &O, bool dual = false)
     return b;
 }
 
-static std::string jit_source(bool f32, const std::string &body, const std::string &body2)
+// The sequence for two inputs (cin into acc at the first time, cin2 into acc2 at the second):
+// each stencil's addresses and weights serve both inputs.  Called only for an O that jit_body
+// accepts.
+static std::string jit_body_pair(const OpSet &O)
+{
+    std::string b;
+    char line[1024];
+    for (int i = 0; i < O.nops; ++i) {
+        const Op &op = O.op[i];
+        if (op.merged) continue;
+        if (op.kind == 0) {
+            snprintf(line, sizeof(line),
+                     "    { const V cs = cin[el.e], cs2 = cin2[el.e]; acc.add(sm_w[%d] * cs.x, sm_w[%d] * cs.y);"
+                     " acc2.add(sm_w2[%d] * cs2.x, sm_w2[%d] * cs2.y); }\n", i, i, i, i);
+        } else if (op.kind == 1) {
+            snprintf(line, sizeof(line),
+                     "    { const V *sr[2] = {cin, cin2}; R sx[2] = {0, 0}, sy[2] = {0, 0};\n"
+                     "      line_role_n<R, %d, %s, 2>(ctx, el, O, O.op[%d], tab, sr, sx, sy);\n"
+                     "      acc.add(sm_w[%d] * sx[0], sm_w[%d] * sy[0]); acc2.add(sm_w2[%d] * sx[1], sm_w2[%d] * sy[1]); }\n",
+                     op.p, op.ra == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW", i, i, i, i, i);
+        } else {
+            const int sb = op.mergeB >= 0 ? O.op[op.mergeB].p : 0;
+            char wl[32], wl2[32];
+            if (sb > 0) {
+                snprintf(wl, sizeof(wl), "sm_w[%d]", op.mergeB);
+                snprintf(wl2, sizeof(wl2), "sm_w2[%d]", op.mergeB);
+            } else {
+                snprintf(wl, sizeof(wl), "(R)0");
+                snprintf(wl2, sizeof(wl2), "(R)0");
+            }
+            snprintf(line, sizeof(line),
+                     "    { const V *sr[2] = {cin, cin2}; R sx[2] = {0, 0}, sy[2] = {0, 0}, lx[2] = {0, 0}, ly[2] = {0, 0};\n"
+                     "      plane_role_n<R, %d, %d, %s, %d, 2>(ctx, el, O, O.op[%d], tab, sr, sx, sy, lx, ly);\n"
+                     "      acc.add(sm_w[%d] * sx[0] + %s * lx[0], sm_w[%d] * sy[0] + %s * ly[0]);\n"
+                     "      acc2.add(sm_w2[%d] * sx[1] + %s * lx[1], sm_w2[%d] * sy[1] + %s * ly[1]); }\n",
+                     op.p, op.q, op.rb == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW", sb, i, i, wl, i, wl, i, wl2, i, wl2);
+        }
+        b += line;
+    }
+    return b;
+}
+
+static std::string jit_source(bool f32, const std::string &body, const std::string &body2, const std::string &body3)
 {
     std::string s;
     s += "#include \"hx_stencil.cuh\"\n";
@@ -142,6 +187,12 @@ static std::string jit_source(bool f32, const std::string &body, const std::stri
          "                                         Acc<R> &acc2, const R *sm_w, const R *sm_w2, const V *cin, const R *tab)\n{\n"
          "    const OpSet &O = args.ops;\n";
     s += body2;
+    s += "}\n";
+    s += "__device__ __forceinline__ void ops_pair(const ApplyArgs &args, const Ctx &ctx, const Elem &el, Acc<R> &acc,\n"
+         "                                         Acc<R> &acc2, const R *sm_w, const R *sm_w2, const V *cin,\n"
+         "                                         const V *cin2, const R *tab)\n{\n"
+         "    const OpSet &O = args.ops;\n";
+    s += body3;
     s += "}\n}  // namespace hx\n";
     // 4 blocks of 256 per SM fit the FP32 kernels in 64 registers without spills (more warps to hide
     // the load latency); the FP64 kernels would spill there and keep 3 blocks (80 registers)
@@ -158,8 +209,17 @@ static std::string jit_source(bool f32, const std::string &body, const std::stri
     s += "hx_apply_specialised_dual(const __grid_constant__ hx::ApplyArgs args)\n{\n"
          "    hx::apply_elements_dual<hx::R>(args, [&](const hx::Ctx &ctx, const hx::Elem &el, hx::Acc<hx::R> &acc,\n"
          "                                             hx::Acc<hx::R> &acc2, const hx::R *sm_w, const hx::R *sm_w2,\n"
-         "                                             const hx::V *cin, const hx::R *tab) {\n"
+         "                                             const hx::V *cin, const hx::V *, const hx::R *tab) {\n"
          "        hx::ops_dual(args, ctx, el, acc, acc2, sm_w, sm_w2, cin, tab);\n"
+         "    });\n}\n";
+    // two inputs at two times (the Magnus method's A_2 (A_1 v) and A_1 (A_2 v))
+    s += f32 ? "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 4)\n"
+             : "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 3)\n";
+    s += "hx_apply_specialised_pair(const __grid_constant__ hx::ApplyArgs args)\n{\n"
+         "    hx::apply_elements_dual<hx::R>(args, [&](const hx::Ctx &ctx, const hx::Elem &el, hx::Acc<hx::R> &acc,\n"
+         "                                             hx::Acc<hx::R> &acc2, const hx::R *sm_w, const hx::R *sm_w2,\n"
+         "                                             const hx::V *cin, const hx::V *cin2, const hx::R *tab) {\n"
+         "        hx::ops_pair(args, ctx, el, acc, acc2, sm_w, sm_w2, cin, cin2, tab);\n"
          "    });\n}\n";
     if (f32) {   // the same product that also computes the Lanczos projections (ApplyFuse)
         s += "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 4)\n"
@@ -216,10 +276,11 @@ static bool compile_and_load(const std::string &src, int dev, JitKernel *out, st
         reason = "loading the compiled kernel failed";
         return false;
     }
-    CUfunction fn_dots = nullptr, fn_dual = nullptr;
+    CUfunction fn_dots = nullptr, fn_dual = nullptr, fn_pair = nullptr;
     if ((src.find("hx_apply_specialised_dots") != std::string::npos &&
          drv.moduleGetFunction(&fn_dots, mod, "hx_apply_specialised_dots") != CUDA_SUCCESS) ||
-        drv.moduleGetFunction(&fn_dual, mod, "hx_apply_specialised_dual") != CUDA_SUCCESS) {
+        drv.moduleGetFunction(&fn_dual, mod, "hx_apply_specialised_dual") != CUDA_SUCCESS ||
+        drv.moduleGetFunction(&fn_pair, mod, "hx_apply_specialised_pair") != CUDA_SUCCESS) {
         reason = "loading the compiled kernel failed";
         return false;
     }
@@ -231,9 +292,11 @@ static bool compile_and_load(const std::string &src, int dev, JitKernel *out, st
     out->fn = fn;
     out->fn_dots = fn_dots;
     out->fn_dual = fn_dual;
+    out->fn_pair = fn_pair;
     out->per_sm = occ(fn);
     out->per_sm_dots = occ(fn_dots);
     out->per_sm_dual = occ(fn_dual);
+    out->per_sm_pair = occ(fn_pair);
     return true;
 }
 
@@ -265,7 +328,8 @@ void jit_prepare(Problem *p)
     auto it = g_jit_cache.find(key);
     if (it == g_jit_cache.end()) {
         JitKernel k;
-        if (!compile_and_load(jit_source(f32, body, jit_body(p->ops, true)), p->device, &k, reason)) return;
+        if (!compile_and_load(jit_source(f32, body, jit_body(p->ops, true), jit_body_pair(p->ops)), p->device, &k, reason))
+            return;
         it = g_jit_cache.emplace(key, k).first;
     }
     p->jit = &it->second;
@@ -277,13 +341,13 @@ int jit_launch(const Problem *p, const void *args, int blocks, cudaStream_t st)
 {
     const JitKernel *k = (const JitKernel *)p->jit;
     const ApplyArgs *a = (const ApplyArgs *)args;
-    const bool dots = a->dvec != nullptr, dual = a->cout2 != nullptr;
+    const bool dots = a->dvec != nullptr, dual = a->cout2 != nullptr, pair = dual && a->cin2 != nullptr;
     if ((dots && !k->fn_dots) || (dots && dual)) {
         set_error("the specialised kernel has no fused projections here (complex64 single products only)");
         return HX_EUNSUPPORTED;
     }
-    CUfunction fn = dual ? k->fn_dual : dots ? k->fn_dots : k->fn;
-    const int per_sm = dual ? k->per_sm_dual : dots ? k->per_sm_dots : k->per_sm;
+    CUfunction fn = pair ? k->fn_pair : dual ? k->fn_dual : dots ? k->fn_dots : k->fn;
+    const int per_sm = pair ? k->per_sm_pair : dual ? k->per_sm_dual : dots ? k->per_sm_dots : k->per_sm;
     // apply_grid(p) blocks at most: the size of the partial-sum buffers
     int grid = std::min(p->num_sms * per_sm, apply_grid(p));
     if (grid > blocks) grid = blocks > 0 ? blocks : 1;

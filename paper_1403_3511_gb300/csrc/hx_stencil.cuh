@@ -32,9 +32,10 @@ struct ApplyArgs : ApplyArgsBase {
     double *dh;                // h (re, im per vector)
     double *dpartials;         // gridDim.x x 2 (dk + 1)
     unsigned *dcounter;        // zero; reset by the last block
-    // a second product of the same input at another time, A(*t_ptr + t_shift2) cin into cout2
-    // (kernels compiled per potential only; cout2 == nullptr: none)
+    // a second product at another time, A(*t_ptr + t_shift2) cin2 into cout2, cin2 == nullptr
+    // meaning cin (kernels compiled per potential only; cout2 == nullptr: none)
     void *cout2;
+    const void *cin2;
     double t_shift2;
 };
 
@@ -187,10 +188,13 @@ __device__ __forceinline__ Row4<double> load_row4(const double *p)
 // degrees <= 3; at degree 8 on short fibres most points lie outside K and the loads they would
 // waste cost more than the overlap gains, so those operators keep the branching generic loop.
 
-// Line operator P(X_a), P of pure parity and degree P (offsets -P, -P+2, ..., P), axis role RA.
-template <typename R, int P, int RA>
-__device__ __forceinline__ void line_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
-                                          const typename Vec2<R>::T *src, R &sx, R &sy)
+// Line operator P(X_a), P of pure parity and degree P (offsets -P, -P+2, ..., P), axis role RA,
+// applied to NSRC inputs at once (the addresses and weights are shared): sx[s], sy[s] get the sum
+// for srcs[s].
+template <typename R, int P, int RA, int NSRC>
+__device__ __forceinline__ void line_role_n(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
+                                            const typename Vec2<R>::T *const (&srcs)[NSRC], R (&sx)[NSRC],
+                                            R (&sy)[NSRC])
 {
     using V = typename Vec2<R>::T;
     const DevSet &S = *c.S;
@@ -209,16 +213,32 @@ __device__ __forceinline__ void line_role(const Ctx &c, const Elem &el, const Op
         else a = s == 0 ? el.e : c.row(el, O.didx[op.dbase + s + P]) + el.k2;
         addr[j] = ok ? a : el.e;
     }
-    V v[NP];
+    V v[NSRC][NP];
 #pragma unroll
-    for (int j = 0; j < NP; ++j) v[j] = src[addr[j]];
+    for (int q = 0; q < NSRC; ++q)
+#pragma unroll
+        for (int j = 0; j < NP; ++j) v[q][j] = srcs[q][addr[j]];
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         const int s = -P + 2 * j;
         const R w = (ka + s >= 0 && s <= top) ? row.v[j] : (R)0;
-        sx += w * v[j].x;
-        sy += w * v[j].y;
+#pragma unroll
+        for (int q = 0; q < NSRC; ++q) {
+            sx[q] += w * v[q][j].x;
+            sy[q] += w * v[q][j].y;
+        }
     }
+}
+
+template <typename R, int P, int RA>
+__device__ __forceinline__ void line_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
+                                          const typename Vec2<R>::T *src, R &sx, R &sy)
+{
+    const typename Vec2<R>::T *srcs[1] = {src};
+    R x[1] = {sx}, y[1] = {sy};
+    line_role_n<R, P, RA, 1>(c, el, O, op, tab, srcs, x, y);
+    sx = x[0];
+    sy = y[0];
 }
 
 // Plane operator wAB P(X_a) Q(X_b) + wBA Q(X_b) P(X_a), pure parities, degrees P, Q; a is a prefix
@@ -229,10 +249,12 @@ __device__ __forceinline__ void line_role(const Ctx &c, const Elem &el, const Op
 // distance to the fibre top.
 // SB > 0: a line operator S(X_b) of degree SB (parity of Q, SB = Q or Q + 2) merged into this op
 // (P is even, so the points s = 0 are footprint points); its sum goes to (lx, ly), which the
-// caller weights with the line operator's own weight.
-template <typename R, int P, int Q, int RB, int SB>
-__device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
-                                           const typename Vec2<R>::T *src, R &sx, R &sy, R &lx, R &ly)
+// caller weights with the line operator's own weight.  NSRC inputs at once (addresses, fibre tops
+// and weights shared): the sums for srcs[q] go to sx[q], sy[q], lx[q], ly[q].
+template <typename R, int P, int Q, int RB, int SB, int NSRC>
+__device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
+                                             const typename Vec2<R>::T *const (&srcs)[NSRC], R (&sx)[NSRC],
+                                             R (&sy)[NSRC], R (&lx)[NSRC], R (&ly)[NSRC])
 {
     using V = typename Vec2<R>::T;
     const DevSet &S = *c.S;
@@ -293,14 +315,18 @@ __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const O
         }
         xaddr[j] = ok ? a : el.e;
     }
-    V v[NS][NS2];
+    V v[NSRC][NS][NS2];
 #pragma unroll
-    for (int i = 0; i < NS; ++i)
+    for (int q = 0; q < NSRC; ++q)
 #pragma unroll
-        for (int j = 0; j < NS2; ++j) v[i][j] = src[addr[i][j]];
-    V xv[NX > 0 ? NX : 1];
+        for (int i = 0; i < NS; ++i)
 #pragma unroll
-    for (int j = 0; j < NX; ++j) xv[j] = src[xaddr[j]];
+            for (int j = 0; j < NS2; ++j) v[q][i][j] = srcs[q][addr[i][j]];
+    V xv[NSRC][NX > 0 ? NX : 1];
+#pragma unroll
+    for (int q = 0; q < NSRC; ++q)
+#pragma unroll
+        for (int j = 0; j < NX; ++j) xv[q][j] = srcs[q][xaddr[j]];
     // weights
     Row4<R> rowS0 = {};
     if (SB > 0) {
@@ -323,12 +349,18 @@ __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const O
             const R cab = inA ? pj * rowQs.v[j] : (R)0;                                   // path via k + s e_a
             const R cba = (kb + s2 >= 0 && s2 <= topB0) ? rowQ0.v[j] * rowPs[j].v[i] : (R)0;   // path via k + s2 e_b
             const R w = ok ? wAB * cab + wBA * cba : (R)0;
-            sx += w * v[i][j].x;
-            sy += w * v[i][j].y;
+#pragma unroll
+            for (int q = 0; q < NSRC; ++q) {
+                sx[q] += w * v[q][i][j].x;
+                sy[q] += w * v[q][i][j].y;
+            }
             if (SB > 0 && s == 0) {                     // k + s2 e_b is also a point of the merged line op
                 const R ws = ok ? rowS0.v[(s2 + SB) / 2] : (R)0;
-                lx += ws * v[i][j].x;
-                ly += ws * v[i][j].y;
+#pragma unroll
+                for (int q = 0; q < NSRC; ++q) {
+                    lx[q] += ws * v[q][i][j].x;
+                    ly[q] += ws * v[q][i][j].y;
+                }
             }
         }
     }
@@ -336,9 +368,25 @@ __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const O
     for (int j = 0; j < NX; ++j) {
         const int s2 = j == 0 ? -SB : SB;
         const R ws = (kb + s2 >= 0 && s2 <= topB0) ? rowS0.v[(s2 + SB) / 2] : (R)0;
-        lx += ws * xv[j].x;
-        ly += ws * xv[j].y;
+#pragma unroll
+        for (int q = 0; q < NSRC; ++q) {
+            lx[q] += ws * xv[q][j].x;
+            ly[q] += ws * xv[q][j].y;
+        }
     }
+}
+
+template <typename R, int P, int Q, int RB, int SB>
+__device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
+                                           const typename Vec2<R>::T *src, R &sx, R &sy, R &lx, R &ly)
+{
+    const typename Vec2<R>::T *srcs[1] = {src};
+    R x[1] = {sx}, y[1] = {sy}, u[1] = {lx}, w[1] = {ly};
+    plane_role_n<R, P, Q, RB, SB, 1>(c, el, O, op, tab, srcs, x, y, u, w);
+    sx = x[0];
+    sy = y[0];
+    lx = u[0];
+    ly = w[0];
 }
 
 
@@ -497,11 +545,11 @@ __device__ __forceinline__ void apply_elements(const ApplyArgs &args, Body body)
     }
 }
 
-// Two products of the same input in one pass: y = A(*t_ptr + t_shift) c into cout and
-// y2 = A(*t_ptr + t_shift2) c into cout2 (the two time nodes of the 2-stage Magnus method).  The
-// stencil sums do not depend on the time, only the operator weights do, so every gather and all
-// index work are shared; body(ctx, el, acc, acc2, sm_w, sm_w2, cin, tab) adds each operator's sum
-// with its weight at either time.
+// Two products in one pass: y = A(*t_ptr + t_shift) c into cout and y2 = A(*t_ptr + t_shift2) c2
+// into cout2, c2 = c unless cin2 is given (the products of the 2-stage Magnus method).  The stencil
+// coefficients do not depend on the time, only the operator weights do, so all index work and the
+// weights are shared, and for c2 = c every gather too; body(ctx, el, acc, acc2, sm_w, sm_w2, cin,
+// cin2, tab) adds each operator's sum with its weight at either time.
 template <typename R, typename Body>
 __device__ __forceinline__ void apply_elements_dual(const ApplyArgs &args, Body body)
 {
@@ -519,17 +567,18 @@ __device__ __forceinline__ void apply_elements_dual(const ApplyArgs &args, Body 
     ctx.S = &S;
     ctx.nrow = args.nrow;
     const V *cin = (const V *)args.cin;
+    const V *cin2 = args.cin2 ? (const V *)args.cin2 : cin;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.size; e += gridDim.x * blockDim.x) {
         const int4 er = __ldg(S.elem + e);
         const Elem el = make_elem(args, e, er);
         Acc<R> acc, acc2;
         if (!args.skip_diag) {
-            const V ce = cin[e];
+            const V ce = cin[e], ce2 = cin2[e];
             const R dj = (R)er.z + (R)0.5 * (R)S.N;
             acc.add(dj * ce.x, dj * ce.y);
-            acc2.add(dj * ce.x, dj * ce.y);
+            acc2.add(dj * ce2.x, dj * ce2.y);
         }
-        body(ctx, el, acc, acc2, (const R *)sm_w, (const R *)sm_w2, cin, (const R *)args.tab);
+        body(ctx, el, acc, acc2, (const R *)sm_w, (const R *)sm_w2, cin, cin2, (const R *)args.tab);
         V y = acc.get(), y2 = acc2.get();
         y.x *= oscale;
         y.y *= oscale;

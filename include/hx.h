@@ -220,8 +220,8 @@ HX_API int hx_apply_specialised(const hx_problem *p);
  * orthogonalisation passes (one for the last vector), the eigensolver and the recombination),
  * or m (per_apply + 2) + 2 for HX_C64 when the product kernel is specialised
  * (hx_apply_specialised) and m <= 8 (that kernel then also computes the projection), and
- * m (4 per_apply + 4) + 2 for HX_SCHEME_MAGNUS4, m (2 per_apply + 4) + 2 with a specialised product kernel
- * (one launch gives A_1 v and A_2 v, another A_2 A_1 v and A_1 A_2 v) (four products and their combination).  Needs a potential;
+ * m (4 per_apply + 4) + 2 for HX_SCHEME_MAGNUS4, m (2 per_apply + 3) + 2 with a specialised product kernel
+ * (one launch gives A_1 v and A_2 v, another A_2 A_1 v and A_1 A_2 v combined into H v) (four products and their combination).  Needs a potential;
  * either pointer may be NULL.  The paper has no counterpart: this reports how the library maps
  * its work onto kernels. */
 HX_API int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step);

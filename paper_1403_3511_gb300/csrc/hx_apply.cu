@@ -203,7 +203,8 @@ int apply_grid(const Problem *p)
 template <typename R, int MD>
 static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *cin, void *cout,
                           const double *t_ptr, double t_shift, const ApplyFuse *fuse, cudaStream_t st,
-                          void *cout2 = nullptr, double t_shift2 = 0.0, const void *cin2 = nullptr)
+                          void *cout2 = nullptr, double t_shift2 = 0.0, const void *cin2 = nullptr,
+                          double mag_g = 0.0)
 {
     ApplyArgs a;
     memset(&a, 0, sizeof(a));
@@ -239,6 +240,7 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
     a.cout2 = cout2;
     a.cin2 = cin2;
     a.t_shift2 = t_shift2;
+    a.mag_g = mag_g;
     const int blocks = (p->set->d.size + kApplyThreads - 1) / kApplyThreads;
     if (!stage1 && p->jit && !g_batch_capture) return jit_launch(p, &a, blocks, st);   // the potential's specialised kernel
     if (cout2) {
@@ -284,15 +286,18 @@ int launch_apply_dual(Problem *p, const void *cin, void *cout, void *cout2, cons
 }
 
 int launch_apply_pair(Problem *p, const void *cin, void *cout, double t_shift, const void *cin2, void *cout2,
-                      double t_shift2, const double *t_ptr, cudaStream_t st)
+                      double t_shift2, const double *t_ptr, cudaStream_t st, void *mag_out, double mag_g)
 {
     if (!apply_dual(p)) {
         int rc = launch_apply(p, cin, cout, t_ptr, t_shift, nullptr, st);
         return rc ? rc : launch_apply(p, cin2, cout2, t_ptr, t_shift2, nullptr, st);
     }
+    // with mag_out: the kernel writes the Magnus combination there and neither product
+    void *o1 = mag_out ? mag_out : cout;
+    const double g = mag_out ? mag_g : 0.0;
     return p->cfg.dtype == HX_C64
-               ? launch_apply_t<float, 3>(p, p->ops, 0, cin, cout, t_ptr, t_shift, nullptr, st, cout2, t_shift2, cin2)
-               : launch_apply_t<double, 3>(p, p->ops, 0, cin, cout, t_ptr, t_shift, nullptr, st, cout2, t_shift2, cin2);
+               ? launch_apply_t<float, 3>(p, p->ops, 0, cin, o1, t_ptr, t_shift, nullptr, st, cout2, t_shift2, cin2, g)
+               : launch_apply_t<double, 3>(p, p->ops, 0, cin, o1, t_ptr, t_shift, nullptr, st, cout2, t_shift2, cin2, g);
 }
 
 bool apply_fuses_dots(const Problem *p)

@@ -986,7 +986,7 @@ int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step)
     const int dots = p->cfg.m <= kMaxFusedDots && apply_fuses_dots(p) ? 0 : 1;
     // 2-stage Magnus: A_1 v and A_2 v in one launch, A_2 A_1 v and A_1 A_2 v in another, with the
     // specialised kernel
-    const int mag = apply_dual(p) ? 2 * a + 4 : 4 * a + 4;
+    const int mag = apply_dual(p) ? 2 * a + 3 : 4 * a + 4;   // the second launch also forms H v
     if (per_step) *per_step = p->cfg.scheme == HX_SCHEME_MAGNUS4 ? p->cfg.m * mag + 2 : p->cfg.m * (a + 2 + dots) + 2;
     return HX_OK;
 }

@@ -105,9 +105,12 @@ bool apply_dual(const Problem *p);        // one launch can give the products at
 // cout = A(t + t_shift) cin and cout2 = A(t + t_shift2) cin, in one launch when apply_dual(p)
 int launch_apply_dual(Problem *p, const void *cin, void *cout, void *cout2, const double *t_ptr, double t_shift,
                       double t_shift2, const ApplyFuse *fuse, cudaStream_t st);
-// cout = A(t + t_shift) cin and cout2 = A(t + t_shift2) cin2, in one launch when apply_dual(p)
+// cout = A(t + t_shift) cin and cout2 = A(t + t_shift2) cin2, in one launch when apply_dual(p);
+// then, with mag_out, that launch writes only (cin + cin2)/2 - i mag_g (cout - cout2) to mag_out
+// (the 2-stage Magnus combination) and apply_dual(p) tells the caller it did
 int launch_apply_pair(Problem *p, const void *cin, void *cout, double t_shift, const void *cin2, void *cout2,
-                      double t_shift2, const double *t_ptr, cudaStream_t st);
+                      double t_shift2, const double *t_ptr, cudaStream_t st, void *mag_out = nullptr,
+                      double mag_g = 0.0);
 
 // hx_apply_project after the argument checks (hx_krylov.cu)
 int apply_project_dispatch(Problem *p, const void *c, void *y, const void *basis, size_t ld, int k, double *h);

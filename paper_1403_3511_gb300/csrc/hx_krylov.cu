@@ -1267,11 +1267,13 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
         if (p->cfg.scheme == HX_SCHEME_MAGNUS4) {   // Eq. (2stageMagnus): nodes 1/2 -+ sqrt(3)/6
             const double c1 = 0.5 - sqrt(3.0) / 6.0, c2 = 0.5 + sqrt(3.0) / 6.0;
             V *a1v = (V *)w->mag, *a2v = a1v + ld, *a2a1v = a2v + ld, *a1a2v = a2a1v + ld;
+            const double g = sqrt(3.0) * dt / 12.0;
+            V *hv = Vb + (size_t)(k + 1) * ld;
             if ((rc = launch_apply_dual(p, Vb + (size_t)k * ld, a1v, a2v, &sc->t, c1 * dt, c2 * dt, &f, st)) ||
-                (rc = launch_apply_pair(p, a1v, a2a1v, c2 * dt, a2v, a1a2v, c1 * dt, &sc->t, st)))
+                (rc = launch_apply_pair(p, a1v, a2a1v, c2 * dt, a2v, a1a2v, c1 * dt, &sc->t, st, hv, g)))
                 return rc;
-            magnus_combine_kernel<V><<<G, T, 0, st>>>(Vb + (size_t)(k + 1) * ld, a1v, a2v, a2a1v, a1a2v, n,
-                                                      sqrt(3.0) * dt / 12.0);
+            if (!apply_dual(p))   // the specialised kernel wrote the combination itself
+                magnus_combine_kernel<V><<<G, T, 0, st>>>(hv, a1v, a2v, a2a1v, a1a2v, n, g);
         } else {
             if (fused) {     // h_i = s_i <v_i, w> from the product kernel's own stores
                 f.dvec = Vb;

@@ -37,6 +37,9 @@ struct ApplyArgs : ApplyArgsBase {
     void *cout2;
     const void *cin2;
     double t_shift2;
+    // with cin2: instead of the two products y, y2 write the 2-stage Magnus combination
+    // (cin + cin2)/2 - i mag_g (y - y2) to cout (0: off)
+    double mag_g;
 };
 
 // Block and grid stages of the reductions: wsum[w][j] (shared, filled by the caller, followed by a
@@ -584,8 +587,17 @@ __device__ __forceinline__ void apply_elements_dual(const ApplyArgs &args, Body 
         y.y *= oscale;
         y2.x *= oscale;
         y2.y *= oscale;
-        ((V *)args.cout)[e] = y;
-        ((V *)args.cout2)[e] = y2;
+        if (args.mag_g != 0.0) {
+            const V a = cin[e], b = cin2[e];
+            const R g = (R)args.mag_g, half = (R)0.5;
+            V r;
+            r.x = half * (a.x + b.x) + g * (y.y - y2.y);        // -i g z = g (z.y, -z.x)
+            r.y = half * (a.y + b.y) - g * (y.x - y2.x);
+            ((V *)args.cout)[e] = r;
+        } else {
+            ((V *)args.cout)[e] = y;
+            ((V *)args.cout2)[e] = y2;
+        }
     }
 }
 

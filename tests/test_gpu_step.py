@@ -233,7 +233,7 @@ def test_magnus4_time_integration_experiment(hx, oracle):
 def test_step_launch_counts(hx):
     # expMPR: the specialised complex64 product kernel computes the projections itself when m <= 8
     per = {0: lambda m, a, spec, c64: m * (a + (2 if spec and c64 and m <= 8 else 3)) + 2,
-           1: lambda m, a, spec, c64: m * ((2 if spec else 4) * a + 4) + 2}
+           1: lambda m, a, spec, c64: m * (2 * a + 3 if spec else 4 * a + 4) + 2}
     for scheme in (0, 1):
         for name in ("hh2_b32", "cos10_b1024"):
             spec = inputs.workload(name) if name == "hh2_b32" else dict(N=3, B=40, L=inputs.half_width(40),

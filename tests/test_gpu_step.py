@@ -312,3 +312,21 @@ def test_large_step_exponential_matches_oracle(hx, oracle, m, h):
     assert info["m_used"] == m
     assert h * (max(info["alpha"]) - min(info["alpha"])) / 2 > 96
     assert rel(got, ref) <= 1e-12, rel(got, ref)
+
+
+@pytest.mark.parametrize("N,B", [(1, 1), (3, 1), (1, 50), (2, 3)])
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
+def test_tiny_problems_step(hx, oracle, N, B, dtype, tol):
+    """Index sets of 1 to 50 elements (fewer than a warp or a pair, odd lengths): the product with its
+    projections, the Gram-Schmidt passes, the exponential and the recombination at their smallest
+    sizes, with the Lanczos process stopping early when the Krylov space is exhausted."""
+    comps = [{"coef": 0.3, "powers": {0: 3}}, {"coef": -0.2, "powers": {0: 1}}]
+    if N > 1:
+        comps.append({"coef": 0.1, "powers": {0: 2, N - 1: 1}})
+    spec = dict(N=N, B=B, L=inputs.half_width(max(B, 2)), potential=comps)
+    S = oracle.IndexSet.hyperbolic(N, B)
+    c0 = inputs.initial_vector({"init": {"kind": "gaussian", "seed": 9}}, S.k)
+    ref, _ = oracle.expmpr_propagate(S, spec, c0, 0.05, 3, 7)
+    got, info, _ = run_gpu(hx, spec, c0, hx.HX_C128 if dtype == "c128" else hx.HX_C64, 0.05, 3)
+    assert info["m_used"] == min(7, S.size) or info["breakdown"]
+    assert rel(got, ref) <= tol, rel(got, ref)

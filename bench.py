@@ -115,11 +115,11 @@ def kernel_source_hash(root: str = None) -> str:
     return h.hexdigest()
 
 
-def profiled_traffic(workload: str, dtype: str, kind: str = "apply_kernel"):
-    """DRAM bytes per launch from the committed ncu summary of this workload (kind "apply_kernel":
-    the product; "apply_project_kernel": the product with the Lanczos projections, averaged over
-    the projection counts of one step), or None when there is none or the kernel sources have
-    changed since it was captured."""
+def profiled_value(workload: str, dtype: str, kind: str, key: str):
+    """An integer figure ("key: N") from the committed ncu summary of this workload and kernel
+    (kind "apply_kernel": the product; "apply_project_kernel": the product with the Lanczos
+    projections, averaged over the projection counts of one step), or None when there is none or
+    the kernel sources have changed since it was captured."""
     import re
     path = os.path.join(ROOT, "profiles", f"{kind}_{workload}_{dtype}.md")
     try:
@@ -127,15 +127,31 @@ def profiled_traffic(workload: str, dtype: str, kind: str = "apply_kernel"):
     except OSError:
         return None
     src = re.search(r"kernel sources sha256 ([0-9a-f]{64})", text)
-    tr = re.search(r"traffic_bytes_per_launch: (\d+)", text)
-    if not src or not tr:
+    val = re.search(re.escape(key) + r": (\d+)", text)
+    if not src or not val:
         return None
     try:
         if kernel_source_hash() != src.group(1):
             return None
     except OSError:
         return None
-    return int(tr.group(1))
+    return int(val.group(1))
+
+
+def profiled_traffic(workload: str, dtype: str, kind: str = "apply_kernel"):
+    """DRAM bytes (read + write) per launch from the committed ncu summary (see profiled_value)."""
+    return profiled_value(workload, dtype, kind, "traffic_bytes_per_launch")
+
+
+def issue_roofline(warp_instructions: int, ms: float, sm_mhz: float, num_sms: int) -> dict:
+    """The product kernels are bound by instruction issue (about 40 instructions per footprint
+    point, DRAM below 25 %): warp instructions per launch (ncu smsp__inst_executed.sum of the same
+    kernel) over the launch time, against one warp instruction per cycle on each of the 4
+    schedulers of every SM at the sampled SM clock."""
+    peak = num_sms * 4 * sm_mhz * 1e6
+    achieved = warp_instructions / (ms * 1e-3)
+    return {"unit": "warp instructions/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+            "warp_instructions_per_launch": warp_instructions, "source": "committed ncu summary (smsp__inst_executed.sum)"}
 
 
 def max_over_ranks(vals, world: int, device):
@@ -405,6 +421,10 @@ def main():
     product = {"kernel": "hx_apply_specialised" if hx.hx_apply_specialised(P.p) else "apply_kernel",
                "ms_per_launch": ms_apply, "achieved": alg_bytes / (ms_apply * 1e-3) / 1e9,
                "traffic": profiled_traffic(spec["name"], args.dtype)}
+    winst = profiled_value(spec["name"], args.dtype, "apply_kernel", "warp_instructions_per_launch")
+    if winst and clk.get("sm_mhz"):
+        product["issue"] = issue_roofline(winst, ms_apply, clk["sm_mhz"],
+                                          torch.cuda.get_device_properties(local).multi_processor_count)
     if fused:
         alg_proj = (16 + 8 * (m - 1) / 2) * n            # mean over k = 0 .. m-1
         achieved = alg_proj / (ms_proj * 1e-3) / 1e9
@@ -412,6 +432,10 @@ def main():
                 "traffic": profiled_traffic(spec["name"], args.dtype, "apply_project_kernel"),
                 "kernel": "hx_apply_specialised_dots", "ms_per_launch": ms_proj,
                 "bytes_per_launch": alg_proj, "peak_source": peak_source, "product_alone": product}
+        winst = profiled_value(spec["name"], args.dtype, "apply_project_kernel", "warp_instructions_per_launch")
+        if winst and clk.get("sm_mhz"):
+            roof["issue"] = issue_roofline(winst, ms_proj, clk["sm_mhz"],
+                                           torch.cuda.get_device_properties(local).multi_processor_count)
     else:
         achieved = product["achieved"]
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

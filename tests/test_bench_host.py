@@ -83,3 +83,26 @@ def test_profiled_traffic_tracks_kernel_source(tmp_path, monkeypatch):
     assert bench.profiled_traffic("w", "c128") is None
     (src / "hx_stencil.cuh").write_text("changed\n")
     assert bench.profiled_traffic("w", "c64") is None
+
+
+def test_issue_roofline_and_profiled_values(tmp_path, monkeypatch):
+    """The product's issue roofline: warp instructions from the committed summary (same source
+    check as the traffic) over the launch time, against 4 instructions per SM and cycle."""
+    import bench
+    src = tmp_path / "paper_1403_3511_gb300" / "csrc"
+    src.mkdir(parents=True)
+    for name in bench.KERNEL_SOURCES:
+        (src / name).write_text(name + " v1\n")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    h = bench.kernel_source_hash(str(tmp_path))
+    (prof / "apply_kernel_w_c64.md").write_text(
+        f"kernel sources sha256 {h}\ntraffic_bytes_per_launch: 1234\nwarp_instructions_per_launch: 608000000\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    w = bench.profiled_value("w", "c64", "apply_kernel", "warp_instructions_per_launch")
+    assert w == 608000000
+    r = bench.issue_roofline(w, 1.0, 2000.0, 152)
+    assert r["peak"] == 152 * 4 * 2000e6
+    assert abs(r["achieved"] - 6.08e11) < 1.0 and abs(r["frac"] - 6.08e11 / r["peak"]) < 1e-12
+    (src / "hx_jit.cu").write_text("changed\n")
+    assert bench.profiled_value("w", "c64", "apply_kernel", "warp_instructions_per_launch") is None

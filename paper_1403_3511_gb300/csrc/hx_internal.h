@@ -13,7 +13,8 @@
 namespace hx {
 
 static_assert(kMaxDeg == HX_MAX_DEG, "hx_types.h and hx.h disagree on the maximal degree");
-static_assert(MOD_COS == HX_MOD_COS && MOD_SIN2 == HX_MOD_SIN2 && MOD_PWCONST == HX_MOD_PWCONST,
+static_assert((int)MOD_COS == (int)HX_MOD_COS && (int)MOD_SIN2 == (int)HX_MOD_SIN2 &&
+                  (int)MOD_PWCONST == (int)HX_MOD_PWCONST,
               "hx_types.h and hx.h disagree on the modulation kinds");
 
 void set_error(const char *fmt, ...);

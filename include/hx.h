@@ -163,7 +163,7 @@ HX_API int hx_set_time(hx_problem *p, double t);
 /* c_out = A(t) c_in at the problem time t: D_K c_in + W^pol(X_K, t) c_in with the
  * configured factor order.  Device pointers of |K| elements of the problem dtype, aligned to
  * the element size (8 bytes for HX_C64, 16 for HX_C128; HX_EINVAL otherwise);
- * c_in and c_out must not overlap.  Asynchronous on the problem stream. */
+ * c_in and c_out must not overlap (HX_EINVAL).  Asynchronous on the problem stream. */
 HX_API int hx_apply(hx_problem *p, const void *c_in, void *c_out);
 /* The product of one Lanczos step with its first Gram-Schmidt projections (Sec. 2.2):
  * y = A(t) c and h_i = <basis_i, y> = sum_j conj(basis_i[j]) y[j] for i = 0..k.
@@ -175,8 +175,8 @@ HX_API int hx_apply(hx_problem *p, const void *c_in, void *c_out);
  * computes both (the projections from the stored y, compensated FP32 partial sums); otherwise the
  * product is followed by a projection kernel (FP64 or compensated FP32 sums).  Asynchronous on
  * the problem stream; the first call allocates a small workspace and synchronises.
- * Errors: HX_EINVAL (NULL pointer, k out of range, ld < |K|, c == y, misaligned pointer, no
- * potential). */
+ * Errors: HX_EINVAL (NULL pointer, k out of range, ld < |K|, y overlapping c or the basis,
+ * misaligned pointer, no potential). */
 HX_API int hx_apply_project(hx_problem *p, const void *c, void *y, const void *basis, size_t ld, int k,
                             double *h);
 /* Same with host buffers: copies in, applies, copies out, synchronises. */

@@ -814,11 +814,23 @@ static bool elem_aligned(const Problem *p, const void *x)
     return (uintptr_t)x % (p->cfg.dtype == HX_C64 ? 8 : 16) == 0;
 }
 
+// Whether the byte ranges [a, a + na) and [b, b + nb) share a byte.
+static bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return na > 0 && nb > 0 && x < y + nb && y < x + na;
+}
+
+static size_t vec_bytes(const Problem *p) { return (size_t)p->set->h.size * (p->cfg.dtype == HX_C64 ? 8 : 16); }
+
 int hx_apply(hx_problem *p, const void *c_in, void *c_out)
 {
     if (!p || !c_in || !c_out) { set_error("hx_apply: NULL argument"); return HX_EINVAL; }
     if (!p->have_pot) { set_error("hx_apply: call hx_potential_set first"); return HX_EINVAL; }
-    if (c_in == c_out) { set_error("hx_apply: c_in and c_out must not overlap"); return HX_EINVAL; }
+    if (c_in == c_out || ranges_overlap(c_in, vec_bytes(p), c_out, vec_bytes(p))) {
+        set_error("hx_apply: c_in and c_out must not overlap");
+        return HX_EINVAL;
+    }
     if (!elem_aligned(p, c_in) || !elem_aligned(p, c_out)) {
         set_error("hx_apply: vectors must be aligned to the element size");
         return HX_EINVAL;
@@ -833,6 +845,14 @@ int hx_apply_project(hx_problem *p, const void *c, void *y, const void *basis, s
     if (c == y) { set_error("hx_apply_project: c and y must not overlap"); return HX_EINVAL; }
     if (k < 0 || k >= kMaxFusedDots) { set_error("hx_apply_project: k must be in [0, %d)", kMaxFusedDots); return HX_EINVAL; }
     if (ld < (size_t)p->set->h.size) { set_error("hx_apply_project: ld below the vector length"); return HX_EINVAL; }
+    {
+        const size_t vb = vec_bytes(p), es = p->cfg.dtype == HX_C64 ? 8 : 16;
+        const size_t bb = (size_t)k * ld * es + vb;   // vectors 0..k of the basis
+        if (ranges_overlap(c, vb, y, vb) || ranges_overlap(y, vb, basis, bb)) {
+            set_error("hx_apply_project: y must overlap neither c nor the basis");
+            return HX_EINVAL;
+        }
+    }
     if (!elem_aligned(p, c) || !elem_aligned(p, y) || !elem_aligned(p, basis) || (uintptr_t)h % 8) {
         set_error("hx_apply_project: vectors must be aligned to the element size");
         return HX_EINVAL;

@@ -337,5 +337,14 @@ def test_apply_project_argument_errors(hx):
                                        ctypes.c_void_p(basis.data_ptr() + 4), P.size, 0,
                                        ctypes.c_void_p(h.data_ptr())) == hx.HX_EINVAL
         assert hx.lib.hx_step(P.p, ctypes.c_void_p(h.data_ptr() + 8), 0.01, 1) == hx.HX_EINVAL
+        # overlapping vectors are refused on the host: one shared element is enough
+        buf = torch.zeros(2 * P.size - 1, dtype=torch.complex64, device="cuda")
+        with pytest.raises(hx.HxError):
+            hx.hx_apply(P.p, buf[: P.size], buf[P.size - 1:])
+        with pytest.raises(hx.HxError):          # y is a basis vector the projections read
+            hx.hx_apply_project(P.p, x, basis[1], basis, 1, h)
+        hx.hx_apply_project(P.p, basis[1], y, basis, 1, h)   # c may be a basis vector
+        hx.hx_apply(P.p, buf[: P.size], torch.empty_like(x))
+        torch.cuda.synchronize()
     finally:
         P.close()

@@ -220,9 +220,10 @@ HX_API int hx_apply_specialised(const hx_problem *p);
  * orthogonalisation passes (one for the last vector), the eigensolver and the recombination),
  * or m (per_apply + 2) + 2 for HX_C64 when the product kernel is specialised
  * (hx_apply_specialised) and m <= 8 (that kernel then also computes the projection), and
- * m (4 per_apply + 4) + 2 for HX_SCHEME_MAGNUS4, m (2 per_apply + 3) + 2 with a specialised product kernel
- * (one launch gives A_1 v and A_2 v, another A_2 A_1 v and A_1 A_2 v combined into H v) (four products and their combination).  Needs a potential;
- * either pointer may be NULL.  The paper has no counterpart: this reports how the library maps
+ * m (4 per_apply + 4) + 2 for HX_SCHEME_MAGNUS4 (per Lanczos vector four products and their
+ * combination into H v), m (2 per_apply + 3) + 2 when the product kernel is specialised (one launch
+ * gives A_1 v and A_2 v, another A_2 A_1 v and A_1 A_2 v and combines them into H v).  Needs a
+ * potential; either pointer may be NULL.  The paper has no counterpart: this reports how the library maps
  * its work onto kernels. */
 HX_API int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step);
 
@@ -231,10 +232,12 @@ HX_API int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step);
 /* A batch of independent problems of any N, B and potential, stepped together: one CUDA graph per
  * time step holds every problem's step (the same kernels as hx_step) as an independent branch, so
  * the GPU runs the problems concurrently; the graph is replayed nsteps times.  The problems keep
- * their own index sets, potentials, times and Krylov workspaces; they must stay alive and unchanged
- * (no hx_potential_set) while the batch exists.  Work is ordered on the first problem's stream.
- * hx_batch_step: c[i] is the DEVICE complex128 state of problem i (in place, 16-byte aligned); the graph is built on
- * the first call and rebuilt when dt or a state pointer changes.  Asynchronous. */
+ * their own index sets, potentials, times and Krylov workspaces; they must stay alive while the
+ * batch exists.  Work is ordered on the first problem's stream.  hx_batch_create: n >= 1 distinct
+ * problems, each with a potential (HX_EINVAL otherwise).
+ * hx_batch_step: c[i] is the DEVICE complex128 state of problem i (in place, 16-byte aligned, no two
+ * states overlapping: HX_EINVAL otherwise); the graph is built on the first call and rebuilt when dt
+ * or a state pointer changes or a member's hx_potential_set ran since.  Asynchronous. */
 typedef struct hx_batch hx_batch;
 HX_API int hx_batch_create(hx_problem *const *probs, int n, hx_batch **out);
 HX_API int hx_batch_step(hx_batch *b, void *const *c, double dt, int nsteps);

@@ -974,8 +974,21 @@ int hx_batch_create(hx_problem *const *probs, int n, hx_batch **out)
 int hx_batch_step(hx_batch *b, void *const *c, double dt, int nsteps)
 {
     if (!b || !c || nsteps < 0 || !(dt == dt)) { set_error("hx_batch_step: bad argument"); return HX_EINVAL; }
-    for (size_t i = 0; i < b->probs.size(); ++i)
+    const size_t np = b->probs.size();
+    for (size_t i = 0; i < np; ++i)
         if (!c[i] || (uintptr_t)c[i] % 16) { set_error("hx_batch_step: state %zu is NULL or not 16-byte aligned", i); return HX_EINVAL; }
+    // the members run concurrently: no two may step the same memory
+    std::vector<std::pair<uintptr_t, uintptr_t>> span(np);
+    for (size_t i = 0; i < np; ++i)
+        span[i] = {(uintptr_t)c[i], (uintptr_t)c[i] + (uintptr_t)b->probs[i]->set->h.size * 16};
+    std::vector<size_t> ord(np);
+    for (size_t i = 0; i < np; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return span[x].first < span[y].first; });
+    for (size_t j = 1; j < np; ++j)
+        if (span[ord[j]].first < span[ord[j - 1]].second) {
+            set_error("hx_batch_step: the states of problems %zu and %zu overlap", ord[j - 1], ord[j]);
+            return HX_EINVAL;
+        }
     if (nsteps == 0) return HX_OK;
     return batch_step(b, c, dt, nsteps);
 }

@@ -89,6 +89,21 @@ def test_batch_argument_errors(hx):
         P.set_potential(spec, 0.0)
         with pytest.raises(hx.HxError):
             hx.hx_batch_create([P.p, P.p])          # the same problem twice
+        Q = hx.Problem(2, 32)
+        try:
+            Q.set_potential(spec, 0.0)
+            b = hx.hx_batch_create([P.p, Q.p])
+            try:
+                buf = torch.zeros(2 * P.size, dtype=torch.complex128, device="cuda")
+                with pytest.raises(hx.HxError):     # one state for both members
+                    hx.hx_batch_step(b, [buf[: P.size], buf[: P.size]], 0.01, 1)
+                with pytest.raises(hx.HxError):     # states sharing one element
+                    hx.hx_batch_step(b, [buf[1: P.size + 1], buf[: P.size]], 0.01, 1)
+                hx.hx_batch_step(b, [buf[: P.size], buf[P.size:]], 0.01, 0)
+            finally:
+                hx.hx_batch_destroy(b)
+        finally:
+            Q.close()
     finally:
         P.close()
 

@@ -230,8 +230,18 @@ def hx_apply_project(p, c, y, basis, k: int, h):
                                 ctypes.c_void_p(basis.data_ptr()), basis.stride(0), k, ctypes.c_void_p(h.data_ptr())))
 
 
+def _host_vec(a: np.ndarray, dtypes) -> ctypes.c_void_p:
+    if not (isinstance(a, np.ndarray) and a.dtype in dtypes and a.flags.c_contiguous):
+        raise ValueError(f"expected a contiguous numpy array of {' or '.join(str(np.dtype(d)) for d in dtypes)}")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
 def hx_apply_host(p, c_in: np.ndarray, c_out: np.ndarray):
-    _check(lib.hx_apply_host(p, c_in.ctypes.data_as(ctypes.c_void_p), c_out.ctypes.data_as(ctypes.c_void_p)))
+    """c_in, c_out: |K| elements of the problem dtype (complex128 or complex64)."""
+    if c_in.dtype != c_out.dtype or not c_out.flags.writeable:
+        raise ValueError("c_in and c_out must have the same dtype and c_out must be writeable")
+    _check(lib.hx_apply_host(p, _host_vec(c_in, (np.complex128, np.complex64)),
+                             _host_vec(c_out, (np.complex128, np.complex64))))
 
 
 def hx_step(p, c, dt: float, nsteps: int) -> int:
@@ -239,7 +249,10 @@ def hx_step(p, c, dt: float, nsteps: int) -> int:
 
 
 def hx_step_host(p, c: np.ndarray, dt: float, nsteps: int) -> int:
-    return _check(lib.hx_step_host(p, c.ctypes.data_as(ctypes.c_void_p), dt, nsteps), allow=(HX_EBREAKDOWN,))
+    """c: the complex128 state (|K| elements), stepped in place."""
+    if not c.flags.writeable:
+        raise ValueError("the state must be writeable")
+    return _check(lib.hx_step_host(p, _host_vec(c, (np.complex128,)), dt, nsteps), allow=(HX_EBREAKDOWN,))
 
 
 def hx_step_info(p, m: int = 32) -> dict:

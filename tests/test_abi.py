@@ -78,6 +78,14 @@ def test_argument_errors_without_device(libhx):
     assert "NULL problem" in hx.hx_last_error()
     assert hx.lib.hx_apply_project(None, None, None, None, 0, 0, None) == hx.HX_EINVAL
     assert "NULL argument" in hx.hx_last_error()
+    # host vectors the library would read or write past their end are refused by the binding
+    with pytest.raises(ValueError):
+        hx.hx_step_host(None, np.zeros(4, np.complex64), 0.01, 1)       # the state is complex128
+    with pytest.raises(ValueError):
+        hx.hx_step_host(None, np.zeros(8, np.complex128)[::2], 0.01, 1)  # strided
+    with pytest.raises(ValueError):
+        hx.hx_apply_host(None, np.zeros(4, np.complex128), np.zeros(4, np.complex64))
+    assert hx.lib.hx_step_host(None, None, 0.01, 1) == hx.HX_EINVAL
 
 
 def test_config_layout_matches_header(libhx):

@@ -203,6 +203,25 @@ HX_API int hx_step(hx_problem *p, void *c, double dt, int nsteps);
 /* Same with a host complex128 vector: copies in, steps, copies out, synchronises (the copies run
  * at full speed from page-locked memory). */
 HX_API int hx_step_host(hx_problem *p, void *c_host, double dt, int nsteps);
+/* Time-dependent potentials re-interpolated every step (the time-propagation algorithm of Sec. 2.2,
+ * step (1): the coefficients alpha_r(t) of W^pol(., t) are computed anew for each step at the times
+ * the integrator prescribes).  fn(t, user) returns the potential to use at time t, in the form
+ * hx_potential_set takes; typically terms with HX_MOD_CONST whose Chebyshev coefficients the
+ * caller interpolated at t (hx_cheb_nodes, hx_cheb_coeffs).  The returned potential (and the
+ * arrays it points to) must stay valid until fn is called again or this function returns; the
+ * library copies what it keeps.
+ * Per step: HX_SCHEME_EXPMPR calls fn once, at t + dt/2; HX_SCHEME_MAGNUS4 calls fn at the two
+ * Gauss-Legendre points t + (1/2 -+ sqrt(3)/6) dt, whose potentials must have the same L and
+ * only HX_MOD_CONST terms (the library evaluates the first at the first point and the second at
+ * the second by piecewise-constant modulations over [t, t + dt)).  Then one step as hx_step does
+ * (same kernels; the step graph is captured anew each step since the coefficient tables change).
+ * After the call the problem holds the potential of the last step.  c: DEVICE complex128, as for
+ * hx_step.  Synchronises the problem stream once per step.  Errors: HX_EINVAL (NULL argument, fn
+ * returned NULL, bad potential as for hx_potential_set, Magnus potentials with other
+ * modulations or different L), HX_EUNSUPPORTED (more operators than one product kernel holds),
+ * and the errors of hx_step. */
+typedef const hx_potential *(*hx_potential_fn)(double t, void *user);
+HX_API int hx_step_reinterp(hx_problem *p, void *c, double dt, int nsteps, hx_potential_fn fn, void *user);
 /* Synchronises the stream and reports the last step: Lanczos size used, alpha/beta of T_m
  * (host arrays of at least m and m-1 doubles, either may be NULL) and the norm of c. */
 HX_API int hx_step_info(hx_problem *p, int *m_used, double *alpha, double *beta, double *norm);

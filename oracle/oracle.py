@@ -21,7 +21,9 @@ Readings of the paper that the oracle fixes (each also listed in the design note
     and the order of Algorithm fast_algorithm (both kept as "eq" / "alg");
   - each term of the fast algorithm restarts from the input vector;
   - Chebyshev nodes of the first kind, R + 1 nodes for degree R;
-  - Lanczos: full reorthogonalisation by classical Gram-Schmidt applied twice.
+  - Lanczos: full reorthogonalisation by classical Gram-Schmidt applied twice;
+  - time-dependent potentials are interpolated anew at every time an integrator
+    evaluates A (the time-propagation algorithm of Sec. 2.2, step (1)).
 """
 from __future__ import annotations
 
@@ -168,8 +170,10 @@ def cheb_coeffs_2d(values: np.ndarray) -> np.ndarray:
 def potential_terms(spec: dict, t: float) -> tuple[np.ndarray, np.ndarray]:
     """alpha_r(t) of W^pol(x, t) = sum_r alpha_r(t) T_r(x / L) for a workload's potential (Sec. 1.3).
 
-    Every component is interpolated on [-L, L]^axes at Chebyshev nodes of the first kind; a
-    monomial is interpolated at its own degree per axis, which reproduces it exactly.
+    Every component is interpolated on [-L, L]^axes at Chebyshev nodes of the first kind, at the
+    time t (a component whose function itself depends on t, "omega" != 0, is interpolated anew
+    for every t); a monomial is interpolated at its own degree per axis, which reproduces it
+    exactly.
     Returns (r, alpha) with r of shape (nterms, N), duplicates merged, zeros dropped."""
     N, L = spec["N"], spec["L"]
     acc: dict[tuple, float] = {}
@@ -194,7 +198,7 @@ def potential_terms(spec: dict, t: float) -> tuple[np.ndarray, np.ndarray]:
             a_ax, b_ax = comp["axes"]
             R = comp["R"]
             u = cheb_nodes(R)
-            vals = np.cos(L * u[:, None] - L * u[None, :])
+            vals = np.cos(L * u[:, None] - L * u[None, :] + comp.get("omega", 0.0) * t)
             coef = cheb_coeffs_2d(vals) * f_t
             for i in range(R + 1):
                 for j in range(R + 1):
@@ -205,7 +209,7 @@ def potential_terms(spec: dict, t: float) -> tuple[np.ndarray, np.ndarray]:
             (ax,) = comp["axes"]
             R = comp["R"]
             u = cheb_nodes(R)
-            coef = cheb_coeffs_1d(np.cos(comp["scale"] * L * u)) * f_t
+            coef = cheb_coeffs_1d(np.cos(comp["scale"] * L * u + comp.get("omega", 0.0) * t)) * f_t
             for i in range(R + 1):
                 r = [0] * N
                 r[ax] = i

@@ -951,6 +951,81 @@ int hx_step_host(hx_problem *p, void *c_host, double dt, int nsteps)
     return rc;
 }
 
+// One step with potentials re-interpolated for it (the time-propagation algorithm, step (1)):
+// the potential at the integrator's evaluation times replaces the problem's, then one hx_step.
+static int reinterp_one_step(hx_problem *p, void *c, double dt, hx_potential_fn fn, void *user)
+{
+    HX_CUDA(cudaStreamSynchronize(p->stream), "hx_step_reinterp");   // no kernel reads the old tables
+    const double t = p->t_host;
+    int rc;
+    if (p->cfg.scheme == HX_SCHEME_MAGNUS4) {
+        // A(t + c1 dt) from the first potential, A(t + c2 dt) from the second: each term is switched
+        // on over its half of [t, t + dt) by a two-interval piecewise-constant modulation (the
+        // Gauss-Legendre points c1 < 1/2 < c2 lie inside the two halves)
+        const double c1 = 0.5 - sqrt(3.0) / 6.0, c2 = 0.5 + sqrt(3.0) / 6.0;
+        static const double first[2] = {1.0, 0.0}, second[2] = {0.0, 1.0};
+        std::vector<hx_term> terms;
+        std::vector<std::vector<double>> coefs;   // copies: the first potential may not outlive the next call
+        double L = 0.0;
+        for (int g = 0; g < 2; ++g) {
+            const hx_potential *pot = fn(t + (g ? c2 : c1) * dt, user);
+            if (!pot || (pot->n_terms > 0 && !pot->terms) || pot->n_terms < 0) {
+                set_error("hx_step_reinterp: the potential callback returned no potential at t = %g", t);
+                return HX_EINVAL;
+            }
+            if (g == 0) L = pot->L;
+            else if (pot->L != L) {
+                set_error("hx_step_reinterp: the two Gauss-point potentials have different L");
+                return HX_EINVAL;
+            }
+            for (int i = 0; i < pot->n_terms; ++i) {
+                hx_term tm = pot->terms[i];
+                if (tm.mod_kind != HX_MOD_CONST) {
+                    set_error("hx_step_reinterp: with HX_SCHEME_MAGNUS4 every term must be HX_MOD_CONST (term %d)", i);
+                    return HX_EINVAL;
+                }
+                if (!tm.coef || tm.n_axes < 1 || tm.n_axes > 2 || tm.deg[0] < 0 || tm.deg[0] > kMaxDeg ||
+                    (tm.n_axes == 2 && (tm.deg[1] < 0 || tm.deg[1] > kMaxDeg))) {
+                    set_error("hx_step_reinterp: term %d: bad coefficients, axes or degrees", i);
+                    return HX_EINVAL;
+                }
+                const int nc = (tm.deg[0] + 1) * (tm.n_axes == 2 ? tm.deg[1] + 1 : 1);
+                coefs.emplace_back(tm.coef, tm.coef + nc);
+                tm.mod_kind = HX_MOD_PWCONST;
+                tm.pw_values = g ? second : first;
+                tm.pw_n = 2;
+                tm.pw_t0 = t;
+                tm.pw_t1 = t + dt;
+                terms.push_back(tm);
+            }
+        }
+        for (size_t i = 0; i < terms.size(); ++i) terms[i].coef = coefs[i].data();
+        hx_potential both = {L, (int)terms.size(), terms.data()};
+        rc = compile_potential(p, &both);
+    } else {
+        const hx_potential *pot = fn(t + 0.5 * dt, user);
+        if (!pot) {
+            set_error("hx_step_reinterp: the potential callback returned no potential at t = %g", t);
+            return HX_EINVAL;
+        }
+        rc = compile_potential(p, pot);
+    }
+    if (rc) return rc;
+    krylov_invalidate(p);   // the captured step refers to the previous tables
+    return hx_step(p, c, dt, 1);
+}
+
+int hx_step_reinterp(hx_problem *p, void *c, double dt, int nsteps, hx_potential_fn fn, void *user)
+{
+    if (!p || !c || !fn || nsteps < 0 || !(dt == dt)) { set_error("hx_step_reinterp: bad argument"); return HX_EINVAL; }
+    if ((uintptr_t)c % 16) { set_error("hx_step_reinterp: the complex128 state must be 16-byte aligned"); return HX_EINVAL; }
+    for (int n = 0; n < nsteps; ++n) {
+        int rc = reinterp_one_step(p, c, dt, fn, user);
+        if (rc) return rc;
+    }
+    return HX_OK;
+}
+
 int hx_batch_create(hx_problem *const *probs, int n, hx_batch **out)
 {
     if (!probs || n < 1 || !out) { set_error("hx_batch_create: need n >= 1 problems and out != NULL"); return HX_EINVAL; }

@@ -155,5 +155,6 @@ int krylov_step(Problem *p, void *c, double dt, int nsteps);
 int krylov_info(Problem *p, int *m_used, double *alpha, double *beta, double *norm);
 void *krylov_host_state(Problem *p);
 void krylov_free(Problem *p);
+void krylov_invalidate(Problem *p);   // drops the captured step graph, keeps the workspace
 
 }  // namespace hx

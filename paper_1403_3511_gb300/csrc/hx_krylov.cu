@@ -1436,6 +1436,17 @@ static int ensure_work(Problem *p)
     return HX_OK;
 }
 
+// The workspace (Krylov vectors, partial sums, scalars) does not depend on the potential; the
+// captured step does (operator parameters and table pointers are kernel arguments).
+void krylov_invalidate(Problem *p)
+{
+    Work *w = work_of(p);
+    if (w && w->exec) {
+        cudaGraphExecDestroy(w->exec);
+        w->exec = nullptr;
+    }
+}
+
 void krylov_free(Problem *p)
 {
     Work *w = work_of(p);

@@ -53,6 +53,10 @@ class hx_config(ctypes.Structure):
                 ("scheme", ctypes.c_int)]
 
 
+# const hx_potential *(*)(double t, void *user)
+POTENTIAL_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p)
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with paper_1403_3511_gb300.build.build() "
@@ -77,6 +81,7 @@ def _load():
         "hx_apply_project": (ctypes.c_int, [P, P, P, P, ctypes.c_size_t, ctypes.c_int, P]),
         "hx_step": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int]),
         "hx_step_host": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int]),
+        "hx_step_reinterp": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int, POTENTIAL_FN, P]),
         "hx_step_info": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), dp, dp, dp]),
         "hx_step_launches": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "hx_apply_specialised": (ctypes.c_int, [P]),
@@ -255,6 +260,24 @@ def hx_step_host(p, c: np.ndarray, dt: float, nsteps: int) -> int:
     return _check(lib.hx_step_host(p, _host_vec(c, (np.complex128,)), dt, nsteps), allow=(HX_EBREAKDOWN,))
 
 
+def hx_step_reinterp(p, c, dt: float, nsteps: int, fn) -> int:
+    """nsteps steps with the potential re-interpolated for every step: fn(t) -> (L, terms), terms
+    as for hx_potential_set, is called at the times the problem's scheme evaluates A (t + dt/2, or
+    the two Gauss-Legendre points of the 2-stage Magnus method)."""
+    held = []
+
+    def cb(t, _user):
+        L, terms = fn(t)
+        pot, keep = _potential(L, terms)
+        held.append((pot, keep))
+        del held[:-2]                       # the library holds at most the last two potentials
+        return ctypes.addressof(pot)
+
+    cfn = POTENTIAL_FN(cb)
+    return _check(lib.hx_step_reinterp(p, ctypes.c_void_p(_tptr(c)), dt, nsteps, cfn, None),
+                  allow=(HX_EBREAKDOWN,))
+
+
 def hx_step_info(p, m: int = 32) -> dict:
     mu = ctypes.c_int()
     a = np.zeros(m)
@@ -374,11 +397,13 @@ def hx_cheb_monomial(p: int, L: float) -> np.ndarray:
     return out
 
 
-def terms_from_spec(spec: dict) -> list:
+def terms_from_spec(spec: dict, t: float = 0.0) -> list:
     """hx_term dictionaries for a workload's potential (see paper_1403_3511_gb300.inputs): monomials
     through hx_cheb_monomial, smooth functions through their values at hx_cheb_nodes and
-    hx_cheb_coeffs.  Evaluating the user's function at the nodes is the only arithmetic here."""
+    hx_cheb_coeffs (a function that itself depends on time, "omega" != 0, at time t).  Evaluating
+    the user's function at the nodes is the only arithmetic here."""
     L = spec["L"]
+    tt = t
     out = []
     for comp in spec["potential"]:
         mod = comp.get("mod", {"kind": "const"})
@@ -400,12 +425,12 @@ def terms_from_spec(spec: dict) -> list:
             R = comp["R"]
             u = hx_cheb_nodes(R)
             t["axes"] = list(comp["axes"])
-            t["coef"] = hx_cheb_coeffs(R, np.cos(L * u[:, None] - L * u[None, :]))
+            t["coef"] = hx_cheb_coeffs(R, np.cos(L * u[:, None] - L * u[None, :] + comp.get("omega", 0.0) * tt))
         elif comp["func"] == "cos_scaled":
             R = comp["R"]
             u = hx_cheb_nodes(R)
             t["axes"] = list(comp["axes"])
-            t["coef"] = hx_cheb_coeffs(R, np.cos(comp["scale"] * L * u))
+            t["coef"] = hx_cheb_coeffs(R, np.cos(comp["scale"] * L * u + comp.get("omega", 0.0) * tt))
         else:
             raise KeyError(comp["func"])
         out.append(t)
@@ -426,7 +451,11 @@ class Problem:
                                    scheme)
 
     def set_potential(self, spec: dict, t: float = 0.0):
-        hx_potential_set(self.p, spec["L"], terms_from_spec(spec), t)
+        hx_potential_set(self.p, spec["L"], terms_from_spec(spec, t), t)
+
+    def step_reinterp(self, spec: dict, c, dt: float, nsteps: int) -> int:
+        """hx_step_reinterp with the workload's potential interpolated at every time the scheme asks for."""
+        return hx_step_reinterp(self.p, c, dt, nsteps, lambda t: (spec["L"], terms_from_spec(spec, t)))
 
     def close(self):
         if getattr(self, "p", None) is not None:

@@ -63,6 +63,15 @@ def time_integration_workload(N: int, K: int, m: int = 7) -> dict:
                 init={"kind": "beta_decay", "beta": 3.0}, T=1.0, m=m)
 
 
+def drifting_cos_chain(N: int, beta: float, omega: float, R: int = 8) -> list:
+    """W(x, t) = beta * sum_d cos(x_d - x_{d+1} + omega t) + beta / 2 * cos(x_1 / 4 + omega t): a
+    potential whose shape, not only its size, changes with t, so that its degree-R Chebyshev
+    interpolant has to be computed anew for every time step."""
+    comps = [{"coef": beta, "func": "cos_diff", "axes": [d, d + 1], "R": R, "omega": omega} for d in range(N - 1)]
+    comps.append({"coef": 0.5 * beta, "func": "cos_scaled", "axes": [0], "scale": 0.25, "R": R, "omega": omega})
+    return comps
+
+
 def cos_chain(N: int, beta: float, R: int = 8) -> list:
     """W = beta * sum_d cos(x_d - x_{d+1}), to be replaced by its degree-R Chebyshev interpolant."""
     return [{"coef": beta, "func": "cos_diff", "axes": [d, d + 1], "R": R} for d in range(N - 1)]

@@ -217,6 +217,77 @@ def test_magnus4_matches_oracle(hx, oracle, dtype, tol, N, B, h, steps):
         assert rel(mpr, ref) > 1e3 * tol
 
 
+def _drifting(N, B):
+    """beta cos(x_d - x_{d+1} + omega t) chain: the interpolant's shape changes with t."""
+    return dict(N=N, B=B, L=inputs.half_width(B), potential=inputs.drifting_cos_chain(N, 0.2, 2.0))
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
+def test_reinterpolated_potential_matches_oracle(hx, oracle, scheme, dtype, tol):
+    """The time-propagation algorithm of Sec. 2.2 with its step (1) every step: the potential's
+    degree-8 Chebyshev interpolant is computed anew at t + h/2 (exponential midpoint rule) or at the
+    two Gauss-Legendre points (2-stage Magnus method) through hx_step_reinterp; the oracle
+    interpolates at the same times."""
+    N, B, h, steps, t0 = 3, 60, 0.02, 10, 0.1
+    spec = _drifting(N, B)
+    S = oracle.IndexSet.hyperbolic(N, B)
+    c0 = inputs.initial_vector({"init": {"kind": "coherent", "q": [0.5, -0.3, 0.2], "eps": 1e-3, "seed": 6}}, S.k)
+    prop = oracle.magnus4_propagate if scheme else oracle.expmpr_propagate
+    ref, t_ref = prop(S, spec, c0, h, steps, 7, t0=t0)
+    P = hx.Problem(N, B, dtype=hx.HX_C128 if dtype == "c128" else hx.HX_C64, scheme=scheme)
+    try:
+        x = torch.from_numpy(np.ascontiguousarray(c0)).to("cuda", torch.complex128)
+        hx.hx_set_time(P.p, t0)
+        P.step_reinterp(spec, x, h, steps)
+        t = hx.hx_get_time(P.p)
+        got = x.cpu().numpy()
+    finally:
+        P.close()
+    assert abs(t - t_ref) < 1e-12
+    assert rel(got, ref) <= tol, rel(got, ref)
+    if dtype == "c128":          # the change of shape matters far beyond the tolerance
+        frozen = dict(spec, potential=[dict(c, omega=0.0) for c in spec["potential"]])
+        assert rel(prop(S, frozen, c0, h, steps, 7, t0=t0)[0], ref) > 1e3 * tol
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_reinterpolating_a_fixed_potential_is_hx_step(hx, dtype):
+    """With a potential that does not change, the per-step path runs the kernels hx_step runs on
+    the same arguments: the states agree bit for bit."""
+    spec = inputs.workload("hh2_b32")
+    dt_ = hx.HX_C128 if dtype == "c128" else hx.HX_C64
+    P, Q = hx.Problem(2, 32, dtype=dt_), hx.Problem(2, 32, dtype=dt_)
+    try:
+        P.set_potential(spec, 0.0)
+        c0 = inputs.initial_vector(spec, hx.hx_indexset_export(P.set, 2))
+        a = torch.from_numpy(c0).to("cuda")
+        b = a.clone()
+        hx.hx_step(P.p, a, 0.01, 5)
+        Q.step_reinterp(spec, b, 0.01, 5)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        assert hx.hx_get_time(Q.p) == pytest.approx(0.05, abs=1e-14)
+    finally:
+        P.close()
+        Q.close()
+
+
+def test_reinterp_argument_errors(hx):
+    import ctypes
+    P = hx.Problem(2, 40, scheme=hx.HX_SCHEME_MAGNUS4)
+    try:
+        x = torch.zeros(P.size, dtype=torch.complex128, device="cuda")
+        nothing = hx.POTENTIAL_FN(lambda t, u: None)
+        assert hx.lib.hx_step_reinterp(P.p, ctypes.c_void_p(x.data_ptr()), 0.01, 1, nothing, None) == hx.HX_EINVAL
+        assert "no potential" in hx.hx_last_error()
+        with pytest.raises(hx.HxError):      # Magnus needs constant terms (it switches them per Gauss point)
+            P.step_reinterp(_laser_hh(2, 40), x, 0.01, 1)
+        assert hx.lib.hx_step_reinterp(P.p, ctypes.c_void_p(x.data_ptr() + 8), 0.01, 1, nothing, None) == hx.HX_EINVAL
+    finally:
+        P.close()
+
+
 def test_magnus4_time_integration_experiment(hx, oracle):
     """The time-integration experiment of Sec. 6.3 (N = 2, K = 40, m = 7, h = 1/10) on the GPU equals
     the oracle's 2-stage Magnus run (whose error against the exact-Galerkin solution the oracle pins

@@ -136,6 +136,33 @@ def test_cos_interpolant_tensor_equals_rank_two_form(oracle):
     assert np.allclose(T, np.outer(c, c) + np.outer(s, s), atol=1e-13)
 
 
+def test_time_dependent_interpolant_by_angle_addition(oracle):
+    """A potential whose shape changes with t, beta cos(x_a - x_b + omega t) + beta/2 cos(x_1/4 + omega t),
+    is interpolated anew at every t (the time-propagation algorithm of Sec. 2.2, step (1)).  By
+    cos(d + th) = cos d cos th - sin d sin th, cos(a - b) = cos a cos b + sin a sin b and
+    sin(a - b) = sin a cos b - cos a sin b, and since tensor interpolation of a product is the product
+    of the 1-D interpolants, its coefficients at each t follow from numpy's 1-D interpolants at the
+    Chebyshev points of the first kind."""
+    N, R, L, beta, omega = 3, 8, inputs.half_width(60), 0.2, 2.0
+    spec = dict(N=N, L=L, potential=inputs.drifting_cos_chain(N, beta, omega, R))
+    cheb = np.polynomial.chebyshev.chebinterpolate
+    ca, sa = cheb(lambda u: np.cos(L * u), R), cheb(lambda u: np.sin(L * u), R)
+    cq, sq = cheb(lambda u: np.cos(0.25 * L * u), R), cheb(lambda u: np.sin(0.25 * L * u), R)
+    cos_d, sin_d = np.outer(ca, ca) + np.outer(sa, sa), np.outer(sa, ca) - np.outer(ca, sa)
+    for t in (0.0, 0.37, 1.9):
+        th = omega * t
+        want = np.zeros((R + 1,) * N)
+        pair = beta * (math.cos(th) * cos_d - math.sin(th) * sin_d)
+        want[:, :, 0] += pair                                      # axes (0, 1), r_2 = 0
+        want[0, :, :] += pair                                      # axes (1, 2), r_0 = 0
+        want[:, 0, 0] += 0.5 * beta * (math.cos(th) * cq - math.sin(th) * sq)
+        r, a = oracle.potential_terms(spec, t)
+        got = np.zeros_like(want)
+        for rr, aa in zip(r.tolist(), a.tolist()):
+            got[tuple(rr)] += aa
+        assert np.abs(got - want).max() <= 1e-13, (t, np.abs(got - want).max())
+
+
 def test_potential_terms_henon_heiles(oracle):
     """lam x1^2 x2 - lam/3 x2^3 in Chebyshev form: x1^2 x2 = L^3/2 (T0 + T2)(u1) T1(u2), x2^3 = L^3/4 (3T1 + T3)(u2)."""
     spec = inputs.workload("hh2_b32")

@@ -145,7 +145,8 @@ HX_API void hx_indexset_destroy(hx_indexset *s);
 /* ---- problem: index set + potential + configuration -------------------------- */
 
 /* cfg may be NULL: HX_C128, HX_ORDER_SYM, m = 7, default stream, HX_SCHEME_EXPMPR.  The index
- * set must outlive the problem.  Errors: HX_EINVAL (bad dtype, order, m or scheme). */
+ * set must outlive the problem.  Errors: HX_EINVAL (bad dtype, order, m or scheme), HX_ENOMEM
+ * (host or device memory), HX_ECUDA (no usable CUDA device). */
 HX_API int hx_problem_create(const hx_indexset *s, const hx_config *cfg, hx_problem **out);
 HX_API void hx_problem_destroy(hx_problem *p);
 
@@ -153,7 +154,8 @@ HX_API void hx_problem_destroy(hx_problem *p);
  * problem time to t.  Terms are copied; the caller's arrays may be freed afterwards.
  * A constant term (all degrees 0) is folded into the diagonal.  Synchronous.
  * Errors: HX_EINVAL (L <= 0, bad axes or degrees, NULL coef), HX_EUNSUPPORTED (n_axes > 2,
- * more than 32 terms after compilation). */
+ * more than 48 operators after compilation: rank-one pieces of two-axis terms, and for high
+ * degrees their two stages, count separately). */
 HX_API int hx_potential_set(hx_problem *p, const hx_potential *pot, double t);
 HX_API int hx_get_time(const hx_problem *p, double *t);
 HX_API int hx_set_time(hx_problem *p, double t);

@@ -759,11 +759,16 @@ int hx_problem_create(const hx_indexset *s, const hx_config *cfg, hx_problem **o
     p->set = s;
     p->cfg = c;
     p->stream = (cudaStream_t)c.stream;
-    cudaGetDevice(&p->device);
-    cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
-    cudaError_t e = cudaMalloc((void **)&p->dscal, 64 * sizeof(double));
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "hx_problem_create: no CUDA device"); }
+    e = cudaMalloc((void **)&p->dscal, 64 * sizeof(double));
     if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaMalloc(scalars)"); }
-    cudaMemset(p->dscal, 0, 64 * sizeof(double));
+    if ((e = cudaMemset(p->dscal, 0, 64 * sizeof(double))) != cudaSuccess) {
+        cudaFree(p->dscal);
+        delete p;
+        return cuda_fail(e, "hx_problem_create: clear scalars");
+    }
     *out = p;
     return HX_OK;
 }

@@ -447,12 +447,20 @@ def _time_dependent_hh2():
                                                                 "mod": {"kind": "sin2", "omega": 2.0}}])
 
 
-def test_magnus4_is_order_four_and_midpoint_order_two(oracle):
+def _drifting_cos2():
+    """cos(x_1 - x_2 + 2t) chain with cos(x_1/4 + 2t): a potential whose interpolant changes shape with t."""
+    N, B = 2, 12
+    return dict(N=N, B=B, L=inputs.half_width(B), potential=inputs.drifting_cos_chain(N, 0.6, 2.0))
+
+
+@pytest.mark.parametrize("make_spec", [_time_dependent_hh2, _drifting_cos2])
+def test_magnus4_is_order_four_and_midpoint_order_two(oracle, make_spec):
     """Eq. (2stageMagnus) has order 4 and Eq. (expMPR) order 2 (Sec. 2.1): with exact exponentials
     (m = |K|), against scipy's DOP853 solution of i c' = A(t) c with the same dense matrices, halving h
-    divides the error by 16 and by 4."""
+    divides the error by 16 and by 4.  Also when the potential is re-interpolated at every evaluation
+    time (a shape that drifts with t)."""
     from scipy.integrate import solve_ivp
-    spec = _time_dependent_hh2()
+    spec = make_spec()
     S = oracle.IndexSet.hyperbolic(spec["N"], spec["B"])
     c0 = inputs.initial_vector({"init": {"kind": "coherent", "q": [0.7, -0.4], "eps": 0.0, "seed": 0}}, S.k)
 

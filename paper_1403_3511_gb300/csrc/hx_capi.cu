@@ -963,11 +963,13 @@ static int reinterp_one_step(hx_problem *p, void *c, double dt, hx_potential_fn 
     HX_CUDA(cudaStreamSynchronize(p->stream), "hx_step_reinterp");   // no kernel reads the old tables
     const double t = p->t_host;
     int rc;
-    if (p->cfg.scheme == HX_SCHEME_MAGNUS4) {
+    if (p->cfg.scheme == HX_SCHEME_MAGNUS4 && dt != 0.0) {
         // A(t + c1 dt) from the first potential, A(t + c2 dt) from the second: each term is switched
-        // on over its half of [t, t + dt) by a two-interval piecewise-constant modulation (the
-        // Gauss-Legendre points c1 < 1/2 < c2 lie inside the two halves)
+        // on over its half of the step interval by a two-interval piecewise-constant modulation (the
+        // Gauss-Legendre points c1 < 1/2 < c2 lie inside the two halves; for dt < 0 the first point
+        // lies in the upper half of [t + dt, t))
         const double c1 = 0.5 - sqrt(3.0) / 6.0, c2 = 0.5 + sqrt(3.0) / 6.0;
+        const bool fwd = dt > 0.0;
         static const double first[2] = {1.0, 0.0}, second[2] = {0.0, 1.0};
         std::vector<hx_term> terms;
         std::vector<std::vector<double>> coefs;   // copies: the first potential may not outlive the next call
@@ -997,17 +999,17 @@ static int reinterp_one_step(hx_problem *p, void *c, double dt, hx_potential_fn 
                 const int nc = (tm.deg[0] + 1) * (tm.n_axes == 2 ? tm.deg[1] + 1 : 1);
                 coefs.emplace_back(tm.coef, tm.coef + nc);
                 tm.mod_kind = HX_MOD_PWCONST;
-                tm.pw_values = g ? second : first;
+                tm.pw_values = (g == 0) == fwd ? first : second;
                 tm.pw_n = 2;
-                tm.pw_t0 = t;
-                tm.pw_t1 = t + dt;
+                tm.pw_t0 = fwd ? t : t + dt;
+                tm.pw_t1 = fwd ? t + dt : t;
                 terms.push_back(tm);
             }
         }
         for (size_t i = 0; i < terms.size(); ++i) terms[i].coef = coefs[i].data();
         hx_potential both = {L, (int)terms.size(), terms.data()};
         rc = compile_potential(p, &both);
-    } else {
+    } else {   // the exponential midpoint rule (and a Magnus step of length 0: both points at t)
         const hx_potential *pot = fn(t + 0.5 * dt, user);
         if (!pot) {
             set_error("hx_step_reinterp: the potential callback returned no potential at t = %g", t);

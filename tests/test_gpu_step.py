@@ -222,14 +222,15 @@ def _drifting(N, B):
     return dict(N=N, B=B, L=inputs.half_width(B), potential=inputs.drifting_cos_chain(N, 0.2, 2.0))
 
 
+@pytest.mark.parametrize("h", [0.02, -0.02])
 @pytest.mark.parametrize("scheme", [0, 1])
 @pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
-def test_reinterpolated_potential_matches_oracle(hx, oracle, scheme, dtype, tol):
+def test_reinterpolated_potential_matches_oracle(hx, oracle, scheme, dtype, tol, h):
     """The time-propagation algorithm of Sec. 2.2 with its step (1) every step: the potential's
     degree-8 Chebyshev interpolant is computed anew at t + h/2 (exponential midpoint rule) or at the
     two Gauss-Legendre points (2-stage Magnus method) through hx_step_reinterp; the oracle
-    interpolates at the same times."""
-    N, B, h, steps, t0 = 3, 60, 0.02, 10, 0.1
+    interpolates at the same times.  Also backwards in time (h < 0)."""
+    N, B, steps, t0 = 3, 60, 10, 0.1
     spec = _drifting(N, B)
     S = oracle.IndexSet.hyperbolic(N, B)
     c0 = inputs.initial_vector({"init": {"kind": "coherent", "q": [0.5, -0.3, 0.2], "eps": 1e-3, "seed": 6}}, S.k)

@@ -1,6 +1,7 @@
 """Host logic of bench.py on CPU: the multi-rank path with two gloo ranks (no GPU, no data-path
-collective; the replicas only agree on the slowest time), the reference arm's rank > 0 doing no
-work, and the roofline traffic taken from the committed ncu summary."""
+collective; the replicas only agree on the slowest time), the reference arm (rank > 0 doing no
+work, rank 0 printing the contract's line), and the roofline traffic taken from the committed ncu
+summary."""
 import argparse
 import io
 import os
@@ -64,6 +65,26 @@ def test_reference_arm_other_ranks_do_nothing():
     with redirect_stdout(buf):
         bench.run_reference(args, rank=1)
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_line(oracle):
+    """Rank 0 of the reference arm times the oracle's full matvec and prints one JSON line with the
+    contract's keys (on a tiny workload here; the default workload takes seconds per step)."""
+    import json
+    import bench
+    args = argparse.Namespace(workload="hh2_b32", steps=3, warmup=1, gpus=1)
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(args, rank=0)
+    lines = [x for x in buf.getvalue().splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "Galerkin matvecs: Gcoeff/s" and d["unit"] == "Gcoeff/s"
+    assert d["steps"] == 3 and d["warmup"] == 1 and d["higher_is_better"] is True and d["value"] > 0
+    assert d["config"]["workload"] == "hh2_b32" and d["config"]["size"] == 119
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "Gcoeff/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["value"] == pytest.approx(119 / (d["ms_per_step"] * 1e-3) / 1e9)
 
 
 def test_profiled_traffic_tracks_kernel_source(tmp_path, monkeypatch):

@@ -232,8 +232,9 @@ HX_API int hx_step_info(hx_problem *p, int *m_used, double *alpha, double *beta,
  * runs the generic kernel; hx_last_error then says why (also when 1).  Both compute the same
  * product.  HX_EINVAL without a potential.  The paper has no counterpart: this reports how the
  * library runs the product.  Setting the environment variable HX_APPLY_SPECIALISE=0 before
- * hx_potential_set selects the generic kernel.  The steps of a batch (hx_batch_step) always run the
- * generic kernel. */
+ * hx_potential_set selects the generic kernel; HX_JIT_SOURCE_DUMP=<file> writes the source of a
+ * newly compiled kernel to that file before compiling it.  The steps of a batch (hx_batch_step)
+ * always run the generic kernel. */
 HX_API int hx_apply_specialised(const hx_problem *p);
 /* Kernel launches of one product hx_apply (1, or 2 when some term is evaluated in two stages
  * through channel vectors) and of one time step of hx_step: m (per_apply + 3) + 2 for

@@ -31,7 +31,7 @@ __device__ __forceinline__ int point_addr(const Ctx &c, const Elem &el, const Op
     const int N = c.S->N;
     const int di = O.didx[op.dbase + pos];
     const int shift = (a == N - 1 ? s : 0) + (b == N - 1 ? s2 : 0);
-    return (di ? c.row(el, di) : el.e - el.k2) + el.k2 + shift;
+    return (di ? c.start(el, di, true) : el.e - el.j) + el.j + shift;
 }
 
 // Number of steps (capped at p) from coordinate i to the top of its fibre, given the product
@@ -112,28 +112,30 @@ __device__ __forceinline__ void plane_op(const Ctx &c, const Elem &el, const OpS
 
 template <typename R, int P, int Q, int SB>
 __device__ __forceinline__ void plane_dispatch_sb(int rb, const Ctx &c, const Elem &el, const OpSet &O, const Op &op,
-                                                  const R *tab, const typename Vec2<R>::T *src, R &sx, R &sy, R &lx, R &ly)
+                                                  const R *tab, const typename Vec2<R>::T *src, typename Vec2<R>::T &s,
+                                                  typename Vec2<R>::T &l)
 {
-    if (rb == ROLE_LAST) plane_role<R, P, Q, ROLE_LAST, SB>(c, el, O, op, tab, src, sx, sy, lx, ly);
-    else plane_role<R, P, Q, ROLE_ROW, SB>(c, el, O, op, tab, src, sx, sy, lx, ly);
+    if (rb == ROLE_LAST) plane_role<R, P, Q, ROLE_LAST, SB>(c, el, O, op, tab, src, s, l);
+    else plane_role<R, P, Q, ROLE_ROW, SB>(c, el, O, op, tab, src, s, l);
 }
 
 // sb: degree of the merged line op (0: none); only sb in {0, Q, Q + 2 <= 3} occurs.
 template <typename R, int P, int Q>
 __device__ __forceinline__ void plane_dispatch(int rb, int sb, const Ctx &c, const Elem &el, const OpSet &O, const Op &op,
-                                               const R *tab, const typename Vec2<R>::T *src, R &sx, R &sy, R &lx, R &ly)
+                                               const R *tab, const typename Vec2<R>::T *src, typename Vec2<R>::T &s,
+                                               typename Vec2<R>::T &l)
 {
-    if (sb == 0) plane_dispatch_sb<R, P, Q, 0>(rb, c, el, O, op, tab, src, sx, sy, lx, ly);
-    else if (sb == Q) plane_dispatch_sb<R, P, Q, Q>(rb, c, el, O, op, tab, src, sx, sy, lx, ly);
-    else if (Q + 2 <= 3) plane_dispatch_sb<R, P, Q, (Q + 2 <= 3 ? Q + 2 : Q)>(rb, c, el, O, op, tab, src, sx, sy, lx, ly);
+    if (sb == 0) plane_dispatch_sb<R, P, Q, 0>(rb, c, el, O, op, tab, src, s, l);
+    else if (sb == Q) plane_dispatch_sb<R, P, Q, Q>(rb, c, el, O, op, tab, src, s, l);
+    else if (Q + 2 <= 3) plane_dispatch_sb<R, P, Q, (Q + 2 <= 3 ? Q + 2 : Q)>(rb, c, el, O, op, tab, src, s, l);
 }
 
 template <typename R, int P>
-__device__ __forceinline__ void line_dispatch(int ra, const Ctx &c, const Elem &el, const OpSet &O, const Op &op,
-                                              const R *tab, const typename Vec2<R>::T *src, R &sx, R &sy)
+__device__ __forceinline__ typename Vec2<R>::T line_dispatch(int ra, const Ctx &c, const Elem &el, const OpSet &O,
+                                                             const Op &op, const R *tab, const typename Vec2<R>::T *src)
 {
-    if (ra == ROLE_LAST) line_role<R, P, ROLE_LAST>(c, el, O, op, tab, src, sx, sy);
-    else line_role<R, P, ROLE_ROW>(c, el, O, op, tab, src, sx, sy);
+    if (ra == ROLE_LAST) return line_role<R, P, ROLE_LAST>(c, el, O, op, tab, src);
+    return line_role<R, P, ROLE_ROW>(c, el, O, op, tab, src);
 }
 
 // MD: largest polynomial degree of the compiled potential (3: unrolled stencils; kMaxDeg: rolled loops).
@@ -158,18 +160,24 @@ __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 3 : 1) apply_kernel(c
                 sy = cs.y;
             } else if (MD <= 3) {
                 const int sb = op.mergeB >= 0 ? O.op[op.mergeB].p : 0;
+                V o = czero<V>(), l = czero<V>();
                 switch (op.cls) {
-                    case CLS_LINE + 1: line_dispatch<R, 1>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                    case CLS_LINE + 2: line_dispatch<R, 2>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                    case CLS_LINE + 3: line_dispatch<R, 3>(op.ra, ctx, el, O, op, tab, src, sx, sy); break;
-                    case CLS_PLANE + 0: plane_dispatch<R, 1, 1>(op.rb, sb, ctx, el, O, op, tab, src, sx, sy, lx, ly); break;
-                    case CLS_PLANE + 3: plane_dispatch<R, 2, 1>(op.rb, sb, ctx, el, O, op, tab, src, sx, sy, lx, ly); break;
-                    case CLS_PLANE + 1: plane_dispatch<R, 1, 2>(op.rb, sb, ctx, el, O, op, tab, src, sx, sy, lx, ly); break;
-                    case CLS_PLANE + 4: plane_dispatch<R, 2, 2>(op.rb, sb, ctx, el, O, op, tab, src, sx, sy, lx, ly); break;
+                    case CLS_LINE + 1: o = line_dispatch<R, 1>(op.ra, ctx, el, O, op, tab, src); break;
+                    case CLS_LINE + 2: o = line_dispatch<R, 2>(op.ra, ctx, el, O, op, tab, src); break;
+                    case CLS_LINE + 3: o = line_dispatch<R, 3>(op.ra, ctx, el, O, op, tab, src); break;
+                    case CLS_PLANE + 0: plane_dispatch<R, 1, 1>(op.rb, sb, ctx, el, O, op, tab, src, o, l); break;
+                    case CLS_PLANE + 3: plane_dispatch<R, 2, 1>(op.rb, sb, ctx, el, O, op, tab, src, o, l); break;
+                    case CLS_PLANE + 1: plane_dispatch<R, 1, 2>(op.rb, sb, ctx, el, O, op, tab, src, o, l); break;
+                    case CLS_PLANE + 4: plane_dispatch<R, 2, 2>(op.rb, sb, ctx, el, O, op, tab, src, o, l); break;
                     default:
                         if (op.kind == 1) line_op<R, 3, true>(ctx, el, O, op, tab, src, sx, sy);
                         else plane_op<R, 3, 3, true>(ctx, el, O, op, tab, src, sx, sy);
+                        o = V{sx, sy};
                 }
+                sx = o.x;
+                sy = o.y;
+                lx = l.x;
+                ly = l.y;
             } else {
                 if (op.kind == 1) line_op<R, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
                 else plane_op<R, kMaxDeg, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
@@ -209,8 +217,9 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
     ApplyArgs a;
     memset(&a, 0, sizeof(a));
     a.S = p->set->d;
-    a.rnb = p->rnb;
-    a.nrow = p->set->d.nrow;
+    a.gnb = p->gnb;
+    a.gstride = p->gstride;
+    memcpy(a.mv, p->roff.mv, sizeof(a.mv));
     a.t_ptr = t_ptr;
     a.t_shift = t_shift;
     a.pw_values = p->pw_values;
@@ -319,19 +328,21 @@ int launch_apply(Problem *p, const void *cin, void *cout, const double *t_ptr, d
 // Row structure on the device
 // ---------------------------------------------------------------------------------------
 
-// Per-element record: the row holding rank e (largest r with start(r) <= e), the product of
-// (1 + k_l), the coordinate sum, and k_{N-1} with the row length above it (both below 2^16).
+// Per-element record: the row holding rank e (largest r with start(r) <= e), its group, the
+// product of (1 + k_l) with the coordinate sum above it, and k_{N-1} with the row length above it
+// (all four below 2^16 since B < 2^16).
 __global__ void elem_info_kernel(DevSet S, int4 *elem)
 {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.size; e += gridDim.x * blockDim.x) {
         int lo = 0, hi = S.nrow - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (S.row_info[mid].x <= e) lo = mid; else hi = mid - 1;
+            if (S.rstart[mid] <= e) lo = mid; else hi = mid - 1;
         }
         const int4 ri = S.row_info[lo];
         const int k2 = e - ri.x;
-        elem[e] = make_int4(lo, ri.y * (1 + k2), ri.z + k2, (int)((unsigned)k2 | ((unsigned)ri.w << 16)));
+        const unsigned qall = (unsigned)(ri.y * (1 + k2)), ksum = (unsigned)(ri.z + k2);
+        elem[e] = make_int4(lo, S.rgrp[lo], (int)(qall | (ksum << 16)), (int)((unsigned)k2 | ((unsigned)ri.w << 16)));
     }
 }
 
@@ -345,35 +356,38 @@ int launch_elem_info(const IndexSetObj *s)
     return HX_OK;
 }
 
-// rnb[d * nrow + r] = start rank of the row whose prefix is prefix(r) + offset d, or -1 when a
-// coordinate turns negative or the prefix product exceeds B; the start is the rank of
-// (prefix, 0), summed level by level from the rank tables.
-__global__ void rowtab_kernel(DevSet S, RowOffsets ro, int *rnb)
+// gnb[g * gstride + m] = first row of the group whose prefix (k_0..k_{N-3}) is that of group g
+// moved by outer move m, or -1 when a coordinate turns negative or the prefix product exceeds B.
+// The first row of a group is the row of the prefix (k_0..k_{N-3}, 0), whose index is
+// sum_{d<N-2} Q_{N-2-d}(q_d, k_d) (the rank tables one level up).
+__global__ void groupnb_kernel(DevSet S, RowOffsets ro, int gstride, int *gnb)
 {
-    const int npre = S.N - 1;
-    const int64_t total = (int64_t)ro.n * S.nrow;
+    const int npre = S.N - 1, nouter = S.N - 2;
+    const int64_t total = (int64_t)S.ngroup * ro.nom;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
-        const int d = (int)(x / S.nrow), r = (int)(x - (int64_t)d * S.nrow);
-        const int a0 = ro.d[d][0], s0 = ro.d[d][1], a1 = ro.d[d][2], s1 = ro.d[d][3];
-        int q = 1, start = 0;
+        const int g = (int)(x / ro.nom), m = (int)(x - (int64_t)g * ro.nom);
+        const int a0 = ro.om[m][0], s0 = ro.om[m][1], a1 = ro.om[m][2], s1 = ro.om[m][3];
+        const int r0 = S.gfirst[g];
+        int q = 1, row = 0;
         bool ok = true;
-        for (int l = 0; l < npre; ++l) {
-            const int kl = (int)S.row_k[(size_t)r * npre + l] + (l == a0 ? s0 : 0) + (l == a1 ? s1 : 0);
+        for (int l = 0; l < nouter; ++l) {
+            const int kl = (int)S.row_k[(size_t)r0 * npre + l] + (l == a0 ? s0 : 0) + (l == a1 ? s1 : 0);
             if (kl < 0 || (int64_t)q * (1 + kl) > S.B) { ok = false; break; }
-            start += S.Q[(size_t)(npre - 1 - l) * S.qtotal + S.qoff[q] + kl];   // level m = N-1-l
+            row += S.Q[(size_t)(nouter - 1 - l) * S.qtotal + S.qoff[q] + kl];   // level m = N-2-l
             q *= 1 + kl;
         }
-        rnb[x] = ok ? start : -1;
+        gnb[(size_t)g * gstride + m] = ok ? row : -1;
     }
 }
 
-int launch_rowtab(const DevSet &S, const RowOffsets &ro, int *rnb, cudaStream_t st)
+int launch_groupnb(const DevSet &S, const RowOffsets &ro, int gstride, int *gnb, cudaStream_t st)
 {
-    const int64_t total = (int64_t)ro.n * S.nrow;
+    const int64_t total = (int64_t)ro.nom * S.ngroup;
+    if (total == 0) return HX_OK;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, 16384);
-    rowtab_kernel<<<std::max(blocks, 1), 256, 0, st>>>(S, ro, rnb);
+    groupnb_kernel<<<std::max(blocks, 1), 256, 0, st>>>(S, ro, gstride, gnb);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "row-offset table kernel");
+    if (e != cudaSuccess) return cuda_fail(e, "group-neighbour table kernel");
     return HX_OK;
 }
 

@@ -76,6 +76,11 @@ static bool counts_by_quotient(int N, int B, std::vector<std::vector<int64_t>> &
 static void enum_rows(int depth, int npre, int q, int ksum, int B, uint16_t *prefix, IndexSetHost &h, int64_t &pos)
 {
     if (depth == npre) {
+        if (npre == 0 || prefix[npre - 1] == 0) {   // first row of a new group (k_{N-2} = 0)
+            h.gfirst.push_back((int)h.row_info.size());
+            h.ngroup = (int)h.gfirst.size();
+        }
+        h.rgrp.push_back(h.ngroup - 1);
         h.row_k.insert(h.row_k.end(), prefix, prefix + npre);
         int len = B / q;
         h.row_info.push_back(make_int4((int)pos, q, ksum, len));
@@ -126,6 +131,9 @@ static int build_host_tables(int N, int B, IndexSetHost &h)
     int64_t pos = 0;
     h.row_info.clear();
     h.row_k.clear();
+    h.rgrp.clear();
+    h.gfirst.clear();
+    h.ngroup = 0;
     enum_rows(0, N - 1, 1, 0, B, prefix, h, pos);
     h.nrow = (int)h.row_info.size();
     if (pos != size) {
@@ -596,18 +604,42 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
         pr->chan_ld = ld;
         if (pr->nch) HX_CUDA(cudaMalloc(&pr->chan, ld * es2 * pr->nch), "cudaMalloc(channels)");
     }
-    // row-offset table: kept when the offsets are those of the previous potential
+    // split every row offset into its move on the group axes 0..N-3 and its step on axis N-2
+    {
+        RowOffsets &ro = cp.roff;
+        ro.nom = 0;
+        for (int d = 0; d < ro.n; ++d) {
+            signed char om[4] = {-1, 0, -1, 0};
+            int n = 0, s4 = 0;
+            for (int i = 0; i < 2; ++i) {
+                const int ax = ro.d[d][2 * i], st = ro.d[d][2 * i + 1];
+                if (ax < 0) continue;
+                if (ax == N - 2) s4 = st;
+                else { om[2 * n] = (signed char)ax; om[2 * n + 1] = (signed char)st; ++n; }
+            }
+            int m = -1;
+            if (n > 0) {
+                for (int i = 0; i < ro.nom && m < 0; ++i)
+                    if (!memcmp(ro.om[i], om, 4)) m = i;
+                if (m < 0) { memcpy(ro.om[ro.nom], om, 4); m = ro.nom++; }
+            }
+            ro.mv[d].om = (short)m;
+            ro.mv[d].s4 = (short)s4;
+        }
+    }
+    // group-neighbour table: kept when the outer moves are those of the previous potential
     const IndexSetHost &h = set->h;
-    bool same = pr->rnb && pr->roff.n == cp.roff.n && !memcmp(pr->roff.d, cp.roff.d, sizeof(cp.roff.d[0]) * cp.roff.n);
+    bool same = pr->gnb && pr->roff.nom == cp.roff.nom && !memcmp(pr->roff.om, cp.roff.om, sizeof(cp.roff.om[0]) * cp.roff.nom);
+    pr->roff = cp.roff;
     if (!same) {
-        if (pr->rnb) cudaFree(pr->rnb);
-        pr->rnb = nullptr;
-        size_t bytes = (size_t)cp.roff.n * std::max(h.nrow, 1) * sizeof(int);
-        HX_CUDA(cudaMalloc((void **)&pr->rnb, bytes), "cudaMalloc(row-offset table)");
-        pr->roff = cp.roff;
-        int rc = launch_rowtab(set->d, pr->roff, pr->rnb, pr->stream);
+        if (pr->gnb) cudaFree(pr->gnb);
+        pr->gnb = nullptr;
+        pr->gstride = std::max(cp.roff.nom, 1);
+        size_t bytes = (size_t)pr->gstride * std::max(h.ngroup, 1) * sizeof(int);
+        HX_CUDA(cudaMalloc((void **)&pr->gnb, bytes), "cudaMalloc(group-neighbour table)");
+        int rc = launch_groupnb(set->d, pr->roff, pr->gstride, pr->gnb, pr->stream);
         if (rc) return rc;
-        HX_CUDA(cudaStreamSynchronize(pr->stream), "row-offset table");
+        HX_CUDA(cudaStreamSynchronize(pr->stream), "group-neighbour table");
     }
     jit_prepare(pr);
     pr->have_pot = true;
@@ -648,9 +680,12 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     size_t b_of = (size_t)std::max<int64_t>(h.size, 1) * sizeof(int4);
     size_t b_qoff = (size_t)(h.B + 2) * sizeof(int);
     size_t b_Q = std::max<size_t>(h.Q.size(), 1) * sizeof(int);
-    size_t b_nt = (size_t)(h.B + 1) * sizeof(int);
+    size_t b_nt = (size_t)(kNtSpan * h.B + 1) * sizeof(int);
+    size_t b_rs = (size_t)(h.nrow + 1) * sizeof(int);
+    size_t b_rg = (size_t)std::max(h.nrow, 1) * sizeof(int);
+    size_t b_gf = (size_t)std::max(h.ngroup, 1) * sizeof(int);
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t total = al(b_info) + al(b_k) + al(b_of) + al(b_qoff) + al(b_Q) + al(b_nt);
+    size_t total = al(b_info) + al(b_k) + al(b_of) + al(b_qoff) + al(b_Q) + al(b_nt) + al(b_rs) + al(b_rg) + al(b_gf);
     cudaGetDevice(&s->device);
     cudaError_t e = cudaMalloc(&s->dmem, total);
     if (e != cudaSuccess) { delete s; return cuda_fail(e, "cudaMalloc(index tables)"); }
@@ -666,8 +701,14 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     int *d_Q = (int *)base;
     base += al(b_Q);
     int *d_nt = (int *)base;
+    base += al(b_nt);
+    int *d_rs = (int *)base;
+    base += al(b_rs);
+    int *d_rg = (int *)base;
+    base += al(b_rg);
+    int *d_gf = (int *)base;
     {
-        std::vector<int> nt(h.B + 1, 0);
+        std::vector<int> nt((size_t)kNtSpan * h.B + 1, 0);
         for (int x = 1; x <= h.B; ++x) nt[x] = h.B / x;
         e = cudaMemcpy(d_nt, nt.data(), b_nt, cudaMemcpyHostToDevice);
     }
@@ -675,6 +716,14 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     if (e == cudaSuccess && !h.row_k.empty())
         e = cudaMemcpy(d_k, h.row_k.data(), h.row_k.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_qoff, h.qoff.data(), b_qoff, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        std::vector<int> rs(h.nrow + 1);
+        for (int r = 0; r < h.nrow; ++r) rs[r] = h.row_info[r].x;
+        rs[h.nrow] = (int)h.size;
+        e = cudaMemcpy(d_rs, rs.data(), b_rs, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(d_rg, h.rgrp.data(), (size_t)h.nrow * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_gf, h.gfirst.data(), (size_t)h.ngroup * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !h.Q.empty()) e = cudaMemcpy(d_Q, h.Q.data(), h.Q.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) {
         cudaFree(s->dmem);
@@ -692,6 +741,10 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     s->d.qoff = d_qoff;
     s->d.Q = d_Q;
     s->d.nt = d_nt;
+    s->d.rstart = d_rs;
+    s->d.rgrp = d_rg;
+    s->d.gfirst = d_gf;
+    s->d.ngroup = h.ngroup;
     rc = launch_elem_info(s);
     if (rc) {
         cudaFree(s->dmem);
@@ -701,6 +754,8 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     // the host copies of the row tables are no longer needed (rank/unrank use Q and qoff)
     std::vector<int4>().swap(s->h.row_info);
     std::vector<uint16_t>().swap(s->h.row_k);
+    std::vector<int>().swap(s->h.rgrp);
+    std::vector<int>().swap(s->h.gfirst);
     *out = s;
     return HX_OK;
 }
@@ -780,7 +835,7 @@ void hx_problem_destroy(hx_problem *p)
     krylov_free(p);
     cudaFree(p->tab);
     cudaFree(p->pw_values);
-    cudaFree(p->rnb);
+    cudaFree(p->gnb);
     cudaFree(p->chan);
     cudaFree(p->dscal);
     for (void *x : p->extra) cudaFree(x);

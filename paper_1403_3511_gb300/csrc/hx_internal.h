@@ -30,6 +30,9 @@ struct IndexSetHost {
     std::vector<int> Q;               // (N - 1) x qtotal
     std::vector<int4> row_info;       // nrow
     std::vector<uint16_t> row_k;      // nrow x (N - 1)
+    int ngroup;
+    std::vector<int> rgrp;            // nrow: group of each row (rows sharing k_0..k_{N-3})
+    std::vector<int> gfirst;          // ngroup: first row of each group
 };
 
 struct Problem;
@@ -74,8 +77,9 @@ struct Problem {
     size_t chan_ld;           // elements between channels
     void *jit;                // kernel compiled for the operator structure (hx_jit.cu), or null
     std::string jit_reason;   // why jit is (or is not) set
-    RowOffsets roff;          // row offsets of ops and ops1
-    int *rnb;                 // row-offset table (device), roff.n x nrow
+    RowOffsets roff;          // row offsets of ops and ops1 (and their outer moves)
+    int *gnb;                 // group-neighbour table (device), ngroup x gstride
+    int gstride;
     bool skip_diag;           // internal: omit D_K (gradient direction operators)
     void *tab;                // device row tables
     size_t tab_bytes;
@@ -96,7 +100,7 @@ int launch_apply(Problem *p, const void *cin, void *cout, const double *t_ptr, d
                  const ApplyFuse *fuse, cudaStream_t st);
 int launch_export(const IndexSetObj *s, int32_t *k_dev, cudaStream_t st);
 int launch_elem_info(const IndexSetObj *s);
-int launch_rowtab(const DevSet &S, const RowOffsets &ro, int *rnb, cudaStream_t st);
+int launch_groupnb(const DevSet &S, const RowOffsets &ro, int gstride, int *gnb, cudaStream_t st);
 int launch_norm(Problem *p, const void *c, int is_c128, double *partials, unsigned *counter, double *result,
                 cudaStream_t st);
 int apply_grid(const Problem *p);

@@ -79,49 +79,101 @@ static bool specialised_plane(const Op &op, int sb)
     return cls && (sb == 0 || sb == op.q || (sb == op.q + 2 && sb <= 3));
 }
 
-static std::string jit_body_pair(const OpSet &O);
+// Factor-order template argument of the plane stencils: 0 both orders with the runtime weights,
+// 1 P(X_a) Q(X_b) alone, 2 Q(X_b) P(X_a) alone (the literal orders, weight 1).
+static int plane_order(const OpSet &O)
+{
+    if (O.wAB == 1.0 && O.wBA == 0.0) return 1;
+    if (O.wAB == 0.0 && O.wBA == 1.0) return 2;
+    return 0;
+}
+
+static const char *role_name(int r) { return r == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW"; }
+
+// Weight expression of the line op merged into plane op i ("" when none); w = "sm_w" or "sm_w2".
+static std::string merged_weight(const OpSet &O, const Op &op, const char *w)
+{
+    if (op.mergeB < 0) return "";
+    return std::string(w) + "[" + std::to_string(op.mergeB) + "]";
+}
+
+// Compile-time row moves of operator i's footprint points (a type with the start / startx
+// functions of ColsRuntime): move (om, s4) of the column that didx gives each position.
+static std::string cols_type(const OpSet &O, const RowOffsets &ro, int i)
+{
+    const Op &op = O.op[i];
+    const int span = (2 * op.p + 1) * (2 * op.q + 1);
+    auto chain = [&](const char *name, int n, auto value) {
+        std::string f = "    __device__ static constexpr int " + std::string(name) + "(int x) { return ";
+        for (int x = 0; x < n; ++x) f += "x == " + std::to_string(x) + " ? " + std::to_string(value(x)) + " : ";
+        f += "0; }\n";
+        return f;
+    };
+    auto col = [&](int dbase, int x) { return (int)O.didx[dbase + x]; };
+    std::string t = "struct ColsK" + std::to_string(i) + " {\n";
+    t += chain("om", span, [&](int x) { return (int)ro.mv[col(op.dbase, x)].om; });
+    t += chain("s4", span, [&](int x) { return (int)ro.mv[col(op.dbase, x)].s4; });
+    if (op.kind == 2 && op.mergeB >= 0) {
+        const Op &ls = O.op[op.mergeB];
+        const int sb = ls.p;
+        t += chain("omx", 2, [&](int j) { return (int)ro.mv[col(ls.dbase, j == 0 ? 0 : 2 * sb)].om; });
+        t += chain("s4x", 2, [&](int j) { return (int)ro.mv[col(ls.dbase, j == 0 ? 0 : 2 * sb)].s4; });
+    } else {
+        t += "    __device__ static constexpr int omx(int) { return -1; }\n";
+        t += "    __device__ static constexpr int s4x(int) { return 0; }\n";
+    }
+    t += "    __device__ static __forceinline__ int start(const Ctx &c, const Elem &el, const OpSet &, const Op &, int pos, bool ok)\n"
+         "    { return c.start_mv(el, om(pos), s4(pos), ok); }\n"
+         "    __device__ static __forceinline__ int startx(const Ctx &c, const Elem &el, const OpSet &, const Op &, int j, int, bool ok)\n"
+         "    { return c.start_mv(el, omx(j), s4x(j), ok); }\n};\n";
+    return t;
+}
+
+static std::string jit_types(const OpSet &O, const RowOffsets &ro)
+{
+    std::string t;
+    for (int i = 0; i < O.nops; ++i)
+        if (O.op[i].kind >= 1 && !O.op[i].merged) t += cols_type(O, ro, i);
+    return t;
+}
 
 // The specialised sequence for O, or "" when some operator needs the generic loop.  dual: each
 // operator's sum also goes to acc2 with its weight at the second time (sm_w2).
 static std::string jit_body(const OpSet &O, bool dual = false)
 {
     std::string b;
-    char line[768];
+    char line[1024];
+    const int ord = plane_order(O);
     for (int i = 0; i < O.nops; ++i) {
         const Op &op = O.op[i];
         if (op.merged) continue;
         if (op.src >= 0 || op.dst >= 0) return "";
-        char add2[256] = "";
+        std::string add2;
         if (op.kind == 0) {
-            if (dual) snprintf(add2, sizeof(add2), " acc2.add(sm_w2[%d] * cs.x, sm_w2[%d] * cs.y);", i, i);
-            snprintf(line, sizeof(line), "    { const V cs = cin[el.e]; acc.add(sm_w[%d] * cs.x, sm_w[%d] * cs.y);%s }\n",
-                     i, i, add2);
+            if (dual) add2 = " acc2.add(cscale(sm_w2[" + std::to_string(i) + "], cs));";
+            snprintf(line, sizeof(line), "    { const V cs = cin[el.e]; acc.add(cscale(sm_w[%d], cs));%s }\n", i,
+                     add2.c_str());
         } else if (op.kind == 1) {
             if (op.cls < CLS_LINE + 1 || op.cls > CLS_LINE + 3 || op.mergeB >= 0) return "";
-            if (dual) snprintf(add2, sizeof(add2), " acc2.add(sm_w2[%d] * sx, sm_w2[%d] * sy);", i, i);
+            if (dual) add2 = " acc2.add(cscale(sm_w2[" + std::to_string(i) + "], o));";
             snprintf(line, sizeof(line),
-                     "    { R sx = 0, sy = 0; line_role<R, %d, %s>(ctx, el, O, O.op[%d], tab, cin, sx, sy);\n"
-                     "      acc.add(sm_w[%d] * sx, sm_w[%d] * sy);%s }\n",
-                     op.p, op.ra == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW", i, i, i, add2);
+                     "    { const V o = line_role<R, %d, %s, ColsK%d>(ctx, el, O, O.op[%d], tab, cin);\n"
+                     "      acc.add(cscale(sm_w[%d], o));%s }\n",
+                     op.p, role_name(op.ra), i, i, i, add2.c_str());
         } else {
             const int sb = op.mergeB >= 0 ? O.op[op.mergeB].p : 0;
             if (!specialised_plane(op, sb)) return "";
-            char wl[32], wl2[32];
-            if (sb > 0) {
-                snprintf(wl, sizeof(wl), "sm_w[%d]", op.mergeB);
-                snprintf(wl2, sizeof(wl2), "sm_w2[%d]", op.mergeB);
-            } else {
-                snprintf(wl, sizeof(wl), "(R)0");
-                snprintf(wl2, sizeof(wl2), "(R)0");
-            }
-            if (dual)
-                snprintf(add2, sizeof(add2), "\n      acc2.add(sm_w2[%d] * sx + %s * lx, sm_w2[%d] * sy + %s * ly);", i,
-                         wl2, i, wl2);
+            const std::string wl = merged_weight(O, op, "sm_w"), wl2 = merged_weight(O, op, "sm_w2");
+            const std::string v1 = wl.empty() ? "cscale(sm_w[" + std::to_string(i) + "], o)"
+                                              : "cmad(" + wl + ", l, cscale(sm_w[" + std::to_string(i) + "], o))";
+            const std::string v2 = wl2.empty() ? "cscale(sm_w2[" + std::to_string(i) + "], o)"
+                                               : "cmad(" + wl2 + ", l, cscale(sm_w2[" + std::to_string(i) + "], o))";
+            if (dual) add2 = "\n      acc2.add(" + v2 + ");";
             snprintf(line, sizeof(line),
-                     "    { R sx = 0, sy = 0, lx = 0, ly = 0;\n"
-                     "      plane_role<R, %d, %d, %s, %d>(ctx, el, O, O.op[%d], tab, cin, sx, sy, lx, ly);\n"
-                     "      acc.add(sm_w[%d] * sx + %s * lx, sm_w[%d] * sy + %s * ly);%s }\n",
-                     op.p, op.q, op.rb == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW", sb, i, i, wl, i, wl, add2);
+                     "    { V o, l;\n"
+                     "      plane_role<R, %d, %d, %s, %d, %d, ColsK%d>(ctx, el, O, O.op[%d], tab, cin, o, l);\n"
+                     "      acc.add(%s);%s }\n",
+                     op.p, op.q, role_name(op.rb), sb, ord, i, i, v1.c_str(), add2.c_str());
         }
         b += line;
     }
@@ -134,47 +186,45 @@ static std::string jit_body(const OpSet &O, bool dual = false)
 static std::string jit_body_pair(const OpSet &O)
 {
     std::string b;
-    char line[1024];
+    char line[1280];
+    const int ord = plane_order(O);
     for (int i = 0; i < O.nops; ++i) {
         const Op &op = O.op[i];
         if (op.merged) continue;
         if (op.kind == 0) {
             snprintf(line, sizeof(line),
-                     "    { const V cs = cin[el.e], cs2 = cin2[el.e]; acc.add(sm_w[%d] * cs.x, sm_w[%d] * cs.y);"
-                     " acc2.add(sm_w2[%d] * cs2.x, sm_w2[%d] * cs2.y); }\n", i, i, i, i);
+                     "    { acc.add(cscale(sm_w[%d], cin[el.e])); acc2.add(cscale(sm_w2[%d], cin2[el.e])); }\n", i, i);
         } else if (op.kind == 1) {
             snprintf(line, sizeof(line),
-                     "    { const V *sr[2] = {cin, cin2}; R sx[2] = {0, 0}, sy[2] = {0, 0};\n"
-                     "      line_role_n<R, %d, %s, 2>(ctx, el, O, O.op[%d], tab, sr, sx, sy);\n"
-                     "      acc.add(sm_w[%d] * sx[0], sm_w[%d] * sy[0]); acc2.add(sm_w2[%d] * sx[1], sm_w2[%d] * sy[1]); }\n",
-                     op.p, op.ra == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW", i, i, i, i, i);
+                     "    { const V *sr[2] = {cin, cin2}; V o[2];\n"
+                     "      line_role_n<R, %d, %s, 2, ColsK%d>(ctx, el, O, O.op[%d], tab, sr, o);\n"
+                     "      acc.add(cscale(sm_w[%d], o[0])); acc2.add(cscale(sm_w2[%d], o[1])); }\n",
+                     op.p, role_name(op.ra), i, i, i, i);
         } else {
             const int sb = op.mergeB >= 0 ? O.op[op.mergeB].p : 0;
-            char wl[32], wl2[32];
-            if (sb > 0) {
-                snprintf(wl, sizeof(wl), "sm_w[%d]", op.mergeB);
-                snprintf(wl2, sizeof(wl2), "sm_w2[%d]", op.mergeB);
-            } else {
-                snprintf(wl, sizeof(wl), "(R)0");
-                snprintf(wl2, sizeof(wl2), "(R)0");
-            }
+            const std::string wl = merged_weight(O, op, "sm_w"), wl2 = merged_weight(O, op, "sm_w2");
+            const std::string is = std::to_string(i);
+            const std::string v1 = wl.empty() ? "cscale(sm_w[" + is + "], o[0])" : "cmad(" + wl + ", l[0], cscale(sm_w[" + is + "], o[0]))";
+            const std::string v2 = wl2.empty() ? "cscale(sm_w2[" + is + "], o[1])" : "cmad(" + wl2 + ", l[1], cscale(sm_w2[" + is + "], o[1]))";
             snprintf(line, sizeof(line),
-                     "    { const V *sr[2] = {cin, cin2}; R sx[2] = {0, 0}, sy[2] = {0, 0}, lx[2] = {0, 0}, ly[2] = {0, 0};\n"
-                     "      plane_role_n<R, %d, %d, %s, %d, 2>(ctx, el, O, O.op[%d], tab, sr, sx, sy, lx, ly);\n"
-                     "      acc.add(sm_w[%d] * sx[0] + %s * lx[0], sm_w[%d] * sy[0] + %s * ly[0]);\n"
-                     "      acc2.add(sm_w2[%d] * sx[1] + %s * lx[1], sm_w2[%d] * sy[1] + %s * ly[1]); }\n",
-                     op.p, op.q, op.rb == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW", sb, i, i, wl, i, wl, i, wl2, i, wl2);
+                     "    { const V *sr[2] = {cin, cin2}; V o[2], l[2];\n"
+                     "      plane_role_n<R, %d, %d, %s, %d, 2, %d, ColsK%d>(ctx, el, O, O.op[%d], tab, sr, o, l);\n"
+                     "      acc.add(%s);\n"
+                     "      acc2.add(%s); }\n",
+                     op.p, op.q, role_name(op.rb), sb, ord, i, i, v1.c_str(), v2.c_str());
         }
         b += line;
     }
     return b;
 }
 
-static std::string jit_source(bool f32, const std::string &body, const std::string &body2, const std::string &body3)
+static std::string jit_source(bool f32, const std::string &types, const std::string &body, const std::string &body2,
+                              const std::string &body3)
 {
     std::string s;
     s += "#include \"hx_stencil.cuh\"\n";
     s += "namespace hx {\n";
+    s += types;
     s += "using R = ";
     s += f32 ? "float" : "double";
     s += ";\nusing V = Vec2<R>::T;\n";
@@ -323,12 +373,21 @@ void jit_prepare(Problem *p)
         return;
     }
     const bool f32 = p->cfg.dtype == HX_C64;
-    const std::string key = std::to_string(p->device) + (f32 ? "|f|" : "|d|") + body;
+    const std::string types = jit_types(p->ops, p->roff);
+    const std::string key = std::to_string(p->device) + (f32 ? "|f|" : "|d|") + types + body;
     std::lock_guard<std::mutex> lock(g_jit_mu);
     auto it = g_jit_cache.find(key);
     if (it == g_jit_cache.end()) {
         JitKernel k;
-        if (!compile_and_load(jit_source(f32, body, jit_body(p->ops, true), jit_body_pair(p->ops)), p->device, &k, reason))
+        // HX_JIT_SOURCE_DUMP=<file>: the generated source is written there before it is compiled
+        if (const char *dump = getenv("HX_JIT_SOURCE_DUMP")) {
+            if (FILE *f = fopen(dump, "w")) {
+                const std::string src = jit_source(f32, types, body, jit_body(p->ops, true), jit_body_pair(p->ops));
+                fwrite(src.data(), 1, src.size(), f);
+                fclose(f);
+            }
+        }
+        if (!compile_and_load(jit_source(f32, types, body, jit_body(p->ops, true), jit_body_pair(p->ops)), p->device, &k, reason))
             return;
         it = g_jit_cache.emplace(key, k).first;
     }

@@ -14,7 +14,6 @@ template <> struct Vec2<double> { using T = double2; };
 
 struct ApplyArgs : ApplyArgsBase {
     OpSet ops;
-    int nrow;                  // row-offset table stride
     const void *cin;
     void *cout;
     const double *out_scale;   // nullptr = 1
@@ -133,39 +132,135 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = (a - (s - bb)) + (b - bb);
 }
 
+// Packed pairs of FP32 values: one instruction applies the IEEE round-to-nearest operation to both
+// halves (the complex64 re/im pair), so a complex-times-real multiply-add or a complex TwoSum step
+// costs one instruction instead of two.
+union F2Bits {
+    float2 f;
+    unsigned long long u;
+};
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c)
+{
+    F2Bits x, y, z, r;
+    x.f = a;
+    y.f = b;
+    z.f = c;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.u) : "l"(x.u), "l"(y.u), "l"(z.u));
+    return r.f;
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b)
+{
+    F2Bits x, y, r;
+    x.f = a;
+    y.f = b;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(x.u), "l"(y.u));
+    return r.f;
+}
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b)
+{
+    F2Bits x, y, r;
+    x.f = a;
+    y.f = b;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(x.u), "l"(y.u));
+    return r.f;
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b)
+{
+    F2Bits x, y, r;
+    x.f = a;
+    y.f = b;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(x.u), "l"(y.u));
+    return r.f;
+}
+
+// acc + w v for a complex v and a real weight w
+__device__ __forceinline__ float2 cmad(float w, float2 v, float2 acc) { return f2_fma(make_float2(w, w), v, acc); }
+__device__ __forceinline__ double2 cmad(double w, double2 v, double2 acc)
+{
+    return make_double2(fma(w, v.x, acc.x), fma(w, v.y, acc.y));
+}
+__device__ __forceinline__ float2 cscale(float w, float2 v) { return f2_mul(make_float2(w, w), v); }
+__device__ __forceinline__ double2 cscale(double w, double2 v) { return make_double2(w * v.x, w * v.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return f2_add(a, b); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V czero();
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+
 template <typename R> struct Acc;
 template <> struct Acc<double> {
-    double x = 0.0, y = 0.0;
-    __device__ void add(double a, double b) { x += a; y += b; }
-    __device__ double2 get() const { return make_double2(x, y); }
+    double2 s = {0.0, 0.0};
+    __device__ void add(double2 a) { s.x += a.x; s.y += a.y; }
+    __device__ void add(double a, double b) { s.x += a; s.y += b; }
+    __device__ double2 get() const { return s; }
 };
 template <> struct Acc<float> {   // compensated accumulation of the operator contributions
-    float x = 0.f, y = 0.f, ex = 0.f, ey = 0.f;
-    __device__ void add(float a, float b)
+    float2 s = {0.f, 0.f}, e = {0.f, 0.f};
+    // TwoSum on both halves at once: s + err == s_old + a exactly, err summed separately
+    __device__ void add(float2 a)
     {
-        float s, e;
-        two_sum(x, a, s, e); x = s; ex += e;
-        two_sum(y, b, s, e); y = s; ey += e;
+        const float2 t = f2_add(s, a), bb = f2_sub(t, s);
+        const float2 err = f2_add(f2_sub(s, f2_sub(t, bb)), f2_sub(a, bb));
+        s = t;
+        e = f2_add(e, err);
     }
-    __device__ float2 get() const { return make_float2(x + ex, y + ey); }
+    __device__ void add(float a, float b) { add(make_float2(a, b)); }
+    __device__ float2 get() const { return f2_add(s, e); }
 };
 
 // Per-thread view of one output element.
 struct Elem {
     int e;                  // rank
-    int k2;                 // last coordinate k_{N-1}
+    int j;                  // last coordinate k_{N-1}
     int qall;               // prod_l (1 + k_l)
+    int ksum;               // sum_l k_l
     int rlen;               // length of the own row
-    const int *nb;          // row-offset table at the own row (column d at nb[d * nrow])
+    int r;                  // own row
+    int k4;                 // k_{N-2} (0 for N = 1)
     const unsigned short *kr;     // prefix k_0..k_{N-2} of the own row
+    const int *gn;                // group-neighbour table row of the own group
 };
 
 struct Ctx {
     const DevSet *S;
-    int nrow;
-    __device__ int k(const Elem &el, int l) const { return l == S->N - 1 ? el.k2 : (int)__ldg(el.kr + l); }
-    // start rank of the row reached by row offset d (d > 0; the point must lie in K)
-    __device__ int row(const Elem &el, int d) const { return __ldg(el.nb + (size_t)d * nrow); }
+    const RowMove *mv;
+    __device__ int k(const Elem &el, int l) const
+    {
+        return l == S->N - 1 ? el.j : (l == S->N - 2 ? el.k4 : (int)__ldg(el.kr + l));
+    }
+    // Start rank of the row reached from the own row by the row move m when ok (the point lies in
+    // K, so that row exists); the start of the own row otherwise.  The group-neighbour entry is
+    // read whatever ok (its slot is always valid); only the row index is selected.
+    __device__ __forceinline__ int start_mv(const Elem &el, int om, int s4, bool ok) const
+    {
+        int row = el.r + s4;
+        if (om >= 0) row = __ldg(el.gn + om) + el.k4 + s4;
+        return __ldg(S->rstart + (ok ? row : el.r));
+    }
+    // the same for row-offset column d
+    __device__ __forceinline__ int start(const Elem &el, int d, bool ok) const
+    {
+        const RowMove m = mv[d];
+        return start_mv(el, m.om, m.s4, ok);
+    }
+};
+
+// Row moves of an operator's footprint points, read at run time from the operator list (the
+// generic kernel); the kernels compiled per potential use generated types with the same two
+// functions whose moves are compile-time constants.  pos: footprint position of the point
+// ((s + p) (2 q + 1) + (s2 + q)); startx: the merged line op's points s2 = -SB, SB.
+struct ColsRuntime {
+    __device__ static __forceinline__ int start(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, int pos,
+                                                bool ok)
+    {
+        return c.start(el, O.didx[op.dbase + pos], ok);
+    }
+    __device__ static __forceinline__ int startx(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, int j,
+                                                 int sb, bool ok)
+    {
+        const Op &ls = O.op[op.mergeB];
+        return c.start(el, O.didx[ls.dbase + (j == 0 ? 0 : 2 * sb)], ok);
+    }
 };
 
 // floor(B / x) for x >= 1 from the table (0 when x > B: no element has those coordinates).
@@ -185,36 +280,47 @@ __device__ __forceinline__ Row4<double> load_row4(const double *p)
 }
 
 // The specialised stencils below issue every load of an operator unconditionally: a footprint
-// point outside K reads the row-offset table at its (always valid) slot and gathers the output
-// element itself, and gets weight 0.  Without branches around them, all loads of an operator are
-// in flight together instead of one dependent pair (table, gather) after another.  This pays for
-// degrees <= 3; at degree 8 on short fibres most points lie outside K and the loads they would
-// waste cost more than the overlap gains, so those operators keep the branching generic loop.
+// point outside K reads the group-neighbour table at its (always valid) slot and gathers the
+// output element itself.  Its weight is then zero without a mask: the tabulated rows of P(J_n / L)
+// are zero at the columns outside the fibre (below 0 or at or above n), and every path through a
+// point outside K meets such an entry.  Without branches around them, all loads of an operator
+// are in flight together instead of one dependent pair (table, gather) after another.  This pays
+// for degrees <= 3; at degree 8 on short fibres most points lie outside K and the loads they
+// would waste cost more than the overlap gains, so those operators keep the branching generic loop.
+//
+// Membership and fibre tops come from integer products only: with r = prod over the other axes
+// of (1 + k_l), the point k + u e_a + v e_b lies in K iff its coordinates are >= 0 and
+// r (1 + k_a + u)(1 + k_b + v) <= B (no overflow: the product is at most 16 B for |u|, |v| <= 3).
 
 // Line operator P(X_a), P of pure parity and degree P (offsets -P, -P+2, ..., P), axis role RA,
-// applied to NSRC inputs at once (the addresses and weights are shared): sx[s], sy[s] get the sum
-// for srcs[s].
-template <typename R, int P, int RA, int NSRC>
+// applied to NSRC inputs at once (the addresses and weights are shared): out[q] = P(X_a) srcs[q]
+// at the element.
+template <typename R, int P, int RA, int NSRC, typename CM = ColsRuntime>
 __device__ __forceinline__ void line_role_n(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
-                                            const typename Vec2<R>::T *const (&srcs)[NSRC], R (&sx)[NSRC],
-                                            R (&sy)[NSRC])
+                                            const typename Vec2<R>::T *const (&srcs)[NSRC],
+                                            typename Vec2<R>::T (&out)[NSRC])
 {
     using V = typename Vec2<R>::T;
-    const DevSet &S = *c.S;
-    const int ka = RA == ROLE_LAST ? el.k2 : c.k(el, op.a);
-    // steps to the top of the a-fibre (>= 0: the element itself is in K)
-    const int top = RA == ROLE_LAST ? el.rlen - 1 - el.k2 : nt_of(S, exact_div(el.qall, 1 + ka)) - 1 - ka;
-    const Row4<R> row = load_row4(tab + op.ptabP + (ka * (P + 1) + min(P, top)) * 4);   // entries at s = -P + 2j
+    const int ka = RA == ROLE_LAST ? el.j : c.k(el, op.a);
+    // steps from k to the top of its a-fibre, capped at P
+    int top;
+    if (RA == ROLE_LAST) {
+        top = min(P, el.rlen - 1 - el.j);
+    } else {
+        const int other = exact_div(el.qall, 1 + ka), slack = c.S->B - el.qall;
+        top = 0;
+#pragma unroll
+        for (int t = 1; t <= P; ++t) top += other * t <= slack ? 1 : 0;
+    }
+    const Row4<R> row = load_row4(tab + op.ptabP + (ka * (P + 1) + top) * 4);   // entries at s = -P + 2j
     constexpr int NP = P + 1;
     int addr[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         const int s = -P + 2 * j;
         const bool ok = ka + s >= 0 && s <= top;
-        int a;
-        if (RA == ROLE_LAST) a = el.e + s;
-        else a = s == 0 ? el.e : c.row(el, O.didx[op.dbase + s + P]) + el.k2;
-        addr[j] = ok ? a : el.e;
+        if (RA == ROLE_LAST) addr[j] = ok ? el.e + s : el.e;
+        else addr[j] = s == 0 ? el.e : CM::start(c, el, O, op, s + P, ok) + el.j;
     }
     V v[NSRC][NP];
 #pragma unroll
@@ -222,85 +328,89 @@ __device__ __forceinline__ void line_role_n(const Ctx &c, const Elem &el, const 
 #pragma unroll
         for (int j = 0; j < NP; ++j) v[q][j] = srcs[q][addr[j]];
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        const int s = -P + 2 * j;
-        const R w = (ka + s >= 0 && s <= top) ? row.v[j] : (R)0;
+    for (int q = 0; q < NSRC; ++q) {
+        V acc = czero<V>();
 #pragma unroll
-        for (int q = 0; q < NSRC; ++q) {
-            sx[q] += w * v[q][j].x;
-            sy[q] += w * v[q][j].y;
-        }
+        for (int j = 0; j < NP; ++j) acc = cmad(row.v[j], v[q][j], acc);
+        out[q] = acc;
     }
 }
 
-template <typename R, int P, int RA>
-__device__ __forceinline__ void line_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
-                                          const typename Vec2<R>::T *src, R &sx, R &sy)
+template <typename R, int P, int RA, typename CM = ColsRuntime>
+__device__ __forceinline__ typename Vec2<R>::T line_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op,
+                                                         const R *tab, const typename Vec2<R>::T *src)
 {
     const typename Vec2<R>::T *srcs[1] = {src};
-    R x[1] = {sx}, y[1] = {sy};
-    line_role_n<R, P, RA, 1>(c, el, O, op, tab, srcs, x, y);
-    sx = x[0];
-    sy = y[0];
+    typename Vec2<R>::T out[1];
+    line_role_n<R, P, RA, 1, CM>(c, el, O, op, tab, srcs, out);
+    return out[0];
 }
 
-// Plane operator wAB P(X_a) Q(X_b) + wBA Q(X_b) P(X_a), pure parities, degrees P, Q; a is a prefix
-// axis, b has role RB.  A footprint point k + s e_a + s2 e_b carries [P]_{k, k+s e_a}
-// [Q]_{k+s e_a, k+s e_a+s2 e_b} (path through k + s e_a) and [Q]_{k, k+s2 e_b} [P]_{k+s2 e_b,
-// k+s2 e_b+s e_a} (path through k + s2 e_b); a path exists only if its intermediate point is in K.
-// Rows of P(J_n / L) and Q(J_n / L) come from the tables, indexed by the coordinate and the
-// distance to the fibre top.
+// Plane operator wAB P(X_a) Q(X_b) + wBA Q(X_b) P(X_a), pure parities, degrees P, Q <= 2; a is a
+// prefix axis, b has role RB.  Evaluated factor by factor:
+//   AB: sum_s [P]_{k, k+s e_a} sum_s2 [Q]_{k+s e_a, k+s e_a+s2 e_b} c(k + s e_a + s2 e_b),
+//   BA: sum_s2 [Q]_{k, k+s2 e_b} sum_s [P]_{k+s2 e_b, k+s2 e_b+s e_a} c(k + s e_a + s2 e_b),
+// with the rows of P(J_n / L) and Q(J_n / L) taken from the tables by coordinate and distance to
+// the fibre top (a path through an intermediate point outside K meets a zero entry).  ORD = 0:
+// both orders with the weights wAB, wBA of O; 1: AB only (weight 1); 2: BA only (weight 1).
 // SB > 0: a line operator S(X_b) of degree SB (parity of Q, SB = Q or Q + 2) merged into this op
-// (P is even, so the points s = 0 are footprint points); its sum goes to (lx, ly), which the
-// caller weights with the line operator's own weight.  NSRC inputs at once (addresses, fibre tops
-// and weights shared): the sums for srcs[q] go to sx[q], sy[q], lx[q], ly[q].
-template <typename R, int P, int Q, int RB, int SB, int NSRC>
+// (P is even, so the points s = 0 are footprint points); its sum goes to lout.  NSRC inputs at once
+// (addresses, fibre tops and weights shared): the sums for srcs[q] go to out[q] and lout[q].
+template <typename R, int P, int Q, int RB, int SB, int NSRC, int ORD = 0, typename CM = ColsRuntime>
 __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
-                                             const typename Vec2<R>::T *const (&srcs)[NSRC], R (&sx)[NSRC],
-                                             R (&sy)[NSRC], R (&lx)[NSRC], R (&ly)[NSRC])
+                                             const typename Vec2<R>::T *const (&srcs)[NSRC],
+                                             typename Vec2<R>::T (&out)[NSRC], typename Vec2<R>::T (&lout)[NSRC])
 {
     using V = typename Vec2<R>::T;
-    const DevSet &S = *c.S;
+    const int B = c.S->B;
     const int ka = c.k(el, op.a);
-    const int kb = RB == ROLE_LAST ? el.k2 : c.k(el, op.b);
+    const int kb = RB == ROLE_LAST ? el.j : c.k(el, op.b);
     const int rab = exact_div(el.qall, (1 + ka) * (1 + kb));
-    const R wAB = (R)O.wAB, wBA = (R)O.wBA;
     const R *tP = tab + op.ptabP, *tQ = tab + op.ptabQ;   // packed rows: entry i at offset -P + 2i
     constexpr int NS = P + 1, NS2 = Q + 1;         // offsets s = -P + 2i, s2 = -Q + 2j
-    // a-fibre tops at k + s2 e_b (-1: that point is not in K), b-fibre tops at k + s e_a
-    int topA[NS2], topB[NS];
+    constexpr int TB = SB > Q ? SB : Q;            // b-distances needed at k
+    // k + u e_a + v e_b in K (u, v compile-time after unrolling: a point with no positive step
+    // lies in K iff its coordinates are >= 0, K being downward closed)
+    auto in_k = [&](int u, int v) {
+        bool r = true;
+        if (u < 0) r = r && ka + u >= 0;
+        if (v < 0) r = r && kb + v >= 0;
+        if (u > 0 || v > 0) r = r && rab * (1 + ka + u) * (1 + kb + v) <= B;
+        return r;
+    };
+    // the row of k + s e_a exists (RB = LAST: its prefix is in K)
+    auto row_in_k = [&](int s) { return s < 0 ? ka + s >= 0 : (s == 0 || rab * (1 + ka + s) <= B); };
+    // distances to the a-fibre top at k + s2 e_b and to the b-fibre top at k + s e_a (0 when that
+    // point is not in K: no step from it stays in K)
+    auto topA = [&](int s2) {
+        int d = 0;
 #pragma unroll
-    for (int j = 0; j < NS2; ++j) {
-        const int s2 = -Q + 2 * j;
-        topA[j] = kb + s2 >= 0 ? nt_of(S, rab * (1 + kb + s2)) - 1 - ka : -1;
-    }
+        for (int t = 1; t <= P; ++t) d += in_k(t, s2) ? 1 : 0;
+        return d;
+    };
+    auto topB = [&](int s, int cap) {
+        int d = 0;
 #pragma unroll
-    for (int i = 0; i < NS; ++i) {
-        const int s = -P + 2 * i;
-        topB[i] = ka + s >= 0 ? nt_of(S, rab * (1 + ka + s)) - 1 - kb : -1;
-    }
-    // fibre tops at k itself (s = 0 or s2 = 0 need not be footprint offsets)
-    const int topA0 = (Q & 1) ? nt_of(S, rab * (1 + kb)) - 1 - ka : topA[Q / 2];
-    const int topB0 = RB == ROLE_LAST ? el.rlen - 1 - el.k2 : ((P & 1) ? nt_of(S, rab * (1 + ka)) - 1 - kb : topB[P / 2]);
-    const Row4<R> rowP0 = load_row4(tP + (ka * (P + 1) + min(P, topA0)) * 4);   // P row at k
-    const Row4<R> rowQ0 = load_row4(tQ + (kb * (Q + 1) + min(Q, topB0)) * 4);   // Q row at k
+        for (int t = 1; t <= TB; ++t) d += (t <= cap && in_k(s, t)) ? 1 : 0;
+        return d;
+    };
     // addresses of the footprint points (own element when the point is not in K)
     int addr[NS][NS2];
-    const int own = el.e - el.k2;                       // start of the own row
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         const int s = -P + 2 * i;
-        int base_s = own;                               // RB = LAST: start of the row of k + s e_a
-        if (RB == ROLE_LAST && s != 0) base_s = c.row(el, O.didx[op.dbase + (s + P) * (2 * Q + 1) + Q]);
+        int base_s = el.e - el.j;                       // RB = LAST: start of the row of k + s e_a
+        if (RB == ROLE_LAST && s != 0)
+            base_s = CM::start(c, el, O, op, (s + P) * (2 * Q + 1) + Q, row_in_k(s));
 #pragma unroll
         for (int j = 0; j < NS2; ++j) {
             const int s2 = -Q + 2 * j;
-            const bool ok = ka + s >= 0 && kb + s2 >= 0 && s <= topA[j];
+            const bool ok = in_k(s, s2);
             int a;
-            if (RB == ROLE_LAST) a = base_s + el.k2 + s2;
+            if (RB == ROLE_LAST) a = ok ? base_s + el.j + s2 : el.e;
             else if (s == 0 && s2 == 0) a = el.e;
-            else a = c.row(el, O.didx[op.dbase + (s + P) * (2 * Q + 1) + (s2 + Q)]) + el.k2;
-            addr[i][j] = ok ? a : el.e;
+            else a = CM::start(c, el, O, op, (s + P) * (2 * Q + 1) + (s2 + Q), ok) + el.j;
+            addr[i][j] = a;
         }
     }
     constexpr int NX = SB > Q ? 2 : 0;                  // merged line points +-SB outside the plane footprint
@@ -308,15 +418,14 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
         const int s2 = j == 0 ? -SB : SB;
-        const bool ok = kb + s2 >= 0 && s2 <= topB0;
+        const bool ok = in_k(0, s2);
         int a;
         if (RB == ROLE_LAST) {
-            a = el.e + s2;
+            a = ok ? el.e + s2 : el.e;
         } else {
-            const Op &ls = O.op[op.mergeB];
-            a = c.row(el, O.didx[ls.dbase + s2 + SB]) + el.k2;
+            a = CM::startx(c, el, O, op, j, SB, ok) + el.j;
         }
-        xaddr[j] = ok ? a : el.e;
+        xaddr[j] = a;
     }
     V v[NSRC][NS][NS2];
 #pragma unroll
@@ -330,66 +439,80 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
     for (int q = 0; q < NSRC; ++q)
 #pragma unroll
         for (int j = 0; j < NX; ++j) xv[q][j] = srcs[q][xaddr[j]];
-    // weights
-    Row4<R> rowS0 = {};
-    if (SB > 0) {
-        const Op &ls = O.op[op.mergeB];
-        rowS0 = load_row4(tab + ls.ptabP + (kb * (SB + 1) + min(SB, topB0)) * 4);   // entry at s2: (s2 + SB) / 2
-    }
-    Row4<R> rowPs[NS2];                                 // P rows at k + s2 e_b
+    const int dB0 = topB(0, TB);                        // b-distance at k, capped at max(Q, SB)
 #pragma unroll
-    for (int j = 0; j < NS2; ++j) rowPs[j] = load_row4(tP + (ka * (P + 1) + max(0, min(P, topA[j]))) * 4);
+    for (int q = 0; q < NSRC; ++q) out[q] = czero<V>();
+    if (ORD != 2) {   // P(X_a) (Q(X_b) c)
+        const Row4<R> rowP0 = load_row4(tP + (ka * (P + 1) + topA(0)) * 4);
+        Row4<R> rowQs[NS];
 #pragma unroll
-    for (int i = 0; i < NS; ++i) {
-        const int s = -P + 2 * i;
-        const bool inA = ka + s >= 0 && s <= topA0;             // k + s e_a in K
-        const R pj = inA ? rowP0.v[i] : (R)0;
-        const Row4<R> rowQs = load_row4(tQ + (kb * (Q + 1) + max(0, min(Q, topB[i]))) * 4);   // Q row at k + s e_a
-#pragma unroll
-        for (int j = 0; j < NS2; ++j) {
-            const int s2 = -Q + 2 * j;
-            const bool ok = ka + s >= 0 && kb + s2 >= 0 && s <= topA[j];
-            const R cab = inA ? pj * rowQs.v[j] : (R)0;                                   // path via k + s e_a
-            const R cba = (kb + s2 >= 0 && s2 <= topB0) ? rowQ0.v[j] * rowPs[j].v[i] : (R)0;   // path via k + s2 e_b
-            const R w = ok ? wAB * cab + wBA * cba : (R)0;
-#pragma unroll
-            for (int q = 0; q < NSRC; ++q) {
-                sx[q] += w * v[q][i][j].x;
-                sy[q] += w * v[q][i][j].y;
-            }
-            if (SB > 0 && s == 0) {                     // k + s2 e_b is also a point of the merged line op
-                const R ws = ok ? rowS0.v[(s2 + SB) / 2] : (R)0;
-#pragma unroll
-                for (int q = 0; q < NSRC; ++q) {
-                    lx[q] += ws * v[q][i][j].x;
-                    ly[q] += ws * v[q][i][j].y;
-                }
-            }
+        for (int i = 0; i < NS; ++i) {
+            const int s = -P + 2 * i;
+            const int d = s == 0 ? min(Q, dB0) : topB(s, Q);
+            rowQs[i] = load_row4(tQ + (kb * (Q + 1) + d) * 4);
         }
-    }
-#pragma unroll
-    for (int j = 0; j < NX; ++j) {
-        const int s2 = j == 0 ? -SB : SB;
-        const R ws = (kb + s2 >= 0 && s2 <= topB0) ? rowS0.v[(s2 + SB) / 2] : (R)0;
 #pragma unroll
         for (int q = 0; q < NSRC; ++q) {
-            lx[q] += ws * xv[q][j].x;
-            ly[q] += ws * xv[q][j].y;
+            V ab = czero<V>();
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                V u = czero<V>();
+#pragma unroll
+                for (int j = 0; j < NS2; ++j) u = cmad(rowQs[i].v[j], v[q][i][j], u);
+                ab = cmad(rowP0.v[i], u, ab);
+            }
+            out[q] = ORD == 0 ? cscale((R)O.wAB, ab) : ab;
         }
+    }
+    if (ORD != 1) {   // Q(X_b) (P(X_a) c)
+        const Row4<R> rowQ0 = load_row4(tQ + (kb * (Q + 1) + min(Q, dB0)) * 4);
+        Row4<R> rowPs[NS2];
+#pragma unroll
+        for (int j = 0; j < NS2; ++j) rowPs[j] = load_row4(tP + (ka * (P + 1) + topA(-Q + 2 * j)) * 4);
+#pragma unroll
+        for (int q = 0; q < NSRC; ++q) {
+            V ba = czero<V>();
+#pragma unroll
+            for (int j = 0; j < NS2; ++j) {
+                V w = czero<V>();
+#pragma unroll
+                for (int i = 0; i < NS; ++i) w = cmad(rowPs[j].v[i], v[q][i][j], w);
+                ba = cmad(rowQ0.v[j], w, ba);
+            }
+            out[q] = ORD == 0 ? cmad((R)O.wBA, ba, out[q]) : ba;
+        }
+    }
+    if (SB > 0) {   // the merged line op: points k + s2 e_b, s2 = -SB, -SB + 2, ..., SB
+        const Op &ls = O.op[op.mergeB];
+        const Row4<R> rowS0 = load_row4(tab + ls.ptabP + (kb * (SB + 1) + min(SB, dB0)) * 4);   // entry (s2 + SB) / 2
+#pragma unroll
+        for (int q = 0; q < NSRC; ++q) {
+            V l = czero<V>();
+#pragma unroll
+            for (int j = 0; j < NS2; ++j) {
+                const int s2 = -Q + 2 * j;
+                l = cmad(rowS0.v[(s2 + SB) / 2], v[q][P / 2][j], l);   // s = 0 is column P / 2
+            }
+#pragma unroll
+            for (int j = 0; j < NX; ++j) l = cmad(rowS0.v[j == 0 ? 0 : SB], xv[q][j], l);
+            lout[q] = l;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NSRC; ++q) lout[q] = czero<V>();
     }
 }
 
-template <typename R, int P, int Q, int RB, int SB>
+template <typename R, int P, int Q, int RB, int SB, int ORD = 0, typename CM = ColsRuntime>
 __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
-                                           const typename Vec2<R>::T *src, R &sx, R &sy, R &lx, R &ly)
+                                           const typename Vec2<R>::T *src, typename Vec2<R>::T &out,
+                                           typename Vec2<R>::T &lout)
 {
     const typename Vec2<R>::T *srcs[1] = {src};
-    R x[1] = {sx}, y[1] = {sy}, u[1] = {lx}, w[1] = {ly};
-    plane_role_n<R, P, Q, RB, SB, 1>(c, el, O, op, tab, srcs, x, y, u, w);
-    sx = x[0];
-    sy = y[0];
-    lx = u[0];
-    ly = w[0];
+    typename Vec2<R>::T o[1], l[1];
+    plane_role_n<R, P, Q, RB, SB, 1, ORD, CM>(c, el, O, op, tab, srcs, o, l);
+    out = o[0];
+    lout = l[0];
 }
 
 
@@ -442,17 +565,21 @@ __device__ __forceinline__ void add_projections(const ApplyArgs &args, int nd, i
     hs = t;
 }
 
-// The per-thread view of element e from its record er = {row, prod (1 + k_l), sum k_l,
+// The per-thread view of element e from its record er = {row, group, prod (1 + k_l) | sum k_l << 16,
 // k_{N-1} | row length << 16}.
 __device__ __forceinline__ Elem make_elem(const ApplyArgs &args, int e, int4 er)
 {
     Elem el;
+    const int N = args.S.N;
     el.e = e;
-    el.k2 = er.w & 0xffff;
-    el.qall = er.y;
+    el.j = er.w & 0xffff;
     el.rlen = (int)((unsigned)er.w >> 16);
-    el.nb = args.rnb + er.x;
-    el.kr = args.S.row_k + (size_t)er.x * (args.S.N - 1);
+    el.qall = er.z & 0xffff;
+    el.ksum = (int)((unsigned)er.z >> 16);
+    el.r = er.x;
+    el.kr = args.S.row_k + (size_t)er.x * (N - 1);
+    el.k4 = N >= 2 ? (int)__ldg(el.kr + N - 2) : 0;
+    el.gn = args.gnb + (size_t)er.y * args.gstride;
     return el;
 }
 
@@ -469,15 +596,13 @@ __device__ __forceinline__ typename Vec2<R>::T apply_element(const ApplyArgs &ar
     const Elem el = make_elem(args, e, er);
     Acc<R> acc;
     if (!args.stage1 && !args.skip_diag) {
-        const V ce = cin[e];
-        const R dj = (R)er.z + (R)0.5 * (R)S.N;   // (D_K)_jj = sum_l (j_l + 1/2)
-        acc.add(dj * ce.x, dj * ce.y);
+        const R dj = (R)el.ksum + (R)0.5 * (R)S.N;   // (D_K)_jj = sum_l (j_l + 1/2)
+        acc.add(cscale(dj, cin[e]));
     }
     body(ctx, el, acc, sm_w, cin, (const R *)args.tab);
     V y = acc.get();
     if (!args.stage1) {
-        y.x *= oscale;
-        y.y *= oscale;
+        y = cscale(oscale, y);
         ((V *)args.cout)[e] = y;
     }
     return y;
@@ -500,7 +625,7 @@ __device__ __forceinline__ void apply_elements(const ApplyArgs &args, Body body)
     __syncthreads();
     Ctx ctx;
     ctx.S = &S;
-    ctx.nrow = args.nrow;
+    ctx.mv = args.mv;
     const int stride = gridDim.x * blockDim.x;
     if constexpr (!DOTS) {
         for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.size; e += stride)
@@ -568,7 +693,7 @@ __device__ __forceinline__ void apply_elements_dual(const ApplyArgs &args, Body 
     __syncthreads();
     Ctx ctx;
     ctx.S = &S;
-    ctx.nrow = args.nrow;
+    ctx.mv = args.mv;
     const V *cin = (const V *)args.cin;
     const V *cin2 = args.cin2 ? (const V *)args.cin2 : cin;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.size; e += gridDim.x * blockDim.x) {
@@ -576,17 +701,12 @@ __device__ __forceinline__ void apply_elements_dual(const ApplyArgs &args, Body 
         const Elem el = make_elem(args, e, er);
         Acc<R> acc, acc2;
         if (!args.skip_diag) {
-            const V ce = cin[e], ce2 = cin2[e];
-            const R dj = (R)er.z + (R)0.5 * (R)S.N;
-            acc.add(dj * ce.x, dj * ce.y);
-            acc2.add(dj * ce2.x, dj * ce2.y);
+            const R dj = (R)el.ksum + (R)0.5 * (R)S.N;
+            acc.add(cscale(dj, cin[e]));
+            acc2.add(cscale(dj, cin2[e]));
         }
         body(ctx, el, acc, acc2, (const R *)sm_w, (const R *)sm_w2, cin, cin2, (const R *)args.tab);
-        V y = acc.get(), y2 = acc2.get();
-        y.x *= oscale;
-        y.y *= oscale;
-        y2.x *= oscale;
-        y2.y *= oscale;
+        const V y = cscale(oscale, acc.get()), y2 = cscale(oscale, acc2.get());
         if (args.mag_g != 0.0) {
             const V a = cin[e], b = cin2[e];
             const R g = (R)args.mag_g, half = (R)0.5;

@@ -13,6 +13,7 @@ constexpr int kMaxDeg = 8;                     // HX_MAX_DEG
 constexpr int kSpan = 2 * kMaxDeg + 1;         // offsets -deg..deg
 constexpr int kMaxKrylov = 32;
 constexpr int kApplyThreads = 256;
+constexpr int kNtSpan = 16;          // the floor(B / x) table covers x <= kNtSpan B (products of shifted points)
 constexpr int kMaxFusedDots = 8;     // projections one product launch can compute (Krylov steps m <= 8)
 
 // time modulations (values of hx_mod_kind)
@@ -30,15 +31,23 @@ enum { MOD_CONST = 0, MOD_COS = 1, MOD_SIN2 = 2, MOD_PWCONST = 3 };
 //   Q_m(q, k) = sum_{i<k} |K_m(floor(B / (q (1 + i))))|,   0 <= k <= floor(B / q),
 // stored at Q[(m - 1) * qtotal + qoff[q] + k].  Then
 //   rank(k) = sum_{d<N-1} Q_{N-1-d}(q_d, k_d) + k_{N-1},   q_d = prod_{l<d} (1 + k_l).
+// A group is the set of rows sharing k_0, ..., k_{N-3} (one group when N <= 2); its rows are
+// consecutive, row k_{N-2} of the group being row gfirst[g] + k_{N-2}.  The row index of a prefix is
+//   row(p) = sum_{d<N-2} Q_{N-2-d}(q_d, p_d) + p_{N-2}
+// (the same tables one level up: Q_m counts the rows below a subtree as |K_m|).
 // ---------------------------------------------------------------------------------------
 struct DevSet {
-    int N, B, size, nrow, qtotal;
+    int N, B, size, nrow, qtotal, ngroup;
     const int4 *row_info;             // nrow: {start rank, q(p), sum_l p_l, length}
     const unsigned short *row_k;            // nrow x (N - 1) prefixes
-    const int4 *elem;                 // size: per element {row, prod_l (1 + k_l), sum_l k_l, k_{N-1} | row length << 16}
+    const int4 *elem;                 // size: per element {row, group, prod_l (1 + k_l) | sum_l k_l << 16,
+                                      //                    k_{N-1} | row length << 16}
+    const int *rstart;                // nrow + 1: start rank of each row, rstart[nrow] = size
+    const int *rgrp;                  // nrow: group of each row
+    const int *gfirst;                // ngroup: first row of each group
     const int *qoff;                  // B + 2
     const int *Q;                     // (N - 1) x qtotal
-    const int *nt;                    // nt[x] = floor(B / x), x = 1..B (nt[0] unused)
+    const int *nt;                    // nt[x] = floor(B / x) for 0 < x <= kNtSpan B, nt[0] = 0
 };
 
 // ---------------------------------------------------------------------------------------
@@ -89,21 +98,33 @@ struct OpSet {
 };
 
 // Row offsets used by a problem's operators: axis0, step0, axis1, step1 (axis -1 = none), over
-// the prefix axes 0..N-2; offset 0 is the zero offset.  The row-offset table holds, for
-// offset d and row r, the start rank of row r + offset d, or -1 when that prefix is not in K:
-//   rnb[d * nrow + r].
+// the prefix axes 0..N-2; offset 0 is the zero offset.  Each offset is split into its move on the
+// group axes 0..N-3 (an "outer move", om >= 0, or none, om = -1) and its step s4 on axis N-2.  The
+// group-neighbour table holds, for group g and outer move om, the first row of the group reached,
+// or -1 when that group is not in K:  gnb[g * gstride + om].  The row of a prefix p moved by
+// offset d is then gnb[g(p) * gstride + om(d)] + p_{N-2} + s4(d) (om(d) >= 0) or row(p) + s4(d).
+struct RowMove {
+    short om;                 // outer move (-1: none)
+    short s4;                 // step on axis N-2
+};
+
 struct RowOffsets {
     int n;
     signed char d[kMaxDelta][4];
+    RowMove mv[kMaxDelta];    // decomposition of each offset
+    int nom;                  // outer moves
+    signed char om[kMaxDelta][4];   // axis0, step0, axis1, step1 of each outer move (axes < N-2)
 };
 
 struct ApplyArgsBase {
     DevSet S;
-    const int *rnb;           // row-offset table, nd x nrow
+    const int *gnb;           // group-neighbour table, ngroup x gstride
+    int gstride;
     const double *t_ptr;      // device time
     double t_shift;           // A is evaluated at *t_ptr + t_shift
     const double *pw_values;  // device
     const void *tab;          // row tables (float or double)
+    RowMove mv[kMaxDelta];    // per row-offset column: outer move and step on axis N-2
 };
 
 }  // namespace hx

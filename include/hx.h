@@ -120,6 +120,11 @@ typedef struct {
     int m;                         /* Lanczos steps per time step, 1 <= m <= 32 */
     void *stream;                  /* cudaStream_t, 0 for the legacy default stream */
     int scheme;                    /* hx_scheme */
+    double tol;                    /* 0: every step is one Lanczos exponential of m steps.  > 0: each
+                                    * step of hx_step is split into sub-steps until the a-posteriori
+                                    * estimate of the relative error of every sub-step's Lanczos
+                                    * exponential, |h| beta_m |e_m^T exp(-ihT_m) e_1| (Sec. 2.2),
+                                    * is at most tol (hx_step_substeps reports the counts) */
 } hx_config;
 
 typedef struct hx_indexset hx_indexset;
@@ -227,6 +232,15 @@ HX_API int hx_step_reinterp(hx_problem *p, void *c, double dt, int nsteps, hx_po
 /* Synchronises the stream and reports the last step: Lanczos size used, alpha/beta of T_m
  * (host arrays of at least m and m-1 doubles, either may be NULL) and the norm of c. */
 HX_API int hx_step_info(hx_problem *p, int *m_used, double *alpha, double *beta, double *norm);
+/* Sub-steps taken by the last hx_step of a problem with hx_config.tol > 0: sub-steps of its last
+ * step (*last), in total (*total), and the largest a-posteriori error estimate over the accepted
+ * sub-steps (*err_max; above tol only when a step reached 65536 sub-steps).  With tol = 0: 1, nsteps
+ * and 0.  A step whose estimate exceeds tol is taken again from its start (the state is saved in a
+ * device copy allocated at the first such call) with twice the sub-steps; after a step whose
+ * estimate is below tol / 2^(m+1) the next one starts from half.  Any pointer may be NULL.  The
+ * estimate follows from the Krylov relation A V_m = V_m T_m + beta_m v_{m+1} e_m^T (Sec. 2.2); the
+ * automatic choice of sub-steps has no counterpart in the paper.  HX_EINVAL before the first step. */
+HX_API int hx_step_substeps(hx_problem *p, int *last, int64_t *total, double *err_max);
 /* 1 when the product runs a kernel compiled at hx_potential_set for this potential's operator
  * structure (NVRTC, sm_103a; every operator of the potential has a specialised stencil), 0 when it
  * runs the generic kernel; hx_last_error then says why (also when 1).  Both compute the same
@@ -295,7 +309,7 @@ HX_API int hx_adjoint_grad(const hx_indexset *s, const hx_config *cfg, const hx_
                            double *J_out);
 
 /* ||c||_2 of a device vector of the problem dtype (aligned to the element size), accumulated in
- * FP64; synchronous. */
+ * FP64; synchronous.  HX_ENONFINITE when the result is not finite (*out is still written). */
 HX_API int hx_norm(hx_problem *p, const void *c, double *out);
 /* The energy <c, A(t) c> (real, since A(t) is Hermitian; not divided by ||c||^2) of a device vector
  * of the problem dtype at the problem time, for monitoring a propagation (Sec. 2.2 assumes a
@@ -313,11 +327,13 @@ HX_API int hx_energy(hx_problem *p, const void *c, double *out);
  * allocation would fail) or a latency-critical loop that must not enter an allocator.
  * Scratch: a fixed 1026-double device array inside libhx.so (1024 block partial sums, the result
  * and the reduction counter), held on every GPU that loads the library until the process exits.
- * The first call on a device looks up that array's device address (cudaGetSymbolAddress); make
- * the first call before any stream capture.  Every call shares the array: calls that overlap on
- * the GPU (from several threads or streams) race, so serialise them.  Errors: as hx_norm, plus
- * HX_EUNSUPPORTED when the reduction would need more than 1024 block partials (a GPU with more
- * than 256 SMs) and HX_EINVAL when the current device is not the problem's device. */
+ * hx_problem_create binds that array on the problem's device (it looks up its device address with
+ * cudaGetSymbolAddress, which loads the module holding it and so reserves its memory there, and
+ * fails the creation if that fails), so hx_norm_noalloc itself needs no set-up.  Every call shares
+ * the array: calls that overlap on the GPU (from several threads or streams) race, so serialise
+ * them.  Errors: as hx_norm (HX_EINVAL for a vector not aligned to its element size, checked before
+ * anything runs), plus HX_EUNSUPPORTED when the reduction would need more than 1024 block partials
+ * (a GPU with more than 256 SMs) and HX_EINVAL when the current device is not the problem's device. */
 HX_API int hx_norm_noalloc(hx_problem *p, const void *c, double *out);
 
 /* ---- Chebyshev helpers for building hx_term coefficients (Sec. 1.3) ----------- */

@@ -396,12 +396,17 @@ def gh_assembly(S: IndexSet, r: np.ndarray, alpha: np.ndarray, L: float, M: int)
 # --------------------------------------------------------------------------- #
 
 def lanczos_exp(apply_fn: Callable[[np.ndarray], np.ndarray], c: np.ndarray, h: float, m: int,
-                breakdown: float = 1e-13):
+                breakdown: float = 1e-13, estimate: bool = False):
     """exp(-i h A) c ~ beta_0 V_m exp(-i h T_m) e_1 with an m-step Hermitian Lanczos process
     (Sec. 2.2), started from v_1 = c / ||c||.  Each new vector is orthogonalised against all
     previous ones by classical Gram-Schmidt, applied twice; T_m's diagonal holds the summed
     projections on v_k, its off-diagonal the norms.  Stops early when beta_k falls below
-    breakdown * max_i(|alpha_i| + beta_i).  Returns (c_new, alphas, betas)."""
+    breakdown * max_i(|alpha_i| + beta_i).  Returns (c_new, alphas, betas).
+
+    estimate=True also returns the a-posteriori estimate of the relative error: the Lanczos
+    relation A V_m = V_m T_m + beta_m v_{m+1} e_m^T leaves the residual beta_m v_{m+1} e_m^T, and
+    the estimate is |h| beta_m |e_m^T exp(-i h T_m) e_1| with beta_m the norm of the m-th vector's
+    remainder after its two orthogonalisations (0 after an early stop: the space is invariant)."""
     beta0 = np.linalg.norm(c)
     n = c.shape[0]
     V = np.zeros((m, n), dtype=np.complex128)
@@ -417,10 +422,12 @@ def lanczos_exp(apply_fn: Callable[[np.ndarray], np.ndarray], c: np.ndarray, h: 
             a_k += coeffs[k].real
         alphas.append(a_k)
         scale = max(scale, abs(a_k) + (betas[-1] if betas else 0.0))
-        if k == m - 1:
-            break
         b_k = float(np.linalg.norm(w))
+        if k == m - 1:
+            beta_m = b_k if b_k > breakdown * scale else 0.0
+            break
         if b_k <= breakdown * scale:
+            beta_m = 0.0
             break
         betas.append(b_k)
         V[k + 1] = w / b_k
@@ -428,7 +435,10 @@ def lanczos_exp(apply_fn: Callable[[np.ndarray], np.ndarray], c: np.ndarray, h: 
     T = np.diag(alphas) + np.diag(betas[: mm - 1], 1) + np.diag(betas[: mm - 1], -1)
     lam, Q = np.linalg.eigh(T)
     y = Q @ (np.exp(-1j * h * lam) * Q[0, :])
-    return beta0 * (y @ V[:mm]), np.array(alphas), np.array(betas[: mm - 1])
+    out = (beta0 * (y @ V[:mm]), np.array(alphas), np.array(betas[: mm - 1]))
+    if estimate:
+        return out + (abs(h) * beta_m * abs(y[mm - 1]) if mm == m else 0.0,)
+    return out
 
 
 def expmpr_propagate(S: IndexSet, spec: dict, c0: np.ndarray, h: float, nsteps: int, m: int,

@@ -802,11 +802,11 @@ int hx_problem_create(const hx_indexset *s, const hx_config *cfg, hx_problem **o
 {
     if (!s || !out) { set_error("hx_problem_create: NULL argument"); return HX_EINVAL; }
     *out = nullptr;
-    hx_config c = {HX_C128, HX_ORDER_SYM, 7, nullptr, HX_SCHEME_EXPMPR};
+    hx_config c = {HX_C128, HX_ORDER_SYM, 7, nullptr, HX_SCHEME_EXPMPR, 0.0};
     if (cfg) c = *cfg;
     if ((c.dtype != HX_C128 && c.dtype != HX_C64) || c.order < 0 || c.order > 2 || c.m < 1 || c.m > kMaxKrylov ||
-        (c.scheme != HX_SCHEME_EXPMPR && c.scheme != HX_SCHEME_MAGNUS4)) {
-        set_error("hx_problem_create: bad dtype, order, m (1..%d) or scheme", kMaxKrylov);
+        (c.scheme != HX_SCHEME_EXPMPR && c.scheme != HX_SCHEME_MAGNUS4) || !(c.tol >= 0.0 && c.tol <= 1.0)) {
+        set_error("hx_problem_create: bad dtype, order, m (1..%d), scheme or tol (0..1)", kMaxKrylov);
         return HX_EINVAL;
     }
     hx_problem *p = new (std::nothrow) hx_problem();
@@ -817,6 +817,8 @@ int hx_problem_create(const hx_indexset *s, const hx_config *cfg, hx_problem **o
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     if (e != cudaSuccess) { delete p; return cuda_fail(e, "hx_problem_create: no CUDA device"); }
+    int rc = noalloc_bind(p->device);   // hx_norm_noalloc's scratch: bound here, where allocation is expected
+    if (rc) { delete p; return rc; }
     e = cudaMalloc((void **)&p->dscal, 64 * sizeof(double));
     if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaMalloc(scalars)"); }
     if ((e = cudaMemset(p->dscal, 0, 64 * sizeof(double))) != cudaSuccess) {
@@ -982,6 +984,10 @@ int hx_norm(hx_problem *p, const void *c, double *out)
     cudaFreeAsync(buf, p->stream);
     cudaStreamSynchronize(p->stream);
     *out = sqrt(r);
+    if (!rc && !isfinite(*out)) {
+        set_error("hx_norm: the norm is not finite (the vector holds a NaN or an infinity, or overflows)");
+        rc = HX_ENONFINITE;
+    }
     return rc;
 }
 
@@ -1165,6 +1171,15 @@ int hx_step_info(hx_problem *p, int *m_used, double *alpha, double *beta, double
 {
     if (!p) { set_error("hx_step_info: NULL problem"); return HX_EINVAL; }
     return krylov_info(p, m_used, alpha, beta, norm);
+}
+
+int hx_step_substeps(hx_problem *p, int *last, int64_t *total, double *err_max)
+{
+    if (!p) { set_error("hx_step_substeps: NULL problem"); return HX_EINVAL; }
+    long long tot = 0;
+    int rc = krylov_substeps(p, last, &tot, err_max);
+    if (!rc && total) *total = tot;
+    return rc;
 }
 
 int hx_cheb_nodes(int R, double *u_out)

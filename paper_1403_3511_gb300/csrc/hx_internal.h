@@ -157,6 +157,10 @@ void batch_free(Batch *b);
 // Krylov stepping (hx_krylov.cu)
 int krylov_step(Problem *p, void *c, double dt, int nsteps);
 int krylov_info(Problem *p, int *m_used, double *alpha, double *beta, double *norm);
+int krylov_substeps(Problem *p, int *last, long long *total, double *err_max);
+
+// binds the allocation-free norm's scratch on device dev (hx_noalloc.cu)
+int noalloc_bind(int dev);
 void *krylov_host_state(Problem *p);
 void krylov_free(Problem *p);
 void krylov_invalidate(Problem *p);   // drops the captured step graph, keeps the workspace

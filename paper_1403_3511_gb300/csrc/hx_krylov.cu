@@ -41,6 +41,8 @@ struct Scal {                       // device scalars of one problem
     double lam[kMaxKrylov];              // eigenvalues of T_m
     double scale;                   // running max_i(|alpha_i| + beta_{i-1}) for the breakdown test
     double norm_out;
+    double err_max;                 // largest a-posteriori error estimate since it was last cleared
+    double t_save;                  // problem time at the start of an adaptive step (restored on retry)
     int m_used;
     int flags;                      // bit 0: breakdown seen, bit 1: non-finite, bit 2: eigensolver stalled
     unsigned counter;
@@ -57,6 +59,14 @@ struct Work {
     cudaGraphExec_t exec;
     cudaStream_t cap_stream;
     double dt;
+    // automatic sub-steps (hx_config.tol > 0)
+    double2 *backup;                // state at the start of the step being attempted
+    double *err_host;               // page-locked copy of err_max
+    int sub;                        // sub-steps per step for the next step
+    int sub_last;                   // sub-steps of the last accepted step
+    long long sub_total;            // sub-steps of the last hx_step call
+    double err_last;                // largest estimate of the last hx_step call
+    int steps_last;                 // steps of the last hx_step call
 };
 
 static Work *work_of(Problem *p) { return (Work *)p->krylov; }
@@ -387,8 +397,12 @@ __device__ void update_scalars(Scal *sc, int k, const double *tot)
         double b = sqrt(tot[0]);
         if (!isfinite(b)) sc->flags |= 2;
         if (b <= 1e-13 * sc->scale) {       // invariant subspace: stop with k + 1 vectors
-            sc->m_used = k + 1;
-            sc->flags |= 1;
+            if (k + 1 < sc->m_used) {
+                sc->m_used = k + 1;
+                sc->flags |= 1;
+            } else {                        // the pass after the last vector (error estimate): exact
+                sc->beta[k] = 0.0;
+            }
         } else {
             sc->beta[k] = b;
             sc->s[k + 1] = 1.0 / b;
@@ -1244,6 +1258,24 @@ static int launch_update_k(const Problem *p, V *wv, const V *Vb, size_t ld, int 
     return HX_EUNSUPPORTED;
 }
 
+// A-posteriori estimate of the relative error of the Lanczos exponential (Sec. 2.2), from the
+// residual of the Krylov relation A V_m = V_m T_m + beta_m v_{m+1} e_m^T:
+//   ||exp(-ihA) c - ||c|| V_m exp(-ihT_m) e_1|| / ||c||  ~  |h| beta_m |e_m^T exp(-ihT_m) e_1|,
+// with beta_m from the pass after the last vector and the last component of exp(-ihT_m) e_1 from
+// the stored combination weights (y_i = beta_0 s_i [exp(-ihT_m) e_1]_i).  Zero after a breakdown
+// (the Krylov space is invariant).  err_max keeps the largest value since it was cleared.
+__global__ void err_est_kernel(Scal *sc, double h, int m)
+{
+    const int mu = sc->m_used;
+    double est = 0.0;
+    if (mu == m && mu > 0 && sc->beta0 > 0.0) {
+        const int i = mu - 1;
+        const double ur = sc->y[2 * i] / (sc->beta0 * sc->s[i]), ui = sc->y[2 * i + 1] / (sc->beta0 * sc->s[i]);
+        est = fabs(h) * sc->beta[i] * sqrt(ur * ur + ui * ui);
+    }
+    if (!(est <= sc->err_max)) sc->err_max = est;   // NaN propagates
+}
+
 template <typename V, int NV>
 static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, double dt)
 {
@@ -1290,17 +1322,20 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
         }
         V *wv = Vb + (size_t)(k + 1) * ld;
         if (!f.dvec) dot_kernel<V, NV><<<Gd, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
+        // the second pass also runs after the last vector when the step estimates its error (beta_m)
+        const bool pass1 = k < m - 1 || p->cfg.tol > 0.0;
         if (NV <= 8) {
             if ((rc = launch_update_k<V>(p, wv, Vb, ld, n, k, 0, w->partials, sc, st)) ||
-                (k < m - 1 && (rc = launch_update_k<V>(p, wv, Vb, ld, n, k, 1, w->partials, sc, st))))
+                (pass1 && (rc = launch_update_k<V>(p, wv, Vb, ld, n, k, 1, w->partials, sc, st))))
                 return rc;
         } else {
             update_kernel<V, NV, 0><<<Gu0, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
-            if (k < m - 1) update_kernel<V, NV, 1><<<Gu1, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
+            if (pass1) update_kernel<V, NV, 1><<<Gu1, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
         }
     }
     if (m <= kEigSmall) expv_kernel<true><<<1, 32, 0, st>>>(sc, dt);
     else expv_kernel<false><<<1, 32, 0, st>>>(sc, dt);
+    if (p->cfg.tol > 0.0) err_est_kernel<<<1, 1, 0, st>>>(sc, dt, m);
     if constexpr (std::is_same<V, float2>::value) {
         switch (m) {
         case 1: launch_combine_m<1>(p, state, Vb, ld, n, w->partials, sc, st); break;
@@ -1458,12 +1493,86 @@ void krylov_free(Problem *p)
     cudaFree(w->partials);
     cudaFree(w->sc);
     cudaFree(w->mag);
+    cudaFree(w->backup);
+    cudaFreeHost(w->err_host);
     delete w;
     p->krylov = nullptr;
 }
 
-// The step graph is captured for one (state pointer, dt) pair and replayed; a call with another
-// vector or step size captures a new graph (a few hundred microseconds).
+// The step graph is captured for one (state pointer, step size) pair and replayed; a call with
+// another vector or step size captures a new graph (a few hundred microseconds).
+static int ensure_graph(Problem *p, Work *w, void *c, double h)
+{
+    if (w->exec && w->dt == h && w->state == (double2 *)c) return HX_OK;
+    if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
+    w->state = (double2 *)c;
+    cudaGraph_t g;
+    cudaError_t e;
+    if ((e = cudaStreamBeginCapture(w->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "begin capture");
+    int rc = enqueue(p, w, w->state, w->cap_stream, h);
+    e = cudaStreamEndCapture(w->cap_stream, &g);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&w->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { w->exec = nullptr; return cuda_fail(e, "graph instantiate"); }
+    w->dt = h;
+    return HX_OK;
+}
+
+// Steps with automatic sub-steps: each step of size dt is taken as s sub-steps of size dt / s; if
+// the largest a-posteriori estimate over them exceeds tol the step is taken again from the saved
+// state with 2 s sub-steps (at most kMaxSub), and after a step whose estimate is far below tol
+// (by 2^(m+1), about what halving the step changes it by when the Lanczos process has converged)
+// the next step tries s / 2.  One host synchronisation per attempted step.
+static int adaptive_steps(Problem *p, Work *w, void *c, double dt, int nsteps)
+{
+    constexpr int kMaxSub = 1 << 16;
+    cudaStream_t st = p->stream;
+    const size_t bytes = (size_t)p->set->h.size * sizeof(double2);
+    cudaError_t e;
+    if (!w->backup && (e = cudaMalloc((void **)&w->backup, std::max<size_t>(bytes, 16))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(step backup)");
+    if (!w->err_host && (e = cudaMallocHost((void **)&w->err_host, sizeof(double))) != cudaSuccess)
+        return cuda_fail(e, "cudaMallocHost(error estimate)");
+    if (w->sub < 1) w->sub = 1;
+    const double tol = p->cfg.tol;
+    w->sub_total = 0;
+    w->err_last = 0.0;
+    for (int n = 0; n < nsteps; ++n) {
+        for (;;) {
+            const int s = w->sub;
+            int rc = ensure_graph(p, w, c, dt / s);
+            if (rc) return rc;
+            if ((e = cudaMemcpyAsync(w->backup, c, bytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(&w->sc->t_save, &w->sc->t, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+                (e = cudaMemsetAsync(&w->sc->err_max, 0, sizeof(double), st)) != cudaSuccess)
+                return cuda_fail(e, "adaptive step set-up");
+            for (int i = 0; i < s; ++i)
+                if ((e = cudaGraphLaunch(w->exec, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
+            if ((e = cudaMemcpyAsync(w->err_host, &w->sc->err_max, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                return cuda_fail(e, "error estimate");
+            const double err = *w->err_host;
+            if (err > tol && s < kMaxSub) {        // reject: restore the state and the time
+                if ((e = cudaMemcpyAsync(c, w->backup, bytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+                    (e = cudaMemcpyAsync(&w->sc->t, &w->sc->t_save, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+                    return cuda_fail(e, "adaptive step restore");
+                w->sub = std::min(2 * s, kMaxSub);
+                continue;
+            }
+            w->sub_last = s;
+            w->sub_total += s;
+            if (!(err <= w->err_last)) w->err_last = err;
+            if (s > 1 && err * ldexp(1.0, p->cfg.m + 1) < tol) w->sub = s / 2;
+            break;
+        }
+    }
+    w->steps_last = nsteps;
+    return HX_OK;
+}
+
 int krylov_step(Problem *p, void *c, double dt, int nsteps)
 {
     int rc = ensure_work(p);
@@ -1471,30 +1580,34 @@ int krylov_step(Problem *p, void *c, double dt, int nsteps)
     Work *w = work_of(p);
     cudaStream_t st = p->stream;
     cudaError_t e;
-    if (!w->exec || w->dt != dt || w->state != (double2 *)c) {
-        if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
-        w->state = (double2 *)c;
-        cudaGraph_t g;
-        if ((e = cudaStreamBeginCapture(w->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-            return cuda_fail(e, "begin capture");
-        rc = enqueue(p, w, w->state, w->cap_stream, dt);
-        e = cudaStreamEndCapture(w->cap_stream, &g);
-        if (rc) return rc;
-        if (e != cudaSuccess) return cuda_fail(e, "end capture");
-        e = cudaGraphInstantiate(&w->exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) { w->exec = nullptr; return cuda_fail(e, "graph instantiate"); }
-        w->dt = dt;
-    }
     // the problem time is authoritative in p->dscal[0]; the step graph advances sc->t
     if ((e = cudaMemcpyAsync(&w->sc->t, p->dscal, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(&w->sc->flags, 0, sizeof(int), st)) != cudaSuccess)
         return cuda_fail(e, "step set-up");
-    for (int s = 0; s < nsteps; ++s)
-        if ((e = cudaGraphLaunch(w->exec, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    if (p->cfg.tol > 0.0) {
+        if ((rc = adaptive_steps(p, w, c, dt, nsteps))) return rc;
+    } else {
+        if ((rc = ensure_graph(p, w, c, dt))) return rc;
+        for (int s = 0; s < nsteps; ++s)
+            if ((e = cudaGraphLaunch(w->exec, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
+        w->sub_last = 1;
+        w->sub_total = nsteps;
+        w->steps_last = nsteps;
+        w->err_last = 0.0;
+    }
     if ((e = cudaMemcpyAsync(p->dscal, &w->sc->t, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return cuda_fail(e, "step copy-out");
     p->t_host += dt * nsteps;
+    return HX_OK;
+}
+
+int krylov_substeps(Problem *p, int *last, long long *total, double *err_max)
+{
+    Work *w = work_of(p);
+    if (!w) { set_error("hx_step_substeps: no step has run"); return HX_EINVAL; }
+    if (last) *last = w->sub_last;
+    if (total) *total = w->sub_total;
+    if (err_max) *err_max = w->err_last;
     return HX_OK;
 }
 

@@ -5,6 +5,8 @@
 // process exits.  Host code never passes the array's name to a kernel (on the host it is only a
 // stand-in symbol); it passes the device address obtained with cudaGetSymbolAddress, looked up
 // once per device with that device current.
+#include <stdint.h>
+
 #include <mutex>
 
 #include "hx_internal.h"
@@ -20,24 +22,35 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocSlots];
 
 constexpr int kMaxDevices = 64;
 static double *g_scratch_ptr[kMaxDevices];
-static std::once_flag g_scratch_once[kMaxDevices];
-static cudaError_t g_scratch_err[kMaxDevices];
+static std::mutex g_scratch_mu;
 
+// The device address of the scratch array on device dev (current), looked up with
+// cudaGetSymbolAddress and kept once found.  A failed lookup is not kept: the next call tries again
+// (it fails, for example, while a stream is being captured).
 static int scratch_for_device(int dev, double **out)
 {
     if (dev < 0 || dev >= kMaxDevices) {
         set_error("hx_norm_noalloc: device %d out of range", dev);
         return HX_EUNSUPPORTED;
     }
-    std::call_once(g_scratch_once[dev], [dev] {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
         void *ptr = nullptr;
-        g_scratch_err[dev] = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_fail(e, "hx_norm_noalloc: cudaGetSymbolAddress");
         g_scratch_ptr[dev] = (double *)ptr;
-    });
-    if (g_scratch_err[dev] != cudaSuccess || !g_scratch_ptr[dev])
-        return cuda_fail(g_scratch_err[dev], "hx_norm_noalloc: cudaGetSymbolAddress");
+    }
     *out = g_scratch_ptr[dev];
     return HX_OK;
+}
+
+// Called by hx_problem_create with the problem's device current: binds the scratch there, so that
+// the module holding the array is loaded (and its memory reserved) where allocation is expected,
+// not at the first hx_norm_noalloc.
+int noalloc_bind(int dev)
+{
+    double *ptr = nullptr;
+    return scratch_for_device(dev, &ptr);
 }
 
 }  // namespace hx
@@ -49,6 +62,10 @@ struct hx_problem : Problem {};
 extern "C" HX_API int hx_norm_noalloc(hx_problem *p, const void *c, double *out)
 {
     if (!p || !c || !out) { set_error("hx_norm_noalloc: NULL argument"); return HX_EINVAL; }
+    if ((uintptr_t)c % (p->cfg.dtype == HX_C64 ? 8 : 16) != 0) {
+        set_error("hx_norm_noalloc: vector not aligned to its element size");
+        return HX_EINVAL;
+    }
     const int G = apply_grid(p);
     if (G > kNoAllocMaxBlocks) {
         set_error("hx_norm_noalloc: the reduction needs %d block partials, the fixed scratch holds %d", G,
@@ -78,5 +95,9 @@ extern "C" HX_API int hx_norm_noalloc(hx_problem *p, const void *c, double *out)
         (e = cudaStreamSynchronize(p->stream)) != cudaSuccess)
         return cuda_fail(e, "hx_norm_noalloc: read result");
     *out = sqrt(r);
+    if (!isfinite(*out)) {
+        set_error("hx_norm_noalloc: the norm is not finite (the vector holds a NaN or an infinity, or overflows)");
+        return HX_ENONFINITE;
+    }
     return HX_OK;
 }

@@ -50,7 +50,7 @@ class hx_control(ctypes.Structure):
 
 class hx_config(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("order", ctypes.c_int), ("m", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("scheme", ctypes.c_int)]
+                ("scheme", ctypes.c_int), ("tol", ctypes.c_double)]
 
 
 # const hx_potential *(*)(double t, void *user)
@@ -83,6 +83,7 @@ def _load():
         "hx_step_host": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int]),
         "hx_step_reinterp": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int, POTENTIAL_FN, P]),
         "hx_step_info": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), dp, dp, dp]),
+        "hx_step_substeps": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64), dp]),
         "hx_step_launches": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "hx_apply_specialised": (ctypes.c_int, [P]),
         "hx_norm": (ctypes.c_int, [P, P, dp]),
@@ -128,6 +129,30 @@ def _tptr(t) -> int:
     return t.data_ptr()
 
 
+# element type and |K| of every problem handle this module created, so that a device vector of the
+# wrong type or length is refused here instead of being read past its end by the library
+_PROBLEMS = {}
+
+
+def _handle(p) -> int:
+    return p.value if isinstance(p, ctypes.c_void_p) else int(p)
+
+
+def _vec(p, t, state: bool = False) -> int:
+    """Device pointer of t after checking it against problem p: complex128 for a time-step state
+    (state=True), else the problem dtype; at least |K| elements."""
+    ptr = _tptr(t)
+    info = _PROBLEMS.get(_handle(p))
+    if info is not None:
+        dtype, size = info
+        want = "torch.complex128" if (state or dtype == HX_C128) else "torch.complex64"
+        if str(t.dtype) != want:
+            raise ValueError(f"expected a {want} tensor for this problem, got {t.dtype}")
+        if t.numel() < size:
+            raise ValueError(f"expected at least |K| = {size} elements, got {t.numel()}")
+    return ptr
+
+
 # ---- index set ---------------------------------------------------------------------------
 
 def hx_indexset_create(N: int, B: int):
@@ -165,14 +190,16 @@ def hx_indexset_destroy(s):
 # ---- problem -----------------------------------------------------------------------------
 
 def hx_problem_create(s, dtype: int = HX_C128, order: int = HX_ORDER_SYM, m: int = 7, stream: int = 0,
-                      scheme: int = HX_SCHEME_EXPMPR):
-    cfg = hx_config(dtype, order, m, ctypes.c_void_p(stream), scheme)
+                      scheme: int = HX_SCHEME_EXPMPR, tol: float = 0.0):
+    cfg = hx_config(dtype, order, m, ctypes.c_void_p(stream), scheme, tol)
     h = ctypes.c_void_p()
     _check(lib.hx_problem_create(s, ctypes.byref(cfg), ctypes.byref(h)))
+    _PROBLEMS[h.value] = (dtype, hx_indexset_size(s))
     return h
 
 
 def hx_problem_destroy(p):
+    _PROBLEMS.pop(_handle(p) if p is not None else None, None)
     lib.hx_problem_destroy(p)
 
 
@@ -221,7 +248,7 @@ def hx_set_time(p, t: float):
 
 
 def hx_apply(p, c_in, c_out):
-    _check(lib.hx_apply(p, ctypes.c_void_p(_tptr(c_in)), ctypes.c_void_p(_tptr(c_out))))
+    _check(lib.hx_apply(p, ctypes.c_void_p(_vec(p, c_in)), ctypes.c_void_p(_vec(p, c_out))))
 
 
 def hx_apply_project(p, c, y, basis, k: int, h):
@@ -231,7 +258,7 @@ def hx_apply_project(p, c, y, basis, k: int, h):
         raise ValueError("basis must be a CUDA tensor of rows with unit element stride")
     if not (h.is_cuda and str(h.dtype) == "torch.float64" and h.is_contiguous()):
         raise ValueError("h must be a contiguous CUDA float64 tensor")
-    _check(lib.hx_apply_project(p, ctypes.c_void_p(_tptr(c)), ctypes.c_void_p(_tptr(y)),
+    _check(lib.hx_apply_project(p, ctypes.c_void_p(_vec(p, c)), ctypes.c_void_p(_vec(p, y)),
                                 ctypes.c_void_p(basis.data_ptr()), basis.stride(0), k, ctypes.c_void_p(h.data_ptr())))
 
 
@@ -250,7 +277,7 @@ def hx_apply_host(p, c_in: np.ndarray, c_out: np.ndarray):
 
 
 def hx_step(p, c, dt: float, nsteps: int) -> int:
-    return _check(lib.hx_step(p, ctypes.c_void_p(_tptr(c)), dt, nsteps), allow=(HX_EBREAKDOWN,))
+    return _check(lib.hx_step(p, ctypes.c_void_p(_vec(p, c, state=True)), dt, nsteps), allow=(HX_EBREAKDOWN,))
 
 
 def hx_step_host(p, c: np.ndarray, dt: float, nsteps: int) -> int:
@@ -274,7 +301,7 @@ def hx_step_reinterp(p, c, dt: float, nsteps: int, fn) -> int:
         return ctypes.addressof(pot)
 
     cfn = POTENTIAL_FN(cb)
-    return _check(lib.hx_step_reinterp(p, ctypes.c_void_p(_tptr(c)), dt, nsteps, cfn, None),
+    return _check(lib.hx_step_reinterp(p, ctypes.c_void_p(_vec(p, c, state=True)), dt, nsteps, cfn, None),
                   allow=(HX_EBREAKDOWN,))
 
 
@@ -286,6 +313,13 @@ def hx_step_info(p, m: int = 32) -> dict:
     st = _check(lib.hx_step_info(p, ctypes.byref(mu), _dptr(a), _dptr(b), ctypes.byref(nr)), allow=(HX_EBREAKDOWN,))
     return {"m_used": mu.value, "alpha": a[: mu.value], "beta": b[: max(mu.value - 1, 0)], "norm": nr.value,
             "breakdown": st == HX_EBREAKDOWN}
+
+
+def hx_step_substeps(p) -> dict:
+    """Sub-steps of the last hx_step (last step, total) and the largest a-posteriori estimate."""
+    last, total, err = ctypes.c_int(), ctypes.c_int64(), ctypes.c_double()
+    _check(lib.hx_step_substeps(p, ctypes.byref(last), ctypes.byref(total), ctypes.byref(err)))
+    return {"last": last.value, "total": total.value, "err_max": err.value}
 
 
 def hx_apply_specialised(p) -> int:
@@ -322,21 +356,21 @@ def hx_batch_destroy(b):
 
 def hx_norm(p, c) -> float:
     out = ctypes.c_double()
-    _check(lib.hx_norm(p, ctypes.c_void_p(_tptr(c)), ctypes.byref(out)))
+    _check(lib.hx_norm(p, ctypes.c_void_p(_vec(p, c)), ctypes.byref(out)))
     return out.value
 
 
 def hx_energy(p, c) -> float:
     """<c, A(t) c> (see include/hx.h)."""
     out = ctypes.c_double()
-    _check(lib.hx_energy(p, ctypes.c_void_p(_tptr(c)), ctypes.byref(out)))
+    _check(lib.hx_energy(p, ctypes.c_void_p(_vec(p, c)), ctypes.byref(out)))
     return out.value
 
 
 def hx_norm_noalloc(p, c) -> float:
     """hx_norm without any device allocation (fixed scratch inside the library); see include/hx.h."""
     out = ctypes.c_double()
-    _check(lib.hx_norm_noalloc(p, ctypes.c_void_p(_tptr(c)), ctypes.byref(out)))
+    _check(lib.hx_norm_noalloc(p, ctypes.c_void_p(_vec(p, c)), ctypes.byref(out)))
     return out.value
 
 
@@ -347,7 +381,7 @@ def hx_adjoint_grad(s, L: float, fixed_terms: list, axis: int, u, t0: float, t1:
     pot, _keep = _potential(L, fixed_terms)
     uu = np.ascontiguousarray(u, dtype=np.float64)
     ctl = hx_control(axis, len(uu), substeps, t0, t1, _dptr(uu))
-    cfg = hx_config(HX_C128, order, m, ctypes.c_void_p(stream), HX_SCHEME_EXPMPR)
+    cfg = hx_config(HX_C128, order, m, ctypes.c_void_p(stream), HX_SCHEME_EXPMPR, 0.0)
     grad = np.zeros(len(uu))
     J = ctypes.c_double()
     _check(lib.hx_adjoint_grad(s, ctypes.byref(cfg), ctypes.byref(pot), ctypes.byref(ctl),
@@ -441,14 +475,14 @@ class Problem:
     """Convenience owner of an index set and a problem (frees both)."""
 
     def __init__(self, N: int, B: int, dtype: int = HX_C128, order: str = "sym", m: int = 7, stream: int = 0,
-                 indexset=None, scheme: int = HX_SCHEME_EXPMPR):
+                 indexset=None, scheme: int = HX_SCHEME_EXPMPR, tol: float = 0.0):
         self._own_set = indexset is None
         self.set = hx_indexset_create(N, B) if indexset is None else indexset
         self.N, self.B = N, B
         self.size = hx_indexset_size(self.set)
         self.dtype = dtype
         self.p = hx_problem_create(self.set, dtype, ORDERS[order] if isinstance(order, str) else order, m, stream,
-                                   scheme)
+                                   scheme, tol)
 
     def set_potential(self, spec: dict, t: float = 0.0):
         hx_potential_set(self.p, spec["L"], terms_from_spec(spec, t), t)

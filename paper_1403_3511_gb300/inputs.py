@@ -99,12 +99,14 @@ def workload(name: str) -> dict:
         return dict(name=name, N=N, B=B, L=half_width(B),
                     potential=henon_heiles_chain(N, 0.111, dipole=(0.05, 1.0)),
                     desc="Henon-Heiles chain lambda=0.111 + 0.05 cos(t) x1",
-                    init={"kind": "gaussian", "seed": 1}, dt=0.01, steps=1000, m=7)
+                    init={"kind": "gaussian", "seed": 1}, dt=0.01, steps=1000, m=7,
+                    dt_converged=2.5e-5)   # each m = 7 exponential within the estimate 1e-6 (about 4e-8)
     if name == "cos10_b1024":      # N=10 cosine chain, degree-8 interpolant, 500 steps
         N, B = 10, 1024
         return dict(name=name, N=N, B=B, L=half_width(B), potential=cos_chain(N, 0.2, 8),
                     desc="0.2 sum cos(x_d - x_{d+1}), degree-8 Chebyshev interpolant",
-                    init={"kind": "decaying", "seed": 2, "power": 2.0}, dt=0.01, steps=500, m=7)
+                    init={"kind": "decaying", "seed": 2, "power": 2.0}, dt=0.01, steps=500, m=7,
+                    dt_converged=1e-3)   # ||A|| about 5e2 (the diagonal): h ||A|| about 0.5
     if name == "ctrl4_b512":       # N=4 control problem for the adjoint gradient
         N, B = 4, 512
         rng = np.random.default_rng(4)

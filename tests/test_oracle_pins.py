@@ -369,6 +369,39 @@ def test_lanczos_matches_dense_expm(oracle):
     assert np.linalg.norm(got7 - ref) > 1e-14         # truncation error of m = 7 is visible
 
 
+def test_lanczos_error_estimate_tracks_true_error(oracle):
+    """The a-posteriori estimate |h| beta_m |e_m^T exp(-ihT_m) e_1| (Sec. 2.2: the residual of the
+    Lanczos relation) against the true relative error from scipy's expm, over step sizes from the
+    unresolved to the converged regime: an upper bound within a factor 2m wherever the error is
+    above round-off, and once converged the ratio tends to m (the leading term of the error is
+    h^m/m! times the product of the betas, that of the estimate h^m/(m-1)! times the same), monotone
+    in h, and zero after an exact breakdown.  A dropped beta_m, a wrong component of exp(-ihT_m) e_1
+    (first instead of last) or a missing h breaks the ratio."""
+    N, B = 2, 30
+    S = oracle.IndexSet.hyperbolic(N, B)
+    spec = dict(inputs.workload("hh2_b32"), B=B, L=inputs.half_width(B))
+    r, a = oracle.potential_terms(spec, 0.0)
+    A = oracle.dense_A(S, r, a, spec["L"])
+    c = inputs.initial_vector({"init": {"kind": "gaussian", "seed": 9}}, S.k)
+    ests, m = [], 7
+    for h in (0.3, 0.2, 0.1, 0.05, 0.02, 0.01):
+        ref = scipy.linalg.expm(-1j * h * A) @ c
+        got, _, _, est = oracle.lanczos_exp(lambda v: A @ v, c, h, m, estimate=True)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(c)
+        ests.append(est)
+        if err > 1e-12:
+            assert 1.0 <= est / err <= 2 * m, (h, est, err)
+        if h <= 0.02:
+            assert abs(est / err - m) <= 0.05 * m, (h, est / err)
+    assert all(x > y for x, y in zip(ests, ests[1:]))
+    S3 = oracle.IndexSet.hyperbolic(3, 30)
+    d = oracle.diag(S3)
+    c3 = np.zeros(S3.size, complex)
+    for lev in (1.5, 3.5, 6.5):
+        c3[np.where(d == lev)[0]] = 1.0
+    assert oracle.lanczos_exp(lambda v: d * v, c3, 0.3, 7, estimate=True)[3] == 0.0
+
+
 def test_lanczos_exact_on_few_levels(oracle):
     """W = 0, c supported on 3 distinct levels of D: Lanczos terminates (breakdown) and the step equals
     the exact c_k exp(-i (|k| + N/2) h)."""

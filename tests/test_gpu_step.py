@@ -402,3 +402,27 @@ def test_tiny_problems_step(hx, oracle, N, B, dtype, tol):
     got, info, _ = run_gpu(hx, spec, c0, hx.HX_C128 if dtype == "c128" else hx.HX_C64, 0.05, 3)
     assert info["m_used"] == min(7, S.size) or info["breakdown"]
     assert rel(got, ref) <= tol, rel(got, ref)
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
+def test_cosine_chain_n10_steps(hx, oracle, dtype, tol):
+    """The N = 10 cosine chain (degree-8 Chebyshev interpolant of 0.2 sum cos(x_d - x_{d+1})) at a
+    reduced bound B = 32 (9,533 coefficients, so that the oracle's term-by-term evaluation of the
+    9 x 9 tensor interpolants stays within seconds): its degree-8 plane terms take the two-stage path
+    through channel vectors (footprint above the direct limit), three steps against the oracle."""
+    base = inputs.workload("cos10_b1024")
+    spec = dict(base, B=32, L=inputs.half_width(32))
+    S = oracle.IndexSet.hyperbolic(10, 32)
+    c0 = inputs.initial_vector(spec, S.k)
+    ref, t_ref = oracle.expmpr_propagate(S, spec, c0, spec["dt"], 3, spec["m"])
+    dt_ = hx.HX_C128 if dtype == "c128" else hx.HX_C64
+    P = hx.Problem(10, 32, dtype=dt_, m=spec["m"])
+    try:
+        P.set_potential(spec, 0.0)
+        assert hx.hx_step_launches(P.p)[0] == 2          # channel stage + main stage
+        x = torch.from_numpy(np.ascontiguousarray(c0)).to("cuda", torch.complex128)
+        hx.hx_step(P.p, x, spec["dt"], 3)
+        got = x.cpu().numpy()
+    finally:
+        P.close()
+    assert rel(got, ref) <= tol, rel(got, ref)

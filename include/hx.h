@@ -125,6 +125,11 @@ typedef struct {
                                     * estimate of the relative error of every sub-step's Lanczos
                                     * exponential, |h| beta_m |e_m^T exp(-ihT_m) e_1| (Sec. 2.2),
                                     * is at most tol (hx_step_substeps reports the counts) */
+    double scale;                  /* basis scaling S of the scaled Hermite functions phi_k(S x)
+                                    * (Sec. 1.4); 0 means 1.  With S != 1 the product is
+                                    * A = S^2 D_K + (1/S^2 - S^2)/2 sum_l X_l^2 + W(X / S), W given in
+                                    * x as for S = 1 (its terms are evaluated on [-S L, S L]); the
+                                    * paper asks S L >= sqrt(2 (K + 1)) + 1 for the interpolation box */
 } hx_config;
 
 typedef struct hx_indexset hx_indexset;
@@ -137,6 +142,14 @@ typedef struct hx_problem hx_problem;
  * (B > 65535 or |K| >= 2^31), HX_ENOMEM, HX_ECUDA. */
 HX_API int hx_indexset_create(int N, int64_t B, hx_indexset **out);
 /* |K|, or -1 for a NULL handle. */
+/* A general downward-closed index set (Sec. 1.2: any K with k in K, j <= k => j in K) from a list of
+ * count multi-indices k[count * N] (host, any order; copied).  Stored in lexicographic order, last
+ * coordinate fastest, like the hyperbolic cross (hx_indexset_export gives that order).  Errors:
+ * HX_EINVAL for a negative coordinate, a duplicate, a set that is not downward closed (a multi-index
+ * whose neighbour k - e_l is missing) or count < 1; HX_EUNSUPPORTED for coordinates above 65534, a
+ * coordinate sum above 65535, rows longer than 65535 or count >= 2^31 - 1.  Products on such sets
+ * run the generic kernel (membership and fibre tops from the row tables). */
+HX_API int hx_indexset_create_list(int N, int64_t count, const int32_t *k, hx_indexset **out);
 HX_API int64_t hx_indexset_size(const hx_indexset *s);
 /* Writes the multi-index of position rank into k_out[0..N-1] (host).  HX_EINVAL if out of range. */
 HX_API int hx_indexset_unrank(const hx_indexset *s, int64_t rank, int32_t *k_out);
@@ -302,6 +315,7 @@ typedef struct {
  * converged propagator), cfg->order and cfg->stream are honoured.  c0, phi: DEVICE complex128
  * vectors of |K|; grad_out: host array of n_intervals doubles, or NULL for J only; J_out: host.
  * Device memory: about (n_intervals + substeps + 2m + 8) vectors.  Synchronous.
+ * cfg->tol is ignored and cfg->scale must be 0 or 1 (else HX_EUNSUPPORTED).
  * Errors: HX_EINVAL (NULL pointers, bad control), HX_EUNSUPPORTED (cfg->scheme other than
  * HX_SCHEME_EXPMPR), HX_ENOMEM, HX_ECUDA, as hx_potential_set. */
 HX_API int hx_adjoint_grad(const hx_indexset *s, const hx_config *cfg, const hx_potential *fixed,

@@ -262,9 +262,22 @@ def fast_algorithm(S: IndexSet, r: np.ndarray, alpha: np.ndarray, L: float, v: n
     return out
 
 
-def apply(S: IndexSet, r: np.ndarray, alpha: np.ndarray, L: float, v: np.ndarray, order: str = "sym") -> np.ndarray:
-    """A(t) v = D_K v + W^pol(X_K, t) v, the right-hand side of Eq. (ODECoefficientsPol)."""
+def apply(S: IndexSet, r: np.ndarray, alpha: np.ndarray, L: float, v: np.ndarray, order: str = "sym",
+          scale: float = 1.0) -> np.ndarray:
+    """A(t) v = D_K v + W^pol(X_K, t) v, the right-hand side of Eq. (ODECoefficientsPol).
+
+    scale = S != 1: the basis of scaled Hermite functions phi_k(S x) (Sec. 1.4).  With y = S x the
+    Hamiltonian is S^2 (-1/2 Laplacian_y) + V(y / S), -1/2 Laplacian_y = H_osc - |y|^2 / 2 with H_osc
+    diagonal (D_K) in this basis, and V = |x|^2 / 2 + W, so
+      A = S^2 D_K + (1/S^2 - S^2)/2 sum_l X_l X_l + W(X / S),
+    X_l the truncated coordinate matrices; W's Chebyshev terms in x / L are terms in y / (S L)."""
     v = np.ascontiguousarray(v, dtype=np.complex128)
+    if scale != 1.0:
+        out = scale ** 2 * diag(S) * v + fast_algorithm(S, r, alpha, L * scale, v, order)
+        c = 0.5 * (1.0 / scale ** 2 - scale ** 2)
+        for l in range(S.N):
+            out += c * direct_op(S, l, direct_op(S, l, v))
+        return out
     r = np.ascontiguousarray(r, dtype=np.int32)
     alpha = np.ascontiguousarray(alpha, dtype=np.float64)
     out = np.empty_like(v)
@@ -340,8 +353,16 @@ def dense_W(S: IndexSet, r: np.ndarray, alpha: np.ndarray, L: float, order: str 
     return W
 
 
-def dense_A(S: IndexSet, r, alpha, L, order="sym") -> np.ndarray:
-    return np.diag(diag(S)) + dense_W(S, r, alpha, L, order)
+def dense_A(S: IndexSet, r, alpha, L, order="sym", scale: float = 1.0) -> np.ndarray:
+    """The matrix of apply (dense), in the basis phi_k(scale x)."""
+    if scale == 1.0:
+        return np.diag(diag(S)) + dense_W(S, r, alpha, L, order)
+    c = 0.5 * (1.0 / scale ** 2 - scale ** 2)
+    A = np.diag(scale ** 2 * diag(S)) + dense_W(S, r, alpha, L * scale, order)
+    for l in range(S.N):
+        X = dense_X(S, l)
+        A += c * (X @ X)
+    return A
 
 
 # --------------------------------------------------------------------------- #
@@ -448,7 +469,7 @@ def expmpr_propagate(S: IndexSet, spec: dict, c0: np.ndarray, h: float, nsteps: 
     t = t0
     for _ in range(nsteps):
         r, alpha = potential_terms(spec, t + 0.5 * h)
-        c, _, _ = lanczos_exp(lambda v: apply(S, r, alpha, spec["L"], v, order), c, h, m)
+        c, _, _ = lanczos_exp(lambda v: apply(S, r, alpha, spec["L"], v, order, spec.get("scale", 1.0)), c, h, m)
         t += h
     return c, t
 

@@ -110,12 +110,17 @@ extern "C" HX_API int hx_adjoint_grad(const hx_indexset *s, const hx_config *cfg
     const int n = (int)s->h.size;
     const int NI = ctl->n_intervals, S = ctl->substeps;
     const double dt = (ctl->t1 - ctl->t0) / ((double)NI * S);
-    hx_config c = {HX_C128, HX_ORDER_SYM, 7, nullptr, HX_SCHEME_EXPMPR};
+    hx_config c = {HX_C128, HX_ORDER_SYM, 7, nullptr, HX_SCHEME_EXPMPR, 0.0, 0.0};
     if (cfg) c = *cfg;
     if (c.scheme != HX_SCHEME_EXPMPR) {
         set_error("hx_adjoint_grad: the gradient is that of the exponential midpoint rule (scheme HX_SCHEME_EXPMPR)");
         return HX_EUNSUPPORTED;
     }
+    if (!(c.scale == 0.0 || c.scale == 1.0)) {
+        set_error("hx_adjoint_grad: the unscaled basis only (scale 0 or 1)");
+        return HX_EUNSUPPORTED;
+    }
+    c.tol = 0.0;                            // fixed Lanczos exponentials (their count sets the sub-steps)
     c.dtype = HX_C128;                      // the gradient is an FP64 computation
     cudaStream_t st = (cudaStream_t)c.stream;
     hx_problem *Pf = nullptr, *Px = nullptr;

@@ -110,6 +110,103 @@ __device__ __forceinline__ void plane_op(const Ctx &c, const Elem &el, const OpS
     }
 }
 
+// ---- general downward-closed sets: membership and fibre tops from the row tables ----------
+//
+// A footprint point's row is reached through its row-offset column (every position of the
+// operator's (2p+1)(2q+1) grid has one for a general set) and Ctx::member decides whether the point
+// lies in K; the distance to a fibre top along axis a is the number of t = 1..p for which the point
+// moved by t along a still lies in K.
+
+// whether the point at grid position (u, v) of op lies in K (u along a, v along b; b = -1 for a
+// line op), and its address (the own element when not)
+__device__ __forceinline__ bool point_g(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, int u, int v,
+                                        int &addr)
+{
+    const int N = c.S->N;
+    const int q = op.kind == 2 ? op.q : 0;
+    const int d = O.didx[op.dbase + (u + op.p) * (2 * q + 1) + (v + q)];
+    const int sh = (op.a == N - 1 ? u : 0) + (op.kind == 2 && op.b == N - 1 ? v : 0);
+    int start;
+    const bool ok = c.member(el, d, sh, start);
+    addr = ok ? start + el.j + sh : el.e;
+    return ok;
+}
+
+template <typename R, int MP, bool UNROLL>
+__device__ __forceinline__ void line_op_g(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
+                                          const typename Vec2<R>::T *cin, R &sx, R &sy)
+{
+    const int p = op.p;
+    const int ka = c.k(el, op.a);
+    int d = 0, addr;
+#pragma unroll(UNROLL ? MP : 1)
+    for (int t = 1; t <= MP; ++t)
+        if (t <= p && point_g(c, el, O, op, t, 0, addr)) d = t;
+    const R *row = tab + op.tabP + ((size_t)ka * (p + 1) + d) * (2 * p + 1) + p;
+#pragma unroll(UNROLL ? 2 * MP + 1 : 1)
+    for (int s = -MP; s <= MP; ++s) {
+        if (s < -p || s > p || !((op.pmask >> (s + p)) & 1)) continue;
+        if (!point_g(c, el, O, op, s, 0, addr)) continue;
+        const typename Vec2<R>::T v = cin[addr];
+        const R w = row[s];
+        sx += w * v.x;
+        sy += w * v.y;
+    }
+}
+
+template <typename R, int MP, int MQ, bool UNROLL>
+__device__ __forceinline__ void plane_op_g(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
+                                           const typename Vec2<R>::T *cin, R &sx, R &sy)
+{
+    const int p = op.p, q = op.q;
+    const int ka = c.k(el, op.a), kb = c.k(el, op.b);
+    const R wAB = (R)O.wAB, wBA = (R)O.wBA;
+    int addr;
+    // fibre-top distances: along a at k + s2 e_b, along b at k + s e_a (0 when that point is not in K)
+    int dA[2 * MQ + 1], dB[2 * MP + 1];
+#pragma unroll(UNROLL ? 2 * MQ + 1 : 1)
+    for (int s2 = -MQ; s2 <= MQ; ++s2) {
+        int d = 0;
+        if (s2 >= -q && s2 <= q)
+            for (int t = 1; t <= p; ++t)
+                if (point_g(c, el, O, op, t, s2, addr)) d = t;
+        dA[s2 + MQ] = d;
+    }
+#pragma unroll(UNROLL ? 2 * MP + 1 : 1)
+    for (int s = -MP; s <= MP; ++s) {
+        int d = 0;
+        if (s >= -p && s <= p)
+            for (int t = 1; t <= q; ++t)
+                if (point_g(c, el, O, op, s, t, addr)) d = t;
+        dB[s + MP] = d;
+    }
+    const int dA0 = dA[MQ], dB0 = dB[MP];
+    const R *rowP0 = tab + op.tabP + ((size_t)ka * (p + 1) + dA0) * (2 * p + 1) + p;
+    const R *rowQ0 = tab + op.tabQ + ((size_t)kb * (q + 1) + dB0) * (2 * q + 1) + q;
+#pragma unroll(UNROLL ? 2 * MP + 1 : 1)
+    for (int s = -MP; s <= MP; ++s) {
+        if (s < -p || s > p || !((op.pmask >> (s + p)) & 1) || ka + s < 0) continue;
+        const bool inA = s == 0 || point_g(c, el, O, op, s, 0, addr);   // k + s e_a in K
+        const R pj = inA ? rowP0[s] : (R)0;
+        const R *rowQs = tab + op.tabQ + ((size_t)kb * (q + 1) + dB[s + MP]) * (2 * q + 1) + q;
+#pragma unroll(UNROLL ? 2 * MQ + 1 : 1)
+        for (int s2 = -MQ; s2 <= MQ; ++s2) {
+            if (s2 < -q || s2 > q || !((op.qmask >> (s2 + q)) & 1) || kb + s2 < 0) continue;
+            if (!point_g(c, el, O, op, s, s2, addr)) continue;              // footprint point not in K
+            const R cab = inA ? pj * rowQs[s2] : (R)0;                      // P(X_a) (Q(X_b) c)
+            R cba = (R)0;                                                   // Q(X_b) (P(X_a) c)
+            if (s2 <= dB0) {
+                const R *rowPs = tab + op.tabP + ((size_t)ka * (p + 1) + dA[s2 + MQ]) * (2 * p + 1) + p;
+                cba = rowQ0[s2] * rowPs[s];
+            }
+            const R w = wAB * cab + wBA * cba;
+            const typename Vec2<R>::T v = cin[addr];
+            sx += w * v.x;
+            sy += w * v.y;
+        }
+    }
+}
+
 template <typename R, int P, int Q, int SB>
 __device__ __forceinline__ void plane_dispatch_sb(int rb, const Ctx &c, const Elem &el, const OpSet &O, const Op &op,
                                                   const R *tab, const typename Vec2<R>::T *src, typename Vec2<R>::T &s,
@@ -141,7 +238,7 @@ __device__ __forceinline__ typename Vec2<R>::T line_dispatch(int ra, const Ctx &
 // MD: largest polynomial degree of the compiled potential (3: unrolled stencils; kMaxDeg: rolled loops).
 // The operator list is read from the launch arguments and dispatched per operator; the kernels
 // compiled at run time for one potential (hx_jit.cu) replace this loop by the fixed sequence.
-template <typename R, int MD>
+template <typename R, int MD, bool GENERAL>
 __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 3 : 1) apply_kernel(const __grid_constant__ ApplyArgs args)
 {
     using V = typename Vec2<R>::T;
@@ -158,6 +255,9 @@ __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 3 : 1) apply_kernel(c
                 const V cs = src[e];
                 sx = cs.x;
                 sy = cs.y;
+            } else if (GENERAL) {
+                if (op.kind == 1) line_op_g<R, (MD <= 3 ? 3 : kMaxDeg), (MD <= 3)>(ctx, el, O, op, tab, src, sx, sy);
+                else plane_op_g<R, (MD <= 3 ? 3 : kMaxDeg), (MD <= 3 ? 3 : kMaxDeg), (MD <= 3)>(ctx, el, O, op, tab, src, sx, sy);
             } else if (MD <= 3) {
                 const int sb = op.mergeB >= 0 ? O.op[op.mergeB].p : 0;
                 V o = czero<V>(), l = czero<V>();
@@ -218,7 +318,9 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
     memset(&a, 0, sizeof(a));
     a.S = p->set->d;
     a.gnb = p->gnb;
+    a.gnbn = p->gnbn;
     a.gstride = p->gstride;
+    a.dscale = p->scale * p->scale;
     memcpy(a.mv, p->roff.mv, sizeof(a.mv));
     a.t_ptr = t_ptr;
     a.t_shift = t_shift;
@@ -257,10 +359,13 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
         return HX_EUNSUPPORTED;
     }
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_kernel<R, MD>, kApplyThreads, 0);
+    const bool general = p->set->d.general != 0;
+    if (general) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_kernel<R, MD, true>, kApplyThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_kernel<R, MD, false>, kApplyThreads, 0);
     int grid = p->num_sms * (per_sm > 0 ? per_sm : 1);     // one wave of resident CTAs
     if (grid > blocks) grid = blocks > 0 ? blocks : 1;
-    apply_kernel<R, MD><<<grid, kApplyThreads, 0, st>>>(a);
+    if (general) apply_kernel<R, MD, true><<<grid, kApplyThreads, 0, st>>>(a);
+    else apply_kernel<R, MD, false><<<grid, kApplyThreads, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "apply kernel launch");
     return HX_OK;

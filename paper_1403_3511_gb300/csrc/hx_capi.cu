@@ -143,8 +143,123 @@ static int build_host_tables(int N, int B, IndexSetHost &h)
     return HX_OK;
 }
 
+// Tables of a general downward-closed set given as a list of multi-indices (any order): the list
+// sorted lexicographically (last coordinate fastest), checked for duplicates, negative coordinates
+// and downward closure, and its rows and groups as for the hyperbolic cross.  B becomes 1 + the
+// largest coordinate (the row tables of the potential cover the coordinates 0..B-1).
+static bool lex_less(const int32_t *a, const int32_t *b, int N)
+{
+    for (int l = 0; l < N; ++l)
+        if (a[l] != b[l]) return a[l] < b[l];
+    return false;
+}
+
+static int64_t list_find(const IndexSetHost &h, const int32_t *k)
+{
+    int64_t lo = 0, hi = h.size - 1;
+    const int N = h.N;
+    while (lo <= hi) {
+        const int64_t mid = (lo + hi) / 2;
+        const int32_t *x = h.list.data() + (size_t)mid * N;
+        if (lex_less(x, k, N)) lo = mid + 1;
+        else if (lex_less(k, x, N)) hi = mid - 1;
+        else return mid;
+    }
+    return -1;
+}
+
+static int build_list_tables(int N, int64_t count, const int32_t *k, IndexSetHost &h)
+{
+    if (count < 1 || count >= ((int64_t)1 << 31) - 1) {
+        set_error("hx_indexset_create_list: need 1 <= count < 2^31 - 1 (got %lld)", (long long)count);
+        return count < 1 ? HX_EINVAL : HX_EUNSUPPORTED;
+    }
+    std::vector<int64_t> idx(count);
+    for (int64_t i = 0; i < count; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return lex_less(k + a * N, k + b * N, N); });
+    h.N = N;
+    h.general = true;
+    h.size = count;
+    h.list.resize((size_t)count * N);
+    int maxc = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        const int32_t *x = k + idx[i] * N;
+        int ksum = 0;
+        for (int l = 0; l < N; ++l) {
+            if (x[l] < 0 || x[l] > 65534) {
+                set_error("hx_indexset_create_list: coordinate %d outside 0..65534", x[l]);
+                return HX_EINVAL;
+            }
+            maxc = std::max(maxc, (int)x[l]);
+            ksum += x[l];
+        }
+        if (ksum > 65535) {
+            set_error("hx_indexset_create_list: a coordinate sum above 65535 is not supported");
+            return HX_EUNSUPPORTED;
+        }
+        memcpy(h.list.data() + (size_t)i * N, x, N * sizeof(int32_t));
+        if (i > 0 && !lex_less(h.list.data() + (size_t)(i - 1) * N, x, N)) {
+            set_error("hx_indexset_create_list: duplicate multi-index");
+            return HX_EINVAL;
+        }
+    }
+    std::vector<int32_t> y(N);
+    for (int64_t i = 0; i < count; ++i) {            // downward closure: k - e_l in K for k_l > 0
+        const int32_t *x = h.list.data() + (size_t)i * N;
+        for (int l = 0; l < N; ++l) {
+            if (x[l] == 0) continue;
+            memcpy(y.data(), x, N * sizeof(int32_t));
+            y[l] -= 1;
+            if (list_find(h, y.data()) < 0) {
+                set_error("hx_indexset_create_list: the set is not downward closed (multi-index %lld lacks its "
+                          "neighbour below it along axis %d)", (long long)i, l);
+                return HX_EINVAL;
+            }
+        }
+    }
+    h.B = maxc + 1;
+    h.qtotal = 0;
+    h.qoff.assign(h.B + 2, 0);
+    h.Q.clear();
+    h.row_info.clear();
+    h.row_k.clear();
+    h.rgrp.clear();
+    h.gfirst.clear();
+    h.ngroup = 0;
+    const int npre = N - 1;
+    for (int64_t i = 0; i < count;) {                // rows: runs of a common prefix k_0..k_{N-2}
+        const int32_t *x = h.list.data() + (size_t)i * N;
+        int64_t j = i + 1;
+        while (j < count && !memcmp(h.list.data() + (size_t)j * N, x, npre * sizeof(int32_t))) ++j;
+        const int len = (int)(j - i);
+        if (len > 65535 || h.list[(size_t)(j - 1) * N + N - 1] != len - 1) {
+            set_error("hx_indexset_create_list: a row longer than 65535 or not contiguous");
+            return len > 65535 ? HX_EUNSUPPORTED : HX_EINVAL;
+        }
+        if (npre == 0 || x[npre - 1] == 0) {
+            h.gfirst.push_back((int)h.row_info.size());
+            h.ngroup = (int)h.gfirst.size();
+        }
+        h.rgrp.push_back(h.ngroup - 1);
+        int ksum = 0;
+        for (int l = 0; l < npre; ++l) {
+            h.row_k.push_back((uint16_t)x[l]);
+            ksum += x[l];
+        }
+        h.row_info.push_back(make_int4((int)i, 0, ksum, len));
+        i = j;
+    }
+    h.nrow = (int)h.row_info.size();
+    return HX_OK;
+}
+
 static int64_t host_rank(const IndexSetHost &h, const int32_t *k)
 {
+    if (h.general) {
+        for (int l = 0; l < h.N; ++l)
+            if (k[l] < 0) return -1;
+        return list_find(h, k);
+    }
     int64_t q = 1;
     for (int l = 0; l < h.N; ++l) {
         if (k[l] < 0) return -1;
@@ -164,6 +279,10 @@ static int64_t host_rank(const IndexSetHost &h, const int32_t *k)
 static int host_unrank(const IndexSetHost &h, int64_t rank, int32_t *k)
 {
     if (rank < 0 || rank >= h.size) return HX_EINVAL;
+    if (h.general) {
+        memcpy(k, h.list.data() + (size_t)rank * h.N, h.N * sizeof(int32_t));
+        return HX_OK;
+    }
     int64_t q = 1, rem = rank;
     for (int d = 0; d < h.N - 1; ++d) {
         int m = h.N - 1 - d;
@@ -392,6 +511,8 @@ struct Compiler {
                     // on the last axis also looks up (s, 0), the row of k + s e_a
                     bool used = ((o.pmask >> (s + o.p)) & 1) &&
                                 (((o.qmask >> (s2 + o.q)) & 1) || (s2 == 0 && o.rb == ROLE_LAST));
+                    // a general set decides membership and fibre tops point by point: all positions
+                    used = used || set->h.general;
                     if (!used) {
                         S.didx[o.dbase + (s + o.p) * (2 * o.q + 1) + (s2 + o.q)] = 0;
                         continue;
@@ -467,6 +588,14 @@ static void rank_one_pieces(std::vector<double> C, int n0, int n1, std::vector<s
     }
 }
 
+// Lexicographic comparison of two coordinate prefixes of length n (<0, 0, >0).
+static int memcmp_u16(const uint16_t *a, const uint16_t *b, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (a[i] != b[i]) return a[i] < b[i] ? -1 : 1;
+    return 0;
+}
+
 static int compile_potential(Problem *pr, const hx_potential *pot)
 {
     const IndexSetObj *set = pr->set;
@@ -477,7 +606,11 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
     }
     Compiler cp;
     cp.set = set;
-    cp.L = pot->L;
+    // basis phi_k(S x): with y = S x, A = S^2 D_K + (1/S^2 - S^2)/2 sum_l Y_l^2 + W(Y / S); W's
+    // Chebyshev expansion in x / L is one in y / (S L), so the terms keep their coefficients on
+    // [-S L, S L], and the quadratic term is a degree-2 line operator on every axis
+    const double S = pr->scale;
+    cp.L = pot->L * S;
     memset(&cp.ops, 0, sizeof(cp.ops));
     memset(&cp.ops1, 0, sizeof(cp.ops1));
     memset(&cp.roff, 0, sizeof(cp.roff));
@@ -545,6 +678,18 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
             }
         }
     }
+    if (S != 1.0) {
+        const double c = 0.5 * (1.0 / (S * S) - S * S), L2 = cp.L * cp.L;
+        const std::vector<double> quad = {0.5 * c * L2, 0.0, 0.5 * c * L2};   // c y^2 = c L^2 (T_0 + T_2) / 2
+        hx_term unit;
+        memset(&unit, 0, sizeof(unit));
+        unit.mod_kind = HX_MOD_CONST;
+        unit.amp = 1.0;
+        for (int l = 0; l < N; ++l) {
+            int rc = cp.add_op(cp.ops, 1, l, -1, quad, quad, unit, 1.0);
+            if (rc) return rc;
+        }
+    }
     // A pure line op on the second axis of a pure plane op, with the parity of the plane op's second
     // polynomial and a degree of q or q + 2, shares the plane op's points k + s2 e_b: evaluate it
     // inside the plane op (one gather per shared point); it keeps its own weight.
@@ -553,7 +698,7 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
     // when the plane op's first degree is even, so that its stencil visits the points s = 0)
     int maxdeg = 0;
     for (int i = 0; i < cp.ops.nops; ++i) maxdeg = std::max(maxdeg, std::max(cp.ops.op[i].p, cp.ops.op[i].q));
-    for (int i = 0; i < cp.ops.nops && maxdeg <= 3; ++i) {
+    for (int i = 0; i < cp.ops.nops && maxdeg <= 3 && !set->h.general; ++i) {
         Op &o = cp.ops.op[i];
         if (o.kind != 2 || o.cls < CLS_PLANE || o.cls >= CLS_GENERIC || o.src >= 0) continue;
         if (o.p > 2 || o.q > 2 || o.p % 2) continue;
@@ -633,13 +778,51 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
     pr->roff = cp.roff;
     if (!same) {
         if (pr->gnb) cudaFree(pr->gnb);
-        pr->gnb = nullptr;
+        if (pr->gnbn) cudaFree(pr->gnbn);
+        pr->gnb = pr->gnbn = nullptr;
         pr->gstride = std::max(cp.roff.nom, 1);
         size_t bytes = (size_t)pr->gstride * std::max(h.ngroup, 1) * sizeof(int);
         HX_CUDA(cudaMalloc((void **)&pr->gnb, bytes), "cudaMalloc(group-neighbour table)");
-        int rc = launch_groupnb(set->d, pr->roff, pr->gstride, pr->gnb, pr->stream);
-        if (rc) return rc;
-        HX_CUDA(cudaStreamSynchronize(pr->stream), "group-neighbour table");
+        if (!h.general) {
+            int rc = launch_groupnb(set->d, pr->roff, pr->gstride, pr->gnb, pr->stream);
+            if (rc) return rc;
+            HX_CUDA(cudaStreamSynchronize(pr->stream), "group-neighbour table");
+        } else {
+            // general set: the neighbour group of every group and outer move, found by binary search
+            // over the groups' prefixes (k_0..k_{N-3}, in lexicographic order), with its row count
+            HX_CUDA(cudaMalloc((void **)&pr->gnbn, bytes), "cudaMalloc(group row counts)");
+            const int npre = N - 1, nout = std::max(N - 2, 0), G = h.ngroup;
+            std::vector<int> first(bytes / sizeof(int), -1), rows(bytes / sizeof(int), 0);
+            auto gprefix = [&](int g) { return h.row_k.data() + (size_t)h.gfirst[g] * npre; };
+            std::vector<uint16_t> key(std::max(nout, 1));
+            for (int g = 0; g < G; ++g) {
+                for (int m = 0; m < cp.roff.nom; ++m) {
+                    bool ok = true;
+                    for (int l = 0; l < nout; ++l) {
+                        int kl = gprefix(g)[l];
+                        if (cp.roff.om[m][0] == l) kl += cp.roff.om[m][1];
+                        if (cp.roff.om[m][2] == l) kl += cp.roff.om[m][3];
+                        if (kl < 0 || kl > 65534) ok = false;
+                        key[l] = (uint16_t)std::max(kl, 0);
+                    }
+                    if (!ok) continue;
+                    int lo = 0, hi = G - 1, found = -1;
+                    while (lo <= hi) {
+                        const int mid = (lo + hi) / 2;
+                        const int c = memcmp_u16(gprefix(mid), key.data(), nout);
+                        if (c < 0) lo = mid + 1;
+                        else if (c > 0) hi = mid - 1;
+                        else { found = mid; break; }
+                    }
+                    if (found < 0) continue;
+                    first[(size_t)g * pr->gstride + m] = h.gfirst[found];
+                    rows[(size_t)g * pr->gstride + m] =
+                        (found + 1 < G ? h.gfirst[found + 1] : h.nrow) - h.gfirst[found];
+                }
+            }
+            HX_CUDA(cudaMemcpy(pr->gnb, first.data(), bytes, cudaMemcpyHostToDevice), "upload group-neighbour table");
+            HX_CUDA(cudaMemcpy(pr->gnbn, rows.data(), bytes, cudaMemcpyHostToDevice), "upload group row counts");
+        }
     }
     jit_prepare(pr);
     pr->have_pot = true;
@@ -647,33 +830,9 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
     return HX_OK;
 }
 
-}  // namespace hx
-
-using namespace hx;
-
-struct hx_indexset : IndexSetObj {};
-struct hx_problem : Problem {};
-struct hx_batch : Batch {};
-
-extern "C" {
-
-const char *hx_last_error(void) { return g_err; }
-
-int hx_indexset_create(int N, int64_t B, hx_indexset **out)
+// Device copies of the index tables of s (one allocation), then the per-element records.
+static int upload_set(IndexSetObj *s)
 {
-    if (!out || N < 1 || N > kMaxN || B < 1) {
-        set_error("hx_indexset_create: need 1 <= N <= %d, B >= 1, out != NULL", kMaxN);
-        return HX_EINVAL;
-    }
-    *out = nullptr;
-    if (B > 65535) {
-        set_error("hx_indexset_create: B = %lld > 65535 is not supported", (long long)B);
-        return HX_EUNSUPPORTED;
-    }
-    hx_indexset *s = new (std::nothrow) hx_indexset();
-    if (!s) { set_error("out of host memory"); return HX_ENOMEM; }
-    int rc = build_host_tables(N, (int)B, s->h);
-    if (rc) { delete s; return rc; }
     const IndexSetHost &h = s->h;
     size_t b_info = (size_t)std::max(h.nrow, 1) * sizeof(int4);
     size_t b_k = std::max<size_t>(h.row_k.size(), 1) * sizeof(uint16_t);
@@ -683,12 +842,12 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     size_t b_nt = (size_t)(kNtSpan * h.B + 1) * sizeof(int);
     size_t b_rs = (size_t)(h.nrow + 1) * sizeof(int);
     size_t b_rg = (size_t)std::max(h.nrow, 1) * sizeof(int);
-    size_t b_gf = (size_t)std::max(h.ngroup, 1) * sizeof(int);
+    size_t b_gf = (size_t)(h.ngroup + 1) * sizeof(int);
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t total = al(b_info) + al(b_k) + al(b_of) + al(b_qoff) + al(b_Q) + al(b_nt) + al(b_rs) + al(b_rg) + al(b_gf);
     cudaGetDevice(&s->device);
     cudaError_t e = cudaMalloc(&s->dmem, total);
-    if (e != cudaSuccess) { delete s; return cuda_fail(e, "cudaMalloc(index tables)"); }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(index tables)");
     char *base = (char *)s->dmem;
     int4 *d_info = (int4 *)base;
     base += al(b_info);
@@ -723,11 +882,15 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
         e = cudaMemcpy(d_rs, rs.data(), b_rs, cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMemcpy(d_rg, h.rgrp.data(), (size_t)h.nrow * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_gf, h.gfirst.data(), (size_t)h.ngroup * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        std::vector<int> gf(h.gfirst);
+        gf.push_back(h.nrow);
+        e = cudaMemcpy(d_gf, gf.data(), b_gf, cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess && !h.Q.empty()) e = cudaMemcpy(d_Q, h.Q.data(), h.Q.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) {
         cudaFree(s->dmem);
-        delete s;
+        s->dmem = nullptr;
         return cuda_fail(e, "upload index tables");
     }
     s->d.N = h.N;
@@ -745,17 +908,70 @@ int hx_indexset_create(int N, int64_t B, hx_indexset **out)
     s->d.rgrp = d_rg;
     s->d.gfirst = d_gf;
     s->d.ngroup = h.ngroup;
-    rc = launch_elem_info(s);
+    s->d.general = h.general ? 1 : 0;
+    int rc = launch_elem_info(s);
     if (rc) {
         cudaFree(s->dmem);
-        delete s;
+        s->dmem = nullptr;
         return rc;
     }
-    // the host copies of the row tables are no longer needed (rank/unrank use Q and qoff)
+    // the host copies of the row tables are no longer needed (rank/unrank use Q and qoff, or the
+    // sorted list); a general set keeps its row prefixes and groups for its group-neighbour tables
     std::vector<int4>().swap(s->h.row_info);
-    std::vector<uint16_t>().swap(s->h.row_k);
     std::vector<int>().swap(s->h.rgrp);
-    std::vector<int>().swap(s->h.gfirst);
+    if (!h.general) {
+        std::vector<uint16_t>().swap(s->h.row_k);
+        std::vector<int>().swap(s->h.gfirst);
+    }
+    return HX_OK;
+}
+
+
+}  // namespace hx
+
+using namespace hx;
+
+struct hx_indexset : IndexSetObj {};
+struct hx_problem : Problem {};
+struct hx_batch : Batch {};
+
+extern "C" {
+
+const char *hx_last_error(void) { return g_err; }
+
+int hx_indexset_create(int N, int64_t B, hx_indexset **out)
+{
+    if (!out || N < 1 || N > kMaxN || B < 1) {
+        set_error("hx_indexset_create: need 1 <= N <= %d, B >= 1, out != NULL", kMaxN);
+        return HX_EINVAL;
+    }
+    *out = nullptr;
+    if (B > 65535) {
+        set_error("hx_indexset_create: B = %lld > 65535 is not supported", (long long)B);
+        return HX_EUNSUPPORTED;
+    }
+    hx_indexset *s = new (std::nothrow) hx_indexset();
+    if (!s) { set_error("out of host memory"); return HX_ENOMEM; }
+    int rc = build_host_tables(N, (int)B, s->h);
+    if (rc) { delete s; return rc; }
+    int rc2 = upload_set(s);
+    if (rc2) { delete s; return rc2; }
+    *out = s;
+    return HX_OK;
+}
+
+int hx_indexset_create_list(int N, int64_t count, const int32_t *k, hx_indexset **out)
+{
+    if (!out || N < 1 || N > kMaxN || !k) {
+        set_error("hx_indexset_create_list: need 1 <= N <= %d, a list and out != NULL", kMaxN);
+        return HX_EINVAL;
+    }
+    *out = nullptr;
+    hx_indexset *s = new (std::nothrow) hx_indexset();
+    if (!s) { set_error("out of host memory"); return HX_ENOMEM; }
+    int rc = build_list_tables(N, count, k, s->h);
+    if (!rc) rc = upload_set(s);
+    if (rc) { delete s; return rc; }
     *out = s;
     return HX_OK;
 }
@@ -802,8 +1018,12 @@ int hx_problem_create(const hx_indexset *s, const hx_config *cfg, hx_problem **o
 {
     if (!s || !out) { set_error("hx_problem_create: NULL argument"); return HX_EINVAL; }
     *out = nullptr;
-    hx_config c = {HX_C128, HX_ORDER_SYM, 7, nullptr, HX_SCHEME_EXPMPR, 0.0};
+    hx_config c = {HX_C128, HX_ORDER_SYM, 7, nullptr, HX_SCHEME_EXPMPR, 0.0, 0.0};
     if (cfg) c = *cfg;
+    if (!(c.scale == 0.0 || (c.scale >= 1e-3 && c.scale <= 1e3))) {
+        set_error("hx_problem_create: scale S must be 0 (meaning 1) or in [1e-3, 1e3]");
+        return HX_EINVAL;
+    }
     if ((c.dtype != HX_C128 && c.dtype != HX_C64) || c.order < 0 || c.order > 2 || c.m < 1 || c.m > kMaxKrylov ||
         (c.scheme != HX_SCHEME_EXPMPR && c.scheme != HX_SCHEME_MAGNUS4) || !(c.tol >= 0.0 && c.tol <= 1.0)) {
         set_error("hx_problem_create: bad dtype, order, m (1..%d), scheme or tol (0..1)", kMaxKrylov);
@@ -813,6 +1033,7 @@ int hx_problem_create(const hx_indexset *s, const hx_config *cfg, hx_problem **o
     if (!p) { set_error("out of host memory"); return HX_ENOMEM; }
     p->set = s;
     p->cfg = c;
+    p->scale = c.scale > 0.0 ? c.scale : 1.0;
     p->stream = (cudaStream_t)c.stream;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -838,6 +1059,7 @@ void hx_problem_destroy(hx_problem *p)
     cudaFree(p->tab);
     cudaFree(p->pw_values);
     cudaFree(p->gnb);
+    cudaFree(p->gnbn);
     cudaFree(p->chan);
     cudaFree(p->dscal);
     for (void *x : p->extra) cudaFree(x);

@@ -33,6 +33,10 @@ struct IndexSetHost {
     int ngroup;
     std::vector<int> rgrp;            // nrow: group of each row (rows sharing k_0..k_{N-3})
     std::vector<int> gfirst;          // ngroup: first row of each group
+    // a general downward-closed set (hx_indexset_create_list): B is 1 + the largest coordinate,
+    // and ranks come from the sorted list instead of the rank tables
+    bool general = false;
+    std::vector<int32_t> list;        // size x N, lexicographic order
 };
 
 struct Problem;
@@ -79,7 +83,9 @@ struct Problem {
     std::string jit_reason;   // why jit is (or is not) set
     RowOffsets roff;          // row offsets of ops and ops1 (and their outer moves)
     int *gnb;                 // group-neighbour table (device), ngroup x gstride
+    int *gnbn;                // general sets: rows of each neighbour group (0: none), same layout
     int gstride;
+    double scale;             // basis scaling S (phi_k(S x)); D_K is multiplied by S^2
     bool skip_diag;           // internal: omit D_K (gradient direction operators)
     void *tab;                // device row tables
     size_t tab_bytes;

@@ -361,6 +361,10 @@ void jit_prepare(Problem *p)
         reason = "disabled by HX_APPLY_SPECIALISE=0";
         return;
     }
+    if (p->set->h.general) {
+        reason = "a general index set: the generic kernel decides membership from the row tables";
+        return;
+    }
     int md = 0;
     for (int i = 0; i < p->ops.nops; ++i) md = std::max(md, std::max(p->ops.op[i].p, p->ops.op[i].q));
     if (md > 3 || p->ops1.nops > 0) {

@@ -219,6 +219,9 @@ struct Elem {
     int k4;                 // k_{N-2} (0 for N = 1)
     const unsigned short *kr;     // prefix k_0..k_{N-2} of the own row
     const int *gn;                // group-neighbour table row of the own group
+    // general sets only: rows of the own group, and the row counts of the neighbour groups
+    int grows;
+    const int *gnn;
 };
 
 struct Ctx {
@@ -242,6 +245,27 @@ struct Ctx {
     {
         const RowMove m = mv[d];
         return start_mv(el, m.om, m.s4, ok);
+    }
+    // General sets (no product test): whether the point reached by row-offset column d and a shift
+    // sh of the last coordinate lies in K, and the start rank of its row (the own row's when not).
+    // The row exists when its group does and its coordinate k_{N-2} is below the group's row
+    // count; the point, when its last coordinate is below that row's length.
+    __device__ __forceinline__ bool member(const Elem &el, int d, int sh, int &start) const
+    {
+        const RowMove m = mv[d];
+        const int i4 = el.k4 + m.s4;
+        int rows = el.grows, row = el.r + m.s4;
+        if (m.om >= 0) {
+            rows = __ldg(el.gnn + m.om);
+            row = __ldg(el.gn + m.om) + i4;
+        }
+        bool ok = i4 >= 0 && i4 < rows;
+        row = ok ? row : el.r;
+        const int st = __ldg(S->rstart + row), len = __ldg(S->rstart + row + 1) - st;
+        const int jj = el.j + sh;
+        ok = ok && jj >= 0 && jj < len;
+        start = ok ? st : el.e - el.j;
+        return ok;
     }
 };
 
@@ -580,6 +604,12 @@ __device__ __forceinline__ Elem make_elem(const ApplyArgs &args, int e, int4 er)
     el.kr = args.S.row_k + (size_t)er.x * (N - 1);
     el.k4 = N >= 2 ? (int)__ldg(el.kr + N - 2) : 0;
     el.gn = args.gnb + (size_t)er.y * args.gstride;
+    el.grows = 0;
+    el.gnn = nullptr;
+    if (args.S.general) {
+        el.grows = __ldg(args.S.gfirst + er.y + 1) - __ldg(args.S.gfirst + er.y);
+        el.gnn = args.gnbn + (size_t)er.y * args.gstride;
+    }
     return el;
 }
 
@@ -596,7 +626,7 @@ __device__ __forceinline__ typename Vec2<R>::T apply_element(const ApplyArgs &ar
     const Elem el = make_elem(args, e, er);
     Acc<R> acc;
     if (!args.stage1 && !args.skip_diag) {
-        const R dj = (R)el.ksum + (R)0.5 * (R)S.N;   // (D_K)_jj = sum_l (j_l + 1/2)
+        const R dj = (R)args.dscale * ((R)el.ksum + (R)0.5 * (R)S.N);   // (D_K)_jj = sum_l (j_l + 1/2), times S^2
         acc.add(cscale(dj, cin[e]));
     }
     body(ctx, el, acc, sm_w, cin, (const R *)args.tab);
@@ -701,7 +731,7 @@ __device__ __forceinline__ void apply_elements_dual(const ApplyArgs &args, Body 
         const Elem el = make_elem(args, e, er);
         Acc<R> acc, acc2;
         if (!args.skip_diag) {
-            const R dj = (R)el.ksum + (R)0.5 * (R)S.N;
+            const R dj = (R)args.dscale * ((R)el.ksum + (R)0.5 * (R)S.N);
             acc.add(cscale(dj, cin[e]));
             acc2.add(cscale(dj, cin2[e]));
         }

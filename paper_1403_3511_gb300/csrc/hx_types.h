@@ -38,13 +38,14 @@ enum { MOD_CONST = 0, MOD_COS = 1, MOD_SIN2 = 2, MOD_PWCONST = 3 };
 // ---------------------------------------------------------------------------------------
 struct DevSet {
     int N, B, size, nrow, qtotal, ngroup;
+    int general;                      // 1: a general downward-closed set (membership from the tables)
     const int4 *row_info;             // nrow: {start rank, q(p), sum_l p_l, length}
     const unsigned short *row_k;            // nrow x (N - 1) prefixes
     const int4 *elem;                 // size: per element {row, group, prod_l (1 + k_l) | sum_l k_l << 16,
                                       //                    k_{N-1} | row length << 16}
     const int *rstart;                // nrow + 1: start rank of each row, rstart[nrow] = size
     const int *rgrp;                  // nrow: group of each row
-    const int *gfirst;                // ngroup: first row of each group
+    const int *gfirst;                // ngroup + 1: first row of each group, gfirst[ngroup] = nrow
     const int *qoff;                  // B + 2
     const int *Q;                     // (N - 1) x qtotal
     const int *nt;                    // nt[x] = floor(B / x) for 0 < x <= kNtSpan B, nt[0] = 0
@@ -119,7 +120,9 @@ struct RowOffsets {
 struct ApplyArgsBase {
     DevSet S;
     const int *gnb;           // group-neighbour table, ngroup x gstride
+    const int *gnbn;          // general sets: rows of each neighbour group (0: none), same layout
     int gstride;
+    double dscale;            // S^2: factor of D_K for the basis phi_k(S x)
     const double *t_ptr;      // device time
     double t_shift;           // A is evaluated at *t_ptr + t_shift
     const double *pw_values;  // device

@@ -50,7 +50,7 @@ class hx_control(ctypes.Structure):
 
 class hx_config(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("order", ctypes.c_int), ("m", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("scheme", ctypes.c_int), ("tol", ctypes.c_double)]
+                ("scheme", ctypes.c_int), ("tol", ctypes.c_double), ("scale", ctypes.c_double)]
 
 
 # const hx_potential *(*)(double t, void *user)
@@ -66,6 +66,7 @@ def _load():
     dp = ctypes.POINTER(ctypes.c_double)
     sig = {
         "hx_indexset_create": (ctypes.c_int, [ctypes.c_int, i64, ctypes.POINTER(P)]),
+        "hx_indexset_create_list": (ctypes.c_int, [ctypes.c_int, i64, i32p, ctypes.POINTER(P)]),
         "hx_indexset_size": (i64, [P]),
         "hx_indexset_unrank": (ctypes.c_int, [P, i64, i32p]),
         "hx_indexset_rank": (i64, [P, i32p]),
@@ -161,6 +162,17 @@ def hx_indexset_create(N: int, B: int):
     return h
 
 
+def hx_indexset_create_list(ks) -> ctypes.c_void_p:
+    """A general downward-closed set from an array of multi-indices, shape (count, N), any order."""
+    kk = np.ascontiguousarray(ks, dtype=np.int32)
+    if kk.ndim != 2:
+        raise ValueError("expected an array of shape (count, N)")
+    h = ctypes.c_void_p()
+    _check(lib.hx_indexset_create_list(kk.shape[1], kk.shape[0], kk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       ctypes.byref(h)))
+    return h
+
+
 def hx_indexset_size(s) -> int:
     return int(lib.hx_indexset_size(s))
 
@@ -190,8 +202,8 @@ def hx_indexset_destroy(s):
 # ---- problem -----------------------------------------------------------------------------
 
 def hx_problem_create(s, dtype: int = HX_C128, order: int = HX_ORDER_SYM, m: int = 7, stream: int = 0,
-                      scheme: int = HX_SCHEME_EXPMPR, tol: float = 0.0):
-    cfg = hx_config(dtype, order, m, ctypes.c_void_p(stream), scheme, tol)
+                      scheme: int = HX_SCHEME_EXPMPR, tol: float = 0.0, scale: float = 0.0):
+    cfg = hx_config(dtype, order, m, ctypes.c_void_p(stream), scheme, tol, scale)
     h = ctypes.c_void_p()
     _check(lib.hx_problem_create(s, ctypes.byref(cfg), ctypes.byref(h)))
     _PROBLEMS[h.value] = (dtype, hx_indexset_size(s))
@@ -381,7 +393,7 @@ def hx_adjoint_grad(s, L: float, fixed_terms: list, axis: int, u, t0: float, t1:
     pot, _keep = _potential(L, fixed_terms)
     uu = np.ascontiguousarray(u, dtype=np.float64)
     ctl = hx_control(axis, len(uu), substeps, t0, t1, _dptr(uu))
-    cfg = hx_config(HX_C128, order, m, ctypes.c_void_p(stream), HX_SCHEME_EXPMPR, 0.0)
+    cfg = hx_config(HX_C128, order, m, ctypes.c_void_p(stream), HX_SCHEME_EXPMPR, 0.0, 0.0)
     grad = np.zeros(len(uu))
     J = ctypes.c_double()
     _check(lib.hx_adjoint_grad(s, ctypes.byref(cfg), ctypes.byref(pot), ctypes.byref(ctl),
@@ -475,14 +487,14 @@ class Problem:
     """Convenience owner of an index set and a problem (frees both)."""
 
     def __init__(self, N: int, B: int, dtype: int = HX_C128, order: str = "sym", m: int = 7, stream: int = 0,
-                 indexset=None, scheme: int = HX_SCHEME_EXPMPR, tol: float = 0.0):
+                 indexset=None, scheme: int = HX_SCHEME_EXPMPR, tol: float = 0.0, scale: float = 0.0):
         self._own_set = indexset is None
         self.set = hx_indexset_create(N, B) if indexset is None else indexset
         self.N, self.B = N, B
         self.size = hx_indexset_size(self.set)
         self.dtype = dtype
         self.p = hx_problem_create(self.set, dtype, ORDERS[order] if isinstance(order, str) else order, m, stream,
-                                   scheme, tol)
+                                   scheme, tol, scale)
 
     def set_potential(self, spec: dict, t: float = 0.0):
         hx_potential_set(self.p, spec["L"], terms_from_spec(spec, t), t)

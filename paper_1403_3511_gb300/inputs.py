@@ -165,6 +165,46 @@ def coherent_state(kidx: np.ndarray, q) -> np.ndarray:
     return out.astype(np.complex128)
 
 
+def lex_sorted(ks: np.ndarray) -> np.ndarray:
+    """Rows of ks in lexicographic order, last coordinate fastest (the canonical order)."""
+    ks = np.asarray(ks, dtype=np.int32)
+    return ks[np.lexsort(ks.T[::-1])]
+
+
+def total_degree_set(N: int, K: int) -> np.ndarray:
+    """The total-degree set {k in N^N : k_1 + ... + k_N <= K}, a downward-closed set (Sec. 1.2)."""
+    out = []
+
+    def rec(prefix, left):
+        if len(prefix) == N:
+            out.append(list(prefix))
+            return
+        for k in range(left + 1):
+            rec(prefix + [k], left - k)
+
+    rec([], K)
+    return lex_sorted(np.array(out, dtype=np.int32))
+
+
+def random_downward_closed_set(N: int, size: int, seed: int) -> np.ndarray:
+    """A seeded random downward-closed set of the given size: starting from {0}, repeatedly add a
+    uniformly chosen point outside the set all of whose lower neighbours k - e_l are in it."""
+    rng = np.random.default_rng(seed)
+    members = {(0,) * N}
+    frontier = {tuple(1 if l == i else 0 for l in range(N)) for i in range(N)}
+    while len(members) < size:
+        cand = sorted(frontier)
+        k = cand[int(rng.integers(len(cand)))]
+        frontier.discard(k)
+        members.add(k)
+        for l in range(N):
+            up = tuple(k[i] + (1 if i == l else 0) for i in range(N))
+            if up not in members and all(tuple(up[i] - (1 if i == d else 0) for i in range(N)) in members
+                                         for d in range(N) if up[d] > 0):
+                frontier.add(up)
+    return lex_sorted(np.array(sorted(members), dtype=np.int32))
+
+
 def initial_vector(spec: dict, kidx: np.ndarray) -> np.ndarray:
     """The normalised initial coefficient vector of a workload, in canonical order of kidx."""
     init = spec["init"]

@@ -320,6 +320,48 @@ def test_coupled_quadratic_spectrum(oracle):
     assert np.allclose(ev[:6], want, atol=1e-9)
 
 
+@pytest.mark.parametrize("scale", [0.8, 1.3])
+def test_scaled_basis_spectra(oracle, scale):
+    """The basis phi_k(S x) (Sec. 1.4) changes the matrix but not the operator: for V = |x|^2 / 2
+    (W = 0) on N = 1 the lowest eigenvalues stay k + 1/2, and for the coupled quadratic V = x^T M x / 2
+    on a 2-d hyperbolic cross they stay sum_i (n_i + 1/2) sqrt(mu_i(M)).  A wrong factor of D_K, a
+    wrong sign or size of the (1/S^2 - S^2)/2 X^2 term, or W not evaluated at X / S moves them."""
+    S1 = oracle.IndexSet.hyperbolic(1, 80)
+    ev = np.sort(np.linalg.eigvalsh(oracle.dense_A(S1, np.zeros((0, 1), np.int32), np.zeros(0), 13.0, scale=scale)))
+    assert np.allclose(ev[:8], np.arange(8) + 0.5, atol=1e-9), ev[:8]
+    N, B = 2, 600
+    M = np.array([[1.3, 0.25], [0.25, 0.8]])
+    S = oracle.IndexSet.hyperbolic(N, B)
+    comps = [{"coef": 0.5 * (M[0, 0] - 1), "powers": {0: 2}}, {"coef": 0.5 * (M[1, 1] - 1), "powers": {1: 2}},
+             {"coef": M[0, 1], "powers": {0: 1, 1: 1}}]
+    spec = dict(N=N, B=B, L=inputs.half_width(B), potential=comps)
+    r, al = oracle.potential_terms(spec, 0.0)
+    A = oracle.dense_A(S, r, al, spec["L"], scale=scale)
+    ev = np.sort(np.linalg.eigvalsh(A))
+    w = np.sqrt(np.linalg.eigvalsh(M))
+    want = np.sort([(n1 + 0.5) * w[0] + (n2 + 0.5) * w[1] for n1 in range(8) for n2 in range(8)])[:6]
+    assert np.allclose(ev[:6], want, atol=1e-8), (ev[:6], want)
+    # the matrix-free product is the same matrix
+    c = inputs.initial_vector({"init": {"kind": "gaussian", "seed": 4}}, S.k)
+    assert np.abs(oracle.apply(S, r, al, spec["L"], c, scale=scale) - A @ c).max() <= 1e-11 * np.abs(A @ c).max()
+
+
+def test_general_downward_closed_sets(oracle):
+    """A total-degree set {|k|_1 <= 6} and a seeded random downward-closed set, given as lists: the
+    matrix-free product equals the dense matrix built from the recurrence on the same set (both
+    orders of the mixed term averaged), and for W = 0 it is D_K exactly."""
+    for ks in (inputs.total_degree_set(3, 6), inputs.random_downward_closed_set(3, 60, seed=8)):
+        S = oracle.IndexSet.from_list(ks)
+        spec = dict(N=3, L=6.0, potential=inputs.henon_heiles_chain(3, 0.111, (0.05, 1.0)))
+        r, al = oracle.potential_terms(spec, 0.3)
+        c = inputs.initial_vector({"init": {"kind": "gaussian", "seed": 5}}, S.k)
+        A = oracle.dense_A(S, r, al, spec["L"])
+        assert np.abs(oracle.apply(S, r, al, spec["L"], c) - A @ c).max() <= 1e-12 * np.abs(A @ c).max()
+        assert np.allclose(A, A.T, atol=1e-12)
+        y0 = oracle.apply(S, np.zeros((0, 3), np.int32), np.zeros(0), spec["L"], c)
+        assert np.array_equal(y0, oracle.diag(S) * c)
+
+
 # --------------------------------------------------------------------------- #
 # paper tables                                                                 #
 # --------------------------------------------------------------------------- #

@@ -381,7 +381,8 @@ def main():
     ms_apply = ea.elapsed_time(eb) / napply
     # the step's own product launches: with the specialised complex64 kernel they also compute the
     # projections h_i = <v_i, A v_k>, i <= k, k = 0 .. m-1 (hx_apply_project), each k once per step
-    fused = bool(hx.hx_apply_specialised(P.p)) and dtype == hx.HX_C64 and m <= 8
+    fused = (bool(hx.hx_apply_specialised(P.p)) and dtype == hx.HX_C64 and m <= 8
+             and hx.hx_step_launches(P.p)[0] == 1)      # one-stage potentials only
     ms_proj = 0.0
     if fused:
         basis = torch.randn((m, n), dtype=vdt, device="cuda")

@@ -268,11 +268,12 @@ HX_API int hx_apply_specialised(const hx_problem *p);
  * HX_SCHEME_EXPMPR (the normalisation, per Lanczos vector the product, one projection and two
  * orthogonalisation passes (one for the last vector), the eigensolver and the recombination),
  * or m (per_apply + 2) + 2 for HX_C64 when the product kernel is specialised
- * (hx_apply_specialised) and m <= 8 (that kernel then also computes the projection), and
- * m (4 per_apply + 4) + 2 for HX_SCHEME_MAGNUS4 (per Lanczos vector four products and their
- * combination into H v), m (2 per_apply + 3) + 2 when the product kernel is specialised (one launch
- * gives A_1 v and A_2 v, another A_2 A_1 v and A_1 A_2 v and combines them into H v).  Needs a
- * potential; either pointer may be NULL.  The paper has no counterpart: this reports how the library maps
+ * (hx_apply_specialised), per_apply = 1 and m <= 8 (that kernel then also computes the
+ * projection), and m (4 per_apply + 4) + 2 for HX_SCHEME_MAGNUS4 (per Lanczos vector four products
+ * and their combination into H v), m (2 per_apply + 3) + 2 when the product kernel is specialised
+ * and per_apply = 1 (one launch gives A_1 v and A_2 v, another A_2 A_1 v and A_1 A_2 v and combines
+ * them into H v); 2 more with hx_config.tol > 0 (the pass after the last vector and the error
+ * estimate), per sub-step.  Needs a potential; either pointer may be NULL.  The paper has no counterpart: this reports how the library maps
  * its work onto kernels. */
 HX_API int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step);
 

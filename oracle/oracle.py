@@ -574,3 +574,36 @@ def control_gradient_dense(S: IndexSet, spec: dict, c0: np.ndarray, phi: np.ndar
         grad_a[(n - 1) // per] += np.vdot(lam, Lf @ states[n - 1])
         lam = U.conj().T @ lam
     return J, 2.0 * np.real(np.conj(amp) * grad_a)
+
+
+def control_gradient_matfree(S: IndexSet, spec: dict, c0: np.ndarray, phi: np.ndarray, dt: float, nsub: int,
+                             n_intervals: int, m: int, order: str = "sym", gl_nodes: int = 8):
+    """The gradient of control_gradient_dense without any matrix: every exponential is an m-step
+    Lanczos exponential (lanczos_exp; the caller takes m and dt where it has converged) and the
+    Frechet derivative of exp at -i dt A_n in the direction -i dt X_1 is applied through its integral
+        lambda^H L psi = int_0^1 (e^{+i s dt A} lambda)^H (-i dt X_1) (e^{-i (1 - s) dt A} psi) ds,
+    evaluated by Gauss-Legendre quadrature in s (the integrand is an entire function of s).  States
+    psi_n are propagated forward, lambda_{n-1} = exp(+i dt A_n) lambda_n backward.  Returns (J, dJ/du)."""
+    x, w = np.polynomial.legendre.leggauss(gl_nodes)
+    s_nodes, s_weights = 0.5 * (x + 1.0), 0.5 * w
+    psi = np.array(c0, dtype=np.complex128)
+    states = [psi]
+    for n in range(nsub):
+        r, a = potential_terms(spec, (n + 0.5) * dt)
+        psi = lanczos_exp(lambda v: apply(S, r, a, spec["L"], v, order), psi, dt, m)[0]
+        states.append(psi)
+    amp = np.vdot(phi, psi)
+    lam = np.array(phi, dtype=np.complex128)
+    grad_a = np.zeros(n_intervals, dtype=np.complex128)
+    per = nsub // n_intervals
+    for n in range(nsub, 0, -1):
+        r, a = potential_terms(spec, (n - 0.5) * dt)
+        Av = lambda v: apply(S, r, a, spec["L"], v, order)
+        term = 0.0j
+        for s, ws in zip(s_nodes, s_weights):
+            right = lanczos_exp(Av, states[n - 1], (1.0 - s) * dt, m)[0]      # e^{-i (1-s) dt A} psi
+            left = lanczos_exp(Av, lam, -s * dt, m)[0]                        # e^{+i s dt A} lambda
+            term += ws * np.vdot(left, -1j * dt * direct_op(S, 0, right))
+        grad_a[(n - 1) // per] += term
+        lam = lanczos_exp(Av, lam, -dt, m)[0]                                 # U_n^H lambda = e^{+i dt A} lambda
+    return float(abs(amp) ** 2), 2.0 * np.real(np.conj(amp) * grad_a)

@@ -404,21 +404,23 @@ struct Compiler {
         return base;
     }
 
-    // Packed rows of a pure-parity polynomial of degree <= 3 (4 entries per row, 4-aligned base).
+    // Packed rows of a pure-parity polynomial of degree <= 8 (packed_width(p) entries per row,
+    // 4-aligned base).
     int packed(const std::vector<double> &a)
     {
         auto it = packed_base.find(PolyKey{a});
         if (it != packed_base.end()) return it->second;
         int p = (int)a.size() - 1;
         int B = set->h.B;
+        const int W = packed_width(p);
         tab.resize((tab.size() + 3) & ~(size_t)3, 0.0);
         int base = (int)tab.size();
-        tab.resize(tab.size() + (size_t)B * (p + 1) * 4, 0.0);
-        double row[2 * 3 + 1];
+        tab.resize(tab.size() + (size_t)B * (p + 1) * W, 0.0);
+        double row[2 * kMaxDeg + 1];
         for (int i = 0; i < B; ++i)
             for (int d = 0; d <= p; ++d) {
                 poly_row(a, L, i, i + 1 + d, row);
-                for (int j = 0; j <= p; ++j) tab[base + ((size_t)i * (p + 1) + d) * 4 + j] = row[2 * j];
+                for (int j = 0; j <= p; ++j) tab[base + ((size_t)i * (p + 1) + d) * W + j] = row[2 * j];
             }
         packed_base[PolyKey{a}] = base;
         return base;
@@ -479,7 +481,7 @@ struct Compiler {
                 return mask == want;
             };
             if (kind == 0) o.cls = CLS_ID;
-            else if (kind == 1 && o.p <= 3 && pure(o.pmask, o.p)) o.cls = CLS_LINE + o.p;
+            else if (kind == 1 && o.p <= kMaxDeg && pure(o.pmask, o.p)) o.cls = CLS_LINE + o.p;
             else if (kind == 2 && o.p <= 3 && o.q <= 3 && pure(o.pmask, o.p) && pure(o.qmask, o.q))
                 o.cls = CLS_PLANE + 3 * (o.p - 1) + (o.q - 1);
             else o.cls = CLS_GENERIC;
@@ -647,7 +649,23 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
             int n0 = t.deg[0] + 1, n1 = t.deg[1] + 1;
             std::vector<double> C(t.coef, t.coef + n0 * n1);
             std::vector<std::vector<double>> U, V;
-            rank_one_pieces(C, n0, n1, U, V);
+            // Split by parity first: T_i T_j with i and j of fixed parities form four blocks, and each
+            // block's rank-one pieces are polynomials of pure parity, which have specialised stencils
+            // with half the footprint (e.g. the interpolant of cos(x_a - x_b) splits exactly into the
+            // cos (x) cos and sin (x) sin pieces).  Blocks at round-off level are dropped.
+            double cmax = 0.0;
+            for (double x : C) cmax = std::max(cmax, fabs(x));
+            for (int pi = 0; pi < 2; ++pi)
+                for (int pj = 0; pj < 2; ++pj) {
+                    std::vector<double> Cb(C.size(), 0.0);
+                    double bmax = 0.0;
+                    for (int i = pi; i < n0; i += 2)
+                        for (int j = pj; j < n1; j += 2) {
+                            Cb[i * n1 + j] = C[i * n1 + j];
+                            bmax = std::max(bmax, fabs(C[i * n1 + j]));
+                        }
+                    if (bmax > 1e-14 * cmax) rank_one_pieces(Cb, n0, n1, U, V);
+                }
             for (size_t k = 0; k < U.size(); ++k) {
                 std::vector<double> P = U[k], Qp = V[k];
                 trim(P);
@@ -1385,7 +1403,9 @@ int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step)
     // 2-stage Magnus: A_1 v and A_2 v in one launch, A_2 A_1 v and A_1 A_2 v in another, with the
     // specialised kernel
     const int mag = apply_dual(p) ? 2 * a + 3 : 4 * a + 4;   // the second launch also forms H v
-    if (per_step) *per_step = p->cfg.scheme == HX_SCHEME_MAGNUS4 ? p->cfg.m * mag + 2 : p->cfg.m * (a + 2 + dots) + 2;
+    // with an error tolerance: the second pass after the last vector and the estimate, per sub-step
+    const int est = p->cfg.tol > 0.0 ? 2 : 0;
+    if (per_step) *per_step = (p->cfg.scheme == HX_SCHEME_MAGNUS4 ? p->cfg.m * mag + 2 : p->cfg.m * (a + 2 + dots) + 2) + est;
     return HX_OK;
 }
 

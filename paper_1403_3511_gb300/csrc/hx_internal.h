@@ -131,6 +131,7 @@ extern thread_local bool g_batch_capture;   // hx_krylov.cu: a batch graph is be
 // kernels compiled at run time for one potential's operator structure (hx_jit.cu)
 void jit_prepare(Problem *p);
 int jit_launch(const Problem *p, const void *args, int blocks, cudaStream_t st);
+bool jit_has_stage1(const Problem *p);   // the compiled kernels include the first (channel) stage
 
 // Lanczos workspaces outside the step graph (hx_krylov.cu), used by the adjoint gradient
 struct LanczosWS {

@@ -37,7 +37,8 @@ struct JitKernel {
     CUfunction fn_dots = nullptr;   // complex64 only: the product with fused projections
     CUfunction fn_dual = nullptr;   // two times at once
     CUfunction fn_pair = nullptr;   // two inputs at two times
-    int per_sm = 1, per_sm_dots = 1, per_sm_dual = 1, per_sm_pair = 1;
+    CUfunction fn_stage1 = nullptr; // the first stage of a two-stage potential (channel vectors)
+    int per_sm = 1, per_sm_dots = 1, per_sm_dual = 1, per_sm_pair = 1, per_sm_stage1 = 1;
 };
 
 // Driver functions, looked up through the runtime (the library does not link the driver library,
@@ -99,7 +100,7 @@ static std::string merged_weight(const OpSet &O, const Op &op, const char *w)
 
 // Compile-time row moves of operator i's footprint points (a type with the start / startx
 // functions of ColsRuntime): move (om, s4) of the column that didx gives each position.
-static std::string cols_type(const OpSet &O, const RowOffsets &ro, int i)
+static std::string cols_type(const OpSet &O, const RowOffsets &ro, int i, const char *prefix)
 {
     const Op &op = O.op[i];
     const int span = (2 * op.p + 1) * (2 * op.q + 1);
@@ -110,7 +111,7 @@ static std::string cols_type(const OpSet &O, const RowOffsets &ro, int i)
         return f;
     };
     auto col = [&](int dbase, int x) { return (int)O.didx[dbase + x]; };
-    std::string t = "struct ColsK" + std::to_string(i) + " {\n";
+    std::string t = "struct " + std::string(prefix) + std::to_string(i) + " {\n";
     t += chain("om", span, [&](int x) { return (int)ro.mv[col(op.dbase, x)].om; });
     t += chain("s4", span, [&](int x) { return (int)ro.mv[col(op.dbase, x)].s4; });
     if (op.kind == 2 && op.mergeB >= 0) {
@@ -129,12 +130,39 @@ static std::string cols_type(const OpSet &O, const RowOffsets &ro, int i)
     return t;
 }
 
-static std::string jit_types(const OpSet &O, const RowOffsets &ro)
+static std::string jit_types(const OpSet &O, const RowOffsets &ro, const char *prefix = "ColsK")
 {
     std::string t;
     for (int i = 0; i < O.nops; ++i)
-        if (O.op[i].kind >= 1 && !O.op[i].merged) t += cols_type(O, ro, i);
+        if (O.op[i].kind >= 1 && !O.op[i].merged) t += cols_type(O, ro, i, prefix);
     return t;
+}
+
+static bool specialised_line(const Op &op) { return op.cls >= CLS_LINE + 1 && op.cls <= CLS_LINE + kMaxDeg; }
+
+// Input vector of op i in the generated code: c, or the channel a first stage wrote.
+static std::string src_expr(const Op &op)
+{
+    if (op.src < 0) return "cin";
+    return "((const V *)args.chan + (size_t)" + std::to_string(op.src) + " * args.chan_ld)";
+}
+
+// The first stage of a two-stage potential (line operators writing the channel vectors
+// P(X_a) c), or "" when some operator needs the generic loop.
+static std::string jit_body_stage1(const OpSet &O)
+{
+    std::string b;
+    char line[768];
+    for (int i = 0; i < O.nops; ++i) {
+        const Op &op = O.op[i];
+        if (op.kind != 1 || !specialised_line(op) || op.src >= 0 || op.dst < 0) return "";
+        snprintf(line, sizeof(line),
+                 "    { const V o = line_role<R, %d, %s, ColsS%d>(ctx, el, O, O.op[%d], tab, cin);\n"
+                 "      ((V *)args.chan)[(size_t)%d * args.chan_ld + el.e] = cscale(sm_w[%d], o); }\n",
+                 op.p, op.ra == ROLE_LAST ? "ROLE_LAST" : "ROLE_ROW", i, i, op.dst, i);
+        b += line;
+    }
+    return b;
 }
 
 // The specialised sequence for O, or "" when some operator needs the generic loop.  dual: each
@@ -147,19 +175,19 @@ static std::string jit_body(const OpSet &O, bool dual = false)
     for (int i = 0; i < O.nops; ++i) {
         const Op &op = O.op[i];
         if (op.merged) continue;
-        if (op.src >= 0 || op.dst >= 0) return "";
+        if (op.dst >= 0 || (op.src >= 0 && op.kind != 1)) return "";
         std::string add2;
         if (op.kind == 0) {
             if (dual) add2 = " acc2.add(cscale(sm_w2[" + std::to_string(i) + "], cs));";
             snprintf(line, sizeof(line), "    { const V cs = cin[el.e]; acc.add(cscale(sm_w[%d], cs));%s }\n", i,
                      add2.c_str());
         } else if (op.kind == 1) {
-            if (op.cls < CLS_LINE + 1 || op.cls > CLS_LINE + 3 || op.mergeB >= 0) return "";
+            if (!specialised_line(op) || op.mergeB >= 0) return "";
             if (dual) add2 = " acc2.add(cscale(sm_w2[" + std::to_string(i) + "], o));";
             snprintf(line, sizeof(line),
-                     "    { const V o = line_role<R, %d, %s, ColsK%d>(ctx, el, O, O.op[%d], tab, cin);\n"
+                     "    { const V o = line_role<R, %d, %s, ColsK%d>(ctx, el, O, O.op[%d], tab, %s);\n"
                      "      acc.add(cscale(sm_w[%d], o));%s }\n",
-                     op.p, role_name(op.ra), i, i, i, add2.c_str());
+                     op.p, role_name(op.ra), i, i, src_expr(op).c_str(), i, add2.c_str());
         } else {
             const int sb = op.mergeB >= 0 ? O.op[op.mergeB].p : 0;
             if (!specialised_plane(op, sb)) return "";
@@ -219,7 +247,7 @@ static std::string jit_body_pair(const OpSet &O)
 }
 
 static std::string jit_source(bool f32, const std::string &types, const std::string &body, const std::string &body2,
-                              const std::string &body3)
+                              const std::string &body3, const std::string &body_s1 = "")
 {
     std::string s;
     s += "#include \"hx_stencil.cuh\"\n";
@@ -243,7 +271,24 @@ static std::string jit_source(bool f32, const std::string &types, const std::str
          "                                         const V *cin2, const R *tab)\n{\n"
          "    const OpSet &O = args.ops;\n";
     s += body3;
-    s += "}\n}  // namespace hx\n";
+    s += "}\n";
+    if (!body_s1.empty()) {
+        s += "__device__ __forceinline__ void ops_stage1(const ApplyArgs &args, const Ctx &ctx, const Elem &el, Acc<R> &acc,\n"
+             "                                           const R *sm_w, const V *cin, const R *tab)\n{\n"
+             "    const OpSet &O = args.ops;\n";
+        s += body_s1;
+        s += "}\n";
+    }
+    s += "}  // namespace hx\n";
+    if (!body_s1.empty()) {   // the first stage of a two-stage potential: writes the channel vectors
+        s += f32 ? "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 4)\n"
+                 : "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 3)\n";
+        s += "hx_apply_specialised_stage1(const __grid_constant__ hx::ApplyArgs args)\n{\n"
+             "    hx::apply_elements<hx::R>(args, [&](const hx::Ctx &ctx, const hx::Elem &el, hx::Acc<hx::R> &acc,\n"
+             "                                        const hx::R *sm_w, const hx::V *cin, const hx::R *tab) {\n"
+             "        hx::ops_stage1(args, ctx, el, acc, sm_w, cin, tab);\n"
+             "    });\n}\n";
+    }
     // 4 blocks of 256 per SM fit the FP32 kernels in 64 registers without spills (more warps to hide
     // the load latency); the FP64 kernels would spill there and keep 3 blocks (80 registers)
     s += f32 ? "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 4)\n"
@@ -326,7 +371,12 @@ static bool compile_and_load(const std::string &src, int dev, JitKernel *out, st
         reason = "loading the compiled kernel failed";
         return false;
     }
-    CUfunction fn_dots = nullptr, fn_dual = nullptr, fn_pair = nullptr;
+    CUfunction fn_dots = nullptr, fn_dual = nullptr, fn_pair = nullptr, fn_stage1 = nullptr;
+    if (src.find("hx_apply_specialised_stage1") != std::string::npos &&
+        drv.moduleGetFunction(&fn_stage1, mod, "hx_apply_specialised_stage1") != CUDA_SUCCESS) {
+        reason = "loading the compiled kernel failed";
+        return false;
+    }
     if ((src.find("hx_apply_specialised_dots") != std::string::npos &&
          drv.moduleGetFunction(&fn_dots, mod, "hx_apply_specialised_dots") != CUDA_SUCCESS) ||
         drv.moduleGetFunction(&fn_dual, mod, "hx_apply_specialised_dual") != CUDA_SUCCESS ||
@@ -343,6 +393,8 @@ static bool compile_and_load(const std::string &src, int dev, JitKernel *out, st
     out->fn_dots = fn_dots;
     out->fn_dual = fn_dual;
     out->fn_pair = fn_pair;
+    out->fn_stage1 = fn_stage1;
+    out->per_sm_stage1 = occ(fn_stage1);
     out->per_sm = occ(fn);
     out->per_sm_dots = occ(fn_dots);
     out->per_sm_dual = occ(fn_dual);
@@ -365,20 +417,25 @@ void jit_prepare(Problem *p)
         reason = "a general index set: the generic kernel decides membership from the row tables";
         return;
     }
-    int md = 0;
-    for (int i = 0; i < p->ops.nops; ++i) md = std::max(md, std::max(p->ops.op[i].p, p->ops.op[i].q));
-    if (md > 3 || p->ops1.nops > 0) {
-        reason = "an operator needs the generic kernel (degree above 3 or a channel stage)";
-        return;
-    }
     const std::string body = jit_body(p->ops);
     if (body.empty()) {
         reason = "an operator has no specialised stencil";
         return;
     }
+    std::string body_s1;
+    if (p->ops1.nops > 0) {
+        body_s1 = jit_body_stage1(p->ops1);
+        if (body_s1.empty()) {
+            reason = "a first-stage operator has no specialised stencil";
+            return;
+        }
+    }
     const bool f32 = p->cfg.dtype == HX_C64;
-    const std::string types = jit_types(p->ops, p->roff);
-    const std::string key = std::to_string(p->device) + (f32 ? "|f|" : "|d|") + types + body;
+    const std::string types = jit_types(p->ops, p->roff) + jit_types(p->ops1, p->roff, "ColsS");
+    const std::string key = std::to_string(p->device) + (f32 ? "|f|" : "|d|") + types + body + body_s1;
+    // the two-time kernels run only for single-stage potentials (apply_dual)
+    const std::string body_dual = p->ops1.nops ? "" : jit_body(p->ops, true);
+    const std::string body_pair = p->ops1.nops ? "" : jit_body_pair(p->ops);
     std::lock_guard<std::mutex> lock(g_jit_mu);
     auto it = g_jit_cache.find(key);
     if (it == g_jit_cache.end()) {
@@ -386,12 +443,12 @@ void jit_prepare(Problem *p)
         // HX_JIT_SOURCE_DUMP=<file>: the generated source is written there before it is compiled
         if (const char *dump = getenv("HX_JIT_SOURCE_DUMP")) {
             if (FILE *f = fopen(dump, "w")) {
-                const std::string src = jit_source(f32, types, body, jit_body(p->ops, true), jit_body_pair(p->ops));
+                const std::string src = jit_source(f32, types, body, body_dual, body_pair, body_s1);
                 fwrite(src.data(), 1, src.size(), f);
                 fclose(f);
             }
         }
-        if (!compile_and_load(jit_source(f32, types, body, jit_body(p->ops, true), jit_body_pair(p->ops)), p->device, &k, reason))
+        if (!compile_and_load(jit_source(f32, types, body, body_dual, body_pair, body_s1), p->device, &k, reason))
             return;
         it = g_jit_cache.emplace(key, k).first;
     }
@@ -405,6 +462,22 @@ int jit_launch(const Problem *p, const void *args, int blocks, cudaStream_t st)
     const JitKernel *k = (const JitKernel *)p->jit;
     const ApplyArgs *a = (const ApplyArgs *)args;
     const bool dots = a->dvec != nullptr, dual = a->cout2 != nullptr, pair = dual && a->cin2 != nullptr;
+    if (a->stage1) {
+        if (!k->fn_stage1) {
+            set_error("internal: no compiled first-stage kernel");
+            return HX_EUNSUPPORTED;
+        }
+        const int grid = std::max(1, std::min({p->num_sms * k->per_sm_stage1, apply_grid(p), blocks}));
+        void *params[] = {const_cast<void *>(args)};
+        CUresult r = driver().launchKernel(k->fn_stage1, grid, 1, 1, kApplyThreads, 1, 1, 0, (CUstream)st, params, nullptr);
+        if (r != CUDA_SUCCESS) {
+            const char *msg = nullptr;
+            driver().errorString(r, &msg);
+            set_error("specialised first-stage kernel launch: %s", msg ? msg : "unknown error");
+            return HX_ECUDA;
+        }
+        return HX_OK;
+    }
     if ((dots && !k->fn_dots) || (dots && dual)) {
         set_error("the specialised kernel has no fused projections here (complex64 single products only)");
         return HX_EUNSUPPORTED;
@@ -426,4 +499,8 @@ int jit_launch(const Problem *p, const void *args, int blocks, cudaStream_t st)
     return HX_OK;
 }
 
+}  // namespace hx
+
+namespace hx {
+bool jit_has_stage1(const Problem *p) { return p->jit && ((const JitKernel *)p->jit)->fn_stage1 != nullptr; }
 }  // namespace hx

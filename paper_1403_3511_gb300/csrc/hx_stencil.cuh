@@ -292,6 +292,32 @@ __device__ __forceinline__ int nt_of(const DevSet &S, int x) { return x <= S.B ?
 
 // One packed row (4 entries, see the packed row tables): a 16-byte load for FP32, two for FP64.
 template <typename R> struct Row4 { R v[4]; };
+// A packed row of W entries (a multiple of 4): W / 4 16-byte loads for FP32, W / 2 for FP64.
+template <typename R, int W> struct RowW { R v[W]; };
+template <int W> __device__ __forceinline__ RowW<float, W> load_roww(const float *p)
+{
+    RowW<float, W> r;
+#pragma unroll
+    for (int i = 0; i < W / 4; ++i) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p) + i);
+        r.v[4 * i] = q.x;
+        r.v[4 * i + 1] = q.y;
+        r.v[4 * i + 2] = q.z;
+        r.v[4 * i + 3] = q.w;
+    }
+    return r;
+}
+template <int W> __device__ __forceinline__ RowW<double, W> load_roww(const double *p)
+{
+    RowW<double, W> r;
+#pragma unroll
+    for (int i = 0; i < W / 2; ++i) {
+        const double2 q = __ldg(reinterpret_cast<const double2 *>(p) + i);
+        r.v[2 * i] = q.x;
+        r.v[2 * i + 1] = q.y;
+    }
+    return r;
+}
 __device__ __forceinline__ Row4<float> load_row4(const float *p)
 {
     const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
@@ -336,7 +362,8 @@ __device__ __forceinline__ void line_role_n(const Ctx &c, const Elem &el, const 
 #pragma unroll
         for (int t = 1; t <= P; ++t) top += other * t <= slack ? 1 : 0;
     }
-    const Row4<R> row = load_row4(tab + op.ptabP + (ka * (P + 1) + top) * 4);   // entries at s = -P + 2j
+    constexpr int W = packed_width(P);
+    const RowW<R, W> row = load_roww<W>(tab + op.ptabP + (ka * (P + 1) + top) * W);   // entries at s = -P + 2j
     constexpr int NP = P + 1;
     int addr[NP];
 #pragma unroll

@@ -61,11 +61,14 @@ struct DevSet {
 //   tab[base + ((i * (p + 1) + d) * (2p + 1)) + (s + p)] = [P(J_n / L)]_{i, i+s},  n = i + 1 + d,
 // where J_n is the n x n truncated Jacobi matrix of the Hermite recurrence (Eq. (Recurrence1D)):
 // row i of a fibre whose top is d steps above i (d = p stands for "p or more").
-// Packed row tables (a polynomial of pure parity and degree p <= 3, whose row has p + 1 entries
-// that can be nonzero, at s = -p, -p + 2, ..., p):
-//   tab[pbase + (i * (p + 1) + d) * 4 + j] = [P(J_n / L)]_{i, i-p+2j},  j <= p, zero for j > p,
-// one 16-byte (FP32) or 32-byte (FP64) load per row.
+// Packed row tables (a polynomial of pure parity and degree p <= 8, whose row has p + 1 entries
+// that can be nonzero, at s = -p, -p + 2, ..., p), W = packed_width(p) = 4 ceil((p + 1) / 4) entries
+// per row:
+//   tab[pbase + (i * (p + 1) + d) * W + j] = [P(J_n / L)]_{i, i-p+2j},  j <= p, zero for j > p,
+// W / 4 16-byte loads (FP32) or W / 2 (FP64) per row.
 // ---------------------------------------------------------------------------------------
+__host__ __device__ constexpr int packed_width(int p) { return 4 * ((p + 4) / 4); }
+
 // op classes with compile-time stencils (pure parity: P has only terms of the parity of its degree)
 enum { CLS_ID = 0, CLS_LINE = 1, CLS_PLANE = 10, CLS_GENERIC = 30 };
 // axis roles: an axis of the row prefix (moving along it changes the row) or the last axis
@@ -73,13 +76,13 @@ enum { ROLE_ROW = 0, ROLE_LAST = 1, ROLE_NONE = 2 };
 
 struct Op {
     int kind;
-    int cls;                  // CLS_ID, CLS_LINE + p, CLS_PLANE + 3 (p-1) + (q-1) (pure parity, p, q <= 3), CLS_GENERIC
+    int cls;                  // CLS_ID, CLS_LINE + p (p <= 8), CLS_PLANE + 3 (p-1) + (q-1) (p, q <= 3), CLS_GENERIC (pure parity)
     int ra, rb;               // axis roles: ROLE_ROW (< N-1), ROLE_LAST (N-1), ROLE_NONE
     int a, b;                 // axes (b = -1 for a line op)
     int p, q;                 // degrees on a and b
     int pmask, qmask;         // bit (s + p) set when the rows can be nonzero at offset s
     int tabP, tabQ;           // row table bases
-    int ptabP, ptabQ;         // packed row table bases (pure parity, degree <= 3; 0 otherwise)
+    int ptabP, ptabQ;         // packed row table bases (pure parity, line degree <= 8, plane degrees <= 3; 0 otherwise)
     int dbase;                // base into didx (footprint position -> row offset index)
     int src, dst;             // input channel (-1 = c), output channel (stage 1 only)
     int mergeB;               // plane ops: index of a line op on axis b evaluated inside this op (-1: none)

@@ -273,11 +273,12 @@ def test_errors(hx):
         P.close()
 
 
-@pytest.mark.parametrize("case", ["hh6_b2000", "ctrl4_b512", "hh3_b300_dipole", "hh2_b40000"])
+@pytest.mark.parametrize("case", ["hh6_b2000", "ctrl4_b512", "hh3_b300_dipole", "hh2_b40000", "cos3_b64"])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_specialised_kernel_matches_generic(hx, case, dtype, monkeypatch):
     """Potentials whose operators all have specialised stencils run a kernel compiled for their
-    operator sequence at hx_potential_set; it computes what the generic kernel computes."""
+    operator sequence at hx_potential_set; it computes what the generic kernel computes (the cosine
+    chain: degree-8 line operators and a compiled channel stage)."""
     spec = CASES[case]()
     dt = hx.HX_C128 if dtype == "c128" else hx.HX_C64
     n = None
@@ -297,9 +298,10 @@ def test_specialised_kernel_matches_generic(hx, case, dtype, monkeypatch):
     assert err <= (1e-14 if dtype == "c128" else 1e-6), err
 
 
-@pytest.mark.parametrize("case,why", [("cos3_b64", "generic kernel"), ("merge4_b160", "no specialised stencil")])
+@pytest.mark.parametrize("case,why", [("merge4_b160", "no specialised stencil"), ("rand4_b90_deg6", "no specialised stencil"),
+                                      ("cos4_b40_deg5", "no specialised stencil")])
 def test_potentials_without_specialised_kernel(hx, case, why):
-    """A channel stage (degree-8 terms) or a plane operator of degree 3 keeps the generic kernel."""
+    """Plane operators of degree 3 or more keep the generic kernel."""
     P = make(hx, CASES[case](), hx.HX_C64)
     try:
         assert hx.hx_apply_specialised(P.p) == 0
@@ -327,7 +329,7 @@ def test_apply_project_matches_oracle(hx, oracle, case, dtype, k, fused):
     ref = oracle.apply(S, r, a, spec["L"], c)
     P = make(hx, spec, dt, t=0.4)
     try:
-        assert bool(hx.hx_apply_specialised(P.p) and dtype == "c64") == fused
+        assert bool(hx.hx_apply_specialised(P.p) and dtype == "c64" and hx.hx_step_launches(P.p)[0] == 1) == fused
         basis = torch.zeros((k + 1, n + 37), dtype=tdt, device="cuda")[:, :n]
         basis.copy_(torch.from_numpy(basis_np).to(tdt))
         x = basis[0].clone()

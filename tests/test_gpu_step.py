@@ -304,8 +304,9 @@ def test_magnus4_time_integration_experiment(hx, oracle):
 
 def test_step_launch_counts(hx):
     # expMPR: the specialised complex64 product kernel computes the projections itself when m <= 8
-    per = {0: lambda m, a, spec, c64: m * (a + (2 if spec and c64 and m <= 8 else 3)) + 2,
-           1: lambda m, a, spec, c64: m * (2 * a + 3 if spec else 4 * a + 4) + 2}
+    # and the product is one launch; Magnus: the two-time kernels need a one-stage product too
+    per = {0: lambda m, a, spec, c64: m * (a + (2 if spec and c64 and m <= 8 and a == 1 else 3)) + 2,
+           1: lambda m, a, spec, c64: m * (2 * a + 3 if spec and a == 1 else 4 * a + 4) + 2}
     for scheme in (0, 1):
         for name in ("hh2_b32", "cos10_b1024"):
             spec = inputs.workload(name) if name == "hh2_b32" else dict(N=3, B=40, L=inputs.half_width(40),
@@ -317,7 +318,7 @@ def test_step_launch_counts(hx):
                     a, step = hx.hx_step_launches(P.p)
                     assert a == (1 if name == "hh2_b32" else 2)
                     specialised = hx.hx_apply_specialised(P.p)
-                    assert specialised == (name == "hh2_b32")
+                    assert specialised == 1        # the cosine chain's channel stage is compiled too
                     assert step == per[scheme](m, a, specialised, dtype == hx.HX_C64)
                 finally:
                     P.close()

@@ -362,6 +362,26 @@ def test_general_downward_closed_sets(oracle):
         assert np.array_equal(y0, oracle.diag(S) * c)
 
 
+def test_matrix_free_adjoint_matches_dense(oracle):
+    """The matrix-free FP64 adjoint gradient (Lanczos exponentials, Gauss-Legendre quadrature of the
+    Frechet derivative) against the dense one (scipy's expm_frechet) on N = 2, B = 10, where m = |K|
+    makes every Lanczos exponential exact.  A sign error in either exponential of the integrand, a
+    missing dt, or lambda propagated the wrong way breaks it."""
+    N, B = 2, 10
+    S = oracle.IndexSet.hyperbolic(N, B)
+    u = np.array([0.07, -0.05, 0.02, 0.09])
+    T, substeps = 0.8, 2
+    spec = dict(N=N, B=B, L=inputs.half_width(B), potential=inputs.control_quartic(u, T))
+    c0 = inputs.initial_vector({"init": {"kind": "coherent", "q": [1.0, 0.0], "eps": 0.0, "seed": 0}}, S.k)
+    phi = np.zeros(S.size, complex)
+    phi[S.rank([1, 0])] = 1.0
+    dt = T / (len(u) * substeps)
+    J_d, g_d = oracle.control_gradient_dense(S, spec, c0, phi, dt, len(u) * substeps, len(u))
+    J_m, g_m = oracle.control_gradient_matfree(S, spec, c0, phi, dt, len(u) * substeps, len(u), m=S.size)
+    assert abs(J_m - J_d) <= 1e-12 * J_d
+    assert np.abs(g_m - g_d).max() <= 1e-11 * np.abs(g_d).max(), (g_m, g_d)
+
+
 # --------------------------------------------------------------------------- #
 # paper tables                                                                 #
 # --------------------------------------------------------------------------- #

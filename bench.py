@@ -296,6 +296,42 @@ def run_batch(args, world: int, local: int, rank: int):
     ms_step = max_over_ranks([e0.elapsed_time(e1) / args.steps], world, "cuda")[0]
     units = sum(sp["m"] * n for sp, n in zip(specs, sizes))
     launches = sum(hx.hx_step_launches(P.p)[1] for P in probs)
+    # mixed against FP64 on the same members at a step where one m = 7 Lanczos exponential is
+    # converged for the largest of them (B = 8192: h ||A|| about 1), both timed over the same steps
+    extra = {}
+    if not args.no_fp64 and dtype == hx.HX_C64:
+        dtc, kc = 1e-5, max(args.converged_steps or 3, 1)
+        p64 = []
+        for sp, P in zip(specs, probs):
+            Q = hx.Problem(sp["N"], sp["B"], dtype=hx.HX_C128, m=sp["m"], stream=stream.cuda_stream, indexset=P.set)
+            Q.set_potential(sp, 0.0)
+            p64.append(Q)
+        starts = [x.clone() for x in states]
+        res = {}
+        for name, group in (("fp64", p64), ("mixed", probs)):
+            for Pp in group:
+                hx.hx_set_time(Pp.p, 0.0)
+            cur = [x.clone() for x in starts]
+            bb = hx.hx_batch_create([Pp.p for Pp in group])
+            hx.hx_batch_step(bb, cur, dtc, 1)                 # captures the graph
+            for Pp in group:
+                hx.hx_set_time(Pp.p, 0.0)
+            for x, x0 in zip(cur, starts):
+                x.copy_(x0)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            hx.hx_batch_step(bb, cur, dtc, kc)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[name] = (1e3 * kc / e0.elapsed_time(e1), cur)
+            hx.hx_batch_destroy(bb)
+        err = max((torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item()
+                  for a, b in zip(res["mixed"][1], res["fp64"][1]))
+        extra = {"fp64_steps_per_s": res["fp64"][0], "mixed_steps_per_s": res["mixed"][0],
+                 "mixed_vs_fp64_rel_err_final": err,
+                 "converged": {"dt": dtc, "steps": kc, "err": "largest member relative 2-norm difference"}}
+        for Q in p64:
+            Q.close()
     if rank == 0:
         print(json.dumps({
             "metric": "Galerkin matvecs: Gcoeff/s", "value": units * world / (ms_step * 1e-3) / 1e9,
@@ -306,7 +342,7 @@ def run_batch(args, world: int, local: int, rank: int):
                        "largest": int(max(sizes)), "m": specs[0]["m"], "dt": dt, "setup_s": setup_s,
                        "potential": "Henon-Heiles chains, lambda ~ U[0.05, 0.15]",
                        "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
-            "gpu_launches": launches * args.steps}), flush=True)
+            "gpu_launches": launches * args.steps, **extra}), flush=True)
     hx.hx_batch_destroy(b)
     for P in probs:
         P.close()

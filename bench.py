@@ -286,7 +286,7 @@ def run_batch(args, world: int, local: int, rank: int):
     setup_s = time.perf_counter() - t0
     b = hx.hx_batch_create([P.p for P in probs])
     dt = specs[0]["dt"]
-    hx.hx_batch_step(b, states, dt, args.warmup)
+    hx.hx_batch_step(b, states, dt, max(args.warmup, 4))     # also times the four schedules
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -295,7 +295,8 @@ def run_batch(args, world: int, local: int, rank: int):
     torch.cuda.synchronize()
     ms_step = max_over_ranks([e0.elapsed_time(e1) / args.steps], world, "cuda")[0]
     units = sum(sp["m"] * n for sp, n in zip(specs, sizes))
-    launches = sum(hx.hx_step_launches(P.p)[1] for P in probs)
+    binfo = hx.hx_batch_info(b)
+    launches = binfo["launches"]
     # mixed against FP64 on the same members at a step where one m = 7 Lanczos exponential is
     # converged for the largest of them (B = 8192: h ||A|| about 1), both timed over the same steps
     extra = {}
@@ -313,7 +314,7 @@ def run_batch(args, world: int, local: int, rank: int):
                 hx.hx_set_time(Pp.p, 0.0)
             cur = [x.clone() for x in starts]
             bb = hx.hx_batch_create([Pp.p for Pp in group])
-            hx.hx_batch_step(bb, cur, dtc, 1)                 # captures the graph
+            hx.hx_batch_step(bb, cur, dtc, 4)                 # captures and times the schedules
             for Pp in group:
                 hx.hx_set_time(Pp.p, 0.0)
             for x, x0 in zip(cur, starts):
@@ -335,13 +336,18 @@ def run_batch(args, world: int, local: int, rank: int):
     if rank == 0:
         print(json.dumps({
             "metric": "Galerkin matvecs: Gcoeff/s", "value": units * world / (ms_step * 1e-3) / 1e9,
-            "unit": "Gcoeff/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "unit": "Gcoeff/s", "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 4),
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64+f64" if dtype == hx.HX_C64 else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "problems": count, "total_size": int(sum(sizes)),
                        "largest": int(max(sizes)), "m": specs[0]["m"], "dt": dt, "setup_s": setup_s,
                        "potential": "Henon-Heiles chains, lambda ~ U[0.05, 0.15]",
-                       "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+                       "l2": "inputs larger than L2", "parallelism": f"replicas x{world}",
+                       "schedule": ["member graphs", "batched products", "hybrid", "serial specialised"][binfo["schedule"]],
+                       "schedule_step_ms": {["member graphs", "batched products", "hybrid", "serial specialised"][k]: round(v, 3)
+                                            for k, v in binfo["step_ms"].items()},
+                       "tile": binfo["tile"],
+                       "tile_candidates_ms": {str(t): round(ms, 4) for t, ms in binfo["candidates"]}},
             "gpu_launches": launches * args.steps, **extra}), flush=True)
     hx.hx_batch_destroy(b)
     for P in probs:

@@ -292,6 +292,49 @@ typedef struct hx_batch hx_batch;
 HX_API int hx_batch_create(hx_problem *const *probs, int n, hx_batch **out);
 HX_API int hx_batch_step(hx_batch *b, void *const *c, double dt, int nsteps);
 HX_API void hx_batch_destroy(hx_batch *b);
+/* Schedules of a batch step.  All three run the same kernels on each member and give the same bits:
+ *   HX_SCHED_MEMBERS  one graph per step holding every member's step as an independent child graph,
+ *                     each member's product its own launch;
+ *   HX_SCHED_BATCHED  per Lanczos index one persistent product launch per (precision, degree <= 3 or
+ *                     not) class over all members: blocks draw tiles of consecutive coefficients of any
+ *                     member from a shared queue, largest members first; the members' projections,
+ *                     Gram-Schmidt passes and exponentials stay their own kernels, forked from and
+ *                     joined to those launches inside the graph;
+ *   HX_SCHED_HYBRID   members with at least one wave of product blocks (|K| >= 4 x 256 x SM count)
+ *                     step on their own streams as in HX_SCHED_MEMBERS, the others as in
+ *                     HX_SCHED_BATCHED;
+ *   HX_SCHED_SERIAL   members with a specialised kernel (hx_apply_specialised) and at least four
+ *                     waves of product blocks take their own step's kernels (the specialised product,
+ *                     in complex64 with fused projections) one member after another with nothing
+ *                     running beside them, then the others as in HX_SCHED_BATCHED.  These members
+ *                     get the bits of hx_step; the first three schedules give one another's bits.
+ * The batched schedules need every member on the exponential midpoint rule with one product stage,
+ * on a hyperbolic cross, with fixed sub-steps (tol = 0); otherwise only HX_SCHED_MEMBERS runs.  The
+ * first steps after a (re)capture run each candidate once, timed between two events, and the rest
+ * use the fastest (with fewer steps than candidates, the next call goes on timing).  The tile size
+ * of the batched launches is chosen before that by timing 256, 512, 1024, 2048 and 4096 elements on
+ * the product of the first Lanczos index.  HX_BATCH_BATCHED=0, 1, 2 or 3 in the environment forces
+ * HX_SCHED_MEMBERS, HX_SCHED_BATCHED, HX_SCHED_HYBRID or HX_SCHED_SERIAL.
+ *
+ * hx_batch_set_budget: seconds >= 0 bounds each block of a batched product launch to that much
+ * SM time (clock64 ticks at the device's clock rate); a block that runs over stops taking tiles and
+ * sets a flag, so the launch ends early with an incomplete product instead of running on.
+ * hx_batch_step then synchronises and returns HX_ETIMEOUT (the states are then not valid).
+ * seconds < 0 (the default) removes the bound.  A change of budget re-captures the batch graphs.
+ *
+ * hx_batch_info: the state after the last hx_batch_step (all zero / -1 before the first). */
+enum { HX_SCHED_MEMBERS = 0, HX_SCHED_BATCHED = 1, HX_SCHED_HYBRID = 2, HX_SCHED_SERIAL = 3 };
+typedef struct {
+    int schedule;        /* HX_SCHED_* in use, -1 while the candidates are still being timed */
+    int tile;            /* elements per tile of the batched launches (0: not tuned) */
+    int launches;        /* kernel launches of one step of the schedule in use */
+    int ntiles;          /* tile-size candidates timed */
+    int tiles[8];        /* their sizes ... */
+    float tile_ms[8];    /* ... and the time of the first Lanczos index's batched products, ms */
+    float step_ms[4];    /* one timed step of each schedule, ms (-1: not a candidate) */
+} hx_batch_stats;
+HX_API int hx_batch_set_budget(hx_batch *b, double seconds);
+HX_API int hx_batch_info(const hx_batch *b, hx_batch_stats *out);
 
 /* ---- gradient with respect to a control (adjoint) ---------------------------- */
 

@@ -238,66 +238,153 @@ __device__ __forceinline__ typename Vec2<R>::T line_dispatch(int ra, const Ctx &
 // MD: largest polynomial degree of the compiled potential (3: unrolled stencils; kMaxDeg: rolled loops).
 // The operator list is read from the launch arguments and dispatched per operator; the kernels
 // compiled at run time for one potential (hx_jit.cu) replace this loop by the fixed sequence.
+// The operator list of args at one element, dispatched per operator (the kernels compiled for one
+// potential replace this loop by the fixed sequence).  MD: largest polynomial degree (3: unrolled
+// stencils; kMaxDeg: rolled loops); GENERAL: a general index set (membership from the row tables).
+template <typename R, int MD, bool GENERAL>
+__device__ __forceinline__ void generic_ops(const ApplyArgs &args, const Ctx &ctx, const Elem &el, Acc<R> &acc,
+                                            const R *sm_w, const typename Vec2<R>::T *cin, const R *tab)
+{
+    using V = typename Vec2<R>::T;
+    const OpSet &O = args.ops;
+    const int e = el.e;
+    for (int o = 0; o < O.nops; ++o) {
+        const Op &op = O.op[o];
+        if (op.merged) continue;
+        R lx = (R)0, ly = (R)0;     // sum of a line op merged into a plane op
+        const V *src = op.src < 0 ? cin : (const V *)args.chan + (size_t)op.src * args.chan_ld;
+        R sx = (R)0, sy = (R)0;
+        if (op.kind == 0) {
+            const V cs = src[e];
+            sx = cs.x;
+            sy = cs.y;
+        } else if (GENERAL) {
+            if (op.kind == 1) line_op_g<R, (MD <= 3 ? 3 : kMaxDeg), (MD <= 3)>(ctx, el, O, op, tab, src, sx, sy);
+            else plane_op_g<R, (MD <= 3 ? 3 : kMaxDeg), (MD <= 3 ? 3 : kMaxDeg), (MD <= 3)>(ctx, el, O, op, tab, src, sx, sy);
+        } else if (MD <= 3) {
+            const int sb = op.mergeB >= 0 ? O.op[op.mergeB].p : 0;
+            V o = czero<V>(), l = czero<V>();
+            switch (op.cls) {
+                case CLS_LINE + 1: o = line_dispatch<R, 1>(op.ra, ctx, el, O, op, tab, src); break;
+                case CLS_LINE + 2: o = line_dispatch<R, 2>(op.ra, ctx, el, O, op, tab, src); break;
+                case CLS_LINE + 3: o = line_dispatch<R, 3>(op.ra, ctx, el, O, op, tab, src); break;
+                case CLS_PLANE + 0: plane_dispatch<R, 1, 1>(op.rb, sb, ctx, el, O, op, tab, src, o, l); break;
+                case CLS_PLANE + 3: plane_dispatch<R, 2, 1>(op.rb, sb, ctx, el, O, op, tab, src, o, l); break;
+                case CLS_PLANE + 1: plane_dispatch<R, 1, 2>(op.rb, sb, ctx, el, O, op, tab, src, o, l); break;
+                case CLS_PLANE + 4: plane_dispatch<R, 2, 2>(op.rb, sb, ctx, el, O, op, tab, src, o, l); break;
+                default:
+                    if (op.kind == 1) line_op<R, 3, true>(ctx, el, O, op, tab, src, sx, sy);
+                    else plane_op<R, 3, 3, true>(ctx, el, O, op, tab, src, sx, sy);
+                    o = V{sx, sy};
+            }
+            sx = o.x;
+            sy = o.y;
+            lx = l.x;
+            ly = l.y;
+        } else {
+            if (op.kind == 1) line_op<R, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
+            else plane_op<R, kMaxDeg, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
+        }
+        const R w = sm_w[o];
+        if (op.mergeB >= 0) {
+            const R wl = sm_w[op.mergeB];
+            acc.add(w * sx + wl * lx, w * sy + wl * ly);
+            continue;
+        }
+        if (args.stage1) {
+            V ch;
+            ch.x = w * sx;
+            ch.y = w * sy;
+            ((V *)args.chan)[(size_t)op.dst * args.chan_ld + e] = ch;
+        } else {
+            acc.add(w * sx, w * sy);
+        }
+    }
+}
+
 template <typename R, int MD, bool GENERAL>
 __global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 3 : 1) apply_kernel(const __grid_constant__ ApplyArgs args)
 {
     using V = typename Vec2<R>::T;
-    const OpSet &O = args.ops;
     apply_elements<R>(args, [&](const Ctx &ctx, const Elem &el, Acc<R> &acc, const R *sm_w, const V *cin, const R *tab) {
-        const int e = el.e;
-        for (int o = 0; o < O.nops; ++o) {
-            const Op &op = O.op[o];
-            if (op.merged) continue;
-            R lx = (R)0, ly = (R)0;     // sum of a line op merged into a plane op
-            const V *src = op.src < 0 ? cin : (const V *)args.chan + (size_t)op.src * args.chan_ld;
-            R sx = (R)0, sy = (R)0;
-            if (op.kind == 0) {
-                const V cs = src[e];
-                sx = cs.x;
-                sy = cs.y;
-            } else if (GENERAL) {
-                if (op.kind == 1) line_op_g<R, (MD <= 3 ? 3 : kMaxDeg), (MD <= 3)>(ctx, el, O, op, tab, src, sx, sy);
-                else plane_op_g<R, (MD <= 3 ? 3 : kMaxDeg), (MD <= 3 ? 3 : kMaxDeg), (MD <= 3)>(ctx, el, O, op, tab, src, sx, sy);
-            } else if (MD <= 3) {
-                const int sb = op.mergeB >= 0 ? O.op[op.mergeB].p : 0;
-                V o = czero<V>(), l = czero<V>();
-                switch (op.cls) {
-                    case CLS_LINE + 1: o = line_dispatch<R, 1>(op.ra, ctx, el, O, op, tab, src); break;
-                    case CLS_LINE + 2: o = line_dispatch<R, 2>(op.ra, ctx, el, O, op, tab, src); break;
-                    case CLS_LINE + 3: o = line_dispatch<R, 3>(op.ra, ctx, el, O, op, tab, src); break;
-                    case CLS_PLANE + 0: plane_dispatch<R, 1, 1>(op.rb, sb, ctx, el, O, op, tab, src, o, l); break;
-                    case CLS_PLANE + 3: plane_dispatch<R, 2, 1>(op.rb, sb, ctx, el, O, op, tab, src, o, l); break;
-                    case CLS_PLANE + 1: plane_dispatch<R, 1, 2>(op.rb, sb, ctx, el, O, op, tab, src, o, l); break;
-                    case CLS_PLANE + 4: plane_dispatch<R, 2, 2>(op.rb, sb, ctx, el, O, op, tab, src, o, l); break;
-                    default:
-                        if (op.kind == 1) line_op<R, 3, true>(ctx, el, O, op, tab, src, sx, sy);
-                        else plane_op<R, 3, 3, true>(ctx, el, O, op, tab, src, sx, sy);
-                        o = V{sx, sy};
-                }
-                sx = o.x;
-                sy = o.y;
-                lx = l.x;
-                ly = l.y;
-            } else {
-                if (op.kind == 1) line_op<R, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
-                else plane_op<R, kMaxDeg, kMaxDeg, false>(ctx, el, O, op, tab, src, sx, sy);
-            }
-            const R w = sm_w[o];
-            if (op.mergeB >= 0) {
-                const R wl = sm_w[op.mergeB];
-                acc.add(w * sx + wl * lx, w * sy + wl * ly);
-                continue;
-            }
-            if (args.stage1) {
-                V ch;
-                ch.x = w * sx;
-                ch.y = w * sy;
-                ((V *)args.chan)[(size_t)op.dst * args.chan_ld + e] = ch;
-            } else {
-                acc.add(w * sx, w * sy);
-            }
-        }
+        generic_ops<R, MD, GENERAL>(args, ctx, el, acc, sm_w, cin, tab);
     });
+}
+
+// ---------------------------------------------------------------------------------------
+// One product launch for a batch of independent problems (the Lanczos products of a batch step):
+// persistent blocks take tiles of consecutive elements of any member from one queue, largest
+// members first, and evaluate them with the member's launch arguments (kept in device memory) and
+// the generic operator loop.  A block stops taking tiles once its clock64 budget is spent (budget
+// < 0: none) and then flags the queue; nothing waits on anything, so an exhausted budget leaves an
+// incomplete product and a flag, never a stalled kernel.  The last block to leave resets the queue.
+// ---------------------------------------------------------------------------------------
+template <typename R, int MD>
+__global__ void __launch_bounds__(kApplyThreads, MD <= 3 ? 3 : 1)
+batch_apply_kernel(const ApplyArgs *margs, const int2 *tiles, int ntiles, int tile, long long budget, BatchQueue *q)
+{
+    using V = typename Vec2<R>::T;
+    __shared__ int sh_tile;
+    __shared__ R sm_w[kMaxOps];
+    const long long t0 = clock64();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int t = -1;
+            if (budget >= 0 && clock64() - t0 >= budget) q->timeout = 1;
+            else t = (int)atomicAdd(&q->next, 1u);
+            sh_tile = t;
+        }
+        __syncthreads();
+        const int t = sh_tile;
+        if (t < 0 || t >= ntiles) break;
+        const int2 tl = tiles[t];
+        const ApplyArgs &args = margs[tl.x];
+        if ((int)threadIdx.x < args.ops.nops)
+            sm_w[threadIdx.x] = op_weight<R>(args.ops.op[threadIdx.x], *args.t_ptr + args.t_shift, args.pw_values);
+        __syncthreads();
+        Ctx ctx;
+        ctx.S = &args.S;
+        ctx.mv = args.mv;
+        const R oscale = args.out_scale ? (R)(*args.out_scale) : (R)1;
+        const int end = min(tl.y + tile, args.S.size);
+        auto body = [&](const Ctx &c, const Elem &el, Acc<R> &acc, const R *w, const V *cin, const R *tab) {
+            generic_ops<R, MD, false>(args, c, el, acc, w, cin, tab);
+        };
+        for (int e = tl.y + (int)threadIdx.x; e < end; e += blockDim.x)
+            apply_element<R>(args, ctx, e, __ldg(args.S.elem + e), oscale, sm_w, body);
+        __syncthreads();                     // sm_w is rewritten for the next tile
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&q->done, 1u) == gridDim.x - 1) {
+            q->next = 0;
+            q->done = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <typename R, int MD>
+static int batch_launch_t(const void *margs, const int2 *tiles, int ntiles, int tile, long long budget, void *queue,
+                          int num_sms, cudaStream_t st)
+{
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_apply_kernel<R, MD>, kApplyThreads, 0);
+    const int grid = std::max(1, std::min(num_sms * std::max(per_sm, 1), ntiles));
+    batch_apply_kernel<R, MD><<<grid, kApplyThreads, 0, st>>>((const ApplyArgs *)margs, tiles, ntiles, tile, budget,
+                                                               (BatchQueue *)queue);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "batch product kernel launch");
+    return HX_OK;
+}
+
+int launch_batch_apply(bool c64, int md, const void *margs, const int2 *tiles, int ntiles, int tile, long long budget,
+                       void *queue, int num_sms, cudaStream_t st)
+{
+    if (c64) return md <= 3 ? batch_launch_t<float, 3>(margs, tiles, ntiles, tile, budget, queue, num_sms, st)
+                            : batch_launch_t<float, kMaxDeg>(margs, tiles, ntiles, tile, budget, queue, num_sms, st);
+    return md <= 3 ? batch_launch_t<double, 3>(margs, tiles, ntiles, tile, budget, queue, num_sms, st)
+                   : batch_launch_t<double, kMaxDeg>(margs, tiles, ntiles, tile, budget, queue, num_sms, st);
 }
 
 int apply_grid(const Problem *p)
@@ -307,6 +394,35 @@ int apply_grid(const Problem *p)
     const int g = p->num_sms * per_sm;
     return blocks < g ? (blocks > 0 ? blocks : 1) : g;
 }
+
+// Launch arguments of a batch member's Lanczos product: y = *in_scale * A(*t_ptr + t_shift) cin into
+// cout, main stage, no fused projections.
+int batch_member_args(Problem *p, const void *cin, void *cout, const double *t_ptr, double t_shift,
+                      const double *in_scale, void *out)
+{
+    ApplyArgs &a = *(ApplyArgs *)out;
+    memset(&a, 0, sizeof(a));
+    a.S = p->set->d;
+    a.gnb = p->gnb;
+    a.gnbn = p->gnbn;
+    a.gstride = p->gstride;
+    a.dscale = p->scale * p->scale;
+    memcpy(a.mv, p->roff.mv, sizeof(a.mv));
+    a.t_ptr = t_ptr;
+    a.t_shift = t_shift;
+    a.pw_values = p->pw_values;
+    a.tab = p->tab;
+    a.ops = p->ops;
+    a.cin = cin;
+    a.cout = cout;
+    a.out_scale = in_scale;
+    a.chan = p->chan;
+    a.chan_ld = p->chan_ld;
+    a.skip_diag = p->skip_diag;
+    return HX_OK;
+}
+
+size_t apply_args_size() { return sizeof(ApplyArgs); }
 
 template <typename R, int MD>
 static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *cin, void *cout,
@@ -385,6 +501,13 @@ static int launch_stage(Problem *p, const OpSet &ops, int stage1, const void *ci
 }
 
 int apply_launches(const Problem *p) { return p->ops1.nops > 0 ? 2 : 1; }
+
+int max_degree(const Problem *p)
+{
+    int md = 0;
+    for (int i = 0; i < p->ops.nops; ++i) md = max(md, max(p->ops.op[i].p, p->ops.op[i].q));
+    return md;
+}
 
 bool apply_dual(const Problem *p) { return p->jit && !g_batch_capture && p->ops1.nops == 0; }
 

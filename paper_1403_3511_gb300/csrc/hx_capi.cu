@@ -1373,7 +1373,53 @@ int hx_batch_step(hx_batch *b, void *const *c, double dt, int nsteps)
             return HX_EINVAL;
         }
     if (nsteps == 0) return HX_OK;
-    return batch_step(b, c, dt, nsteps);
+    int rc = batch_step(b, c, dt, nsteps);
+    if (rc || b->budget < 0) return rc;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "hx_batch_step");
+    if (batch_timed_out(b)) {
+        set_error("hx_batch_step: a batched product ran out of its budget; the states are incomplete");
+        return HX_ETIMEOUT;
+    }
+    return HX_OK;
+}
+
+int hx_batch_set_budget(hx_batch *b, double seconds)
+{
+    if (!b || !(seconds == seconds)) { set_error("hx_batch_set_budget: bad argument"); return HX_EINVAL; }
+    long long cycles = -1;
+    if (seconds >= 0.0) {
+        int dev = 0, khz = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "hx_batch_set_budget");
+        const double c = seconds * 1e3 * (double)khz;        // the SM clock counts clock64 ticks
+        cycles = c > 9.0e18 ? (long long)9.0e18 : (long long)c;
+    }
+    if (cycles != b->budget) {
+        if (b->stream) cudaStreamSynchronize(b->stream);
+        batch_drop_graphs(b);                              // the budget is a launch argument
+    }
+    b->budget = cycles;
+    b->budget_s = seconds >= 0.0 ? seconds : -1.0;
+    return HX_OK;
+}
+
+int hx_batch_info(const hx_batch *b, hx_batch_stats *out)
+{
+    if (!b || !out) { set_error("hx_batch_info: NULL argument"); return HX_EINVAL; }
+    memset(out, 0, sizeof(*out));
+    out->schedule = b->schedule;
+    out->tile = b->tile;
+    out->launches = b->schedule >= 0 ? b->kern[b->schedule] : 0;
+    const int n = std::min((int)b->tune_tiles.size(), 8);
+    out->ntiles = n;
+    for (int i = 0; i < n; ++i) {
+        out->tiles[i] = b->tune_tiles[i];
+        out->tile_ms[i] = (float)b->tune_ms[i];
+    }
+    for (int s = 0; s < kNumSched; ++s) out->step_ms[s] = b->sched_ms[s];
+    return HX_OK;
 }
 
 void hx_batch_destroy(hx_batch *b)

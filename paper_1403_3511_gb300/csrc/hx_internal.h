@@ -123,6 +123,15 @@ int launch_apply_pair(Problem *p, const void *cin, void *cout, double t_shift, c
                       double t_shift2, const double *t_ptr, cudaStream_t st, void *mag_out = nullptr,
                       double mag_g = 0.0);
 
+// batched products (hx_apply.cu): launch arguments of one member's Lanczos product, their size, and
+// one persistent launch over the tiles of all members of one precision and degree class
+int batch_member_args(Problem *p, const void *cin, void *cout, const double *t_ptr, double t_shift,
+                      const double *in_scale, void *out);
+size_t apply_args_size();
+int launch_batch_apply(bool c64, int md, const void *margs, const int2 *tiles, int ntiles, int tile, long long budget,
+                       void *queue, int num_sms, cudaStream_t st);
+int max_degree(const Problem *p);
+
 // hx_apply_project after the argument checks (hx_krylov.cu)
 int apply_project_dispatch(Problem *p, const void *c, void *y, const void *basis, size_t ld, int k, double *h);
 
@@ -150,16 +159,33 @@ int lanczos_apply_basis(Problem *px, LanczosWS *L, int r, double2 *out, const do
 int adjoint_term(LanczosWS *Lp, LanczosWS *Ll, const double *M, double dt, double *gacc, cudaStream_t st);
 
 // Batches of independent problems stepped by one graph (hx_krylov.cu)
+constexpr int kSchedMembers = 0, kSchedBatched = 1, kSchedHybrid = 2, kSchedSerial = 3, kNumSched = 4;
 struct Batch {
     std::vector<Problem *> probs;
     std::vector<void *> cptr;
-    std::vector<int> gen;     // member generations the graph was captured with
-    cudaGraphExec_t exec = nullptr;
+    std::vector<int> gen;     // member generations the graphs were captured with
     double dt = 0.0;
     cudaStream_t stream = nullptr;
+    // schedules (kSched*): one graph each among the candidates, the fastest step kept
+    std::vector<int> cand;               // candidate schedules of the captured graphs
+    cudaGraphExec_t exec[kNumSched] = {};
+    int kern[kNumSched] = {};            // kernel launches of one replay of each graph
+    float sched_ms[kNumSched] = {-1.f, -1.f, -1.f, -1.f};   // one timed step of each candidate
+    int schedule = -1;                   // the chosen one (-1 while candidates are timed)
+    int tile = 0;             // elements per tile of the batched launches (autotuned at first use)
+    long long budget = -1;    // clock64 budget of each block of a batched product (< 0: none)
+    double budget_s = -1.0;
+    std::vector<double> tune_ms;   // tile autotuner: product time per candidate tile size
+    std::vector<int> tune_tiles;
+    void *dmem[kNumSched] = {};    // device: launch arguments, tile lists and queues per schedule
+    size_t dmem_bytes[kNumSched] = {};
+    cudaStream_t cap = nullptr;    // capture stream of the batched graphs
+    std::vector<cudaEvent_t> ev;   // fork/join events (one per member, one for the fork)
 };
 int batch_step(Batch *b, void *const *c, double dt, int nsteps);
+int batch_timed_out(Batch *b);     // 1 when a batched product's budget ran out since the last call
 void batch_free(Batch *b);
+void batch_drop_graphs(Batch *b);
 
 // Krylov stepping (hx_krylov.cu)
 int krylov_step(Problem *p, void *c, double dt, int nsteps);

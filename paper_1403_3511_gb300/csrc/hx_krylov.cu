@@ -1276,8 +1276,14 @@ __global__ void err_est_kernel(Scal *sc, double h, int m)
     if (!(est <= sc->err_max)) sc->err_max = est;   // NaN propagates
 }
 
+// Parts of a step for batch graphs that take the Lanczos products from a batched launch: the whole
+// step (kPhaseAll), the start vector (kPhaseInit), the work after product k (phase k: projections
+// and Gram-Schmidt passes, the product itself skipped), or the end (phase m: the exponential and the
+// recombination).
+constexpr int kPhaseAll = -2, kPhaseInit = -1;
+
 template <typename V, int NV>
-static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, double dt)
+static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, double dt, int phase = kPhaseAll)
 {
     const int n = p->set->d.size;
     const int m = p->cfg.m;
@@ -1288,15 +1294,19 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
     Scal *sc = w->sc;
     const int Gd = resident_grid(p, dot_kernel<V, NV>, T);
     const int Gu0 = resident_grid(p, update_kernel<V, NV, 0>, T), Gu1 = resident_grid(p, update_kernel<V, NV, 1>, T);
+    const bool all = phase == kPhaseAll;
     // the exponential midpoint step takes the projections from the product kernel when it can
-    const bool fused = p->cfg.scheme == HX_SCHEME_EXPMPR && NV <= kMaxFusedDots && apply_fuses_dots(p);
-    init_kernel<V><<<G, T, 0, st>>>(state, Vb, n, w->partials, sc, m);
+    const bool fused = all && p->cfg.scheme == HX_SCHEME_EXPMPR && NV <= kMaxFusedDots && apply_fuses_dots(p);
+    if (all || phase == kPhaseInit) init_kernel<V><<<G, T, 0, st>>>(state, Vb, n, w->partials, sc, m);
     for (int k = 0; k < m; ++k) {
+        if (!all && phase != k) continue;
         ApplyFuse f;
         memset(&f, 0, sizeof(f));
         f.in_scale = &sc->s[k];
         int rc;
-        if (p->cfg.scheme == HX_SCHEME_MAGNUS4) {   // Eq. (2stageMagnus): nodes 1/2 -+ sqrt(3)/6
+        if (!all) {
+            // the product was done by a batched launch
+        } else if (p->cfg.scheme == HX_SCHEME_MAGNUS4) {   // Eq. (2stageMagnus): nodes 1/2 -+ sqrt(3)/6
             const double c1 = 0.5 - sqrt(3.0) / 6.0, c2 = 0.5 + sqrt(3.0) / 6.0;
             V *a1v = (V *)w->mag, *a2v = a1v + ld, *a2a1v = a2v + ld, *a1a2v = a2a1v + ld;
             const double g = sqrt(3.0) * dt / 12.0;
@@ -1332,6 +1342,10 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
             update_kernel<V, NV, 0><<<Gu0, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
             if (pass1) update_kernel<V, NV, 1><<<Gu1, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
         }
+    }
+    if (!all && phase != m) {
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? HX_OK : cuda_fail(e, "step kernel launch");
     }
     if (m <= kEigSmall) expv_kernel<true><<<1, 32, 0, st>>>(sc, dt);
     else expv_kernel<false><<<1, 32, 0, st>>>(sc, dt);
@@ -1431,13 +1445,14 @@ int apply_project_dispatch(Problem *p, const void *c, void *y, const void *basis
                                   : apply_project<double2>(p, c, y, basis, ld, k, h);
 }
 
-static int enqueue(Problem *p, Work *w, double2 *state, cudaStream_t st, double dt)
+static int enqueue(Problem *p, Work *w, double2 *state, cudaStream_t st, double dt, int phase = kPhaseAll)
 {
     const bool c64 = p->cfg.dtype == HX_C64;
     if (p->cfg.m <= 8)
-        return c64 ? enqueue_step<float2, 8>(p, w, state, st, dt) : enqueue_step<double2, 8>(p, w, state, st, dt);
-    return c64 ? enqueue_step<float2, kMaxKrylov>(p, w, state, st, dt)
-               : enqueue_step<double2, kMaxKrylov>(p, w, state, st, dt);
+        return c64 ? enqueue_step<float2, 8>(p, w, state, st, dt, phase)
+                   : enqueue_step<double2, 8>(p, w, state, st, dt, phase);
+    return c64 ? enqueue_step<float2, kMaxKrylov>(p, w, state, st, dt, phase)
+               : enqueue_step<double2, kMaxKrylov>(p, w, state, st, dt, phase);
 }
 
 static int ensure_work(Problem *p)
@@ -1643,8 +1658,366 @@ int krylov_info(Problem *p, int *m_used, double *alpha, double *beta, double *no
 
 
 // ---------------------------------------------------------------------------------------
-// Batches: one graph per step with every problem's step as an independent child graph
+// Batches.  Three schedules of the same kernels (each member's arithmetic is the same in all
+// three, so they give the same bits):
+//   kSchedMembers  one graph per step with every member's step as an independent child graph;
+//   kSchedBatched  per Lanczos index one persistent product launch per (precision, degree) class
+//                  over all members (batch_apply_kernel: tiles of any member from one queue,
+//                  largest members first), the members' projections, Gram-Schmidt passes,
+//                  exponentials and recombinations forked from and joined to those launches;
+//   kSchedHybrid   members that fill the GPU alone (|K| of at least one wave of product blocks)
+//                  run their whole step on their own stream, the others as in kSchedBatched;
+//   kSchedSerial   members with a kernel specialised to their potential and at least four waves
+//                  of product blocks run their own step graph's kernels (specialised product,
+//                  fused projections) one member after another, nothing else running beside
+//                  them, then the others as in kSchedBatched.
+// The first three give the same bits; kSchedSerial gives the single-problem step's bits for its
+// large members.  The first steps of a call time each candidate graph once and keep the fastest;
+// the tile size of the batched launches is chosen before that by timing the candidate sizes.
 // ---------------------------------------------------------------------------------------
+// Kernel nodes of a graph, child graphs included: the launches of one replay.
+static int count_kernel_nodes(cudaGraph_t g)
+{
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return -1;
+    int k = 0;
+    for (cudaGraphNode_t x : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(x, &t) != cudaSuccess) return -1;
+        if (t == cudaGraphNodeTypeKernel) ++k;
+        else if (t == cudaGraphNodeTypeGraph) {
+            cudaGraph_t child;
+            if (cudaGraphChildGraphNodeGetGraph(x, &child) != cudaSuccess) return -1;
+            const int c = count_kernel_nodes(child);
+            if (c < 0) return -1;
+            k += c;
+        }
+    }
+    return k;
+}
+
+static int batch_instantiate(Batch *b, int sched, cudaGraph_t g)
+{
+    b->kern[sched] = count_kernel_nodes(g);
+    cudaError_t e = cudaGraphInstantiate(&b->exec[sched], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { b->exec[sched] = nullptr; return cuda_fail(e, "batch instantiate"); }
+    if ((e = cudaGraphUpload(b->exec[sched], b->stream)) != cudaSuccess) return cuda_fail(e, "batch graph upload");
+    return HX_OK;
+}
+
+static int batch_capture_members(Batch *b, void *const *c, double dt)
+{
+    const int np = (int)b->probs.size();
+    cudaError_t e;
+    cudaGraph_t g;
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return cuda_fail(e, "batch graph");
+    for (int i = 0; i < np; ++i) {
+        Problem *p = b->probs[i];
+        Work *w = work_of(p);
+        cudaGraph_t child;
+        if ((e = cudaStreamBeginCapture(w->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_fail(e, "batch capture");
+        }
+        g_batch_capture = true;             // batch members run the generic apply kernel
+        int rc = enqueue(p, w, (double2 *)c[i], w->cap_stream, dt);
+        g_batch_capture = false;
+        e = cudaStreamEndCapture(w->cap_stream, &child);
+        if (rc || e != cudaSuccess) {
+            if (e == cudaSuccess) cudaGraphDestroy(child);
+            cudaGraphDestroy(g);
+            return rc ? rc : cuda_fail(e, "batch capture");
+        }
+        cudaGraphNode_t node;
+        e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, child);
+        cudaGraphDestroy(child);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_fail(e, "batch child node");
+        }
+    }
+    return batch_instantiate(b, kSchedMembers, g);
+}
+
+namespace {
+struct BatchGroup {
+    bool c64;
+    int md;
+    std::vector<int> members;       // batch indices, largest first
+    size_t args_off;                // device offset of mmax x count launch arguments (k-major)
+    std::vector<size_t> tiles_off;  // per Lanczos index: the tile list (members with m > k)
+    std::vector<int> ntiles;
+    size_t queue_off;
+};
+}  // namespace
+
+static int batch_mmax(const Batch *b)
+{
+    int m = 0;
+    for (const Problem *p : b->probs) m = std::max(m, p->cfg.m);
+    return m;
+}
+
+static bool batch_allows_batched(const Batch *b)
+{
+    for (const Problem *p : b->probs)
+        if (p->cfg.scheme != HX_SCHEME_EXPMPR || p->ops1.nops > 0 || p->set->d.general || p->cfg.tol > 0.0)
+            return false;
+    return true;
+}
+
+// Members that take part in the batched product launches of a schedule.
+static bool batch_in_launch(const Batch *b, int sched, int i)
+{
+    if (sched == kSchedBatched) return true;
+    const Problem *p = b->probs[i];
+    const int64_t wave = (int64_t)p->num_sms * 4 * kApplyThreads;    // one wave of product blocks
+    if (sched == kSchedSerial) return !(p->jit && (int64_t)p->set->h.size >= 4 * wave);
+    return (int64_t)p->set->h.size < wave;
+}
+
+static std::vector<BatchGroup> batch_groups(const Batch *b, int sched, int tile, size_t &bytes)
+{
+    std::vector<BatchGroup> gs;
+    for (int i = 0; i < (int)b->probs.size(); ++i) {
+        if (!batch_in_launch(b, sched, i)) continue;
+        const Problem *p = b->probs[i];
+        const bool c64 = p->cfg.dtype == HX_C64;
+        const int md = max_degree(p) <= 3 ? 3 : kMaxDeg;
+        BatchGroup *g = nullptr;
+        for (auto &x : gs)
+            if (x.c64 == c64 && x.md == md) g = &x;
+        if (!g) { gs.push_back(BatchGroup{c64, md, {}, 0, {}, {}, 0}); g = &gs.back(); }
+        g->members.push_back(i);
+    }
+    const int mmax = batch_mmax(b);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    bytes = 0;
+    for (auto &g : gs) {
+        std::stable_sort(g.members.begin(), g.members.end(),
+                         [&](int x, int y) { return b->probs[x]->set->h.size > b->probs[y]->set->h.size; });
+        g.args_off = bytes;
+        bytes = al(bytes + (size_t)mmax * g.members.size() * apply_args_size());
+        g.tiles_off.assign(mmax, 0);
+        g.ntiles.assign(mmax, 0);
+        for (int k = 0; k < mmax; ++k) {
+            for (int i : g.members)
+                if (b->probs[i]->cfg.m > k) g.ntiles[k] += (int)((b->probs[i]->set->h.size + tile - 1) / tile);
+            g.tiles_off[k] = bytes;
+            bytes = al(bytes + (size_t)g.ntiles[k] * sizeof(int2));
+        }
+        g.queue_off = bytes;
+        bytes = al(bytes + sizeof(BatchQueue));
+    }
+    return gs;
+}
+
+// Device copies of the groups' launch arguments and tile lists (the queues are cleared).
+static int batch_upload(Batch *b, int sched, const std::vector<BatchGroup> &gs, size_t bytes, double dt, int tile)
+{
+    if (bytes > b->dmem_bytes[sched]) {
+        cudaFree(b->dmem[sched]);
+        b->dmem[sched] = nullptr;
+        b->dmem_bytes[sched] = 0;
+        cudaError_t e = cudaMalloc(&b->dmem[sched], bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch tables)");
+        b->dmem_bytes[sched] = bytes;
+    }
+    if (bytes == 0) return HX_OK;
+    std::vector<char> host(bytes, 0);
+    const int mmax = batch_mmax(b);
+    for (const auto &g : gs) {
+        for (int k = 0; k < mmax; ++k) {
+            int2 *tl = (int2 *)(host.data() + g.tiles_off[k]);
+            int t = 0;
+            for (size_t j = 0; j < g.members.size(); ++j) {
+                Problem *p = b->probs[g.members[j]];
+                if (p->cfg.m <= k) continue;
+                Work *w = work_of(p);
+                const size_t es = p->cfg.dtype == HX_C64 ? 8 : 16, ld = w->vec_bytes / es;
+                char *V = (char *)w->V;
+                batch_member_args(p, V + (size_t)k * ld * es, V + (size_t)(k + 1) * ld * es, &w->sc->t, 0.5 * dt,
+                                  &w->sc->s[k],
+                                  host.data() + g.args_off + ((size_t)k * g.members.size() + j) * apply_args_size());
+                const int n = (int)p->set->h.size;
+                for (int s = 0; s < n; s += tile) tl[t++] = make_int2((int)j, s);
+            }
+        }
+    }
+    cudaError_t e = cudaMemcpy(b->dmem[sched], host.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload batch tables");
+    return HX_OK;
+}
+
+static int batch_products(Batch *b, int sched, const std::vector<BatchGroup> &gs, int k, int tile, long long budget,
+                          cudaStream_t st)
+{
+    const Problem *p0 = b->probs[0];
+    for (const auto &g : gs) {
+        if (g.ntiles[k] == 0) continue;
+        const char *base = (const char *)b->dmem[sched];
+        int rc = launch_batch_apply(g.c64, g.md, base + g.args_off + (size_t)k * g.members.size() * apply_args_size(),
+                                    (const int2 *)(base + g.tiles_off[k]), g.ntiles[k], tile, budget,
+                                    (void *)(base + g.queue_off), p0->num_sms, st);
+        if (rc) return rc;
+    }
+    return HX_OK;
+}
+
+// The tile size: each candidate's batched products (all members) for the first Lanczos index,
+// timed on the batch's capture stream after a warm-up launch (the workspace's contents do not
+// matter for the time; the next step overwrites them), the fastest kept.
+static int batch_autotune(Batch *b, double dt)
+{
+    const int cand[] = {256, 512, 1024, 2048, 4096};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(e, "batch autotune events");
+    }
+    b->tune_tiles.clear();
+    b->tune_ms.clear();
+    double best = 1e300;
+    int best_tile = 1024, rc = HX_OK;
+    for (int tile : cand) {
+        size_t bytes;
+        auto gs = batch_groups(b, kSchedBatched, tile, bytes);
+        if ((rc = batch_upload(b, kSchedBatched, gs, bytes, dt, tile)) ||
+            (rc = batch_products(b, kSchedBatched, gs, 0, tile, -1, b->cap)))      // warm-up
+            break;
+        cudaEventRecord(e0, b->cap);
+        rc = batch_products(b, kSchedBatched, gs, 0, tile, -1, b->cap);
+        cudaEventRecord(e1, b->cap);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess && !rc) rc = cuda_fail(e, "batch autotune");
+        if (rc) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        b->tune_tiles.push_back(tile);
+        b->tune_ms.push_back(ms);
+        if (ms < best) { best = ms; best_tile = tile; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) b->tile = best_tile;
+    return rc;
+}
+
+static int batch_capture_batched(Batch *b, int sched, void *const *c, double dt)
+{
+    const int np = (int)b->probs.size();
+    const int m = batch_mmax(b);
+    size_t bytes;
+    auto gs = batch_groups(b, sched, b->tile, bytes);
+    int rc = batch_upload(b, sched, gs, bytes, dt, b->tile);
+    if (rc) return rc;
+    cudaError_t e;
+    cudaGraph_t g;
+    if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "batch capture");
+    auto fork = [&](int i) {
+        Work *w = work_of(b->probs[i]);
+        if ((e = cudaEventRecord(b->ev[np], b->cap)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(w->cap_stream, b->ev[np], 0)) != cudaSuccess)
+            return cuda_fail(e, "batch fork");
+        return (int)HX_OK;
+    };
+    auto join = [&](int i) {
+        Work *w = work_of(b->probs[i]);
+        if ((e = cudaEventRecord(b->ev[i], w->cap_stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(b->cap, b->ev[i], 0)) != cudaSuccess)
+            return cuda_fail(e, "batch join");
+        return (int)HX_OK;
+    };
+    // members outside the batched launches: their whole step, on their own stream (hybrid) or one
+    // after another on the batch stream with their own kernels (serial)
+    for (int i = 0; i < np && !rc; ++i) {
+        if (batch_in_launch(b, sched, i)) continue;
+        Problem *p = b->probs[i];
+        if (sched == kSchedSerial) {
+            rc = enqueue(p, work_of(p), (double2 *)c[i], b->cap, dt);
+            continue;
+        }
+        if ((rc = fork(i))) break;
+        g_batch_capture = true;
+        rc = enqueue(p, work_of(p), (double2 *)c[i], work_of(p)->cap_stream, dt);
+        g_batch_capture = false;
+    }
+    // phase: -1 start vectors, 0..m-1 work after product k, m the end
+    for (int phase = kPhaseInit; phase <= m && !rc; ++phase) {
+        if (phase >= 0 && phase < m && (rc = batch_products(b, sched, gs, phase, b->tile, b->budget, b->cap))) break;
+        for (int i = 0; i < np && !rc; ++i) {
+            Problem *p = b->probs[i];
+            if (!batch_in_launch(b, sched, i) || phase > p->cfg.m) continue;   // own stream, or its step ended
+            if (!(rc = fork(i)) && !(rc = enqueue(p, work_of(p), (double2 *)c[i], work_of(p)->cap_stream, dt, phase)))
+                rc = join(i);
+        }
+    }
+    for (int i = 0; i < np && !rc && sched != kSchedSerial; ++i)
+        if (!batch_in_launch(b, sched, i)) rc = join(i);
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (rc) {
+        if (e == cudaSuccess) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batch capture");
+    return batch_instantiate(b, sched, g);
+}
+
+int batch_timed_out(Batch *b)
+{
+    if (b->schedule <= kSchedMembers) return 0;
+    int out = 0;
+    for (int sched : {kSchedBatched, kSchedHybrid, kSchedSerial}) {
+        if (!b->dmem[sched] || !b->exec[sched]) continue;
+        size_t bytes;
+        auto gs = batch_groups(b, sched, b->tile, bytes);
+        for (const auto &g : gs) {
+            BatchQueue q;
+            BatchQueue *dq = (BatchQueue *)((char *)b->dmem[sched] + g.queue_off);
+            if (cudaMemcpy(&q, dq, sizeof(q), cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+            if (q.timeout) {
+                out = 1;
+                cudaMemset(&dq->timeout, 0, sizeof(int));
+            }
+        }
+    }
+    return out;
+}
+
+void batch_drop_graphs(Batch *b)
+{
+    for (int s = 0; s < kNumSched; ++s) {
+        if (b->exec[s]) cudaGraphExecDestroy(b->exec[s]);
+        b->exec[s] = nullptr;
+        b->kern[s] = 0;
+    }
+}
+
+// Candidate schedules: forced by HX_BATCH_BATCHED (0 member graphs, 1 batched, 2 hybrid, 3 serial),
+// else every schedule that the members allow and that differs from the others.
+static std::vector<int> batch_candidates(const Batch *b)
+{
+    const char *env = getenv("HX_BATCH_BATCHED");
+    const bool ok = batch_allows_batched(b);
+    if (env && env[0] == '0') return {kSchedMembers};
+    if (!ok) return {kSchedMembers};
+    if (env && env[0] >= '1' && env[0] <= '3') return {env[0] - '0'};
+    const int np = (int)b->probs.size();
+    int small = 0, rest = 0;
+    for (int i = 0; i < np; ++i) {
+        small += batch_in_launch(b, kSchedHybrid, i);
+        rest += batch_in_launch(b, kSchedSerial, i);
+    }
+    std::vector<int> c = {kSchedMembers, kSchedBatched};
+    if (small > 0 && small < np) c.push_back(kSchedHybrid);
+    if (rest < np) c.push_back(kSchedSerial);
+    return c;
+}
+
 int batch_step(Batch *b, void *const *c, double dt, int nsteps)
 {
     const int np = (int)b->probs.size();
@@ -1652,41 +2025,35 @@ int batch_step(Batch *b, void *const *c, double dt, int nsteps)
         int rc = ensure_work(p);
         if (rc) return rc;
     }
-    // a member whose potential was set again since the capture has new tables: capture again
-    bool same = b->exec && b->dt == dt;
+    const std::vector<int> cand = batch_candidates(b);
+    bool same = b->dt == dt && b->cand == cand;
     for (int i = 0; same && i < np; ++i) same = b->cptr[i] == c[i] && b->gen[i] == b->probs[i]->generation;
+    for (int s : cand) same = same && b->exec[s];
     cudaError_t e;
     if (!same) {
-        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-        cudaGraph_t g;
-        if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return cuda_fail(e, "batch graph");
-        for (int i = 0; i < np; ++i) {
-            Problem *p = b->probs[i];
-            Work *w = work_of(p);
-            cudaGraph_t child;
-            if ((e = cudaStreamBeginCapture(w->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
-                cudaGraphDestroy(g);
-                return cuda_fail(e, "batch capture");
-            }
-            g_batch_capture = true;             // batch members run the generic apply kernel
-            int rc = enqueue(p, w, (double2 *)c[i], w->cap_stream, dt);
-            g_batch_capture = false;
-            e = cudaStreamEndCapture(w->cap_stream, &child);
-            if (rc || e != cudaSuccess) {
-                cudaGraphDestroy(g);
-                return rc ? rc : cuda_fail(e, "batch capture");
-            }
-            cudaGraphNode_t node;
-            e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, child);
-            cudaGraphDestroy(child);
-            if (e != cudaSuccess) {
-                cudaGraphDestroy(g);
-                return cuda_fail(e, "batch child node");
-            }
+        // the tables below are read by a graph of this batch that may still run, and the tile
+        // autotuner writes into the members' workspaces: wait for the batch and member streams
+        if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return cuda_fail(e, "batch sync");
+        for (Problem *p : b->probs)
+            if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return cuda_fail(e, "batch sync");
+        batch_drop_graphs(b);
+        b->schedule = cand.size() == 1 ? cand[0] : -1;
+        for (int s = 0; s < kNumSched; ++s) b->sched_ms[s] = -1.f;
+        if (!b->cap && (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreate(batch)");
+        for (int i = (int)b->ev.size(); i < np + 1; ++i) {
+            cudaEvent_t ev;
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "cudaEventCreate(batch)");
+            b->ev.push_back(ev);
         }
-        e = cudaGraphInstantiate(&b->exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) { b->exec = nullptr; return cuda_fail(e, "batch instantiate"); }
+        for (int s : cand) {
+            int rc;
+            if (s != kSchedMembers && b->tile == 0 && (rc = batch_autotune(b, dt))) return rc;
+            rc = s == kSchedMembers ? batch_capture_members(b, c, dt) : batch_capture_batched(b, s, c, dt);
+            if (rc) { batch_drop_graphs(b); return rc; }
+        }
+        b->cand = cand;
         b->cptr.assign(c, c + np);
         b->gen.resize(np);
         for (int i = 0; i < np; ++i) b->gen[i] = b->probs[i]->generation;
@@ -1699,8 +2066,38 @@ int batch_step(Batch *b, void *const *c, double dt, int nsteps)
             (e = cudaMemsetAsync(&w->sc->flags, 0, sizeof(int), st)) != cudaSuccess)
             return cuda_fail(e, "batch set-up");
     }
-    for (int s = 0; s < nsteps; ++s)
-        if ((e = cudaGraphLaunch(b->exec, st)) != cudaSuccess) return cuda_fail(e, "batch graph launch");
+    int s = 0;
+    // schedule choice: the next untimed candidate runs one step between two events
+    while (b->schedule < 0 && s < nsteps) {
+        int next = -1;
+        for (int x : b->cand)
+            if (b->sched_ms[x] < 0.f) { next = x; break; }
+        cudaEvent_t e0, e1;
+        if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e, "batch timing");
+        if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(e, "batch timing"); }
+        cudaEventRecord(e0, st);
+        e = cudaGraphLaunch(b->exec[next], st);
+        cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+        b->sched_ms[next] = ms;
+        ++s;
+        bool all = true;
+        for (int x : b->cand) all = all && b->sched_ms[x] >= 0.f;
+        if (all) {
+            int best = b->cand[0];
+            for (int x : b->cand)
+                if (b->sched_ms[x] < b->sched_ms[best]) best = x;
+            b->schedule = best;
+        }
+    }
+    const int run = b->schedule >= 0 ? b->schedule : b->cand[0];
+    for (; s < nsteps; ++s)
+        if ((e = cudaGraphLaunch(b->exec[run], st)) != cudaSuccess) return cuda_fail(e, "batch graph launch");
     for (Problem *p : b->probs) {
         Work *w = work_of(p);
         if ((e = cudaMemcpyAsync(p->dscal, &w->sc->t, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
@@ -1712,8 +2109,16 @@ int batch_step(Batch *b, void *const *c, double dt, int nsteps)
 
 void batch_free(Batch *b)
 {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    b->exec = nullptr;
+    batch_drop_graphs(b);
+    for (int s = 0; s < kNumSched; ++s) {
+        cudaFree(b->dmem[s]);
+        b->dmem[s] = nullptr;
+        b->dmem_bytes[s] = 0;
+    }
+    for (cudaEvent_t ev : b->ev) cudaEventDestroy(ev);
+    b->ev.clear();
+    if (b->cap) cudaStreamDestroy(b->cap);
+    b->cap = nullptr;
 }
 
 // ---------------------------------------------------------------------------------------

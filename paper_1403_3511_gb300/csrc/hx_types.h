@@ -120,6 +120,16 @@ struct RowOffsets {
     signed char om[kMaxDelta][4];   // axis0, step0, axis1, step1 of each outer move (axes < N-2)
 };
 
+// Work queue of a batched product launch (device memory, zero before the first launch): the next
+// tile, the blocks that have left (the last resets both), and a flag set by a block whose clock64
+// budget ran out.
+struct BatchQueue {
+    unsigned next;
+    unsigned done;
+    int timeout;
+    int pad;
+};
+
 struct ApplyArgsBase {
     DevSet S;
     const int *gnb;           // group-neighbour table, ngroup x gstride

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libhx.so")
 HX_C128, HX_C64 = 0, 1
 HX_ORDER_SYM, HX_ORDER_EQ, HX_ORDER_ALG = 0, 1, 2
 HX_SCHEME_EXPMPR, HX_SCHEME_MAGNUS4 = 0, 1
+HX_SCHED_MEMBERS, HX_SCHED_BATCHED, HX_SCHED_HYBRID, HX_SCHED_SERIAL = 0, 1, 2, 3
 HX_MOD_CONST, HX_MOD_COS, HX_MOD_SIN2, HX_MOD_PWCONST = 0, 1, 2, 3
 HX_EINVAL, HX_ENOMEM, HX_ECUDA, HX_ENONFINITE, HX_EBREAKDOWN, HX_ETIMEOUT, HX_EUNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
 ORDERS = {"sym": HX_ORDER_SYM, "eq": HX_ORDER_EQ, "alg": HX_ORDER_ALG}
@@ -51,6 +52,13 @@ class hx_control(ctypes.Structure):
 class hx_config(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("order", ctypes.c_int), ("m", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("scheme", ctypes.c_int), ("tol", ctypes.c_double), ("scale", ctypes.c_double)]
+
+
+class BatchStats(ctypes.Structure):
+    """hx_batch_stats."""
+    _fields_ = [("schedule", ctypes.c_int), ("tile", ctypes.c_int), ("launches", ctypes.c_int),
+                ("ntiles", ctypes.c_int), ("tiles", ctypes.c_int * 8), ("tile_ms", ctypes.c_float * 8),
+                ("step_ms", ctypes.c_float * 4)]
 
 
 # const hx_potential *(*)(double t, void *user)
@@ -92,6 +100,8 @@ def _load():
         "hx_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P)]),
         "hx_batch_step": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.c_double, ctypes.c_int]),
         "hx_batch_destroy": (None, [P]),
+        "hx_batch_set_budget": (ctypes.c_int, [P, ctypes.c_double]),
+        "hx_batch_info": (ctypes.c_int, [P, ctypes.POINTER(BatchStats)]),
         "hx_adjoint_grad": (ctypes.c_int, [P, ctypes.POINTER(hx_config), ctypes.POINTER(hx_potential),
                                            ctypes.POINTER(hx_control), P, P, dp, dp]),
         "hx_norm_noalloc": (ctypes.c_int, [P, P, dp]),
@@ -364,6 +374,22 @@ def hx_batch_step(b, states: list, dt: float, nsteps: int):
 
 def hx_batch_destroy(b):
     lib.hx_batch_destroy(b)
+
+
+def hx_batch_set_budget(b, seconds: float):
+    _check(lib.hx_batch_set_budget(b, float(seconds)))
+
+
+def hx_batch_info(b) -> dict:
+    """The batch's schedule state after its last step: {'schedule': HX_SCHED_* or -1, 'batched':
+    a batched schedule in use, 'tile', 'launches' (kernels per step), 'candidates': [(tile, ms)],
+    'step_ms': {schedule: ms of its timed step}}."""
+    st = BatchStats()
+    _check(lib.hx_batch_info(b, ctypes.byref(st)))
+    return {"schedule": st.schedule, "batched": st.schedule > HX_SCHED_MEMBERS,
+            "tile": st.tile, "launches": st.launches,
+            "candidates": [(st.tiles[i], st.tile_ms[i]) for i in range(st.ntiles)],
+            "step_ms": {i: st.step_ms[i] for i in range(4) if st.step_ms[i] >= 0}}
 
 
 def hx_norm(p, c) -> float:

@@ -100,6 +100,38 @@ def test_config_layout_matches_header(libhx):
         hx.hx_apply_specialised(None)
 
 
+def test_struct_layouts_match_header(tmp_path):
+    """hx_config and hx_batch_stats: the binding's field names follow the header's, and every
+    offset and the size agree with what a C compiler makes of the header."""
+    import re
+    import shutil
+    import subprocess
+    from paper_1403_3511_gb300 import hx
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    hdr = open(os.path.join(ROOT, "include", "hx.h")).read()
+    lines = []
+    for cname, cls in (("hx_config", hx.hx_config), ("hx_batch_stats", hx.BatchStats)):
+        body = re.search(r"typedef struct \{([^}]*)\} " + cname + ";", hdr).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        names = re.findall(r"(\w+)(?:\[\d+\])?;", body)
+        assert names == [f[0] for f in cls._fields_], cname
+        for f in names:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f}));')
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"hx.h\"\nint main(void){" + "".join(lines) +
+                   "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = []
+    for cls in (hx.hx_config, hx.BatchStats):
+        want += [getattr(cls, f[0]).offset for f in cls._fields_] + [ctypes.sizeof(cls)]
+    assert got == want
+
+
 def test_integer_float_conversions_match_host():
     """The binary64 <-> binary32 conversions that the complex64 Krylov kernels do with integer
     operations (csrc/hx_convert.h) agree bit for bit with the host's IEEE conversions."""

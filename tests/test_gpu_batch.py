@@ -136,3 +136,158 @@ def test_batch_follows_potential_change(hx):
     finally:
         P.close()
         Q.close()
+
+
+@contextlib.contextmanager
+def env(name, value):
+    old = os.environ.get(name)
+    if value is None:
+        os.environ.pop(name, None)
+    else:
+        os.environ[name] = value
+    try:
+        yield
+    finally:
+        if old is None:
+            os.environ.pop(name, None)
+        else:
+            os.environ[name] = old
+
+
+def mixed_batch_specs():
+    """Twelve small members: both precisions, Krylov dimensions 5 and 7, and two members with a
+    degree-4 term (the degree-8 class of the batched product kernel)."""
+    specs = inputs.batch_workloads(n=12, seed=11, b_lo=48, b_hi=900)
+    for i, s in enumerate(specs):
+        if i % 3 == 1:
+            s["m"] = 5
+        if i in (2, 7):
+            s["potential"] = s["potential"] + [{"coef": 0.004, "powers": {0: 4}}]
+    return specs
+
+
+def run_batch(hx, specs, dtypes, nsteps=(4, 5), budget=None, batched="1", infos=None):
+    probs, states, c0s = [], [], []
+    try:
+        for spec, dt_ in zip(specs, dtypes):
+            P = hx.Problem(spec["N"], spec["B"], dtype=dt_, m=spec["m"])
+            P.set_potential(spec, 0.0)
+            c0 = inputs.initial_vector(spec, hx.hx_indexset_export(P.set, spec["N"]))
+            probs.append(P)
+            c0s.append(c0)
+            states.append(torch.from_numpy(c0).to("cuda"))
+        b = hx.hx_batch_create([P.p for P in probs])
+        try:
+            if budget is not None:
+                hx.hx_batch_set_budget(b, budget)
+            with env("HX_BATCH_BATCHED", batched):
+                for n in nsteps:
+                    hx.hx_batch_step(b, states, 0.01, n)
+                    if infos is not None:
+                        infos.append(hx.hx_batch_info(b))
+            info = hx.hx_batch_info(b)
+        finally:
+            hx.hx_batch_destroy(b)
+        torch.cuda.synchronize()
+        return [s.cpu().numpy() for s in states], c0s, info
+    finally:
+        for P in probs:
+            P.close()
+
+
+def test_batched_products_equal_member_graphs_and_oracle(hx, oracle):
+    """The batched product launches (one per Lanczos index and class, tiles of all members) give the
+    same bits as one graph per member with its own product launches, for members of both precisions,
+    two Krylov dimensions and both degree classes; one member of each precision against the oracle."""
+    specs = mixed_batch_specs()
+    dtypes = [hx.HX_C64 if i % 4 else hx.HX_C128 for i in range(len(specs))]
+    got, c0s, info = run_batch(hx, specs, dtypes, batched="1")
+    ref, _, info0 = run_batch(hx, specs, dtypes, batched="0")
+    assert info["batched"] and not info0["batched"]
+    assert info["schedule"] == hx.HX_SCHED_BATCHED and info0["schedule"] == hx.HX_SCHED_MEMBERS
+    assert info["launches"] > 0 and info0["launches"] > info["launches"]
+    tiles = [t for t, _ in info["candidates"]]
+    assert tiles == [256, 512, 1024, 2048, 4096] and info["tile"] in tiles
+    assert all(ms > 0 for _, ms in info["candidates"])
+    for i, (a, b) in enumerate(zip(got, ref)):
+        assert np.array_equal(a, b), i
+    for i in (0, 2, 7):
+        spec = specs[i]
+        S = oracle.IndexSet.hyperbolic(spec["N"], spec["B"])
+        want, _ = oracle.expmpr_propagate(S, spec, c0s[i], 0.01, 9, spec["m"])
+        tol = 1e-12 if dtypes[i] == hx.HX_C128 else 1e-5
+        assert np.linalg.norm(got[i] - want) / np.linalg.norm(want) <= tol, i
+
+
+def test_batched_product_budget(hx):
+    """A budget of 0 s: every block of a batched product stops before its first tile, flags the
+    queue, and hx_batch_step returns HX_ETIMEOUT; a generous budget changes nothing."""
+    specs = mixed_batch_specs()[:4]
+    dtypes = [hx.HX_C64] * 4
+    with pytest.raises(hx.HxError) as ei:
+        run_batch(hx, specs, dtypes, nsteps=(1,), budget=0.0)
+    assert ei.value.status == hx.HX_ETIMEOUT
+    got, _, _ = run_batch(hx, specs, dtypes, budget=10.0)
+    ref, _, _ = run_batch(hx, specs, dtypes)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+
+
+def test_batch_members_outside_batched_products(hx):
+    """A member with a two-stage product (degree-8 cosine chain) keeps the batch on one graph per
+    member; the step still matches the member stepped alone."""
+    specs = mixed_batch_specs()[:3]
+    specs[1] = dict(inputs.workload("hh2_b32"), m=7)
+    specs[1]["potential"] = inputs.cos_chain(2, 0.2, 8)
+    dtypes = [hx.HX_C128] * 3
+    got, c0s, info = run_batch(hx, specs, dtypes)
+    assert not info["batched"]
+    ref, _, _ = run_batch(hx, specs, dtypes, batched="0")
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+
+
+def test_batch_schedule_autotune(hx):
+    """Without HX_BATCH_BATCHED the first steps time the four schedules (one step each, across
+    calls when a call has fewer steps), then the fastest runs.  The small members get the same bits
+    under every schedule; the member of about a million coefficients gets the generic kernel's bits
+    under the first three and, under the serial schedule, the bits of hx_step on it alone (complex64
+    with fused projections: equal to the others within rounding)."""
+    specs = mixed_batch_specs()[:6]
+    big = dict(inputs.batch_workloads(n=1, seed=5)[0], N=3, B=20000)
+    big["L"] = inputs.half_width(big["B"])
+    big["potential"] = inputs.henon_heiles_chain(3, 0.1)
+    big["init"] = dict(big["init"], q=[0.3, -0.2, 0.5])
+    specs.append(big)
+    dtypes = [hx.HX_C64] * len(specs)
+    infos = []
+    got, c0s, _ = run_batch(hx, specs, dtypes, nsteps=(1, 2, 6), batched=None, infos=infos)
+    assert infos[0]["schedule"] == -1 and len(infos[0]["step_ms"]) == 1
+    last = infos[-1]
+    assert sorted(last["step_ms"]) == [hx.HX_SCHED_MEMBERS, hx.HX_SCHED_BATCHED, hx.HX_SCHED_HYBRID,
+                                       hx.HX_SCHED_SERIAL]
+    assert last["schedule"] == min(last["step_ms"], key=last["step_ms"].get)
+    refs = {}
+    for forced in ("0", "1", "2", "3"):
+        refs[int(forced)], _, info = run_batch(hx, specs, dtypes, nsteps=(9,), batched=forced)
+        assert info["schedule"] == int(forced)
+    for sched, ref in refs.items():
+        for i in range(len(specs) - 1):
+            assert np.array_equal(ref[i], got[i]), (sched, i)
+    for sched in (1, 2):
+        assert np.array_equal(refs[sched][-1], refs[0][-1]), sched
+    # the timed steps ran every schedule once, so the large member took steps of both kinds
+    assert np.linalg.norm(got[-1] - refs[0][-1]) <= 1e-5 * np.linalg.norm(refs[0][-1])
+    # the serial schedule's large member: hx_step on the problem alone, with its specialised kernel
+    P = hx.Problem(big["N"], big["B"], dtype=hx.HX_C64, m=big["m"])
+    try:
+        P.set_potential(big, 0.0)
+        assert hx.hx_apply_specialised(P.p) == 1
+        x = torch.from_numpy(c0s[-1]).to("cuda")
+        hx.hx_step(P.p, x, 0.01, 9)
+        torch.cuda.synchronize()
+        alone = x.cpu().numpy()
+    finally:
+        P.close()
+    assert np.array_equal(refs[3][-1], alone)
+    assert np.linalg.norm(refs[3][-1] - refs[0][-1]) <= 1e-5 * np.linalg.norm(refs[0][-1])

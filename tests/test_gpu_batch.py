@@ -291,3 +291,52 @@ def test_batch_schedule_autotune(hx):
         P.close()
     assert np.array_equal(refs[3][-1], alone)
     assert np.linalg.norm(refs[3][-1] - refs[0][-1]) <= 1e-5 * np.linalg.norm(refs[0][-1])
+
+
+def _hc_size(N, B, _memo={}):
+    """|{k in N^N : prod (1 + k_l) <= B}| by recursion on the first coordinate."""
+    if N == 0:
+        return 1
+    key = (N, B)
+    if key not in _memo:
+        _memo[key] = sum(_hc_size(N - 1, B // (1 + k)) for k in range(B))
+    return _memo[key]
+
+
+def test_batch_members_of_the_256_problem_workload(hx, oracle):
+    """Members of the 256-problem workload itself (N ~ U{2..8}, B log-uniform in [64, 8192]): the six
+    smallest, three of about 9e4 coefficients and the two closest to 2.4 M and 3.1 M, stepped
+    together in complex64 under the batched and the serial schedules.  Every member equals hx_step
+    on it alone bit for bit (the generic kernel for members in the batched launches, its
+    specialised kernel for a large member under the serial schedule); the two smallest match the
+    oracle."""
+    all_specs = inputs.batch_workloads(n=256, seed=3)
+    by_size = sorted(range(len(all_specs)), key=lambda i: _hc_size(all_specs[i]["N"], all_specs[i]["B"]))
+    sizes = {i: _hc_size(all_specs[i]["N"], all_specs[i]["B"]) for i in by_size}
+    mid = [i for i in by_size if 8e4 < sizes[i] < 2e5][:3]
+    large = [min(by_size, key=lambda i: abs(sizes[i] - t)) for t in (2.4e6, 3.1e6)]
+    pick = by_size[:6] + mid + large
+    specs = [all_specs[i] for i in pick]
+    dtypes = [hx.HX_C64] * len(specs)
+    nsteps = (2, 1)
+    serial, c0s, info = run_batch(hx, specs, dtypes, nsteps=nsteps, batched="3")
+    batched, _, _ = run_batch(hx, specs, dtypes, nsteps=nsteps, batched="1")
+    assert info["schedule"] == hx.HX_SCHED_SERIAL
+    for j, (spec, c0) in enumerate(zip(specs, c0s)):
+        for generic, want in ((True, batched[j]), (j < len(specs) - 2, serial[j])):
+            P = hx.Problem(spec["N"], spec["B"], dtype=hx.HX_C64, m=spec["m"])
+            try:
+                with env("HX_APPLY_SPECIALISE", "0" if generic else None):
+                    P.set_potential(spec, 0.0)
+                assert generic or hx.hx_apply_specialised(P.p) == 1
+                x = torch.from_numpy(c0).to("cuda")
+                hx.hx_step(P.p, x, 0.01, sum(nsteps))
+                torch.cuda.synchronize()
+                assert np.array_equal(x.cpu().numpy(), want), (j, generic)
+            finally:
+                P.close()
+    for j in (0, 1):
+        spec = specs[j]
+        S = oracle.IndexSet.hyperbolic(spec["N"], spec["B"])
+        ref, _ = oracle.expmpr_propagate(S, spec, c0s[j], 0.01, sum(nsteps), spec["m"])
+        assert np.linalg.norm(serial[j] - ref) <= 1e-5 * np.linalg.norm(ref), j

@@ -261,20 +261,22 @@ HX_API int hx_step_substeps(hx_problem *p, int *last, int64_t *total, double *er
  * library runs the product.  Setting the environment variable HX_APPLY_SPECIALISE=0 before
  * hx_potential_set selects the generic kernel; HX_JIT_SOURCE_DUMP=<file> writes the source of a
  * newly compiled kernel to that file before compiling it.  The steps of a batch (hx_batch_step)
- * always run the generic kernel. */
+ * run the generic kernel, except the large members of the HX_SCHED_SERIAL schedule. */
 HX_API int hx_apply_specialised(const hx_problem *p);
 /* Kernel launches of one product hx_apply (1, or 2 when some term is evaluated in two stages
- * through channel vectors) and of one time step of hx_step: m (per_apply + 3) + 2 for
- * HX_SCHEME_EXPMPR (the normalisation, per Lanczos vector the product, one projection and two
- * orthogonalisation passes (one for the last vector), the eigensolver and the recombination),
- * or m (per_apply + 2) + 2 for HX_C64 when the product kernel is specialised
- * (hx_apply_specialised), per_apply = 1 and m <= 8 (that kernel then also computes the
- * projection), and m (4 per_apply + 4) + 2 for HX_SCHEME_MAGNUS4 (per Lanczos vector four products
- * and their combination into H v), m (2 per_apply + 3) + 2 when the product kernel is specialised
- * and per_apply = 1 (one launch gives A_1 v and A_2 v, another A_2 A_1 v and A_1 A_2 v and combines
- * them into H v); 2 more with hx_config.tol > 0 (the pass after the last vector and the error
- * estimate), per sub-step.  Needs a potential; either pointer may be NULL.  The paper has no counterpart: this reports how the library maps
- * its work onto kernels. */
+ * through channel vectors) and of one time step of hx_step.  Per Lanczos vector: the product
+ * (per_apply launches), one projection launch unless the product computes the projections itself
+ * (HX_C64, a specialised product kernel (hx_apply_specialised), per_apply = 1, m <= 8), and the
+ * Gram-Schmidt work: one sweep for m <= 8, two passes for m > 8 (the last vector's second pass only
+ * with hx_config.tol > 0).  HX_SCHEME_MAGNUS4 takes, instead of the product, four products and
+ * their combination into H v (4 per_apply + 1), or with a specialised kernel and per_apply = 1 two
+ * launches (one gives A_1 v and A_2 v, the other A_2 A_1 v and A_1 A_2 v combined into H v), and
+ * always the projection launch.  Then the start vector, the exponential and the recombination: 3
+ * more (for m > 8 counted as 2, the last vector's skipped second pass taken off), and with
+ * hx_config.tol > 0 the error estimate: 1 more (for m > 8 2, with that pass), per sub-step.  For
+ * example m (per_apply + 1) + 3 for HX_C64 with a specialised kernel and m <= 8.
+ * Needs a potential; either pointer may be NULL.  The paper has no counterpart: this reports how
+ * the library maps its work onto kernels. */
 HX_API int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step);
 
 /* ---- batches of independent problems ----------------------------------------------- */

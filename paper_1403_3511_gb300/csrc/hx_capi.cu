@@ -1444,14 +1444,21 @@ int hx_step_launches(const hx_problem *p, int *per_apply, int *per_step)
     if (!p->have_pot) { set_error("hx_step_launches: call hx_potential_set first"); return HX_EINVAL; }
     const int a = apply_launches(p);
     if (per_apply) *per_apply = a;
+    const int m = p->cfg.m;
     // expMPR: the product kernel computes the projections itself when it is specialised (m <= 8)
-    const int dots = p->cfg.m <= kMaxFusedDots && apply_fuses_dots(p) ? 0 : 1;
+    const int dots = m <= kMaxFusedDots && apply_fuses_dots(p) ? 0 : 1;
+    // Gram-Schmidt per Lanczos vector: one sweep for m <= 8, else two passes (the second pass of the
+    // last vector only with an error tolerance); then the start vector, the exponential and the
+    // recombination, and with a tolerance the error estimate
+    const bool sweep = m <= kMaxFusedDots;
+    const int gs = sweep ? 1 : 2;
+    const int fixed = sweep ? 3 : 2;
+    const int est = p->cfg.tol > 0.0 ? (sweep ? 1 : 2) : 0;
     // 2-stage Magnus: A_1 v and A_2 v in one launch, A_2 A_1 v and A_1 A_2 v in another, with the
-    // specialised kernel
-    const int mag = apply_dual(p) ? 2 * a + 3 : 4 * a + 4;   // the second launch also forms H v
-    // with an error tolerance: the second pass after the last vector and the estimate, per sub-step
-    const int est = p->cfg.tol > 0.0 ? 2 : 0;
-    if (per_step) *per_step = (p->cfg.scheme == HX_SCHEME_MAGNUS4 ? p->cfg.m * mag + 2 : p->cfg.m * (a + 2 + dots) + 2) + est;
+    // specialised kernel (the second launch also forms H v), else four products and a combination;
+    // then the projections and the Gram-Schmidt launches
+    const int mag = (apply_dual(p) ? 2 * a : 4 * a + 1) + 1 + gs;
+    if (per_step) *per_step = (p->cfg.scheme == HX_SCHEME_MAGNUS4 ? m * mag : m * (a + gs + dots)) + fixed + est;
     return HX_OK;
 }
 

@@ -43,6 +43,10 @@ struct Scal {                       // device scalars of one problem
     double norm_out;
     double err_max;                 // largest a-posteriori error estimate since it was last cleared
     double t_save;                  // problem time at the start of an adaptive step (restored on retry)
+    // one-sweep Gram-Schmidt (m <= 8): p_j = <v_j, u_k> of the next vector's first-pass direction
+    // u_k = s_k V_k against the finished v_j, and nu = ||u_k - sum_j p_j v_j|| (see sweep_k_kernel)
+    double p[2 * kMaxFusedDots];
+    double nu;
     int m_used;
     int flags;                      // bit 0: breakdown seen, bit 1: non-finite, bit 2: eigensolver stalled
     unsigned counter;
@@ -503,112 +507,201 @@ __global__ void __launch_bounds__(256, (sizeof(V) == 8 && NV <= 8) ? 3 : 1) upda
     if (reduce_partials(vals, nval, partials, &sc->counter, tot) && threadIdx.x == 0) update_scalars<pass>(sc, k, tot);
 }
 
-// The update for one Lanczos index K <= 7 known at compile time (the step graph launches one per
-// k): register arrays of exactly K + 1 vectors, and for small K each thread loads U grid-stride
-// iterations before using them, so that enough bytes are in flight to cover the memory latency
-// when only K + 2 vectors stream.
+// Lanczos index K < 8 in one sweep over the vectors: classical Gram-Schmidt in which the second
+// pass of each vector is done by the sweep of the next index.  On entry slot K holds V_K with
+// u_K = s_K V_K, the first-pass direction of the K-th vector (unit norm), the finished v_j = V_j
+// (j < K, s_j = 1), sc->p_j = <v_j, u_K> and sc->nu = ||u_K - sum_j p_j v_j|| from the sweep of
+// index K - 1, and slot K + 1 holds z = A u_K with q_i = sc->h_i = s_i <V_i, z> (i <= K) from the
+// product launch.  The sweep writes
+//   v_K = (u_K - sum_{j<K} p_j v_j) / nu                                 (second pass of v_K)
+//   w   = (z - sum_{j<K} q_j v_j) / nu - c_K v_K,  c_K = (q_K - sum_j conj(p_j) q_j) / nu^2,
+// which is A v_K - sum_{j<=K} <v_j, A v_K> v_j (first pass of the next vector): A v_K = (z - sum_j
+// p_j A v_j) / nu and, the Krylov relation giving A v_j in span(v_0 .. v_{j+1}) with
+// <v_K, A v_{K-1}> = beta_{K-1}, the coefficients collapse to those above.  It also sums
+// d_l = <v_l, w> (l <= K) and ||w||^2.  Then h_K = <v_K, A v_K> = c_K - p_{K-1} beta_{K-1} / nu and,
+// as with two passes per vector, alpha_K = Re(h_K + d_K); the next direction is u_{K+1} = w / ||w||
+// with p'_l = d_l / ||w||, nu' = sqrt(1 - sum |p'_l|^2) and beta_K = ||w|| nu'.  In exact arithmetic
+// alpha, beta and the v's are those of two full passes per vector; each vector is read once per
+// Lanczos index instead of twice.
 template <typename V, int K>
-constexpr int update_k_blocks()   // resident blocks per SM that keep the kernel free of spills
+constexpr int sweep_k_blocks()   // resident blocks per SM that keep the kernel free of spills
 {
-    return sizeof(V) == 8 ? (K < 6 ? 3 : 2) : (K < 3 ? 2 : 1);
+    return sizeof(V) == 8 ? (K < 5 ? 3 : 2) : (K < 3 ? 2 : 1);
 }
 
-template <typename V, int K, int pass>
-__global__ void __launch_bounds__(256, update_k_blocks<V, K>()) update_k_kernel(V *w, const V *Vb, size_t ld, int n, double *partials, Scal *sc)
+constexpr int kSweepVals = 2 * kMaxFusedDots + 2;   // d_l (re, im), l < 8, and ||w||^2
+
+template <typename V, int K>
+__global__ void __launch_bounds__(256, sweep_k_blocks<V, K>()) sweep_k_kernel(V *Vb, size_t ld, int n, double *partials,
+                                                                                 Scal *sc)
 {
-    constexpr int NK = K + 1;
-    constexpr int U = K + 2 >= 5 ? 1 : (K + 2 >= 3 ? 2 : 4);
+    constexpr int NK = K + 1, NVAL = 2 * NK + 1;
+    constexpr int U = K + 3 >= 5 ? 1 : (K + 3 >= 3 ? 2 : 4);
     using R = typename Real<V>::T;
-    __shared__ double tot[2 * NK];
+    __shared__ double tot[kSweepVals];
+    __shared__ double cf[4 * NK + 2];   // b_j (j < K), c_i (i <= K) as re, im pairs; a; 1 / nu
     if (K >= sc->m_used) return;
-    const double *coef = pass == 0 ? sc->h : sc->h2;
-    R cr[NK], ci[NK];
+    if (threadIdx.x == 0) {
+        const double nu = K == 0 ? 1.0 : sc->nu, inv = 1.0 / nu;
+        double cr = sc->h[2 * K], ci = sc->h[2 * K + 1];            // q_K - sum_j conj(p_j) q_j
+        for (int j = 0; j < K; ++j) {
+            const double pr = sc->p[2 * j], pi = sc->p[2 * j + 1], qr = sc->h[2 * j], qi = sc->h[2 * j + 1];
+            cf[2 * j] = pr * inv;
+            cf[2 * j + 1] = pi * inv;
+            cf[2 * K + 2 * j] = qr * inv;
+            cf[2 * K + 2 * j + 1] = qi * inv;
+            cr -= pr * qr + pi * qi;
+            ci -= pr * qi - pi * qr;
+        }
+        cf[4 * K] = cr * inv * inv;
+        cf[4 * K + 1] = ci * inv * inv;
+        cf[4 * K + 2] = sc->s[K] * inv;
+        cf[4 * K + 3] = inv;
+    }
+    __syncthreads();
+    R br[K > 0 ? K : 1], bi[K > 0 ? K : 1], cr[NK], ci[NK];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        br[j] = (R)cf[2 * j];
+        bi[j] = (R)cf[2 * j + 1];
+    }
 #pragma unroll
     for (int i = 0; i < NK; ++i) {
-        cr[i] = (R)(coef[2 * i] * sc->s[i]);
-        ci[i] = (R)(coef[2 * i + 1] * sc->s[i]);
+        cr[i] = (R)cf[2 * K + 2 * i];
+        ci[i] = (R)cf[2 * K + 2 * i + 1];
     }
+    const R a = (R)cf[4 * K + 2], inv = (R)cf[4 * K + 3];
+    V *const uk = Vb + (size_t)K * ld, *const zk = Vb + (size_t)(K + 1) * ld;
     using A = typename PairAccOf<V>::T;
-    A acc[pass == 0 ? NK : 1];
+    A acc[NK];
     A nrm;
     const int npair = n >> 1;
     const int gid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+    auto element = [&](V u, V z, const V *v, V &vk, V &w) {
+        vk.x = a * u.x;
+        vk.y = a * u.y;
+#pragma unroll
+        for (int j = 0; j < K; ++j) sub_scaled(vk, br[j], bi[j], v[j]);
+        w.x = inv * z.x;
+        w.y = inv * z.y;
+#pragma unroll
+        for (int j = 0; j < K; ++j) sub_scaled(w, cr[j], ci[j], v[j]);
+        sub_scaled(w, cr[K], ci[K], vk);
+    };
     for (int q0 = gid; q0 < npair; q0 += U * gstride) {
-        Pair<V> x[U], v[U][NK];
+        Pair<V> x[U], y[U], v[U][K > 0 ? K : 1];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int q = q0 + u * gstride;
             if (q < npair) {
-                x[u] = load_pair(w, 2 * q);
+                x[u] = load_pair(uk, 2 * q);
+                y[u] = load_pair(zk, 2 * q);
 #pragma unroll
-                for (int i = 0; i < NK; ++i) v[u][i] = load_pair(Vb + i * ld, 2 * q);
+                for (int j = 0; j < K; ++j) v[u][j] = load_pair(Vb + j * ld, 2 * q);
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int q = q0 + u * gstride;
             if (q < npair) {
+                V va[K > 0 ? K : 1], vb[K > 0 ? K : 1];
 #pragma unroll
-                for (int i = 0; i < NK; ++i) {
-                    sub_scaled(x[u].a, cr[i], ci[i], v[u][i].a);
-                    sub_scaled(x[u].b, cr[i], ci[i], v[u][i].b);
+                for (int j = 0; j < K; ++j) {
+                    va[j] = v[u][j].a;
+                    vb[j] = v[u][j].b;
                 }
-                store_pair(w, 2 * q, x[u]);
-                if constexpr (pass == 0) {
+                Pair<V> vk, w;
+                element(x[u].a, y[u].a, va, vk.a, w.a);
+                element(x[u].b, y[u].b, vb, vk.b, w.b);
+                store_pair(uk, 2 * q, vk);
+                store_pair(zk, 2 * q, w);
 #pragma unroll
-                    for (int i = 0; i < NK; ++i) add_pair(acc[i], v[u][i].a, x[u].a, v[u][i].b, x[u].b);
-                } else {
-                    add_pair(nrm, x[u].a, x[u].a, x[u].b, x[u].b);
-                }
+                for (int j = 0; j < K; ++j) add_pair(acc[j], va[j], w.a, vb[j], w.b);
+                add_pair(acc[K], vk.a, w.a, vk.b, w.b);
+                add_pair(nrm, w.a, w.a, w.b, w.b);
             }
         }
     }
     if ((n & 1) && gid == 0) {                              // odd length: the last element
         const int e = n - 1;
-        V x = w[e];
-        V v[NK];
+        V v[K > 0 ? K : 1];
 #pragma unroll
-        for (int i = 0; i < NK; ++i) {
-            v[i] = Vb[i * ld + e];
-            sub_scaled(x, cr[i], ci[i], v[i]);
-        }
-        w[e] = x;
-        if constexpr (pass == 0) {
+        for (int j = 0; j < K; ++j) v[j] = Vb[j * ld + e];
+        V vk, w;
+        element(uk[e], zk[e], v, vk, w);
+        uk[e] = vk;
+        zk[e] = w;
 #pragma unroll
-            for (int i = 0; i < NK; ++i) acc[i].add(v[i], x);
-        } else {
-            nrm.add(x, x);
-        }
+        for (int j = 0; j < K; ++j) acc[j].add(v[j], w);
+        acc[K].add(vk, w);
+        nrm.add(w, w);
     }
-    if constexpr (pass == 0 && std::is_same<V, float2>::value) {
-        // the 2 (K + 1) projections: warp sums in FP32 pairs, one FP64 value per warp and projection
-        constexpr int NV = pow2_at_least(2 * NK);
+    bool last;
+    if constexpr (std::is_same<V, float2>::value) {
+        // the 2 (K + 1) projections and the norm: warp sums in FP32 pairs, one FP64 value per warp
+        constexpr int NV = pow2_at_least(NVAL);
         float ps[NV], pc[NV];
 #pragma unroll
-        for (int i = 0; i < NV / 2; ++i) {
-            ps[2 * i] = i < NK ? acc[i].re.s : 0.f;
-            pc[2 * i] = i < NK ? acc[i].re.c : 0.f;
-            ps[2 * i + 1] = i < NK ? acc[i].im.s : 0.f;
-            pc[2 * i + 1] = i < NK ? acc[i].im.c : 0.f;
+        for (int i = 0; i < NV; ++i) {
+            ps[i] = 0.f;
+            pc[i] = 0.f;
         }
-        __shared__ double wsum[8][2 * kMaxFusedDots];
-        warp_pair_sums<NV>(ps, pc, 2 * NK, wsum);
-        __syncthreads();
-        if (reduce_warp_sums<2 * kMaxFusedDots>(wsum, 2 * NK, partials, &sc->counter, tot) && threadIdx.x == 0)
-            update_scalars<pass>(sc, K, tot);
-    } else {
-        double vals[pass == 0 ? 2 * NK : 1];
-        if constexpr (pass == 0) {
 #pragma unroll
-            for (int i = 0; i < NK; ++i) {
-                vals[2 * i] = acc[i].r();
-                vals[2 * i + 1] = acc[i].i();
+        for (int i = 0; i < NK; ++i) {
+            ps[2 * i] = acc[i].re.s;
+            pc[2 * i] = acc[i].re.c;
+            ps[2 * i + 1] = acc[i].im.s;
+            pc[2 * i + 1] = acc[i].im.c;
+        }
+        ps[2 * NK] = nrm.re.s;
+        pc[2 * NK] = nrm.re.c;
+        __shared__ double wsum[8][kSweepVals];
+        warp_pair_sums<NV>(ps, pc, NVAL, wsum);
+        __syncthreads();
+        last = reduce_warp_sums<kSweepVals>(wsum, NVAL, partials, &sc->counter, tot);
+    } else {
+        double vals[NVAL];
+#pragma unroll
+        for (int i = 0; i < NK; ++i) {
+            vals[2 * i] = acc[i].r();
+            vals[2 * i + 1] = acc[i].i();
+        }
+        vals[2 * NK] = nrm.r();
+        last = reduce_partials<kSweepVals>(vals, NVAL, partials, &sc->counter, tot);
+    }
+    if (last && threadIdx.x == 0) {
+        const double nu = K == 0 ? 1.0 : sc->nu;
+        const double nw = sqrt(tot[2 * NK]);
+        // h_K = c_K - p_{K-1} beta_{K-1} / nu (real part), alpha_K = Re(h_K + d_K)
+        double hk = cf[4 * K];
+        if (K > 0) hk -= sc->p[2 * (K - 1)] * sc->beta[K - 1] / nu;
+        const double a_k = hk + tot[2 * K];
+        sc->alpha[K] = a_k;
+        const double sc_k = fabs(a_k) + (K > 0 ? sc->beta[K - 1] : 0.0);
+        if (sc_k > sc->scale) sc->scale = sc_k;
+        sc->s[K] = 1.0;                                      // v_K is stored normalised
+        double pp = 0.0;
+        for (int l = 0; l < NK; ++l) {
+            const double pr = tot[2 * l] / nw, pi = tot[2 * l + 1] / nw;
+            sc->p[2 * l] = pr;
+            sc->p[2 * l + 1] = pi;
+            pp += pr * pr + pi * pi;
+        }
+        const double nu1 = sqrt(fmax(1.0 - pp, 0.0)), b = nw * nu1;
+        if (!isfinite(b)) sc->flags |= 2;
+        if (b <= 1e-13 * sc->scale) {                        // invariant subspace: stop with K + 1 vectors
+            if (K + 1 < sc->m_used) {
+                sc->m_used = K + 1;
+                sc->flags |= 1;
+            } else {                                         // after the last vector (error estimate): exact
+                sc->beta[K] = 0.0;
             }
         } else {
-            vals[0] = nrm.r();
+            sc->beta[K] = b;
+            sc->s[K + 1] = 1.0 / nw;
+            sc->nu = nu1;
         }
-        if (reduce_partials(vals, pass == 0 ? 2 * NK : 1, partials, &sc->counter, tot) && threadIdx.x == 0)
-            update_scalars<pass>(sc, K, tot);
+        sc->counter = 0;
     }
 }
 
@@ -1231,30 +1324,28 @@ __global__ void magnus_combine_kernel(V *out, const V *a1v, const V *a2v, const 
     }
 }
 
-template <typename V, int K, int pass>
-static void launch_update_k_t(const Problem *p, V *wv, const V *Vb, size_t ld, int n, double *partials, Scal *sc,
-                              cudaStream_t st)
+template <typename V, int K>
+static void launch_sweep_k_t(const Problem *p, V *Vb, size_t ld, int n, double *partials, Scal *sc, cudaStream_t st)
 {
-    const int G = resident_grid(p, update_k_kernel<V, K, pass>, 256);
-    update_k_kernel<V, K, pass><<<G, 256, 0, st>>>(wv, Vb, ld, n, partials, sc);
+    const int G = resident_grid(p, sweep_k_kernel<V, K>, 256);
+    sweep_k_kernel<V, K><<<G, 256, 0, st>>>(Vb, ld, n, partials, sc);
 }
 
-// The update pass for Lanczos index k < 8 with the kernel specialised for k.
+// The Gram-Schmidt sweep of Lanczos index k < 8 with the kernel specialised for k.
 template <typename V>
-static int launch_update_k(const Problem *p, V *wv, const V *Vb, size_t ld, int n, int k, int pass, double *partials,
-                           Scal *sc, cudaStream_t st)
+static int launch_sweep_k(const Problem *p, V *Vb, size_t ld, int n, int k, double *partials, Scal *sc,
+                          cudaStream_t st)
 {
-#define HX_UPDATE_K(K)                                                                  \
-    case K:                                                                             \
-        if (pass == 0) launch_update_k_t<V, K, 0>(p, wv, Vb, ld, n, partials, sc, st);  \
-        else launch_update_k_t<V, K, 1>(p, wv, Vb, ld, n, partials, sc, st);            \
+#define HX_SWEEP_K(K)                                               \
+    case K:                                                         \
+        launch_sweep_k_t<V, K>(p, Vb, ld, n, partials, sc, st);     \
         return HX_OK;
     switch (k) {
-        HX_UPDATE_K(0) HX_UPDATE_K(1) HX_UPDATE_K(2) HX_UPDATE_K(3)
-        HX_UPDATE_K(4) HX_UPDATE_K(5) HX_UPDATE_K(6) HX_UPDATE_K(7)
+        HX_SWEEP_K(0) HX_SWEEP_K(1) HX_SWEEP_K(2) HX_SWEEP_K(3)
+        HX_SWEEP_K(4) HX_SWEEP_K(5) HX_SWEEP_K(6) HX_SWEEP_K(7)
     }
-#undef HX_UPDATE_K
-    set_error("internal: update kernel for k = %d", k);
+#undef HX_SWEEP_K
+    set_error("internal: Gram-Schmidt sweep kernel for k = %d", k);
     return HX_EUNSUPPORTED;
 }
 
@@ -1293,7 +1384,6 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
     const size_t ld = w->vec_bytes / sizeof(V);
     Scal *sc = w->sc;
     const int Gd = resident_grid(p, dot_kernel<V, NV>, T);
-    const int Gu0 = resident_grid(p, update_kernel<V, NV, 0>, T), Gu1 = resident_grid(p, update_kernel<V, NV, 1>, T);
     const bool all = phase == kPhaseAll;
     // the exponential midpoint step takes the projections from the product kernel when it can
     const bool fused = all && p->cfg.scheme == HX_SCHEME_EXPMPR && NV <= kMaxFusedDots && apply_fuses_dots(p);
@@ -1332,13 +1422,13 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
         }
         V *wv = Vb + (size_t)(k + 1) * ld;
         if (!f.dvec) dot_kernel<V, NV><<<Gd, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
-        // the second pass also runs after the last vector when the step estimates its error (beta_m)
-        const bool pass1 = k < m - 1 || p->cfg.tol > 0.0;
-        if (NV <= 8) {
-            if ((rc = launch_update_k<V>(p, wv, Vb, ld, n, k, 0, w->partials, sc, st)) ||
-                (pass1 && (rc = launch_update_k<V>(p, wv, Vb, ld, n, k, 1, w->partials, sc, st))))
-                return rc;
+        if constexpr (NV <= 8) {   // one sweep per vector (the second pass of v_k and the first of v_{k+1})
+            if ((rc = launch_sweep_k<V>(p, Vb, ld, n, k, w->partials, sc, st))) return rc;
         } else {
+            // two passes; the second also runs after the last vector when the step estimates its
+            // error (beta_m)
+            const bool pass1 = k < m - 1 || p->cfg.tol > 0.0;
+            const int Gu0 = resident_grid(p, update_kernel<V, NV, 0>, T), Gu1 = resident_grid(p, update_kernel<V, NV, 1>, T);
             update_kernel<V, NV, 0><<<Gu0, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
             if (pass1) update_kernel<V, NV, 1><<<Gu1, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
         }

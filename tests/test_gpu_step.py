@@ -94,7 +94,7 @@ def test_fused_projections_lanczos_coefficients(hx, oracle, m):
     try:
         P.set_potential(spec, 0.0)
         assert hx.hx_apply_specialised(P.p) == 1
-        assert hx.hx_step_launches(P.p)[1] == m * 3 + 2       # no separate projection kernel
+        assert hx.hx_step_launches(P.p)[1] == m * 2 + 3       # no separate projection kernel
         x = torch.from_numpy(c0).to("cuda")
         hx.hx_step(P.p, x, h, 1)
         info = hx.hx_step_info(P.p)
@@ -305,8 +305,16 @@ def test_magnus4_time_integration_experiment(hx, oracle):
 def test_step_launch_counts(hx):
     # expMPR: the specialised complex64 product kernel computes the projections itself when m <= 8
     # and the product is one launch; Magnus: the two-time kernels need a one-stage product too
-    per = {0: lambda m, a, spec, c64: m * (a + (2 if spec and c64 and m <= 8 and a == 1 else 3)) + 2,
-           1: lambda m, a, spec, c64: m * (2 * a + 3 if spec and a == 1 else 4 * a + 4) + 2}
+    # Gram-Schmidt: one sweep per vector for m <= 8 (then start, exponential, recombination: 3),
+    # two passes for m > 8 (the last vector's second pass skipped: 2)
+    def gs(m):
+        return 1 if m <= 8 else 2
+
+    def fixed(m):
+        return 3 if m <= 8 else 2
+
+    per = {0: lambda m, a, spec, c64: m * (a + gs(m) + (0 if spec and c64 and m <= 8 and a == 1 else 1)) + fixed(m),
+           1: lambda m, a, spec, c64: m * ((2 * a if spec and a == 1 else 4 * a + 1) + 1 + gs(m)) + fixed(m)}
     for scheme in (0, 1):
         for name in ("hh2_b32", "cos10_b1024"):
             spec = inputs.workload(name) if name == "hh2_b32" else dict(N=3, B=40, L=inputs.half_width(40),

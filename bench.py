@@ -119,8 +119,8 @@ def kernel_source_hash(root: str = None) -> str:
 
 def profiled_value(workload: str, dtype: str, kind: str, key: str):
     """An integer figure ("key: N") from the committed ncu summary of this workload and kernel
-    (kind "apply_kernel": the product; "apply_project_kernel": the product with the Lanczos
-    projections, averaged over the projection counts of one step), or None when there is none or
+    (kind "apply_kernel": the product; "apply_rq_kernel": the product with the Rayleigh quotient of
+    its input, as the time step launches it), or None when there is none or
     the kernel sources have changed since it was captured."""
     import re
     path = os.path.join(ROOT, "profiles", f"{kind}_{workload}_{dtype}.md")
@@ -421,24 +421,21 @@ def main():
     eb.record(stream)
     barrier()
     ms_apply = ea.elapsed_time(eb) / napply
-    # the step's own product launches: with the specialised complex64 kernel they also compute the
-    # projections h_i = <v_i, A v_k>, i <= k, k = 0 .. m-1 (hx_apply_project), each k once per step
+    # the step's own product launches: with the specialised complex64 kernel each also computes the
+    # Rayleigh quotient <v_k, A v_k> of its input (hx_apply_rayleigh), m launches per step
     fused = (bool(hx.hx_apply_specialised(P.p)) and dtype == hx.HX_C64 and m <= 8
              and hx.hx_step_launches(P.p)[0] == 1)      # one-stage potentials only
     ms_proj = 0.0
     if fused:
-        basis = torch.randn((m, n), dtype=vdt, device="cuda")
-        hproj = torch.empty(16, dtype=torch.float64, device="cuda")
-        for k in range(m):
-            hx.hx_apply_project(P.p, basis[k], y, basis, k, hproj)
-        nproj = m * max(2, args.steps)
+        rq = torch.empty(2, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            hx.hx_apply_rayleigh(P.p, x, y, rq)
         ea.record(stream)
-        for i in range(nproj):
-            hx.hx_apply_project(P.p, basis[i % m], y, basis, i % m, hproj)
+        for _ in range(napply):
+            hx.hx_apply_rayleigh(P.p, x, y, rq)
         eb.record(stream)
         barrier()
-        ms_proj = ea.elapsed_time(eb) / nproj
-        del basis
+        ms_proj = ea.elapsed_time(eb) / napply
     clk = clocks.stop()
     ms_step, ms_apply, ms_proj = max_over_ranks([ms_step, ms_apply, ms_proj], world, "cuda")
     value = whole_job_gcoeff_s(m, n, world, ms_step * 1e-3)
@@ -534,13 +531,13 @@ def main():
         product["issue"] = issue_roofline(winst, ms_apply, clk["sm_mhz"],
                                           torch.cuda.get_device_properties(local).multi_processor_count)
     if fused:
-        alg_proj = (16 + 8 * (m - 1) / 2) * n            # mean over k = 0 .. m-1
+        alg_proj = alg_bytes                              # the quotient re-reads the input: no extra bytes
         achieved = alg_proj / (ms_proj * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(spec["name"], args.dtype, "apply_project_kernel"),
-                "kernel": "hx_apply_specialised_dots", "ms_per_launch": ms_proj,
+                "traffic": profiled_traffic(spec["name"], args.dtype, "apply_rq_kernel"),
+                "kernel": "hx_apply_specialised_rq", "ms_per_launch": ms_proj,
                 "bytes_per_launch": alg_proj, "peak_source": peak_source, "product_alone": product}
-        winst = profiled_value(spec["name"], args.dtype, "apply_project_kernel", "warp_instructions_per_launch")
+        winst = profiled_value(spec["name"], args.dtype, "apply_rq_kernel", "warp_instructions_per_launch")
         if winst and clk.get("sm_mhz"):
             roof["issue"] = issue_roofline(winst, ms_proj, clk["sm_mhz"],
                                            torch.cuda.get_device_properties(local).multi_processor_count)

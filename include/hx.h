@@ -374,9 +374,18 @@ HX_API int hx_norm(hx_problem *p, const void *c, double *out);
 /* The energy <c, A(t) c> (real, since A(t) is Hermitian; not divided by ||c||^2) of a device vector
  * of the problem dtype at the problem time, for monitoring a propagation (Sec. 2.2 assumes a
  * Hermitian A(t); for a time-independent W the exponential midpoint rule keeps it up to the
- * Lanczos error).  One product with its projection (hx_apply_project, k = 0) into a temporary
- * vector; synchronous.  Errors as hx_apply. */
+ * Lanczos error).  One hx_apply_rayleigh into a temporary vector; synchronous.  Errors as hx_apply. */
 HX_API int hx_energy(hx_problem *p, const void *c, double *out);
+/* y = A(t) c and r = <c, y> = c^H A(t) c (r[0] real part, r[1] imaginary part, zero up to rounding
+ * for a Hermitian A) at the problem time: the product of a Lanczos step together with the
+ * diagonal entry of T_m (Sec. 2.2).  One launch when the product kernel is specialised
+ * (hx_apply_specialised) and the dtype is HX_C64 (the product kernel sums conj(c_e) y_e itself in
+ * compensated FP32 and the blocks' sums in FP64); otherwise the product and one reduction kernel.
+ * c, y: DEVICE vectors of the problem dtype and size |K|, aligned to the element size, not
+ * overlapping; r: DEVICE pointer to 2 doubles, 8-byte aligned, overlapping neither.  Asynchronous on
+ * the problem stream.  Errors: HX_EINVAL (NULL or misaligned pointers, overlap, no potential),
+ * HX_ECUDA.  Two calls on one problem must not run concurrently (they share a workspace). */
+HX_API int hx_apply_rayleigh(hx_problem *p, const void *c, void *y, double *r);
 
 /* ---- allocation-free norm ------------------------------------------------------- */
 

@@ -459,6 +459,16 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
         a.dh = fuse->h;
         a.dpartials = fuse->partials;
         a.dcounter = fuse->counter;
+    } else if (fuse && fuse->rq) {
+        if (stage1 || !apply_fuses_dots(p)) {
+            set_error("a Rayleigh quotient requested from a product kernel that cannot compute it");
+            return HX_EUNSUPPORTED;
+        }
+        a.drq = 1;
+        a.ds = fuse->s;
+        a.dh = fuse->h;
+        a.dpartials = fuse->partials;
+        a.dcounter = fuse->counter;
     }
     a.chan = p->chan;
     a.chan_ld = p->chan_ld;

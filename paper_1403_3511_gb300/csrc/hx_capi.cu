@@ -1192,7 +1192,7 @@ int hx_energy(hx_problem *p, const void *c, double *out)
     const size_t hoff = ((bytes + 255) / 256) * 256;
     HX_CUDA(cudaMallocAsync((void **)&buf, hoff + 256, p->stream), "cudaMallocAsync(energy)");
     double *h = (double *)(buf + hoff);
-    int rc = apply_project_dispatch(p, c, buf, c, (size_t)p->set->h.size, 0, h);
+    int rc = apply_rayleigh_dispatch(p, c, buf, h);
     double hv[2] = {0.0, 0.0};
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(hv, h, sizeof(hv), cudaMemcpyDeviceToHost, p->stream);
@@ -1203,6 +1203,22 @@ int hx_energy(hx_problem *p, const void *c, double *out)
     cudaStreamSynchronize(p->stream);
     *out = hv[0];
     return rc;
+}
+
+int hx_apply_rayleigh(hx_problem *p, const void *c, void *y, double *r)
+{
+    if (!p || !c || !y || !r) { set_error("hx_apply_rayleigh: NULL argument"); return HX_EINVAL; }
+    if (!p->have_pot) { set_error("hx_apply_rayleigh: call hx_potential_set first"); return HX_EINVAL; }
+    if (!elem_aligned(p, c) || !elem_aligned(p, y) || (uintptr_t)r % 8) {
+        set_error("hx_apply_rayleigh: vectors must be aligned to the element size and r to 8 bytes");
+        return HX_EINVAL;
+    }
+    const size_t bytes = (size_t)p->set->h.size * (p->cfg.dtype == HX_C64 ? 8 : 16);
+    if (ranges_overlap(c, bytes, y, bytes) || ranges_overlap(c, bytes, r, 16) || ranges_overlap(y, bytes, r, 16)) {
+        set_error("hx_apply_rayleigh: c, y and r must not overlap");
+        return HX_EINVAL;
+    }
+    return apply_rayleigh_dispatch(p, c, y, r);
 }
 
 int hx_norm(hx_problem *p, const void *c, double *out)

@@ -61,6 +61,9 @@ struct ApplyFuse {
     double *h;                // 2 (dk + 1) doubles: h_i (re, im)
     double *partials;         // apply_grid(p) x 2 (dk + 1) doubles
     unsigned *counter;        // zero-initialised; reset by the last block
+    // rq: instead of the projections, s[0] <c_in, y> (the input's Rayleigh quotient) into h[0..1]
+    // (partials: apply_grid(p) x 2 doubles); only when apply_fuses_dots(p)
+    bool rq;
 };
 
 
@@ -134,6 +137,7 @@ int max_degree(const Problem *p);
 
 // hx_apply_project after the argument checks (hx_krylov.cu)
 int apply_project_dispatch(Problem *p, const void *c, void *y, const void *basis, size_t ld, int k, double *h);
+int apply_rayleigh_dispatch(Problem *p, const void *c, void *y, double *r);
 
 extern thread_local bool g_batch_capture;   // hx_krylov.cu: a batch graph is being captured
 

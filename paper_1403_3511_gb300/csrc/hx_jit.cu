@@ -35,10 +35,11 @@ namespace hx {
 struct JitKernel {
     CUfunction fn = nullptr;
     CUfunction fn_dots = nullptr;   // complex64 only: the product with fused projections
+    CUfunction fn_rq = nullptr;     // complex64 only: the product with the Rayleigh quotient <c, y>
     CUfunction fn_dual = nullptr;   // two times at once
     CUfunction fn_pair = nullptr;   // two inputs at two times
     CUfunction fn_stage1 = nullptr; // the first stage of a two-stage potential (channel vectors)
-    int per_sm = 1, per_sm_dots = 1, per_sm_dual = 1, per_sm_pair = 1, per_sm_stage1 = 1;
+    int per_sm = 1, per_sm_dots = 1, per_sm_rq = 1, per_sm_dual = 1, per_sm_pair = 1, per_sm_stage1 = 1;
 };
 
 // Driver functions, looked up through the runtime (the library does not link the driver library,
@@ -319,8 +320,15 @@ static std::string jit_source(bool f32, const std::string &types, const std::str
     if (f32) {   // the same product that also computes the Lanczos projections (ApplyFuse)
         s += "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 4)\n"
              "hx_apply_specialised_dots(const __grid_constant__ hx::ApplyArgs args)\n{\n"
-             "    hx::apply_elements<hx::R, true>(args, [&](const hx::Ctx &ctx, const hx::Elem &el, hx::Acc<hx::R> &acc,\n"
-             "                                              const hx::R *sm_w, const hx::V *cin, const hx::R *tab) {\n"
+             "    hx::apply_elements<hx::R, 1>(args, [&](const hx::Ctx &ctx, const hx::Elem &el, hx::Acc<hx::R> &acc,\n"
+             "                                           const hx::R *sm_w, const hx::V *cin, const hx::R *tab) {\n"
+             "        hx::ops(args, ctx, el, acc, sm_w, cin, tab);\n"
+             "    });\n}\n";
+        // the same product with the Rayleigh quotient <c, y> of its input (the Lanczos step's sweep)
+        s += "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 4)\n"
+             "hx_apply_specialised_rq(const __grid_constant__ hx::ApplyArgs args)\n{\n"
+             "    hx::apply_elements<hx::R, 2>(args, [&](const hx::Ctx &ctx, const hx::Elem &el, hx::Acc<hx::R> &acc,\n"
+             "                                           const hx::R *sm_w, const hx::V *cin, const hx::R *tab) {\n"
              "        hx::ops(args, ctx, el, acc, sm_w, cin, tab);\n"
              "    });\n}\n";
     }
@@ -377,8 +385,11 @@ static bool compile_and_load(const std::string &src, int dev, JitKernel *out, st
         reason = "loading the compiled kernel failed";
         return false;
     }
+    CUfunction fn_rq = nullptr;
     if ((src.find("hx_apply_specialised_dots") != std::string::npos &&
          drv.moduleGetFunction(&fn_dots, mod, "hx_apply_specialised_dots") != CUDA_SUCCESS) ||
+        (src.find("hx_apply_specialised_rq") != std::string::npos &&
+         drv.moduleGetFunction(&fn_rq, mod, "hx_apply_specialised_rq") != CUDA_SUCCESS) ||
         drv.moduleGetFunction(&fn_dual, mod, "hx_apply_specialised_dual") != CUDA_SUCCESS ||
         drv.moduleGetFunction(&fn_pair, mod, "hx_apply_specialised_pair") != CUDA_SUCCESS) {
         reason = "loading the compiled kernel failed";
@@ -391,12 +402,14 @@ static bool compile_and_load(const std::string &src, int dev, JitKernel *out, st
     };
     out->fn = fn;
     out->fn_dots = fn_dots;
+    out->fn_rq = fn_rq;
     out->fn_dual = fn_dual;
     out->fn_pair = fn_pair;
     out->fn_stage1 = fn_stage1;
     out->per_sm_stage1 = occ(fn_stage1);
     out->per_sm = occ(fn);
     out->per_sm_dots = occ(fn_dots);
+    out->per_sm_rq = occ(fn_rq);
     out->per_sm_dual = occ(fn_dual);
     out->per_sm_pair = occ(fn_pair);
     return true;
@@ -461,7 +474,7 @@ int jit_launch(const Problem *p, const void *args, int blocks, cudaStream_t st)
 {
     const JitKernel *k = (const JitKernel *)p->jit;
     const ApplyArgs *a = (const ApplyArgs *)args;
-    const bool dots = a->dvec != nullptr, dual = a->cout2 != nullptr, pair = dual && a->cin2 != nullptr;
+    const bool dots = a->dvec != nullptr, rq = a->drq != 0, dual = a->cout2 != nullptr, pair = dual && a->cin2 != nullptr;
     if (a->stage1) {
         if (!k->fn_stage1) {
             set_error("internal: no compiled first-stage kernel");
@@ -478,12 +491,12 @@ int jit_launch(const Problem *p, const void *args, int blocks, cudaStream_t st)
         }
         return HX_OK;
     }
-    if ((dots && !k->fn_dots) || (dots && dual)) {
+    if ((dots && !k->fn_dots) || (rq && !k->fn_rq) || ((dots || rq) && dual) || (dots && rq)) {
         set_error("the specialised kernel has no fused projections here (complex64 single products only)");
         return HX_EUNSUPPORTED;
     }
-    CUfunction fn = pair ? k->fn_pair : dual ? k->fn_dual : dots ? k->fn_dots : k->fn;
-    const int per_sm = pair ? k->per_sm_pair : dual ? k->per_sm_dual : dots ? k->per_sm_dots : k->per_sm;
+    CUfunction fn = pair ? k->fn_pair : dual ? k->fn_dual : dots ? k->fn_dots : rq ? k->fn_rq : k->fn;
+    const int per_sm = pair ? k->per_sm_pair : dual ? k->per_sm_dual : dots ? k->per_sm_dots : rq ? k->per_sm_rq : k->per_sm;
     // apply_grid(p) blocks at most: the size of the partial-sum buffers
     int grid = std::min(p->num_sms * per_sm, apply_grid(p));
     if (grid > blocks) grid = blocks > 0 ? blocks : 1;

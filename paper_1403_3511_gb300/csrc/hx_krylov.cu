@@ -507,22 +507,55 @@ __global__ void __launch_bounds__(256, (sizeof(V) == 8 && NV <= 8) ? 3 : 1) upda
     if (reduce_partials(vals, nval, partials, &sc->counter, tot) && threadIdx.x == 0) update_scalars<pass>(sc, k, tot);
 }
 
+// out = *scale <u, z> (re, im), skipped when k >= *m_used (m_used may be null): the Rayleigh quotient
+// of a Lanczos step whose product launch does not compute it (u = V_k, z = A u_k, scale = s_k), and
+// of hx_apply_rayleigh.  paired: u and z 16-byte aligned (two elements per 16-byte load).
+template <typename V>
+__global__ void __launch_bounds__(256) rayleigh_kernel(const V *u, const V *z, int n, bool paired, const double *scale,
+                                                      const int *m_used, int k, double *out, double *partials,
+                                                      unsigned *counter)
+{
+    __shared__ double tot[2];
+    if (m_used && k >= *m_used) return;
+    typename PairAccOf<V>::T acc;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+    if (paired) {
+        for (int q = gid; q < (n >> 1); q += gstride) {
+            const Pair<V> a = load_pair(u, 2 * q), x = load_pair(z, 2 * q);
+            add_pair(acc, a.a, x.a, a.b, x.b);
+        }
+        if ((n & 1) && gid == 0) acc.add(u[n - 1], z[n - 1]);
+    } else {
+        for (int e = gid; e < n; e += gstride) acc.add(u[e], z[e]);
+    }
+    const double vals[2] = {acc.r(), acc.i()};
+    if (reduce_partials<2>(vals, 2, partials, counter, tot) && threadIdx.x == 0) {
+        out[0] = *scale * tot[0];
+        out[1] = *scale * tot[1];
+        *counter = 0;
+    }
+}
+
 // Lanczos index K < 8 in one sweep over the vectors: classical Gram-Schmidt in which the second
 // pass of each vector is done by the sweep of the next index.  On entry slot K holds V_K with
 // u_K = s_K V_K, the first-pass direction of the K-th vector (unit norm), the finished v_j = V_j
 // (j < K, s_j = 1), sc->p_j = <v_j, u_K> and sc->nu = ||u_K - sum_j p_j v_j|| from the sweep of
-// index K - 1, and slot K + 1 holds z = A u_K with q_i = sc->h_i = s_i <V_i, z> (i <= K) from the
-// product launch.  The sweep writes
+// index K - 1, and slot K + 1 holds z = A u_K with r = sc->h_0 = <u_K, z> from the product launch
+// (or rayleigh_kernel).  The sweep writes
 //   v_K = (u_K - sum_{j<K} p_j v_j) / nu                                 (second pass of v_K)
-//   w   = (z - sum_{j<K} q_j v_j) / nu - c_K v_K,  c_K = (q_K - sum_j conj(p_j) q_j) / nu^2,
+//   w   = (z - sum_{j<K} q_j v_j) / nu - c_K v_K,  c_K = (r - sum_j conj(p_j) q_j) / nu^2,
 // which is A v_K - sum_{j<=K} <v_j, A v_K> v_j (first pass of the next vector): A v_K = (z - sum_j
-// p_j A v_j) / nu and, the Krylov relation giving A v_j in span(v_0 .. v_{j+1}) with
-// <v_K, A v_{K-1}> = beta_{K-1}, the coefficients collapse to those above.  It also sums
-// d_l = <v_l, w> (l <= K) and ||w||^2.  Then h_K = <v_K, A v_K> = c_K - p_{K-1} beta_{K-1} / nu and,
-// as with two passes per vector, alpha_K = Re(h_K + d_K); the next direction is u_{K+1} = w / ||w||
-// with p'_l = d_l / ||w||, nu' = sqrt(1 - sum |p'_l|^2) and beta_K = ||w|| nu'.  In exact arithmetic
-// alpha, beta and the v's are those of two full passes per vector; each vector is read once per
-// Lanczos index instead of twice.
+// p_j A v_j) / nu, and the Krylov relation A v_j = beta_{j-1} v_{j-1} + alpha_j v_j + beta_j v_{j+1}
+// (A Hermitian) gives both <v_K, A v_{K-1}> = beta_{K-1} and q_j = <v_j, z> = <A v_j, u_K> =
+// beta_{j-1} p_{j-1} + alpha_j p_j + beta_j p_{j+1} (p_K read as nu), so the coefficients collapse
+// to those above and z's only measured projection is r.  The terms the three-term relation drops
+// are of the size of the rounding; what they leave in w, like the rounding itself, is removed by the
+// measured second pass.  The sweep also sums d_l = <v_l, w> (l <= K) and ||w||^2.  Then
+// h_K = <v_K, A v_K> = c_K - p_{K-1} beta_{K-1} / nu and, as with two passes per vector,
+// alpha_K = Re(h_K + d_K); the next direction is u_{K+1} = w / ||w|| with p'_l = d_l / ||w||,
+// nu' = sqrt(1 - sum |p'_l|^2) and beta_K = ||w|| nu'.  In exact arithmetic alpha, beta and the v's
+// are those of two full passes per vector; each basis vector is read once per Lanczos index instead
+// of three times (the projections of z and two update passes).
 template <typename V, int K>
 constexpr int sweep_k_blocks()   // resident blocks per SM that keep the kernel free of spills
 {
@@ -543,9 +576,21 @@ __global__ void __launch_bounds__(256, sweep_k_blocks<V, K>()) sweep_k_kernel(V 
     if (K >= sc->m_used) return;
     if (threadIdx.x == 0) {
         const double nu = K == 0 ? 1.0 : sc->nu, inv = 1.0 / nu;
-        double cr = sc->h[2 * K], ci = sc->h[2 * K + 1];            // q_K - sum_j conj(p_j) q_j
+        double cr = sc->h[0], ci = sc->h[1];                        // r - sum_j conj(p_j) q_j
         for (int j = 0; j < K; ++j) {
-            const double pr = sc->p[2 * j], pi = sc->p[2 * j + 1], qr = sc->h[2 * j], qi = sc->h[2 * j + 1];
+            const double pr = sc->p[2 * j], pi = sc->p[2 * j + 1];
+            // q_j = beta_{j-1} p_{j-1} + alpha_j p_j + beta_j p_{j+1}, p_K = nu
+            double qr = sc->alpha[j] * pr, qi = sc->alpha[j] * pi;
+            if (j > 0) {
+                qr += sc->beta[j - 1] * sc->p[2 * (j - 1)];
+                qi += sc->beta[j - 1] * sc->p[2 * (j - 1) + 1];
+            }
+            if (j + 1 < K) {
+                qr += sc->beta[j] * sc->p[2 * (j + 1)];
+                qi += sc->beta[j] * sc->p[2 * (j + 1) + 1];
+            } else {
+                qr += sc->beta[j] * nu;
+            }
             cf[2 * j] = pr * inv;
             cf[2 * j + 1] = pi * inv;
             cf[2 * K + 2 * j] = qr * inv;
@@ -1383,7 +1428,7 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
     V *Vb = (V *)w->V;
     const size_t ld = w->vec_bytes / sizeof(V);
     Scal *sc = w->sc;
-    const int Gd = resident_grid(p, dot_kernel<V, NV>, T);
+    const int Gd = resident_grid(p, dot_kernel<V, NV>, T), Gr = resident_grid(p, rayleigh_kernel<V>, T);
     const bool all = phase == kPhaseAll;
     // the exponential midpoint step takes the projections from the product kernel when it can
     const bool fused = all && p->cfg.scheme == HX_SCHEME_EXPMPR && NV <= kMaxFusedDots && apply_fuses_dots(p);
@@ -1407,12 +1452,9 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
             if (!apply_dual(p))   // the specialised kernel wrote the combination itself
                 magnus_combine_kernel<V><<<G, T, 0, st>>>(hv, a1v, a2v, a2a1v, a1a2v, n, g);
         } else {
-            if (fused) {     // h_i = s_i <v_i, w> from the product kernel's own stores
-                f.dvec = Vb;
-                f.dld = ld;
-                f.dk = k;
-                f.m_used = &sc->m_used;
-                f.s = sc->s;
+            if (fused) {     // r = s_k <V_k, y> from the product kernel's own values (one sweep, m <= 8)
+                f.rq = true;
+                f.s = &sc->s[k];
                 f.h = sc->h;
                 f.partials = w->partials;
                 f.counter = &sc->counter;
@@ -1421,10 +1463,13 @@ static int enqueue_step(Problem *p, Work *w, double2 *state, cudaStream_t st, do
             if (rc) return rc;
         }
         V *wv = Vb + (size_t)(k + 1) * ld;
-        if (!f.dvec) dot_kernel<V, NV><<<Gd, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
         if constexpr (NV <= 8) {   // one sweep per vector (the second pass of v_k and the first of v_{k+1})
+            if (!f.rq)
+                rayleigh_kernel<V><<<Gr, T, 0, st>>>(Vb + (size_t)k * ld, wv, n, true, &sc->s[k], &sc->m_used, k, sc->h,
+                                                     w->partials, &sc->counter);
             if ((rc = launch_sweep_k<V>(p, Vb, ld, n, k, w->partials, sc, st))) return rc;
         } else {
+            if (!f.dvec) dot_kernel<V, NV><<<Gd, T, 0, st>>>(wv, Vb, ld, n, k, w->partials, sc);
             // two passes; the second also runs after the last vector when the step estimates its
             // error (beta_m)
             const bool pass1 = k < m - 1 || p->cfg.tol > 0.0;
@@ -1533,6 +1578,40 @@ int apply_project_dispatch(Problem *p, const void *c, void *y, const void *basis
 {
     return p->cfg.dtype == HX_C64 ? apply_project<float2>(p, c, y, basis, ld, k, h)
                                   : apply_project<double2>(p, c, y, basis, ld, k, h);
+}
+
+// y = A c and r = <c, y>: one launch of the specialised complex64 kernel, else the product and
+// rayleigh_kernel.  The projection workspace supplies the unit scale, partial sums and counter.
+template <typename V>
+static int apply_rayleigh(Problem *p, const void *c, void *y, double *r)
+{
+    ProjWS *ws = proj_ws(p);
+    if (!ws) return HX_ECUDA;
+    cudaStream_t st = p->stream;
+    if (apply_fuses_dots(p)) {
+        ApplyFuse f;
+        memset(&f, 0, sizeof(f));
+        f.rq = true;
+        f.s = ws->sc.s;
+        f.h = r;
+        f.partials = ws->partials;
+        f.counter = &ws->sc.counter;
+        return launch_apply(p, c, y, p->dscal, 0.0, &f, st);
+    }
+    int rc = launch_apply(p, c, y, p->dscal, 0.0, nullptr, st);
+    if (rc) return rc;
+    const bool paired = (uintptr_t)c % 16 == 0 && (uintptr_t)y % 16 == 0;
+    const int G = resident_grid(p, rayleigh_kernel<V>, 256);
+    rayleigh_kernel<V><<<G, 256, 0, st>>>((const V *)c, (const V *)y, p->set->d.size, paired, ws->sc.s, nullptr, 0, r,
+                                          ws->partials, &ws->sc.counter);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "Rayleigh quotient kernel");
+    return HX_OK;
+}
+
+int apply_rayleigh_dispatch(Problem *p, const void *c, void *y, double *r)
+{
+    return p->cfg.dtype == HX_C64 ? apply_rayleigh<float2>(p, c, y, r) : apply_rayleigh<double2>(p, c, y, r);
 }
 
 static int enqueue(Problem *p, Work *w, double2 *state, cudaStream_t st, double dt, int phase = kPhaseAll)

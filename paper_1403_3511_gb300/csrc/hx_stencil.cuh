@@ -31,6 +31,10 @@ struct ApplyArgs : ApplyArgsBase {
     double *dh;                // h (re, im per vector)
     double *dpartials;         // gridDim.x x 2 (dk + 1)
     unsigned *dcounter;        // zero; reset by the last block
+    // drq = 1: instead, the one projection ds[0] <cin, y> of the input (the Rayleigh quotient of a
+    // Lanczos step) into dh[0..1], with dpartials (gridDim.x x 2) and dcounter (kernels compiled per
+    // potential only)
+    int drq;
     // a second product at another time, A(*t_ptr + t_shift2) cin2 into cout2, cin2 == nullptr
     // meaning cin (kernels compiled per potential only; cout2 == nullptr: none)
     void *cout2;
@@ -671,7 +675,7 @@ __device__ __forceinline__ typename Vec2<R>::T apply_element(const ApplyArgs &ar
 // adds its warp sum to one compensated FP32 sum (TwoSum), and the sums are reduced over the grid
 // at the end.  The loop then runs warp-uniformly (whole warps per trip) so that every lane takes
 // part in the exchanges.
-template <typename R, bool DOTS = false, typename Body>
+template <typename R, int DOTS = 0, typename Body>
 __device__ __forceinline__ void apply_elements(const ApplyArgs &args, Body body)
 {
     __shared__ R sm_w[kMaxOps];
@@ -684,9 +688,48 @@ __device__ __forceinline__ void apply_elements(const ApplyArgs &args, Body body)
     ctx.S = &S;
     ctx.mv = args.mv;
     const int stride = gridDim.x * blockDim.x;
-    if constexpr (!DOTS) {
+    if constexpr (DOTS == 0) {
         for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.size; e += stride)
             apply_element<R>(args, ctx, e, __ldg(S.elem + e), oscale, sm_w, body);
+    } else if constexpr (DOTS == 2) {
+        // the Rayleigh quotient ds[0] <cin, y>: each thread keeps a TwoSum-compensated FP32 sum of
+        // conj(cin_e) y_e (cin_e is in L1 from the diagonal term), warps add the pairs by shuffles,
+        // blocks by reduce_warp_sums
+        static_assert(sizeof(R) == 4, "the fused Rayleigh quotient is implemented for complex64 vectors");
+        const float2 *cin = (const float2 *)args.cin;
+        float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
+        auto add = [](float &sum, float &comp, float x) {
+            const float t = sum + x, bb = t - sum;
+            comp += (sum - (t - bb)) + (x - bb);
+            sum = t;
+        };
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.size; e += stride) {
+            const float2 y = apply_element<R>(args, ctx, e, __ldg(S.elem + e), oscale, sm_w, body);
+            const float2 x = cin[e];
+            add(rs, rc, fmaf(x.x, y.x, x.y * y.y));
+            add(is, ic, fmaf(x.x, y.y, -x.y * y.x));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ors = __shfl_xor_sync(0xffffffffu, rs, o), orc = __shfl_xor_sync(0xffffffffu, rc, o);
+            const float ois = __shfl_xor_sync(0xffffffffu, is, o), oic = __shfl_xor_sync(0xffffffffu, ic, o);
+            rc += orc;
+            add(rs, rc, ors);
+            ic += oic;
+            add(is, ic, ois);
+        }
+        __shared__ double wsum[8][2];
+        if ((threadIdx.x & 31) == 0) {
+            wsum[threadIdx.x >> 5][0] = (double)rs + (double)rc;
+            wsum[threadIdx.x >> 5][1] = (double)is + (double)ic;
+        }
+        __syncthreads();
+        __shared__ double tot[2];
+        if (reduce_warp_sums<2>(wsum, 2, args.dpartials, args.dcounter, tot) && threadIdx.x == 0) {
+            args.dh[0] = args.ds[0] * tot[0];
+            args.dh[1] = args.ds[0] * tot[1];
+            *args.dcounter = 0;
+        }
     } else {
         // the element records stream from DRAM: each trip loads the next trip's record before it
         // works on its own, so that the load's latency overlaps a whole element's stencil (measured

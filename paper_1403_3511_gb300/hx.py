@@ -97,6 +97,7 @@ def _load():
         "hx_apply_specialised": (ctypes.c_int, [P]),
         "hx_norm": (ctypes.c_int, [P, P, dp]),
         "hx_energy": (ctypes.c_int, [P, P, dp]),
+        "hx_apply_rayleigh": (ctypes.c_int, [P, P, P, P]),
         "hx_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P)]),
         "hx_batch_step": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.c_double, ctypes.c_int]),
         "hx_batch_destroy": (None, [P]),
@@ -282,6 +283,14 @@ def hx_apply_project(p, c, y, basis, k: int, h):
         raise ValueError("h must be a contiguous CUDA float64 tensor")
     _check(lib.hx_apply_project(p, ctypes.c_void_p(_vec(p, c)), ctypes.c_void_p(_vec(p, y)),
                                 ctypes.c_void_p(basis.data_ptr()), basis.stride(0), k, ctypes.c_void_p(h.data_ptr())))
+
+
+def hx_apply_rayleigh(p, c, y, r):
+    """y = A(t) c and r = <c, y> (r: CUDA float64 tensor of 2 values, re and im); see include/hx.h."""
+    if not (r.is_cuda and str(r.dtype) == "torch.float64" and r.is_contiguous() and r.numel() >= 2):
+        raise ValueError("r must be a contiguous CUDA float64 tensor of at least 2 values")
+    _check(lib.hx_apply_rayleigh(p, ctypes.c_void_p(_vec(p, c)), ctypes.c_void_p(_vec(p, y)),
+                                 ctypes.c_void_p(r.data_ptr())))
 
 
 def _host_vec(a: np.ndarray, dtypes) -> ctypes.c_void_p:

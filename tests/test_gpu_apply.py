@@ -384,3 +384,44 @@ def test_apply_project_argument_errors(hx):
         torch.cuda.synchronize()
     finally:
         P.close()
+
+
+@pytest.mark.parametrize("dtype,specialise,offset", [("c64", True, 0), ("c64", True, 1), ("c64", False, 0),
+                                                     ("c64", False, 1), ("c128", True, 0)])
+def test_apply_rayleigh_matches_oracle(hx, oracle, dtype, specialise, offset, monkeypatch):
+    """hx_apply_rayleigh: y = A c and r = <c, y> against the oracle, with the product kernel that
+    computes r itself (complex64, specialised), with the product and the reduction kernel, and on
+    vectors starting 8 bytes off a 16-byte boundary (offset 1 element, complex64)."""
+    N, B = 3, 200
+    spec = dict(N=N, B=B, L=inputs.half_width(B), potential=inputs.henon_heiles_chain(N, 0.111, (0.05, 1.0)))
+    S = oracle.IndexSet.hyperbolic(N, B)
+    c = inputs.initial_vector({"init": {"kind": "gaussian", "seed": 12}}, S.k)
+    r_, a_ = oracle.potential_terms(spec, 0.3)
+    ref = oracle.apply(S, r_, a_, spec["L"], c)
+    dt = hx.HX_C64 if dtype == "c64" else hx.HX_C128
+    if not specialise:
+        monkeypatch.setenv("HX_APPLY_SPECIALISE", "0")
+    P = make(hx, spec, dt, t=0.3)
+    try:
+        assert hx.hx_apply_specialised(P.p) == (1 if specialise else 0)
+        tdt = torch.complex64 if dt == hx.HX_C64 else torch.complex128
+        buf = torch.zeros(2 * (S.size + 2), dtype=tdt, device="cuda")
+        x = buf[offset: offset + S.size]
+        y = buf[S.size + 2 + offset: S.size + 2 + offset + S.size]
+        x.copy_(torch.from_numpy(c).to(tdt))
+        r = torch.zeros(2, dtype=torch.float64, device="cuda")
+        hx.hx_apply_rayleigh(P.p, x, y, r)
+        torch.cuda.synchronize()
+        yy = y.cpu().numpy().astype(np.complex128)
+        cc = x.cpu().numpy().astype(np.complex128)
+        want = np.vdot(cc, ref)
+        got = complex(*r.cpu().numpy())
+        scale = np.linalg.norm(cc) * np.linalg.norm(ref)
+        tol = 1e-12 if dt == hx.HX_C128 else 1e-5
+        assert np.linalg.norm(yy - ref) <= tol * np.linalg.norm(ref)
+        assert abs(got - want) <= tol * scale, (got, want)
+        assert abs(hx.hx_energy(P.p, x) - want.real) <= tol * scale
+        with pytest.raises(hx.HxError):                 # r inside y
+            hx.hx_apply_rayleigh(P.p, x, y, y.view(torch.float64)[:2])
+    finally:
+        P.close()

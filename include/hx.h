@@ -383,8 +383,10 @@ HX_API int hx_energy(hx_problem *p, const void *c, double *out);
  * compensated FP32 and the blocks' sums in FP64); otherwise the product and one reduction kernel.
  * c, y: DEVICE vectors of the problem dtype and size |K|, aligned to the element size, not
  * overlapping; r: DEVICE pointer to 2 doubles, 8-byte aligned, overlapping neither.  Asynchronous on
- * the problem stream.  Errors: HX_EINVAL (NULL or misaligned pointers, overlap, no potential),
- * HX_ECUDA.  Two calls on one problem must not run concurrently (they share a workspace). */
+ * the problem stream; the first call of this or hx_apply_project on a problem allocates a small
+ * workspace and synchronises.  Errors: HX_EINVAL (NULL or misaligned pointers, overlap, no
+ * potential), HX_ECUDA.  Calls of this and hx_apply_project on one problem must not run
+ * concurrently on different streams (they share that workspace; the problem stream orders them). */
 HX_API int hx_apply_rayleigh(hx_problem *p, const void *c, void *y, double *r);
 
 /* ---- allocation-free norm ------------------------------------------------------- */

@@ -78,6 +78,10 @@ def test_argument_errors_without_device(libhx):
     assert "NULL problem" in hx.hx_last_error()
     assert hx.lib.hx_apply_project(None, None, None, None, 0, 0, None) == hx.HX_EINVAL
     assert "NULL argument" in hx.hx_last_error()
+    assert hx.lib.hx_apply_rayleigh(None, None, None, None) == hx.HX_EINVAL
+    assert "NULL argument" in hx.hx_last_error()
+    assert hx.lib.hx_batch_set_budget(None, 1.0) == hx.HX_EINVAL
+    assert hx.lib.hx_batch_info(None, None) == hx.HX_EINVAL
     # host vectors the library would read or write past their end are refused by the binding
     with pytest.raises(ValueError):
         hx.hx_step_host(None, np.zeros(4, np.complex64), 0.01, 1)       # the state is complex128

@@ -479,8 +479,11 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
     a.t_shift2 = t_shift2;
     a.mag_g = mag_g;
     const int blocks = (p->set->d.size + kApplyThreads - 1) / kApplyThreads;
-    if (p->jit && !g_batch_capture && (!stage1 || jit_has_stage1(p)))
-        return jit_launch(p, &a, blocks, st);   // the potential's specialised kernel
+    if (p->jit && !g_batch_capture && (!stage1 || jit_has_stage1(p))) {   // the potential's specialised kernel
+        a.tops = p->tops;
+        a.tops_words = p->tops ? jit_tops_words(p) : 0;
+        return jit_launch(p, &a, blocks, st);
+    }
     if (cout2) {
         set_error("internal: a two-time product needs the specialised kernel");
         return HX_EUNSUPPORTED;

@@ -843,6 +843,7 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
         }
     }
     jit_prepare(pr);
+    if (int rc = jit_fill_tops(pr)) return rc;
     pr->have_pot = true;
     pr->generation++;
     return HX_OK;
@@ -1078,6 +1079,7 @@ void hx_problem_destroy(hx_problem *p)
     cudaFree(p->pw_values);
     cudaFree(p->gnb);
     cudaFree(p->gnbn);
+    cudaFree(p->tops);
     cudaFree(p->chan);
     cudaFree(p->dscal);
     for (void *x : p->extra) cudaFree(x);

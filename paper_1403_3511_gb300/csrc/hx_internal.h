@@ -87,6 +87,11 @@ struct Problem {
     RowOffsets roff;          // row offsets of ops and ops1 (and their outer moves)
     int *gnb;                 // group-neighbour table (device), ngroup x gstride
     int *gnbn;                // general sets: rows of each neighbour group (0: none), same layout
+    // the specialised kernel's fibre-top fields per element (jit_fill_tops), and the kernel they were
+    // packed for
+    unsigned *tops;
+    size_t tops_bytes;
+    const void *tops_src;
     int gstride;
     double scale;             // basis scaling S (phi_k(S x)); D_K is multiplied by S^2
     bool skip_diag;           // internal: omit D_K (gradient direction operators)
@@ -145,6 +150,8 @@ extern thread_local bool g_batch_capture;   // hx_krylov.cu: a batch graph is be
 void jit_prepare(Problem *p);
 int jit_launch(const Problem *p, const void *args, int blocks, cudaStream_t st);
 bool jit_has_stage1(const Problem *p);   // the compiled kernels include the first (channel) stage
+int jit_tops_words(const Problem *p);   // 32-bit words of fibre-top fields the compiled kernels read
+int jit_fill_tops(Problem *p);          // after jit_prepare: packs those fields for the problem's set
 
 // Lanczos workspaces outside the step graph (hx_krylov.cu), used by the adjoint gradient
 struct LanczosWS {

@@ -39,6 +39,8 @@ struct JitKernel {
     CUfunction fn_dual = nullptr;   // two times at once
     CUfunction fn_pair = nullptr;   // two inputs at two times
     CUfunction fn_stage1 = nullptr; // the first stage of a two-stage potential (channel vectors)
+    CUfunction fn_tops = nullptr;   // packs each element's fibre-top fields (tops_words > 0)
+    int tops_words = 0;
     int per_sm = 1, per_sm_dots = 1, per_sm_rq = 1, per_sm_dual = 1, per_sm_pair = 1, per_sm_stage1 = 1;
 };
 
@@ -99,9 +101,65 @@ static std::string merged_weight(const OpSet &O, const Op &op, const char *w)
     return std::string(w) + "[" + std::to_string(op.mergeB) + "]";
 }
 
+// Fields of the precomputed fibre-top distances (the element's top words): per plane operator
+// topA at v = 0 and at the footprint's steps v along b (width for 0..P), topB at the footprint's
+// steps s along a (width for 0..TB at s = 0, 0..Q elsewhere); per line operator along a prefix axis
+// its top (0..P).  No field straddles a 32-bit word.  on = false when they need more than
+// kTopWords words (the kernels then compute the tops themselves).
+struct TopLayout {
+    bool on = false;
+    int words = 0;
+    std::map<int, std::map<int, int>> offA, offB;   // op -> step -> bit offset
+    std::map<int, int> offT, wA;
+    std::map<int, std::map<int, int>> wB;
+};
+
+static int field_bits(int maxval)
+{
+    int b = 1;
+    while ((1 << b) <= maxval) ++b;
+    return b;
+}
+
+static TopLayout top_layout(const OpSet &O)
+{
+    TopLayout L;
+    int cur = 0;
+    auto place = [&](int w) {
+        if ((cur & 31) + w > 32) cur = (cur + 31) & ~31;
+        const int off = cur;
+        cur += w;
+        return off;
+    };
+    for (int i = 0; i < O.nops; ++i) {
+        const Op &op = O.op[i];
+        if (op.merged) continue;
+        if (op.kind == 2) {
+            const int P = op.p, Q = op.q, SB = op.mergeB >= 0 ? O.op[op.mergeB].p : 0, TB = SB > Q ? SB : Q;
+            L.wA[i] = field_bits(P);
+            L.offA[i][0] = place(L.wA[i]);
+            for (int j = 0; j <= Q; ++j)
+                if (-Q + 2 * j != 0) L.offA[i][-Q + 2 * j] = place(L.wA[i]);
+            for (int k = 0; k <= P; ++k) {
+                const int st = -P + 2 * k, w = field_bits(st == 0 ? TB : Q);
+                L.wB[i][st] = w;
+                L.offB[i][st] = place(w);
+            }
+        } else if (op.kind == 1 && op.ra == ROLE_ROW) {
+            L.wA[i] = field_bits(op.p);
+            L.offT[i] = place(L.wA[i]);
+        }
+    }
+    L.words = (cur + 31) / 32;
+    L.on = L.words > 0 && L.words <= kTopWords;
+    return L;
+}
+
 // Compile-time row moves of operator i's footprint points (a type with the start / startx
-// functions of ColsRuntime): move (om, s4) of the column that didx gives each position.
-static std::string cols_type(const OpSet &O, const RowOffsets &ro, int i, const char *prefix)
+// functions of ColsRuntime): move (om, s4) of the column that didx gives each position; with a top
+// layout also the offsets of its fibre-top fields and their readers.
+static std::string cols_type(const OpSet &O, const RowOffsets &ro, int i, const char *prefix,
+                             const TopLayout *L = nullptr)
 {
     const Op &op = O.op[i];
     const int span = (2 * op.p + 1) * (2 * op.q + 1);
@@ -127,16 +185,60 @@ static std::string cols_type(const OpSet &O, const RowOffsets &ro, int i, const 
     t += "    __device__ static __forceinline__ int start(const Ctx &c, const Elem &el, const OpSet &, const Op &, int pos, bool ok)\n"
          "    { return c.start_mv(el, om(pos), s4(pos), ok); }\n"
          "    __device__ static __forceinline__ int startx(const Ctx &c, const Elem &el, const OpSet &, const Op &, int j, int, bool ok)\n"
-         "    { return c.start_mv(el, omx(j), s4x(j), ok); }\n};\n";
+         "    { return c.start_mv(el, omx(j), s4x(j), ok); }\n";
+    const bool bits = L && L->on && (L->offA.count(i) || L->offT.count(i));
+    t += std::string("    static constexpr bool kTopsBits = ") + (bits ? "true" : "false") + ";\n";
+    if (bits) {
+        auto steps = [](const std::map<int, int> &m, const char *name) {
+            std::string f = "    __device__ static constexpr int " + std::string(name) + "(int v) { return ";
+            for (const auto &kv : m) f += "v == " + std::to_string(kv.first) + " ? " + std::to_string(kv.second) + " : ";
+            f += "0; }\n";
+            return f;
+        };
+        if (L->offA.count(i)) {
+            t += steps(L->offA.at(i), "offA");
+            t += steps(L->offB.at(i), "offB");
+            t += steps(L->wB.at(i), "wB");
+            t += "    static constexpr int wA = " + std::to_string(L->wA.at(i)) + ";\n";
+            t += "    __device__ static __forceinline__ int topA(const Elem &el, int v) { return top_field(el, offA(v), wA); }\n"
+                 "    __device__ static __forceinline__ int topB(const Elem &el, int s) { return top_field(el, offB(s), wB(s)); }\n";
+        } else {
+            t += "    static constexpr int offT = " + std::to_string(L->offT.at(i)) + ", wT = " + std::to_string(L->wA.at(i)) + ";\n";
+            t += "    __device__ static __forceinline__ int lineTop(const Elem &el) { return top_field(el, offT, wT); }\n";
+        }
+    }
+    t += "};\n";
     return t;
 }
 
-static std::string jit_types(const OpSet &O, const RowOffsets &ro, const char *prefix = "ColsK")
+static std::string jit_types(const OpSet &O, const RowOffsets &ro, const char *prefix = "ColsK",
+                             const TopLayout *L = nullptr)
 {
     std::string t;
     for (int i = 0; i < O.nops; ++i)
-        if (O.op[i].kind >= 1 && !O.op[i].merged) t += cols_type(O, ro, i, prefix);
+        if (O.op[i].kind >= 1 && !O.op[i].merged) t += cols_type(O, ro, i, prefix, L);
     return t;
+}
+
+// The packing of the top fields, one call per operator with fields (the top-word kernel's body).
+static std::string jit_body_tops(const OpSet &O, const TopLayout &L)
+{
+    std::string b;
+    char line[512];
+    for (int i = 0; i < O.nops; ++i) {
+        const Op &op = O.op[i];
+        if (op.merged) continue;
+        if (L.offA.count(i)) {
+            const int sb = op.mergeB >= 0 ? O.op[op.mergeB].p : 0;
+            snprintf(line, sizeof(line), "        plane_tops<%d, %d, %s, %d, ColsK%d>(ctx, el, O.op[%d], tw);\n", op.p,
+                     op.q, role_name(op.rb), sb, i, i);
+            b += line;
+        } else if (L.offT.count(i)) {
+            snprintf(line, sizeof(line), "        line_tops<%d, ColsK%d>(ctx, el, O.op[%d], tw);\n", op.p, i, i);
+            b += line;
+        }
+    }
+    return b;
 }
 
 static bool specialised_line(const Op &op) { return op.cls >= CLS_LINE + 1 && op.cls <= CLS_LINE + kMaxDeg; }
@@ -248,7 +350,8 @@ static std::string jit_body_pair(const OpSet &O)
 }
 
 static std::string jit_source(bool f32, const std::string &types, const std::string &body, const std::string &body2,
-                              const std::string &body3, const std::string &body_s1 = "")
+                              const std::string &body3, const std::string &body_s1 = "",
+                              const std::string &body_tops = "", int tops_words = 0)
 {
     std::string s;
     s += "#include \"hx_stencil.cuh\"\n";
@@ -317,6 +420,21 @@ static std::string jit_source(bool f32, const std::string &types, const std::str
          "                                             const hx::V *cin, const hx::V *cin2, const hx::R *tab) {\n"
          "        hx::ops_pair(args, ctx, el, acc, acc2, sm_w, sm_w2, cin, cin2, tab);\n"
          "    });\n}\n";
+    if (!body_tops.empty()) {   // each element's fibre-top fields, packed once per potential and index set
+        s += "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads)\n"
+             "hx_apply_tops(const __grid_constant__ hx::ApplyArgs args)\n{\n"
+             "    using namespace hx;\n"
+             "    Ctx ctx;\n"
+             "    ctx.S = &args.S;\n"
+             "    ctx.mv = args.mv;\n"
+             "    const OpSet &O = args.ops;\n"
+             "    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < args.S.size; e += gridDim.x * blockDim.x) {\n"
+             "        const Elem el = make_elem(args, e, __ldg(args.S.elem + e));\n"
+             "        unsigned tw[kTopWords] = {};\n";
+        s += body_tops;
+        s += "        for (int w = 0; w < " + std::to_string(tops_words) + "; ++w) args.tops_out[(size_t)w * args.S.size + e] = tw[w];\n"
+             "    }\n}\n";
+    }
     if (f32) {   // the same product that also computes the Lanczos projections (ApplyFuse)
         s += "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 4)\n"
              "hx_apply_specialised_dots(const __grid_constant__ hx::ApplyArgs args)\n{\n"
@@ -379,7 +497,12 @@ static bool compile_and_load(const std::string &src, int dev, JitKernel *out, st
         reason = "loading the compiled kernel failed";
         return false;
     }
-    CUfunction fn_dots = nullptr, fn_dual = nullptr, fn_pair = nullptr, fn_stage1 = nullptr;
+    CUfunction fn_dots = nullptr, fn_dual = nullptr, fn_pair = nullptr, fn_stage1 = nullptr, fn_tops = nullptr;
+    if (src.find("hx_apply_tops") != std::string::npos &&
+        drv.moduleGetFunction(&fn_tops, mod, "hx_apply_tops") != CUDA_SUCCESS) {
+        reason = "loading the compiled kernel failed";
+        return false;
+    }
     if (src.find("hx_apply_specialised_stage1") != std::string::npos &&
         drv.moduleGetFunction(&fn_stage1, mod, "hx_apply_specialised_stage1") != CUDA_SUCCESS) {
         reason = "loading the compiled kernel failed";
@@ -406,6 +529,7 @@ static bool compile_and_load(const std::string &src, int dev, JitKernel *out, st
     out->fn_dual = fn_dual;
     out->fn_pair = fn_pair;
     out->fn_stage1 = fn_stage1;
+    out->fn_tops = fn_tops;
     out->per_sm_stage1 = occ(fn_stage1);
     out->per_sm = occ(fn);
     out->per_sm_dots = occ(fn_dots);
@@ -444,7 +568,11 @@ void jit_prepare(Problem *p)
         }
     }
     const bool f32 = p->cfg.dtype == HX_C64;
-    const std::string types = jit_types(p->ops, p->roff) + jit_types(p->ops1, p->roff, "ColsS");
+    const TopLayout L = top_layout(p->ops);
+    const std::string body_tops = L.on ? jit_body_tops(p->ops, L) : "";
+    const int tops_words = body_tops.empty() ? 0 : L.words;
+    const std::string types = jit_types(p->ops, p->roff, "ColsK", body_tops.empty() ? nullptr : &L) +
+                              jit_types(p->ops1, p->roff, "ColsS");
     const std::string key = std::to_string(p->device) + (f32 ? "|f|" : "|d|") + types + body + body_s1;
     // the two-time kernels run only for single-stage potentials (apply_dual)
     const std::string body_dual = p->ops1.nops ? "" : jit_body(p->ops, true);
@@ -456,13 +584,15 @@ void jit_prepare(Problem *p)
         // HX_JIT_SOURCE_DUMP=<file>: the generated source is written there before it is compiled
         if (const char *dump = getenv("HX_JIT_SOURCE_DUMP")) {
             if (FILE *f = fopen(dump, "w")) {
-                const std::string src = jit_source(f32, types, body, body_dual, body_pair, body_s1);
+                const std::string src = jit_source(f32, types, body, body_dual, body_pair, body_s1, body_tops, tops_words);
                 fwrite(src.data(), 1, src.size(), f);
                 fclose(f);
             }
         }
-        if (!compile_and_load(jit_source(f32, types, body, body_dual, body_pair, body_s1), p->device, &k, reason))
+        if (!compile_and_load(jit_source(f32, types, body, body_dual, body_pair, body_s1, body_tops, tops_words), p->device,
+                              &k, reason))
             return;
+        k.tops_words = k.fn_tops ? tops_words : 0;
         it = g_jit_cache.emplace(key, k).first;
     }
     p->jit = &it->second;
@@ -516,4 +646,46 @@ int jit_launch(const Problem *p, const void *args, int blocks, cudaStream_t st)
 
 namespace hx {
 bool jit_has_stage1(const Problem *p) { return p->jit && ((const JitKernel *)p->jit)->fn_stage1 != nullptr; }
+
+int jit_tops_words(const Problem *p) { return p->jit ? ((const JitKernel *)p->jit)->tops_words : 0; }
+
+// Packs the fibre-top fields of every element for the specialised kernel (once per kernel and index
+// set: kept while both stay the same).
+int jit_fill_tops(Problem *p)
+{
+    const JitKernel *k = (const JitKernel *)p->jit;
+    if (!k || k->tops_words == 0) return HX_OK;
+    const size_t n = (size_t)p->set->d.size, bytes = n * k->tops_words * sizeof(unsigned);
+    if (p->tops && p->tops_src == (const void *)k && p->tops_bytes == bytes) return HX_OK;
+    if (p->tops_bytes != bytes) {
+        cudaFree(p->tops);
+        p->tops = nullptr;
+        p->tops_bytes = 0;
+        cudaError_t e = cudaMalloc((void **)&p->tops, std::max<size_t>(bytes, 4));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(fibre-top fields)");
+        p->tops_bytes = bytes;
+    }
+    p->tops_src = nullptr;
+    ApplyArgs a;
+    memset(&a, 0, sizeof(a));
+    a.S = p->set->d;
+    memcpy(a.mv, p->roff.mv, sizeof(a.mv));
+    a.ops = p->ops;
+    a.tops_out = p->tops;
+    const int blocks = (int)std::min<size_t>((n + kApplyThreads - 1) / kApplyThreads, (size_t)p->num_sms * 8);
+    void *params[] = {&a};
+    const Driver &drv = driver();
+    CUresult r = drv.launchKernel(k->fn_tops, std::max(blocks, 1), 1, 1, kApplyThreads, 1, 1, 0, (CUstream)p->stream, params,
+                                  nullptr);
+    if (r != CUDA_SUCCESS) {
+        const char *msg = nullptr;
+        drv.errorString(r, &msg);
+        set_error("fibre-top kernel launch: %s", msg ? msg : "unknown error");
+        return HX_ECUDA;
+    }
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fibre-top kernel");
+    p->tops_src = k;
+    return HX_OK;
+}
 }  // namespace hx

@@ -226,7 +226,16 @@ struct Elem {
     // general sets only: rows of the own group, and the row counts of the neighbour groups
     int grows;
     const int *gnn;
+    unsigned tw[kTopWords];       // precomputed fibre-top distances (kernels compiled per potential)
 };
+
+// Field of width w at bit off of an element's top words (off and w compile-time after unrolling),
+// and the packing counterpart.
+__device__ __forceinline__ int top_field(const Elem &el, int off, int w)
+{
+    return (int)((el.tw[off >> 5] >> (off & 31)) & ((1u << w) - 1u));
+}
+__device__ __forceinline__ void put_top_field(unsigned *tw, int off, int x) { tw[off >> 5] |= (unsigned)x << (off & 31); }
 
 struct Ctx {
     const DevSet *S;
@@ -278,6 +287,7 @@ struct Ctx {
 // functions whose moves are compile-time constants.  pos: footprint position of the point
 // ((s + p) (2 q + 1) + (s2 + q)); startx: the merged line op's points s2 = -SB, SB.
 struct ColsRuntime {
+    static constexpr bool kTopsBits = false;     // fibre tops computed in the kernel
     __device__ static __forceinline__ int start(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, int pos,
                                                 bool ok)
     {
@@ -346,6 +356,50 @@ __device__ __forceinline__ Row4<double> load_row4(const double *p)
 // of (1 + k_l), the point k + u e_a + v e_b lies in K iff its coordinates are >= 0 and
 // r (1 + k_a + u)(1 + k_b + v) <= B (no overflow: the product is at most 16 B for |u|, |v| <= 3).
 
+// Steps from k to the top of its fibre along a prefix axis with coordinate ka, capped at P.
+template <int P>
+__device__ __forceinline__ int line_top(const Ctx &c, const Elem &el, int ka)
+{
+    const int other = exact_div(el.qall, 1 + ka), slack = c.S->B - el.qall;
+    int top = 0;
+#pragma unroll
+    for (int t = 1; t <= P; ++t) top += other * t <= slack ? 1 : 0;
+    return top;
+}
+
+// Membership and fibre-top distances around k for a plane operator on axes a, b: with
+// r = prod over the other axes of (1 + k_l), k + u e_a + v e_b lies in K iff its coordinates are >= 0
+// and r (1 + k_a + u)(1 + k_b + v) <= B (u, v compile-time after unrolling; a point with no positive
+// step is in K once its coordinates are, K being downward closed).  topA(v): steps to the a-fibre
+// top at k + v e_b, capped at P; topB(u, cap): steps to the b-fibre top at k + u e_a, capped at
+// min(cap, TB) (0 when that point is not in K: no step from it stays in K).
+template <int P, int TB>
+struct PlaneTops {
+    int ka, kb, rab, B;
+    __device__ __forceinline__ bool in_k(int u, int v) const
+    {
+        bool r = true;
+        if (u < 0) r = r && ka + u >= 0;
+        if (v < 0) r = r && kb + v >= 0;
+        if (u > 0 || v > 0) r = r && rab * (1 + ka + u) * (1 + kb + v) <= B;
+        return r;
+    }
+    __device__ __forceinline__ int topA(int v) const
+    {
+        int d = 0;
+#pragma unroll
+        for (int t = 1; t <= P; ++t) d += in_k(t, v) ? 1 : 0;
+        return d;
+    }
+    __device__ __forceinline__ int topB(int u, int cap) const
+    {
+        int d = 0;
+#pragma unroll
+        for (int t = 1; t <= TB; ++t) d += (t <= cap && in_k(u, t)) ? 1 : 0;
+        return d;
+    }
+};
+
 // Line operator P(X_a), P of pure parity and degree P (offsets -P, -P+2, ..., P), axis role RA,
 // applied to NSRC inputs at once (the addresses and weights are shared): out[q] = P(X_a) srcs[q]
 // at the element.
@@ -360,11 +414,10 @@ __device__ __forceinline__ void line_role_n(const Ctx &c, const Elem &el, const 
     int top;
     if (RA == ROLE_LAST) {
         top = min(P, el.rlen - 1 - el.j);
+    } else if constexpr (CM::kTopsBits) {
+        top = CM::lineTop(el);
     } else {
-        const int other = exact_div(el.qall, 1 + ka), slack = c.S->B - el.qall;
-        top = 0;
-#pragma unroll
-        for (int t = 1; t <= P; ++t) top += other * t <= slack ? 1 : 0;
+        top = line_top<P>(c, el, ka);
     }
     constexpr int W = packed_width(P);
     const RowW<R, W> row = load_roww<W>(tab + op.ptabP + (ka * (P + 1) + top) * W);   // entries at s = -P + 2j
@@ -420,34 +473,46 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
     const int B = c.S->B;
     const int ka = c.k(el, op.a);
     const int kb = RB == ROLE_LAST ? el.j : c.k(el, op.b);
-    const int rab = exact_div(el.qall, (1 + ka) * (1 + kb));
     const R *tP = tab + op.ptabP, *tQ = tab + op.ptabQ;   // packed rows: entry i at offset -P + 2i
     constexpr int NS = P + 1, NS2 = Q + 1;         // offsets s = -P + 2i, s2 = -Q + 2j
     constexpr int TB = SB > Q ? SB : Q;            // b-distances needed at k
-    // k + u e_a + v e_b in K (u, v compile-time after unrolling: a point with no positive step
-    // lies in K iff its coordinates are >= 0, K being downward closed)
-    auto in_k = [&](int u, int v) {
-        bool r = true;
-        if (u < 0) r = r && ka + u >= 0;
-        if (v < 0) r = r && kb + v >= 0;
-        if (u > 0 || v > 0) r = r && rab * (1 + ka + u) * (1 + kb + v) <= B;
-        return r;
-    };
-    // the row of k + s e_a exists (RB = LAST: its prefix is in K)
-    auto row_in_k = [&](int s) { return s < 0 ? ka + s >= 0 : (s == 0 || rab * (1 + ka + s) <= B); };
-    // distances to the a-fibre top at k + s2 e_b and to the b-fibre top at k + s e_a (0 when that
-    // point is not in K: no step from it stays in K)
+    // membership and fibre-top distances: computed here (PlaneTops), or read from the element's
+    // top words, which plane_tops filled with the same PlaneTops (kernels compiled per potential)
+    const PlaneTops<P, TB> G{ka, kb, CM::kTopsBits ? 0 : exact_div(el.qall, (1 + ka) * (1 + kb)), B};
     auto topA = [&](int s2) {
-        int d = 0;
-#pragma unroll
-        for (int t = 1; t <= P; ++t) d += in_k(t, s2) ? 1 : 0;
-        return d;
+        if constexpr (CM::kTopsBits) return CM::topA(el, s2);
+        else return G.topA(s2);
     };
     auto topB = [&](int s, int cap) {
-        int d = 0;
+        if constexpr (CM::kTopsBits) return CM::topB(el, s);   // stored with cap TB at s = 0, Q elsewhere
+        else return G.topB(s, cap);
+    };
+    // k + u e_a + v e_b in K (with the top words: a point with a positive step along a is in K iff
+    // that many steps stay below the a-fibre top at k + v e_b, one with only a positive step along b
+    // iff they stay below the b-fibre top at k + u e_a)
+    auto in_k = [&](int u, int v) {
+        if constexpr (!CM::kTopsBits) {
+            return G.in_k(u, v);
+        } else {
+            bool r = true;
+            if (u < 0) r = r && ka + u >= 0;
+            if (v < 0) r = r && kb + v >= 0;
+            if (u > 0) r = r && topA(v) >= u;
+            else if (v > 0) r = r && topB(u, v) >= v;
+            return r;
+        }
+    };
+    // RB = LAST: the row of k + s e_a exists (with the top words: it holds a footprint point in K,
+    // which is all the addresses need)
+    auto row_in_k = [&](int s) {
+        if constexpr (!CM::kTopsBits) {
+            return s < 0 ? ka + s >= 0 : (s == 0 || G.rab * (1 + ka + s) <= B);
+        } else {
+            bool r = s == 0;
 #pragma unroll
-        for (int t = 1; t <= TB; ++t) d += (t <= cap && in_k(s, t)) ? 1 : 0;
-        return d;
+            for (int j = 0; j < NS2; ++j) r = r || in_k(s, -Q + 2 * j);
+            return r;
+        }
     };
     // addresses of the footprint points (own element when the point is not in K)
     int addr[NS][NS2];
@@ -558,6 +623,34 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
     }
 }
 
+// The fibre-top distances plane_role_n reads from the top words (CM::kTopsBits), computed and
+// packed at the offsets of CM: topA at v = 0 and at the footprint's steps along b, topB at the
+// footprint's steps along a (cap TB at 0, Q elsewhere).
+template <int P, int Q, int RB, int SB, typename CM>
+__device__ __forceinline__ void plane_tops(const Ctx &c, const Elem &el, const Op &op, unsigned *tw)
+{
+    constexpr int TB = SB > Q ? SB : Q;
+    const int ka = c.k(el, op.a);
+    const int kb = RB == ROLE_LAST ? el.j : c.k(el, op.b);
+    const PlaneTops<P, TB> G{ka, kb, exact_div(el.qall, (1 + ka) * (1 + kb)), c.S->B};
+    put_top_field(tw, CM::offA(0), G.topA(0));
+#pragma unroll
+    for (int j = 0; j <= Q; ++j)
+        if (-Q + 2 * j != 0) put_top_field(tw, CM::offA(-Q + 2 * j), G.topA(-Q + 2 * j));
+#pragma unroll
+    for (int i = 0; i <= P; ++i) {
+        const int s = -P + 2 * i;
+        put_top_field(tw, CM::offB(s), G.topB(s, s == 0 ? TB : Q));
+    }
+}
+
+// The same for a line operator along a prefix axis (line_role_n with the top words).
+template <int P, typename CM>
+__device__ __forceinline__ void line_tops(const Ctx &c, const Elem &el, const Op &op, unsigned *tw)
+{
+    put_top_field(tw, CM::offT, line_top<P>(c, el, c.k(el, op.a)));
+}
+
 template <typename R, int P, int Q, int RB, int SB, int ORD = 0, typename CM = ColsRuntime>
 __device__ __forceinline__ void plane_role(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const R *tab,
                                            const typename Vec2<R>::T *src, typename Vec2<R>::T &out,
@@ -635,6 +728,9 @@ __device__ __forceinline__ Elem make_elem(const ApplyArgs &args, int e, int4 er)
     el.kr = args.S.row_k + (size_t)er.x * (N - 1);
     el.k4 = N >= 2 ? (int)__ldg(el.kr + N - 2) : 0;
     el.gn = args.gnb + (size_t)er.y * args.gstride;
+#pragma unroll
+    for (int w = 0; w < kTopWords; ++w)
+        el.tw[w] = w < args.tops_words ? __ldg(args.tops + (size_t)w * args.S.size + e) : 0u;
     el.grows = 0;
     el.gnn = nullptr;
     if (args.S.general) {

@@ -14,6 +14,7 @@ constexpr int kSpan = 2 * kMaxDeg + 1;         // offsets -deg..deg
 constexpr int kMaxKrylov = 32;
 constexpr int kApplyThreads = 256;
 constexpr int kNtSpan = 16;          // the floor(B / x) table covers x <= kNtSpan B (products of shifted points)
+constexpr int kTopWords = 4;        // 32-bit words of precomputed fibre tops per element (at most)
 constexpr int kMaxFusedDots = 8;     // projections one product launch can compute (Krylov steps m <= 8)
 
 // time modulations (values of hx_mod_kind)
@@ -141,6 +142,12 @@ struct ApplyArgsBase {
     const double *pw_values;  // device
     const void *tab;          // row tables (float or double)
     RowMove mv[kMaxDelta];    // per row-offset column: outer move and step on axis N-2
+    // kernels compiled per potential: each element's fibre-top distances packed in tops_words
+    // 32-bit words, word w of element e at tops[w * S.size + e] (tops_words = 0: none); tops_out:
+    // where the kernel that packs them writes
+    const unsigned *tops;
+    int tops_words;
+    unsigned *tops_out;
 };
 
 }  // namespace hx

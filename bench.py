@@ -215,6 +215,16 @@ def whole_job_gcoeff_s(m: int, n: int, world: int, seconds: float) -> float:
     return m * n * world / seconds / 1e9
 
 
+def step_bytes_per_coef(m: int, vec_bytes: int) -> int:
+    """Algorithmic bytes per coefficient of one exponential-midpoint step with one Gram-Schmidt
+    sweep per Lanczos vector (m <= 8): the start vector (read the complex128 state, write v_0), per
+    Lanczos index k the product (read v_k, write z) and the sweep (read u_k, z, v_0 .. v_{k-1}, write
+    v_k and w), and the recombination (read v_0 .. v_{m-1}, write the state)."""
+    state = 16
+    per_k = sum(2 * vec_bytes + vec_bytes * (k + 4) for k in range(m))
+    return state + vec_bytes + per_k + m * vec_bytes + state
+
+
 def run_reference(args, rank):
     """The oracle (plain single-threaded C, FP64) on the same workload: each step is one full
     Galerkin matvec y = A(t)c over all |K| coefficients (about 2-3 s at N=6, B=4096, so that the
@@ -558,6 +568,11 @@ def main():
                 "gpu_launches": launches_per_step * args.steps,
                 "matvec_gcoeff_s": n / (ms_apply * 1e-3) / 1e9,
                 "roofline": roof, "e2e": e2e, "clocks": clk, **extra}
+        if m <= 8:   # the whole step against the same HBM roof (every kernel's algorithmic bytes)
+            sb = step_bytes_per_coef(m, 8 if dtype == hx.HX_C64 else 16) * n
+            line["step_roofline"] = {"bound": "hbm", "bytes_per_step": sb, "achieved": sb / (ms_step * 1e-3) / 1e9,
+                                     "peak": peak, "unit": "GB/s", "frac": sb / (ms_step * 1e-3) / 1e9 / peak,
+                                     "note": "algorithmic bytes of every kernel of one step"}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(spec)
         print(json.dumps(line), flush=True)

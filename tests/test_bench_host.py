@@ -127,3 +127,11 @@ def test_issue_roofline_and_profiled_values(tmp_path, monkeypatch):
     assert abs(r["achieved"] - 6.08e11) < 1.0 and abs(r["frac"] - 6.08e11 / r["peak"]) < 1e-12
     (src / "hx_jit.cu").write_text("changed\n")
     assert bench.profiled_value("w", "c64", "apply_kernel", "warp_instructions_per_launch") is None
+
+
+def test_step_bytes_per_coefficient():
+    """Algorithmic bytes of one complex64 step at m = 7: start 24, products 7 x 16, sweeps
+    8 (4 + 5 + ... + 10) = 392, recombination 7 x 8 + 16 = 72: 600 B per coefficient."""
+    import bench
+    assert bench.step_bytes_per_coef(7, 8) == 24 + 7 * 16 + 8 * sum(range(4, 11)) + 7 * 8 + 16 == 600
+    assert bench.step_bytes_per_coef(1, 8) == 24 + 16 + 8 * 4 + 8 + 16

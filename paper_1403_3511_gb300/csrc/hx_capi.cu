@@ -798,10 +798,11 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
         if (pr->gnb) cudaFree(pr->gnb);
         if (pr->gnbn) cudaFree(pr->gnbn);
         pr->gnb = pr->gnbn = nullptr;
-        pr->gstride = std::max(cp.roff.nom, 1);
+        pr->gstride = (std::max(cp.roff.nom, 1) + 3) & ~3;   // 16-byte rows (the compiled kernels read them so)
         size_t bytes = (size_t)pr->gstride * std::max(h.ngroup, 1) * sizeof(int);
         HX_CUDA(cudaMalloc((void **)&pr->gnb, bytes), "cudaMalloc(group-neighbour table)");
         if (!h.general) {
+            HX_CUDA(cudaMemsetAsync(pr->gnb, 0xff, bytes, pr->stream), "clear group-neighbour table");
             int rc = launch_groupnb(set->d, pr->roff, pr->gstride, pr->gnb, pr->stream);
             if (rc) return rc;
             HX_CUDA(cudaStreamSynchronize(pr->stream), "group-neighbour table");

@@ -182,10 +182,49 @@ static std::string cols_type(const OpSet &O, const RowOffsets &ro, int i, const 
         t += "    __device__ static constexpr int omx(int) { return -1; }\n";
         t += "    __device__ static constexpr int s4x(int) { return 0; }\n";
     }
-    t += "    __device__ static __forceinline__ int start(const Ctx &c, const Elem &el, const OpSet &, const Op &, int pos, bool ok)\n"
-         "    { return c.start_mv(el, om(pos), s4(pos), ok); }\n"
-         "    __device__ static __forceinline__ int startx(const Ctx &c, const Elem &el, const OpSet &, const Op &, int j, int, bool ok)\n"
-         "    { return c.start_mv(el, omx(j), s4x(j), ok); }\n";
+    // the outer moves this operator's points take: their group-neighbour entries are read with
+    // 16-byte loads of the group's row (gstride is a multiple of 4) when they span at most 4 of them
+    int mlo = 1 << 30, mhi = -1;
+    for (int x = 0; x < span; ++x) {
+        const int m = ro.mv[col(op.dbase, x)].om;
+        if (m >= 0) { mlo = std::min(mlo, m); mhi = std::max(mhi, m); }
+    }
+    if (op.kind == 2 && op.mergeB >= 0) {
+        const Op &ls = O.op[op.mergeB];
+        for (int j = 0; j < 2; ++j) {
+            const int m = ro.mv[col(ls.dbase, j == 0 ? 0 : 2 * ls.p)].om;
+            if (m >= 0) { mlo = std::min(mlo, m); mhi = std::max(mhi, m); }
+        }
+    }
+    const int qlo = mhi >= 0 ? mlo / 4 : 0, nq = mhi >= 0 ? mhi / 4 - mlo / 4 + 1 : 0;
+    if (nq > 4) {
+        t += "    struct Gn {};\n"
+             "    __device__ static __forceinline__ Gn gn_load(const Elem &) { return {}; }\n"
+             "    __device__ static __forceinline__ int start(const Ctx &c, const Elem &el, const OpSet &, const Op &, const Gn &, int pos, bool ok)\n"
+             "    { return c.start_mv(el, om(pos), s4(pos), ok); }\n"
+             "    __device__ static __forceinline__ int startx(const Ctx &c, const Elem &el, const OpSet &, const Op &, const Gn &, int j, int, bool ok)\n"
+             "    { return c.start_mv(el, omx(j), s4x(j), ok); }\n";
+    } else {
+        t += "    static constexpr int kGnLo = " + std::to_string(qlo) + ", kGnN = " + std::to_string(nq) + ";\n"
+             "    struct Gn { int4 q[kGnN > 0 ? kGnN : 1]; };\n"
+             "    __device__ static __forceinline__ Gn gn_load(const Elem &el)\n"
+             "    {\n"
+             "        Gn g;\n"
+             "#pragma unroll\n"
+             "        for (int i = 0; i < kGnN; ++i) g.q[i] = __ldg(reinterpret_cast<const int4 *>(el.gn) + kGnLo + i);\n"
+             "        return g;\n"
+             "    }\n"
+             "    __device__ static __forceinline__ int gnv(const Gn &g, int m)\n"
+             "    {\n"
+             "        const int k = m - 4 * kGnLo;\n"
+             "        const int4 q = g.q[k >> 2];\n"
+             "        return (k & 3) == 0 ? q.x : (k & 3) == 1 ? q.y : (k & 3) == 2 ? q.z : q.w;\n"
+             "    }\n"
+             "    __device__ static __forceinline__ int start(const Ctx &c, const Elem &el, const OpSet &, const Op &, const Gn &g, int pos, bool ok)\n"
+             "    { return c.start_row(el, om(pos) >= 0 ? gnv(g, om(pos)) + el.k4 + s4(pos) : el.r + s4(pos), ok); }\n"
+             "    __device__ static __forceinline__ int startx(const Ctx &c, const Elem &el, const OpSet &, const Op &, const Gn &g, int j, int, bool ok)\n"
+             "    { return c.start_row(el, omx(j) >= 0 ? gnv(g, omx(j)) + el.k4 + s4x(j) : el.r + s4x(j), ok); }\n";
+    }
     const bool bits = L && L->on && (L->offA.count(i) || L->offT.count(i));
     t += std::string("    static constexpr bool kTopsBits = ") + (bits ? "true" : "false") + ";\n";
     if (bits) {

@@ -244,14 +244,23 @@ struct Ctx {
     {
         return l == S->N - 1 ? el.j : (l == S->N - 2 ? el.k4 : (int)__ldg(el.kr + l));
     }
-    // Start rank of the row reached from the own row by the row move m when ok (the point lies in
-    // K, so that row exists); the start of the own row otherwise.  The group-neighbour entry is
-    // read whatever ok (its slot is always valid); only the row index is selected.
+    // Start rank of the row reached from the own row by the row move (om, s4) when ok (the point
+    // lies in K, so that row exists); the start of the own row otherwise.
     __device__ __forceinline__ int start_mv(const Elem &el, int om, int s4, bool ok) const
     {
-        int row = el.r + s4;
-        if (om >= 0) row = __ldg(el.gn + om) + el.k4 + s4;
-        return __ldg(S->rstart + (ok ? row : el.r));
+        int st = el.e - el.j;
+        if (ok) {   // a predicated pair of loads: lanes whose point lies outside K read nothing
+            const int row = om >= 0 ? __ldg(el.gn + om) + el.k4 + s4 : el.r + s4;
+            st = __ldg(S->rstart + row);
+        }
+        return st;
+    }
+    // the same for a row already known (the group-neighbour entry read by the caller)
+    __device__ __forceinline__ int start_row(const Elem &el, int row, bool ok) const
+    {
+        int st = el.e - el.j;
+        if (ok) st = __ldg(S->rstart + row);
+        return st;
     }
     // the same for row-offset column d
     __device__ __forceinline__ int start(const Elem &el, int d, bool ok) const
@@ -288,13 +297,15 @@ struct Ctx {
 // ((s + p) (2 q + 1) + (s2 + q)); startx: the merged line op's points s2 = -SB, SB.
 struct ColsRuntime {
     static constexpr bool kTopsBits = false;     // fibre tops computed in the kernel
-    __device__ static __forceinline__ int start(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, int pos,
-                                                bool ok)
+    struct Gn {};                                // group-neighbour entries read per point
+    __device__ static __forceinline__ Gn gn_load(const Elem &) { return {}; }
+    __device__ static __forceinline__ int start(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const Gn &,
+                                                int pos, bool ok)
     {
         return c.start(el, O.didx[op.dbase + pos], ok);
     }
-    __device__ static __forceinline__ int startx(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, int j,
-                                                 int sb, bool ok)
+    __device__ static __forceinline__ int startx(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const Gn &,
+                                                 int j, int sb, bool ok)
     {
         const Op &ls = O.op[op.mergeB];
         return c.start(el, O.didx[ls.dbase + (j == 0 ? 0 : 2 * sb)], ok);
@@ -343,14 +354,12 @@ __device__ __forceinline__ Row4<double> load_row4(const double *p)
     return {{a.x, a.y, b.x, b.y}};
 }
 
-// The specialised stencils below issue every load of an operator unconditionally: a footprint
-// point outside K reads the group-neighbour table at its (always valid) slot and gathers the
-// output element itself.  Its weight is then zero without a mask: the tabulated rows of P(J_n / L)
-// are zero at the columns outside the fibre (below 0 or at or above n), and every path through a
-// point outside K meets such an entry.  Without branches around them, all loads of an operator
-// are in flight together instead of one dependent pair (table, gather) after another.  This pays
-// for degrees <= 3; at degree 8 on short fibres most points lie outside K and the loads they
-// would waste cost more than the overlap gains, so those operators keep the branching generic loop.
+// The specialised stencils below issue the loads of an operator without branches: every footprint
+// point's row start and gather are predicated on its membership in K (a lane whose point lies
+// outside K reads nothing and contributes zero; the tabulated rows of P(J_n / L) are zero at the
+// columns outside the fibre as well), so all loads of an operator are in flight together instead
+// of one dependent pair (table, gather) after another.  This pays for degrees <= 3; at degree 8 on
+// short fibres most points lie outside K, so those operators keep the branching generic loop.
 //
 // Membership and fibre tops come from integer products only: with r = prod over the other axes
 // of (1 + k_l), the point k + u e_a + v e_b lies in K iff its coordinates are >= 0 and
@@ -422,19 +431,26 @@ __device__ __forceinline__ void line_role_n(const Ctx &c, const Elem &el, const 
     constexpr int W = packed_width(P);
     const RowW<R, W> row = load_roww<W>(tab + op.ptabP + (ka * (P + 1) + top) * W);   // entries at s = -P + 2j
     constexpr int NP = P + 1;
+    const auto gn = CM::gn_load(el);
     int addr[NP];
+    bool okj[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         const int s = -P + 2 * j;
         const bool ok = ka + s >= 0 && s <= top;
-        if (RA == ROLE_LAST) addr[j] = ok ? el.e + s : el.e;
-        else addr[j] = s == 0 ? el.e : CM::start(c, el, O, op, s + P, ok) + el.j;
+        okj[j] = ok;
+        if (RA == ROLE_LAST) addr[j] = el.e + s;
+        else addr[j] = s == 0 ? el.e : CM::start(c, el, O, op, gn, s + P, ok) + el.j;
     }
+    // gathers predicated on membership (a point outside K contributes nothing)
     V v[NSRC][NP];
 #pragma unroll
     for (int q = 0; q < NSRC; ++q)
 #pragma unroll
-        for (int j = 0; j < NP; ++j) v[q][j] = srcs[q][addr[j]];
+        for (int j = 0; j < NP; ++j) {
+            v[q][j] = czero<V>();
+            if (okj[j]) v[q][j] = srcs[q][addr[j]];
+        }
 #pragma unroll
     for (int q = 0; q < NSRC; ++q) {
         V acc = czero<V>();
@@ -514,36 +530,42 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
             return r;
         }
     };
-    // addresses of the footprint points (own element when the point is not in K)
+    // addresses of the footprint points and their membership; the gathers are predicated on it (a
+    // point outside K contributes nothing)
+    const auto gn = CM::gn_load(el);
     int addr[NS][NS2];
+    bool okp[NS][NS2];
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         const int s = -P + 2 * i;
         int base_s = el.e - el.j;                       // RB = LAST: start of the row of k + s e_a
         if (RB == ROLE_LAST && s != 0)
-            base_s = CM::start(c, el, O, op, (s + P) * (2 * Q + 1) + Q, row_in_k(s));
+            base_s = CM::start(c, el, O, op, gn, (s + P) * (2 * Q + 1) + Q, row_in_k(s));
 #pragma unroll
         for (int j = 0; j < NS2; ++j) {
             const int s2 = -Q + 2 * j;
             const bool ok = in_k(s, s2);
+            okp[i][j] = ok;
             int a;
-            if (RB == ROLE_LAST) a = ok ? base_s + el.j + s2 : el.e;
+            if (RB == ROLE_LAST) a = base_s + el.j + s2;
             else if (s == 0 && s2 == 0) a = el.e;
-            else a = CM::start(c, el, O, op, (s + P) * (2 * Q + 1) + (s2 + Q), ok) + el.j;
+            else a = CM::start(c, el, O, op, gn, (s + P) * (2 * Q + 1) + (s2 + Q), ok) + el.j;
             addr[i][j] = a;
         }
     }
     constexpr int NX = SB > Q ? 2 : 0;                  // merged line points +-SB outside the plane footprint
     int xaddr[NX > 0 ? NX : 1];
+    bool okx[NX > 0 ? NX : 1];
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
         const int s2 = j == 0 ? -SB : SB;
         const bool ok = in_k(0, s2);
+        okx[j] = ok;
         int a;
         if (RB == ROLE_LAST) {
-            a = ok ? el.e + s2 : el.e;
+            a = el.e + s2;
         } else {
-            a = CM::startx(c, el, O, op, j, SB, ok) + el.j;
+            a = CM::startx(c, el, O, op, gn, j, SB, ok) + el.j;
         }
         xaddr[j] = a;
     }
@@ -553,12 +575,18 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
 #pragma unroll
         for (int i = 0; i < NS; ++i)
 #pragma unroll
-            for (int j = 0; j < NS2; ++j) v[q][i][j] = srcs[q][addr[i][j]];
+            for (int j = 0; j < NS2; ++j) {
+                v[q][i][j] = czero<V>();
+                if (okp[i][j]) v[q][i][j] = srcs[q][addr[i][j]];
+            }
     V xv[NSRC][NX > 0 ? NX : 1];
 #pragma unroll
     for (int q = 0; q < NSRC; ++q)
 #pragma unroll
-        for (int j = 0; j < NX; ++j) xv[q][j] = srcs[q][xaddr[j]];
+        for (int j = 0; j < NX; ++j) {
+            xv[q][j] = czero<V>();
+            if (okx[j]) xv[q][j] = srcs[q][xaddr[j]];
+        }
     const int dB0 = topB(0, TB);                        // b-distance at k, capped at max(Q, SB)
 #pragma unroll
     for (int q = 0; q < NSRC; ++q) out[q] = czero<V>();

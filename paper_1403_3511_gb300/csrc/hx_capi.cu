@@ -426,6 +426,28 @@ struct Compiler {
         return base;
     }
 
+    // The second factor of a plane operator when it has degree 1: the rows of both fibre-top
+    // distances side by side, tab[base + 4 i + 2 d + j] = [Q(J_n / L)]_{i, i-1+2j}, n = i + 1 + d,
+    // so that one 4-entry load gives both (4-aligned base).
+    std::map<PolyKey, int> pair_base;
+    int packed_pairs(const std::vector<double> &a)
+    {
+        auto it = pair_base.find(PolyKey{a});
+        if (it != pair_base.end()) return it->second;
+        const int B = set->h.B;
+        tab.resize((tab.size() + 3) & ~(size_t)3, 0.0);
+        const int base = (int)tab.size();
+        tab.resize(tab.size() + (size_t)B * 4, 0.0);
+        double row[3];
+        for (int i = 0; i < B; ++i)
+            for (int d = 0; d <= 1; ++d) {
+                poly_row(a, L, i, i + 1 + d, row);
+                for (int j = 0; j <= 1; ++j) tab[base + (size_t)i * 4 + 2 * d + j] = row[2 * j];
+            }
+        pair_base[PolyKey{a}] = base;
+        return base;
+    }
+
     RowOffsets roff;                     // row offsets of both stages (0: zero offset)
 
     // Column of the row-offset table for the point k + s0 e_a0 + s1 e_a1 (moves along the last
@@ -488,7 +510,7 @@ struct Compiler {
             o.ptabP = o.ptabQ = 0;
             if (o.cls != CLS_ID && o.cls != CLS_GENERIC) {
                 o.ptabP = packed(P);
-                if (kind == 2) o.ptabQ = packed(Q);
+                if (kind == 2) o.ptabQ = o.q == 1 ? packed_pairs(Q) : packed(Q);
             }
         }
         o.mod = t.mod_kind;

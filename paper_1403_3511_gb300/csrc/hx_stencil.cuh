@@ -588,6 +588,21 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
             if (okx[j]) xv[q][j] = srcs[q][xaddr[j]];
         }
     const int dB0 = topB(0, TB);                        // b-distance at k, capped at max(Q, SB)
+    // rows of Q(J_n / L) at k_b for distance d to the b-fibre top: for degree 1 both distances come
+    // from one 4-entry load (the rows are stored side by side)
+    [[maybe_unused]] Row4<R> qpair;
+    if constexpr (Q == 1) qpair = load_row4(tQ + kb * 4);
+    auto rowQ = [&](int d) {
+        if constexpr (Q == 1) {
+            Row4<R> r;
+            r.v[0] = d ? qpair.v[2] : qpair.v[0];
+            r.v[1] = d ? qpair.v[3] : qpair.v[1];
+            r.v[2] = r.v[3] = (R)0;
+            return r;
+        } else {
+            return load_row4(tQ + (kb * (Q + 1) + d) * 4);
+        }
+    };
 #pragma unroll
     for (int q = 0; q < NSRC; ++q) out[q] = czero<V>();
     if (ORD != 2) {   // P(X_a) (Q(X_b) c)
@@ -597,7 +612,7 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
         for (int i = 0; i < NS; ++i) {
             const int s = -P + 2 * i;
             const int d = s == 0 ? min(Q, dB0) : topB(s, Q);
-            rowQs[i] = load_row4(tQ + (kb * (Q + 1) + d) * 4);
+            rowQs[i] = rowQ(d);
         }
 #pragma unroll
         for (int q = 0; q < NSRC; ++q) {
@@ -613,7 +628,7 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
         }
     }
     if (ORD != 1) {   // Q(X_b) (P(X_a) c)
-        const Row4<R> rowQ0 = load_row4(tQ + (kb * (Q + 1) + min(Q, dB0)) * 4);
+        const Row4<R> rowQ0 = rowQ(min(Q, dB0));
         Row4<R> rowPs[NS2];
 #pragma unroll
         for (int j = 0; j < NS2; ++j) rowPs[j] = load_row4(tP + (ka * (P + 1) + topA(-Q + 2 * j)) * 4);

@@ -83,7 +83,8 @@ struct Op {
     int p, q;                 // degrees on a and b
     int pmask, qmask;         // bit (s + p) set when the rows can be nonzero at offset s
     int tabP, tabQ;           // row table bases
-    int ptabP, ptabQ;         // packed row table bases (pure parity, line degree <= 8, plane degrees <= 3; 0 otherwise)
+    int ptabP, ptabQ;         // packed row table bases (pure parity, line degree <= 8, plane degrees <= 3; 0 otherwise);
+                              // a plane operator's degree-1 second factor has its two rows per coordinate side by side
     int dbase;                // base into didx (footprint position -> row offset index)
     int src, dst;             // input channel (-1 = c), output channel (stage 1 only)
     int mergeB;               // plane ops: index of a line op on axis b evaluated inside this op (-1: none)

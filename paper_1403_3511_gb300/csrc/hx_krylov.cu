@@ -1282,9 +1282,34 @@ __device__ __forceinline__ void combine_term(F2 &xr, F2 &xi, float4 y, float2 v)
     xi.c = fmaf(y.y, v.y, fmaf(y.w, v.x, xi.c));
 }
 
+// The same compensated accumulation for the real and imaginary parts at once, in packed FP32x2
+// instructions (each lane the IEEE operation of F2::add_prod, in the same order).
+struct F2x2 {
+    float2 s = {0.f, 0.f}, c = {0.f, 0.f};
+    __device__ __forceinline__ void add_prod(float2 a, float2 b)
+    {
+        const float2 p = f2_mul(a, b);
+        const float2 e = f2_fma(a, b, make_float2(-p.x, -p.y));
+        const float2 t = f2_add(s, p), bb = f2_sub(t, s);
+        const float2 q = f2_add(f2_sub(s, f2_sub(t, bb)), f2_sub(p, bb));
+        s = t;
+        c = f2_add(c, f2_add(q, e));
+    }
+};
+
+// combine_term on both parts: (re, im) += (yr + i yi) (vx + i vy) with y = (yr_hi, yr_lo, yi_hi, yi_lo)
+__device__ __forceinline__ void combine_term2(F2x2 &x, float4 y, float2 v)
+{
+    const float2 vs = make_float2(v.y, v.x);
+    x.add_prod(make_float2(y.x, y.x), v);            // yr_hi (vx, vy)
+    x.add_prod(make_float2(-y.z, y.z), vs);          // yi_hi (-vy, vx)
+    x.c = f2_fma(make_float2(y.y, y.y), v, f2_fma(make_float2(-y.w, y.w), vs, x.c));
+}
+
 // The complex64 recombination for m = M <= 8 known at compile time: two elements per thread and
 // iteration (16-byte loads of every basis vector, all issued before the arithmetic), the split
-// coefficients in shared memory.  Same arithmetic per element as combine_kernel.
+// coefficients in shared memory.  Same arithmetic per element as combine_kernel, in packed FP32x2
+// instructions.
 template <int M>
 __global__ void __launch_bounds__(256) combine_m_kernel(double2 *c, const float2 *Vb, size_t ld, int n,
                                                         double *partials, Scal *sc)
@@ -1307,16 +1332,16 @@ __global__ void __launch_bounds__(256) combine_m_kernel(double2 *c, const float2
 #pragma unroll
         for (int i = 0; i < M; ++i)
             if (i < mu) v[i] = load_pair(Vb + i * ld, e);
-        F2 ar, ai, br, bi;
+        F2x2 pa, pb;
 #pragma unroll
         for (int i = 0; i < M; ++i)
             if (i < mu) {
                 const float4 y = ys[i];
-                combine_term(ar, ai, y, v[i].a);
-                combine_term(br, bi, y, v[i].b);
+                combine_term2(pa, y, v[i].a);
+                combine_term2(pb, y, v[i].b);
             }
-        const double2 xa = make_double2(f2d_exact(ar.s) + f2d_exact(ar.c), f2d_exact(ai.s) + f2d_exact(ai.c));
-        const double2 xb = make_double2(f2d_exact(br.s) + f2d_exact(br.c), f2d_exact(bi.s) + f2d_exact(bi.c));
+        const double2 xa = make_double2(f2d_exact(pa.s.x) + f2d_exact(pa.c.x), f2d_exact(pa.s.y) + f2d_exact(pa.c.y));
+        const double2 xb = make_double2(f2d_exact(pb.s.x) + f2d_exact(pb.c.x), f2d_exact(pb.s.y) + f2d_exact(pb.c.y));
         c[e] = xa;
         c[e + 1] = xb;
         na.add(xa.x);

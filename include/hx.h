@@ -170,10 +170,13 @@ HX_API void hx_problem_destroy(hx_problem *p);
 
 /* Compiles W^pol (Sec. 1.3) into the coefficient tables the kernels read and sets the
  * problem time to t.  Terms are copied; the caller's arrays may be freed afterwards.
- * A constant term (all degrees 0) is folded into the diagonal.  Synchronous.
+ * A constant term (all degrees 0) is folded into the diagonal.  With a product kernel
+ * specialised to the potential's operator structure (hx_apply_specialised) it also packs each
+ * element's fibre-top distances for that kernel (up to 16 bytes per coefficient of device memory,
+ * kept while the structure stays the same).  Synchronous.
  * Errors: HX_EINVAL (L <= 0, bad axes or degrees, NULL coef), HX_EUNSUPPORTED (n_axes > 2,
  * more than 48 operators after compilation: rank-one pieces of two-axis terms, and for high
- * degrees their two stages, count separately). */
+ * degrees their two stages, count separately), HX_ENOMEM / HX_ECUDA. */
 HX_API int hx_potential_set(hx_problem *p, const hx_potential *pot, double t);
 HX_API int hx_get_time(const hx_problem *p, double *t);
 HX_API int hx_set_time(hx_problem *p, double t);

@@ -158,7 +158,7 @@ static TopLayout top_layout(const OpSet &O)
 // Compile-time row moves of operator i's footprint points (a type with the start / startx
 // functions of ColsRuntime): move (om, s4) of the column that didx gives each position; with a top
 // layout also the offsets of its fibre-top fields and their readers.
-static std::string cols_type(const OpSet &O, const RowOffsets &ro, int i, const char *prefix,
+static std::string cols_type(const OpSet &O, const RowOffsets &ro, int i, const char *prefix, int N,
                              const TopLayout *L = nullptr)
 {
     const Op &op = O.op[i];
@@ -171,6 +171,8 @@ static std::string cols_type(const OpSet &O, const RowOffsets &ro, int i, const 
     };
     auto col = [&](int dbase, int x) { return (int)O.didx[dbase + x]; };
     std::string t = "struct " + std::string(prefix) + std::to_string(i) + " {\n";
+    t += "    static constexpr int kA = " + std::to_string(op.a) + ", kB = " + std::to_string(op.kind == 2 ? op.b : -1) +
+         ", kN = " + std::to_string(N) + ";\n";
     t += chain("om", span, [&](int x) { return (int)ro.mv[col(op.dbase, x)].om; });
     t += chain("s4", span, [&](int x) { return (int)ro.mv[col(op.dbase, x)].s4; });
     if (op.kind == 2 && op.mergeB >= 0) {
@@ -250,12 +252,12 @@ static std::string cols_type(const OpSet &O, const RowOffsets &ro, int i, const 
     return t;
 }
 
-static std::string jit_types(const OpSet &O, const RowOffsets &ro, const char *prefix = "ColsK",
+static std::string jit_types(const OpSet &O, const RowOffsets &ro, int N, const char *prefix = "ColsK",
                              const TopLayout *L = nullptr)
 {
     std::string t;
     for (int i = 0; i < O.nops; ++i)
-        if (O.op[i].kind >= 1 && !O.op[i].merged) t += cols_type(O, ro, i, prefix, L);
+        if (O.op[i].kind >= 1 && !O.op[i].merged) t += cols_type(O, ro, i, prefix, N, L);
     return t;
 }
 
@@ -610,8 +612,9 @@ void jit_prepare(Problem *p)
     const TopLayout L = top_layout(p->ops);
     const std::string body_tops = L.on ? jit_body_tops(p->ops, L) : "";
     const int tops_words = body_tops.empty() ? 0 : L.words;
-    const std::string types = jit_types(p->ops, p->roff, "ColsK", body_tops.empty() ? nullptr : &L) +
-                              jit_types(p->ops1, p->roff, "ColsS");
+    const int N = p->set->h.N;
+    const std::string types = jit_types(p->ops, p->roff, N, "ColsK", body_tops.empty() ? nullptr : &L) +
+                              jit_types(p->ops1, p->roff, N, "ColsS");
     const std::string key = std::to_string(p->device) + (f32 ? "|f|" : "|d|") + types + body + body_s1;
     // the two-time kernels run only for single-stage potentials (apply_dual)
     const std::string body_dual = p->ops1.nops ? "" : jit_body(p->ops, true);

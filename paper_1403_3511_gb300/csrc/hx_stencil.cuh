@@ -291,12 +291,34 @@ struct Ctx {
     }
 };
 
+// Coordinate k_l of the element on axis l: l compile-time (CM::kA, CM::kB >= 0 with N = CM::kN, the
+// kernels compiled per potential: equal reads of two operators are one load) or read from the
+// operator at run time.
+template <int L, int N>
+__device__ __forceinline__ int coord_ct(const Elem &el)
+{
+    return L == N - 1 ? el.j : (L == N - 2 ? el.k4 : (int)__ldg(el.kr + L));
+}
+template <typename CM>
+__device__ __forceinline__ int coord_a(const Ctx &c, const Elem &el, const Op &op)
+{
+    if constexpr (CM::kA >= 0) return coord_ct<CM::kA, CM::kN>(el);
+    else return c.k(el, op.a);
+}
+template <typename CM>
+__device__ __forceinline__ int coord_b(const Ctx &c, const Elem &el, const Op &op)
+{
+    if constexpr (CM::kB >= 0) return coord_ct<CM::kB, CM::kN>(el);
+    else return c.k(el, op.b);
+}
+
 // Row moves of an operator's footprint points, read at run time from the operator list (the
 // generic kernel); the kernels compiled per potential use generated types with the same two
 // functions whose moves are compile-time constants.  pos: footprint position of the point
 // ((s + p) (2 q + 1) + (s2 + q)); startx: the merged line op's points s2 = -SB, SB.
 struct ColsRuntime {
     static constexpr bool kTopsBits = false;     // fibre tops computed in the kernel
+    static constexpr int kA = -1, kB = -1, kN = 0;   // the operator's axes and N read at run time
     struct Gn {};                                // group-neighbour entries read per point
     __device__ static __forceinline__ Gn gn_load(const Elem &) { return {}; }
     __device__ static __forceinline__ int start(const Ctx &c, const Elem &el, const OpSet &O, const Op &op, const Gn &,
@@ -418,7 +440,7 @@ __device__ __forceinline__ void line_role_n(const Ctx &c, const Elem &el, const 
                                             typename Vec2<R>::T (&out)[NSRC])
 {
     using V = typename Vec2<R>::T;
-    const int ka = RA == ROLE_LAST ? el.j : c.k(el, op.a);
+    const int ka = RA == ROLE_LAST ? el.j : coord_a<CM>(c, el, op);
     // steps from k to the top of its a-fibre, capped at P
     int top;
     if (RA == ROLE_LAST) {
@@ -487,8 +509,8 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
 {
     using V = typename Vec2<R>::T;
     const int B = c.S->B;
-    const int ka = c.k(el, op.a);
-    const int kb = RB == ROLE_LAST ? el.j : c.k(el, op.b);
+    const int ka = coord_a<CM>(c, el, op);
+    const int kb = RB == ROLE_LAST ? el.j : coord_b<CM>(c, el, op);
     const R *tP = tab + op.ptabP, *tQ = tab + op.ptabQ;   // packed rows: entry i at offset -P + 2i
     constexpr int NS = P + 1, NS2 = Q + 1;         // offsets s = -P + 2i, s2 = -Q + 2j
     constexpr int TB = SB > Q ? SB : Q;            // b-distances needed at k
@@ -673,8 +695,8 @@ template <int P, int Q, int RB, int SB, typename CM>
 __device__ __forceinline__ void plane_tops(const Ctx &c, const Elem &el, const Op &op, unsigned *tw)
 {
     constexpr int TB = SB > Q ? SB : Q;
-    const int ka = c.k(el, op.a);
-    const int kb = RB == ROLE_LAST ? el.j : c.k(el, op.b);
+    const int ka = coord_a<CM>(c, el, op);
+    const int kb = RB == ROLE_LAST ? el.j : coord_b<CM>(c, el, op);
     const PlaneTops<P, TB> G{ka, kb, exact_div(el.qall, (1 + ka) * (1 + kb)), c.S->B};
     put_top_field(tw, CM::offA(0), G.topA(0));
 #pragma unroll
@@ -691,7 +713,7 @@ __device__ __forceinline__ void plane_tops(const Ctx &c, const Elem &el, const O
 template <int P, typename CM>
 __device__ __forceinline__ void line_tops(const Ctx &c, const Elem &el, const Op &op, unsigned *tw)
 {
-    put_top_field(tw, CM::offT, line_top<P>(c, el, c.k(el, op.a)));
+    put_top_field(tw, CM::offT, line_top<P>(c, el, coord_a<CM>(c, el, op)));
 }
 
 template <typename R, int P, int Q, int RB, int SB, int ORD = 0, typename CM = ColsRuntime>

@@ -75,7 +75,7 @@ __device__ __forceinline__ void plane_op(const Ctx &c, const Elem &el, const OpS
     const int a = op.a, b = op.b, p = op.p, q = op.q;
     const int ka = c.k(el, a), kb = c.k(el, b);
     const int rab = exact_div(el.qall, (1 + ka) * (1 + kb));
-    const R wAB = (R)O.wAB, wBA = (R)O.wBA;
+    const R wAB = rconst<R>(O.wAB, O.wAB32), wBA = rconst<R>(O.wBA, O.wBA32);
     // fibre-top distances: along a at k + s2 e_b, along b at k + s e_a
     int dA[2 * MQ + 1], dB[2 * MP + 1];
 #pragma unroll(UNROLL ? 2 * MQ + 1 : 1)
@@ -160,7 +160,7 @@ __device__ __forceinline__ void plane_op_g(const Ctx &c, const Elem &el, const O
 {
     const int p = op.p, q = op.q;
     const int ka = c.k(el, op.a), kb = c.k(el, op.b);
-    const R wAB = (R)O.wAB, wBA = (R)O.wBA;
+    const R wAB = rconst<R>(O.wAB, O.wAB32), wBA = rconst<R>(O.wBA, O.wBA32);
     int addr;
     // fibre-top distances: along a at k + s2 e_b, along b at k + s e_a (0 when that point is not in K)
     int dA[2 * MQ + 1], dB[2 * MP + 1];
@@ -407,6 +407,7 @@ int batch_member_args(Problem *p, const void *cin, void *cout, const double *t_p
     a.gnbn = p->gnbn;
     a.gstride = p->gstride;
     a.dscale = p->scale * p->scale;
+    a.dscale32 = (float)a.dscale;
     memcpy(a.mv, p->roff.mv, sizeof(a.mv));
     a.t_ptr = t_ptr;
     a.t_shift = t_shift;
@@ -437,6 +438,7 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
     a.gnbn = p->gnbn;
     a.gstride = p->gstride;
     a.dscale = p->scale * p->scale;
+    a.dscale32 = (float)a.dscale;
     memcpy(a.mv, p->roff.mv, sizeof(a.mv));
     a.t_ptr = t_ptr;
     a.t_shift = t_shift;
@@ -478,6 +480,7 @@ static int launch_apply_t(Problem *p, const OpSet &ops, int stage1, const void *
     a.cin2 = cin2;
     a.t_shift2 = t_shift2;
     a.mag_g = mag_g;
+    a.mag_g32 = (float)mag_g;
     const int blocks = (p->set->d.size + kApplyThreads - 1) / kApplyThreads;
     if (p->jit && !g_batch_capture && (!stage1 || jit_has_stage1(p))) {   // the potential's specialised kernel
         a.tops = p->tops;

@@ -643,6 +643,8 @@ static int compile_potential(Problem *pr, const hx_potential *pot)
     int order = pr->cfg.order;
     cp.ops.wAB = order == HX_ORDER_SYM ? 0.5 : (order == HX_ORDER_EQ ? 1.0 : 0.0);
     cp.ops.wBA = order == HX_ORDER_SYM ? 0.5 : (order == HX_ORDER_ALG ? 1.0 : 0.0);
+    cp.ops.wAB32 = (float)cp.ops.wAB;
+    cp.ops.wBA32 = (float)cp.ops.wBA;
     for (int ti = 0; ti < pot->n_terms; ++ti) {
         const hx_term &t = pot->terms[ti];
         if (t.n_axes < 1 || t.n_axes > 2) {

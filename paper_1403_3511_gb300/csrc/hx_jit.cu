@@ -84,11 +84,13 @@ static bool specialised_plane(const Op &op, int sb)
 }
 
 // Factor-order template argument of the plane stencils: 0 both orders with the runtime weights,
-// 1 P(X_a) Q(X_b) alone, 2 Q(X_b) P(X_a) alone (the literal orders, weight 1).
+// 1 P(X_a) Q(X_b) alone, 2 Q(X_b) P(X_a) alone (the literal orders, weight 1), 3 both with weight
+// 1/2 (the symmetric order).
 static int plane_order(const OpSet &O)
 {
     if (O.wAB == 1.0 && O.wBA == 0.0) return 1;
     if (O.wAB == 0.0 && O.wBA == 1.0) return 2;
+    if (O.wAB == 0.5 && O.wBA == 0.5) return 3;
     return 0;
 }
 

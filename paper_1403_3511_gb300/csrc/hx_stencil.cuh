@@ -43,6 +43,7 @@ struct ApplyArgs : ApplyArgsBase {
     // with cin2: instead of the two products y, y2 write the 2-stage Magnus combination
     // (cin + cin2)/2 - i mag_g (y - y2) to cout (0: off)
     double mag_g;
+    float mag_g32;             // mag_g in FP32 (read by the FP32 kernels)
 };
 
 // Block and grid stages of the reductions: wsum[w][j] (shared, filled by the caller, followed by a
@@ -187,6 +188,16 @@ __device__ __forceinline__ float2 cscale(float w, float2 v) { return f2_mul(make
 __device__ __forceinline__ double2 cscale(double w, double2 v) { return make_double2(w * v.x, w * v.y); }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return f2_add(a, b); }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+// A launch constant in the stencil precision: the FP32 kernels read the FP32 copy the host stores
+// beside the FP64 field (a conversion of the FP64 field, which the compiler may repeat at every use
+// under register pressure, runs on the FP64 pipe, a small fraction of the FP32 rate on GB300).
+template <typename R>
+__device__ __forceinline__ R rconst(double d, float f)
+{
+    if constexpr (sizeof(R) == 4) return f;
+    else return (R)d;
+}
 template <typename V> __device__ __forceinline__ V czero();
 template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
@@ -498,7 +509,8 @@ __device__ __forceinline__ typename Vec2<R>::T line_role(const Ctx &c, const Ele
 //   BA: sum_s2 [Q]_{k, k+s2 e_b} sum_s [P]_{k+s2 e_b, k+s2 e_b+s e_a} c(k + s e_a + s2 e_b),
 // with the rows of P(J_n / L) and Q(J_n / L) taken from the tables by coordinate and distance to
 // the fibre top (a path through an intermediate point outside K meets a zero entry).  ORD = 0:
-// both orders with the weights wAB, wBA of O; 1: AB only (weight 1); 2: BA only (weight 1).
+// both orders with the weights wAB, wBA of O; 1: AB only (weight 1); 2: BA only (weight 1); 3: both
+// orders with weight 1/2 each, (AB + BA) / 2 (the same rounding: halving is exact).
 // SB > 0: a line operator S(X_b) of degree SB (parity of Q, SB = Q or Q + 2) merged into this op
 // (P is even, so the points s = 0 are footprint points); its sum goes to lout.  NSRC inputs at once
 // (addresses, fibre tops and weights shared): the sums for srcs[q] go to out[q] and lout[q].
@@ -646,7 +658,7 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
                 for (int j = 0; j < NS2; ++j) u = cmad(rowQs[i].v[j], v[q][i][j], u);
                 ab = cmad(rowP0.v[i], u, ab);
             }
-            out[q] = ORD == 0 ? cscale((R)O.wAB, ab) : ab;
+            out[q] = ORD == 0 ? cscale(rconst<R>(O.wAB, O.wAB32), ab) : ab;
         }
     }
     if (ORD != 1) {   // Q(X_b) (P(X_a) c)
@@ -664,7 +676,8 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
                 for (int i = 0; i < NS; ++i) w = cmad(rowPs[j].v[i], v[q][i][j], w);
                 ba = cmad(rowQ0.v[j], w, ba);
             }
-            out[q] = ORD == 0 ? cmad((R)O.wBA, ba, out[q]) : ba;
+            out[q] = ORD == 0 ? cmad(rconst<R>(O.wBA, O.wBA32), ba, out[q])
+                   : ORD == 3 ? cscale((R)0.5, cadd(out[q], ba)) : ba;
         }
     }
     if (SB > 0) {   // the merged line op: points k + s2 e_b, s2 = -SB, -SB + 2, ..., SB
@@ -818,7 +831,7 @@ __device__ __forceinline__ typename Vec2<R>::T apply_element(const ApplyArgs &ar
     const Elem el = make_elem(args, e, er);
     Acc<R> acc;
     if (!args.stage1 && !args.skip_diag) {
-        const R dj = (R)args.dscale * ((R)el.ksum + (R)0.5 * (R)S.N);   // (D_K)_jj = sum_l (j_l + 1/2), times S^2
+        const R dj = rconst<R>(args.dscale, args.dscale32) * ((R)el.ksum + (R)0.5 * (R)S.N);   // (D_K)_jj = sum_l (j_l + 1/2), times S^2
         acc.add(cscale(dj, cin[e]));
     }
     body(ctx, el, acc, sm_w, cin, (const R *)args.tab);
@@ -962,7 +975,7 @@ __device__ __forceinline__ void apply_elements_dual(const ApplyArgs &args, Body 
         const Elem el = make_elem(args, e, er);
         Acc<R> acc, acc2;
         if (!args.skip_diag) {
-            const R dj = (R)args.dscale * ((R)el.ksum + (R)0.5 * (R)S.N);
+            const R dj = rconst<R>(args.dscale, args.dscale32) * ((R)el.ksum + (R)0.5 * (R)S.N);
             acc.add(cscale(dj, cin[e]));
             acc2.add(cscale(dj, cin2[e]));
         }
@@ -970,7 +983,7 @@ __device__ __forceinline__ void apply_elements_dual(const ApplyArgs &args, Body 
         const V y = cscale(oscale, acc.get()), y2 = cscale(oscale, acc2.get());
         if (args.mag_g != 0.0) {
             const V a = cin[e], b = cin2[e];
-            const R g = (R)args.mag_g, half = (R)0.5;
+            const R g = rconst<R>(args.mag_g, args.mag_g32), half = (R)0.5;
             V r;
             r.x = half * (a.x + b.x) + g * (y.y - y2.y);        // -i g z = g (z.y, -z.x)
             r.y = half * (a.y + b.y) - g * (y.x - y2.x);

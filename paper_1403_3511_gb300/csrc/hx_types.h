@@ -98,6 +98,7 @@ struct Op {
 struct OpSet {
     int nops;
     double wAB, wBA;          // factor-order weights for plane ops
+    float wAB32, wBA32;       // the same in FP32 (read by the FP32 kernels)
     int ndidx;
     Op op[kMaxOps];
     unsigned char didx[kMaxDidx];   // footprint position -> column of the row-offset table
@@ -138,6 +139,7 @@ struct ApplyArgsBase {
     const int *gnbn;          // general sets: rows of each neighbour group (0: none), same layout
     int gstride;
     double dscale;            // S^2: factor of D_K for the basis phi_k(S x)
+    float dscale32;           // the same in FP32 (read by the FP32 kernels)
     const double *t_ptr;      // device time
     double t_shift;           // A is evaluated at *t_ptr + t_shift
     const double *pw_values;  // device

@@ -262,8 +262,8 @@ HX_API int hx_step_substeps(hx_problem *p, int *last, int64_t *total, double *er
  * runs the generic kernel; hx_last_error then says why (also when 1).  Both compute the same
  * product.  HX_EINVAL without a potential.  The paper has no counterpart: this reports how the
  * library runs the product.  Setting the environment variable HX_APPLY_SPECIALISE=0 before
- * hx_potential_set selects the generic kernel; HX_JIT_SOURCE_DUMP=<file> writes the source of a
- * newly compiled kernel to that file before compiling it.  The steps of a batch (hx_batch_step)
+ * hx_potential_set selects the generic kernel; HX_JIT_SOURCE_DUMP=<file> appends the source of
+ * each newly compiled kernel set to that file before compiling it.  The steps of a batch (hx_batch_step)
  * run the generic kernel, except the large members of the HX_SCHED_SERIAL schedule. */
 HX_API int hx_apply_specialised(const hx_problem *p);
 /* Kernel launches of one product hx_apply (1, or 2 when some term is evaluated in two stages

@@ -625,9 +625,11 @@ void jit_prepare(Problem *p)
     auto it = g_jit_cache.find(key);
     if (it == g_jit_cache.end()) {
         JitKernel k;
-        // HX_JIT_SOURCE_DUMP=<file>: the generated source is written there before it is compiled
+        // HX_JIT_SOURCE_DUMP=<file>: the generated source is appended there before it is compiled
+        // (one source per kernel set the process compiles)
         if (const char *dump = getenv("HX_JIT_SOURCE_DUMP")) {
-            if (FILE *f = fopen(dump, "w")) {
+            if (FILE *f = fopen(dump, "a")) {
+                fprintf(f, "// ---- kernel set %s, N = %d\n", f32 ? "complex64" : "complex128", N);
                 const std::string src = jit_source(f32, types, body, body_dual, body_pair, body_s1, body_tops, tops_words);
                 fwrite(src.data(), 1, src.size(), f);
                 fclose(f);

@@ -445,9 +445,10 @@ static std::string jit_source(bool f32, const std::string &types, const std::str
          "                                        const hx::R *sm_w, const hx::V *cin, const hx::R *tab) {\n"
          "        hx::ops(args, ctx, el, acc, sm_w, cin, tab);\n"
          "    });\n}\n";
-    // two times at once (the 2-stage Magnus method's A_1 v and A_2 v)
-    s += f32 ? "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 4)\n"
-             : "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 3)\n";
+    // two times at once (the 2-stage Magnus method's A_1 v and A_2 v).  The two-time kernels keep 3
+    // blocks of 256 per SM in both precisions: at 4 (64 registers) the complex64 ones spilled (the
+    // Hénon-Heiles chain at N=6: 112 and 588 bytes) and ran the Magnus step 24 % slower
+    s += "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 3)\n";
     s += "hx_apply_specialised_dual(const __grid_constant__ hx::ApplyArgs args)\n{\n"
          "    hx::apply_elements_dual<hx::R>(args, [&](const hx::Ctx &ctx, const hx::Elem &el, hx::Acc<hx::R> &acc,\n"
          "                                             hx::Acc<hx::R> &acc2, const hx::R *sm_w, const hx::R *sm_w2,\n"
@@ -455,8 +456,7 @@ static std::string jit_source(bool f32, const std::string &types, const std::str
          "        hx::ops_dual(args, ctx, el, acc, acc2, sm_w, sm_w2, cin, tab);\n"
          "    });\n}\n";
     // two inputs at two times (the Magnus method's A_2 (A_1 v) and A_1 (A_2 v))
-    s += f32 ? "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 4)\n"
-             : "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 3)\n";
+    s += "extern \"C\" __global__ void __launch_bounds__(hx::kApplyThreads, 3)\n";
     s += "hx_apply_specialised_pair(const __grid_constant__ hx::ApplyArgs args)\n{\n"
          "    hx::apply_elements_dual<hx::R>(args, [&](const hx::Ctx &ctx, const hx::Elem &el, hx::Acc<hx::R> &acc,\n"
          "                                             hx::Acc<hx::R> &acc2, const hx::R *sm_w, const hx::R *sm_w2,\n"

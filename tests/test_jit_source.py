@@ -1,0 +1,67 @@
+"""The kernels compiled per potential (csrc/hx_jit.cu writes their source, NVRTC compiles it when a
+potential is set) are built from templates in csrc/hx_stencil.cuh that the library's own build does
+not instantiate.  This compiles a generated source (tests/native/jit_hh6_c64.cu: the N=6 Hénon-Heiles
+chain of the benchmark) against the current header with nvcc for sm_103a, so that a header change that
+breaks those kernels fails here rather than at run time (where the library would fall back to the
+generic kernel), and checks the register budgets the launch bounds give: the single-time product
+kernels in 64 registers without spills, the two-time (Magnus) kernels in 80 registers."""
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1403_3511_gb300", "csrc")
+
+
+def _nvcc():
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
+        if cand and os.path.exists(cand):
+            return cand
+    return None
+
+
+@pytest.fixture(scope="module")
+def ptxas_info():
+    nvcc = _nvcc()
+    if nvcc is None:
+        pytest.skip("nvcc not found")
+    out_dir = os.path.join(ROOT, "paper_1403_3511_gb300", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    r = subprocess.run([nvcc, "-cubin", "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-O3",
+                        "-I", CSRC, os.path.join(ROOT, "tests", "native", "jit_hh6_c64.cu"),
+                        "-o", os.path.join(out_dir, "jit_hh6_c64.cubin"), "-Xptxas", "-v"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    info, cur = {}, None
+    for line in r.stderr.splitlines():
+        m = re.search(r"entry function '(\w+)'", line)
+        if m:
+            cur = info.setdefault(m.group(1), {})
+        m = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", line)
+        if m and cur is not None:
+            cur["spill"] = int(m.group(1))   # bytes of spill stores
+        m = re.search(r"Used (\d+) registers", line)
+        if m and cur is not None:
+            cur["regs"] = int(m.group(1))
+    return info
+
+
+def test_generated_source_compiles_with_every_kernel(ptxas_info):
+    want = {"hx_apply_specialised", "hx_apply_specialised_rq", "hx_apply_specialised_dots",
+            "hx_apply_specialised_dual", "hx_apply_specialised_pair", "hx_apply_tops"}
+    assert want <= set(ptxas_info), sorted(ptxas_info)
+
+
+@pytest.mark.parametrize("kernel", ["hx_apply_specialised", "hx_apply_specialised_rq"])
+def test_single_time_products_fit_64_registers_without_spills(ptxas_info, kernel):
+    k = ptxas_info[kernel]
+    assert k["regs"] <= 64 and k["spill"] == 0, k
+
+
+@pytest.mark.parametrize("kernel,max_spill", [("hx_apply_specialised_dual", 0), ("hx_apply_specialised_pair", 128)])
+def test_two_time_products_fit_80_registers(ptxas_info, kernel, max_spill):
+    k = ptxas_info[kernel]
+    assert k["regs"] <= 80 and k["spill"] <= max_spill, k

@@ -35,17 +35,23 @@ def ptxas_info():
                         "-o", os.path.join(out_dir, "jit_hh6_c64.cubin"), "-Xptxas", "-v"],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
-    info, cur = {}, None
+    # per kernel: "Compiling entry function 'k'", "Function properties for k" with its stack frame and
+    # spills (functions it calls get their own properties lines), "Used n registers"
+    info, cur, prop = {}, None, None
     for line in r.stderr.splitlines():
         m = re.search(r"entry function '(\w+)'", line)
         if m:
-            cur = info.setdefault(m.group(1), {})
+            cur, prop = m.group(1), None
+            info[cur] = {}
+        m = re.search(r"Function properties for (\w+)", line)
+        if m:
+            prop = m.group(1)
         m = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", line)
-        if m and cur is not None:
-            cur["spill"] = int(m.group(1))   # bytes of spill stores
+        if m and cur is not None and prop == cur:
+            info[cur]["spill"] = int(m.group(1))   # bytes of spill stores
         m = re.search(r"Used (\d+) registers", line)
         if m and cur is not None:
-            cur["regs"] = int(m.group(1))
+            info[cur]["regs"] = int(m.group(1))
     return info
 
 

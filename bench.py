@@ -176,10 +176,11 @@ def fp64_peak_tflops() -> float:
 
 # FP64 operations per coefficient of the product at the Henon-Heiles chain, counted from the
 # factorised stencils: per plane operator P(X_a) Q(X_b) of degrees (2, 1) with its merged cubic line,
-# 22 complex-times-real multiply-adds (4 flops each: 6 + 3 for P(X_a) Q(X_b), 6 + 2 for Q(X_b) P(X_a),
-# 1 for the order weight, 4 for the merged line) and 10 flops of weighting and accumulation; the
-# dipole line 12, the diagonal 4, the output scale 2
-FP64_FLOPS_PER_COEF = {"hh6_b4096": 5 * (22 * 4 + 10) + 12 + 4 + 2}
+# the 6 footprint weights of both factor orders (5 products of the order weights with the rows at k,
+# then a product and a multiply-add per point: 5 + 18 flops), 10 complex-times-real multiply-adds
+# (4 flops each: 6 for the points, 4 for the merged line) and 10 flops of weighting and accumulation;
+# the dipole line 12, the diagonal 4, the output scale 2
+FP64_FLOPS_PER_COEF = {"hh6_b4096": 5 * (5 + 18 + 10 * 4 + 10) + 12 + 4 + 2}
 
 
 def fp64_roofline(spec, n: int, ms: float, dtype_bytes: int) -> dict:

@@ -639,6 +639,45 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
     };
 #pragma unroll
     for (int q = 0; q < NSRC; ++q) out[q] = czero<V>();
+    if constexpr (sizeof(R) == 8 && NSRC == 1 && (ORD == 0 || ORD == 3)) {
+        // FP64, one input, both orders: one real weight per footprint point,
+        //   w_ij = wAB [P]_{k, k+s e_a} [Q]_{k+s e_a, k+s e_a+s2 e_b} + wBA [Q]_{k, k+s2 e_b} [P]_{k+s2 e_b, k+s e_a+s2 e_b},
+        // then one complex multiply-add per point: 2 NS NS2 + NS + NS2 operations for the weights and
+        // 4 NS NS2 for the sums, instead of 8 NS NS2 + 4 for the two nested sums (the FP64 kernels are
+        // bound by their FP64 arithmetic); the same rows and the same exact-zero entries outside K.
+        // The FP32 kernels keep the nested sums: at their 64-register limit the weights spilled.
+        const R wab = ORD == 3 ? (R)0.5 : (R)O.wAB, wba = ORD == 3 ? (R)0.5 : (R)O.wBA;
+        const Row4<R> rowP0 = load_row4(tP + (ka * (P + 1) + topA(0)) * 4);
+        const Row4<R> rowQ0 = rowQ(min(Q, dB0));
+        R hp[NS], hq[NS2];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) hp[i] = wab * rowP0.v[i];
+#pragma unroll
+        for (int j = 0; j < NS2; ++j) hq[j] = wba * rowQ0.v[j];
+        R w[NS][NS2];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const int s = -P + 2 * i;
+            const Row4<R> rq = rowQ(s == 0 ? min(Q, dB0) : topB(s, Q));
+#pragma unroll
+            for (int j = 0; j < NS2; ++j) w[i][j] = hp[i] * rq.v[j];
+        }
+#pragma unroll
+        for (int j = 0; j < NS2; ++j) {
+            const Row4<R> rp = load_row4(tP + (ka * (P + 1) + topA(-Q + 2 * j)) * 4);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) w[i][j] = fma(hq[j], rp.v[i], w[i][j]);
+        }
+#pragma unroll
+        for (int q = 0; q < NSRC; ++q) {
+            V o = czero<V>();
+#pragma unroll
+            for (int i = 0; i < NS; ++i)
+#pragma unroll
+                for (int j = 0; j < NS2; ++j) o = cmad(w[i][j], v[q][i][j], o);
+            out[q] = o;
+        }
+    } else {
     if (ORD != 2) {   // P(X_a) (Q(X_b) c)
         const Row4<R> rowP0 = load_row4(tP + (ka * (P + 1) + topA(0)) * 4);
         Row4<R> rowQs[NS];
@@ -679,6 +718,7 @@ __device__ __forceinline__ void plane_role_n(const Ctx &c, const Elem &el, const
             out[q] = ORD == 0 ? cmad(rconst<R>(O.wBA, O.wBA32), ba, out[q])
                    : ORD == 3 ? cscale((R)0.5, cadd(out[q], ba)) : ba;
         }
+    }
     }
     if (SB > 0) {   // the merged line op: points k + s2 e_b, s2 = -SB, -SB + 2, ..., SB
         const Op &ls = O.op[op.mergeB];
